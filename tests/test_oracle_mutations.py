@@ -1,0 +1,71 @@
+"""The pins must catch plausible mistakes in the oracle.
+
+Each case plants one mistake in a copy of ``oracle/vi_oracle.c`` (a dropped
+term, a wrong sign or index, a transposed operand, an off-by-one), builds it on
+the CPU and runs the pin suite against it; the suite has to fail.
+"""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "vi_oracle.c")
+
+MUTATIONS = {
+    "inclusive-buffer": ("double stored = s->T[t];", "double stored = s->T[t] * (1.0 - alpha);"),
+    "slice-off-by-one": ("fmaf((float)k, lt->dL, lt->min)", "fmaf((float)(k + 1), lt->dL, lt->min)"),
+    "slice-floor-not-nearest": ("float lh = lam + 0.5f;", "float lh = lam;"),
+    "voxel-corner-not-centre": ("float x = fmaf(P[a], (float)N[a], -0.5f);",
+                                "float x = fmaf(P[a], (float)N[a], 0.0f);"),
+    "trilinear-weight-swap": ("double w = (bx ? f[0] : 1.0 - f[0]) * (by ? f[1] : 1.0 - f[1]) * (bz ? f[2] : 1.0 - f[2]);\n        acc += w * voxel(v, bx ? hi[0] : lo[0], by ? hi[1] : lo[1], bz ? hi[2] : lo[2]);\n    }\n    return acc;\n}\n\n/* Same",
+                              "double w = (bx ? 1.0 - f[0] : f[0]) * (by ? f[1] : 1.0 - f[1]) * (bz ? f[2] : 1.0 - f[2]);\n        acc += w * voxel(v, bx ? hi[0] : lo[0], by ? hi[1] : lo[1], bz ? hi[2] : lo[2]);\n    }\n    return acc;\n}\n\n/* Same"),
+    "tf-scale-M": ("* (double)(tf->M - 1);", "* (double)(tf->M);"),
+    "back-to-front": ("C[ch] = C[ch] + (1.0 - A) * csrc;", "C[ch] = (1.0 - alpha) * C[ch] + csrc;"),
+    "u-v-transposed": ("ray->lo[1] = fmaf(dot3f(oc, lt->U)", "ray->lo[1] = fmaf(dot3f(oc, lt->V)"),
+    "light-sign": ("o->L[a] = dir[a] / len;", "o->L[a] = -dir[a] / len;"),
+    "cone-away-from-light": ("o[0] = -(float)ring;", "o[0] = (float)ring;"),
+    "cone-rotation-sign": ("case 1: *cu = -bv; *cv = bu; break;", "case 1: *cu = bv; *cv = bu; break;"),
+    "cone-radius-dropped-tan": ("float radw = dist * tanphi;", "float radw = dist;"),
+    "shell-radius-units": ("float r = ro->shell_radius_vox / (float)fr->Nmax;",
+                           "float r = ro->shell_radius_vox / (float)(2 * fr->Nmax);"),
+    "sample-count-le": ("if (!(t < ray.t1)) break;", "if (!(t <= ray.t1)) break;"),
+    "opacity-correction-exponent": ("alpha = 1.0 - pow(1.0 - alpha, s->spacing_vox);",
+                                    "alpha = 1.0 - pow(1.0 - alpha, 1.0 / s->spacing_vox);"),
+    "background-not-weighted": ("o[ch] = outC[ch] + (1.0 - outA) * (double)ro->bg[ch];",
+                                "o[ch] = outC[ch] + (double)ro->bg[ch];"),
+    "emission-not-opacity-weighted": ("double csrc = lf * (double)ro->color[ch] * alpha * rgba[ch];",
+                                      "double csrc = lf * (double)ro->color[ch] * rgba[ch];"),
+    "light-colour-dropped": ("double csrc = lf * (double)ro->color[ch] * alpha * rgba[ch];",
+                             "double csrc = lf * alpha * rgba[ch];"),
+    "eq8-max-as-min": ("if (c == 0 || d > mx) mx = d;", "if (c == 0 || d < mx) mx = d;"),
+    "basis-axis-most-aligned": ("if (fabsf(o->L[1]) < fabsf(o->L[ax])) ax = 1;",
+                                "if (fabsf(o->L[1]) > fabsf(o->L[ax])) ax = 1;"),
+    "ert-threshold-shifted": ("const double ert = (double)ro->ert, band = ro->ert_band;",
+                              "const double ert = (double)ro->ert + 0.03, band = ro->ert_band;"),
+    "comp-n-inverted": ("stored = stored * pow(1.0 + alpha, (double)s->opt->comp_n);",
+                        "stored = stored / pow(1.0 + alpha, (double)s->opt->comp_n);"),
+    "texel-centre-offset": ("float qi = (float)(2 * i + 1) / (float)lt->R;",
+                            "float qi = (float)(2 * i) / (float)lt->R;"),
+    "shadow-at-sample-light-coords-dropped-kappa": ("ray->ld[0] = dot3f(lt->L, ray->d) * lt->kappa;",
+                                                    "ray->ld[0] = dot3f(lt->L, ray->d);"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new = MUTATIONS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not unique"
+    mutated = tmp_path / "vi_oracle_mut.c"
+    mutated.write_text(src.replace(old, new))
+    so = tmp_path / "libvi_oracle_mut.so"
+    subprocess.run([os.environ.get("CC", "cc"), "-std=c11", "-O2", "-ffp-contract=off",
+                    "-fno-fast-math", "-fPIC", "-shared", "-pthread", "-o", str(so),
+                    str(mutated), "-lm"], check=True)
+    env = dict(os.environ, VI_ORACLE_LIB=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"pins did not catch mutation {name}:\n{r.stdout[-2000:]}"
