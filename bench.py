@@ -1,0 +1,369 @@
+#!/usr/bin/env python3
+"""Cold-frame throughput of slice-based illuminated ray casting on GB300.
+
+One step = one whole frame through the hot path: the light-space attenuation
+sweep (256 slices of 512 x 512 FP32 texels) followed by the cone-scattering
+eye march (1024 x 1024 perspective, step 0.5 voxel, early ray termination at
+0.99) over a 256^3 uint16 CT-like ellipsoid phantom (seed 2) with a 4096-entry
+RGBA transfer function.  Inputs are synthetic and seeded.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank renders its own
+frames (replicas; frames are independent) and the slowest rank's time counts.
+``--impl reference`` times the FP64 CPU oracle on this host's cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = ("ct256-u16 ellipsoid phantom, 256x512^2 FP32 attenuation stack, cone 15deg, "
+            "1024x1024 perspective, step 0.5 vox, ERT 0.99")
+L2_FLUSH_BYTES = 256 << 20   # > 129 MB of L2
+FP32_LANES_PER_SM = 128
+# Algorithmic FP32 flops per eye sample (an FMA counts 2): position + t (8),
+# voxel coordinates (6), trilinear (21), transfer function (14), compositing
+# (15) for every sample; light coordinates (6) + light factor (2) + per lookup
+# 12 (3 adds for its coordinates, 3 lerps) + the average, for samples with
+# alpha > 0 only.
+FLOPS_BASE = 8 + 6 + 21 + 14 + 15
+FLOPS_LIT = {0: 0, 1: 6 + 2 + 12, 2: 6 + 2 + 6 * 12 + 7, 3: 6 + 2 + 8 * 12 + 9}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.reader.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# CPU oracle (the baseline and the reference arm).
+
+def oracle_sample(scene, bands: int, band: int, stack, light):
+    """Time one band (1/bands of the texel rows and of the image rows) of the
+    oracle's sweep + march; returns seconds."""
+    import numpy as np
+
+    import oracle
+    R, H, W = scene.slice_res, scene.height, scene.width
+    j0, j1 = band * R // bands, (band + 1) * R // bands
+    y0, y1 = band * H // bands, (band + 1) * H // bands
+    ys, xs = np.mgrid[y0:y1, 0:W]
+    ro = oracle.render_opts(scene.mode, scene.step_vox, scene.ert, scene.bg, scene.light_color,
+                            cone_half_angle_deg=scene.cone_half_angle_deg)
+    t0 = time.perf_counter()
+    oracle.build_stack_rows(scene.volume, scene.tf, scene.vmin, scene.vmax, light, j0, j1, stack)
+    oracle.render_pixels(scene.volume, scene.tf, scene.vmin, scene.vmax, light, stack,
+                         scene.camera, W, H, ro, xs.ravel(), ys.ravel())
+    return time.perf_counter() - t0
+
+
+def oracle_setup(scene):
+    import oracle
+    oracle.build()
+    light = oracle.light_setup(scene.light_dir, scene.n_slices, scene.slice_res)
+    stack = oracle.build_stack(scene.volume, scene.tf, scene.vmin, scene.vmax, light)
+    return light, stack
+
+
+def cpu_baseline(scene):
+    """The oracle, as it stands, on a bounded sample: 1/8 of the sweep's texel
+    rows and 1/8 of the image rows (rows spread over the frame), scaled x8."""
+    import oracle
+    light, stack = oracle_setup(scene)
+    bands = 8
+    secs = oracle_sample(scene, bands, 3, stack, light)
+    fps = 1.0 / (secs * bands)
+    return {"value": round(fps, 4), "unit": "frames/s", "cores": oracle.threads(),
+            "kind": "oracle",
+            "sample": f"texel rows {3 * scene.slice_res // bands}-"
+                      f"{4 * scene.slice_res // bands} of every slice + image rows "
+                      f"{3 * scene.height // bands}-{4 * scene.height // bands}, FP64, "
+                      f"{secs:.2f} s, scaled x{bands} to one frame"}
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2008_06134_gb300 import phantoms as ph
+    scene = ph.ct256_cone()
+    light, stack = oracle_setup(scene)
+    bands = 64
+    for w in range(args.warmup):
+        oracle_sample(scene, bands, w % bands, stack, light)
+    secs = [oracle_sample(scene, bands, s % bands, stack, light) for s in range(args.steps)]
+    total = sum(secs)
+    fps = args.steps / (total * bands)
+    line = {"metric": "frames/s", "value": round(fps, 5), "unit": "frames/s", "impl": "reference",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1000 * total * bands / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "impl": "FP64 CPU oracle (oracle/vi_oracle.c)"},
+            "cpu_baseline": {"value": round(fps, 5), "unit": "frames/s", "kind": "oracle",
+                             "cores": oracle.threads(),
+                             "sample": f"each step: 1/{bands} of the texel rows of the sweep "
+                                       f"+ 1/{bands} of the image rows, bands rotating over "
+                                       f"the frame; frames/s scaled x{bands}"},
+            "e2e": {"value": round(fps, 5), "unit": "frames/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# GB300 arm.
+
+def gb300_arm(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2008_06134_gb300 import build, phantoms as ph, vi
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+
+    sc = ph.ct256_cone()
+    H, W = sc.height, sc.width
+    ctx = vi.Context(local)
+    vol_dev = torch.from_numpy(sc.volume.view(np.int16)).cuda()
+    ctx.load_volume(vol_dev, dtype=vi.U16)
+    ctx.set_transfer_function(sc.tf, sc.vmin, sc.vmax)
+    ctx.set_light(sc.light_dir, sc.light_color)
+    out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def build_stack():
+        ctx.build_attenuation(sc.n_slices, sc.slice_res, sc.mode,
+                              cone_half_angle_deg=sc.cone_half_angle_deg)
+
+    def render(o=None, **kw):
+        return ctx.render(sc.camera, W, H, sc.step_vox, out=out if o is None else o, ert=sc.ert,
+                          bg=sc.bg, **kw)
+
+    # One counted frame (untimed): samples composited and samples that were lit.
+    counts = torch.zeros((H, W), dtype=torch.int32, device="cuda")
+    lit = torch.zeros((H, W), dtype=torch.int32, device="cuda")
+    build_stack()
+    render(sample_counts=counts, lit_counts=lit)
+    torch.cuda.synchronize()
+    samples = int(counts.sum().item())
+    lit_samples = int(lit.sum().item())
+
+    for _ in range(args.warmup):
+        flush.fill_(0)
+        build_stack()
+        render()
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = ctx.launch_count()
+    wall0 = time.perf_counter()
+    for s in range(K):
+        flush.fill_(s & 0xFF)          # evict L2 between steps (outside the timed events)
+        ev[s][0].record()
+        build_stack()
+        ev[s][1].record()
+        render()
+        ev[s][2].record()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    clock = clocks.stop()
+    launches = ctx.launch_count() - launches0
+    sweep_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    march_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    total_ms = sum(sweep_ms) + sum(march_ms)
+    t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    max_total_ms = float(t.item())
+
+    # End to end through the public API: host volume / TF in, host frame out.
+    e2e = None
+    if not args.no_e2e:
+        pinned_vol = torch.empty(sc.volume.shape, dtype=torch.int16, pin_memory=True)
+        pinned_vol.numpy()[...] = sc.volume.view(np.int16)
+        pinned_out = torch.empty((H, W, 4), dtype=torch.float32, pin_memory=True)
+        tf = np.ascontiguousarray(sc.tf, dtype=np.float32)
+
+        def e2e_step():
+            ctx.load_volume(pinned_vol, dtype=vi.U16)
+            ctx.set_transfer_function(tf, sc.vmin, sc.vmax)
+            ctx.set_light(sc.light_dir, sc.light_color)
+            build_stack()
+            render(o=pinned_out)        # host output: returns once the frame is in host memory
+
+        for _ in range(args.warmup):
+            e2e_step()
+        secs = 0.0
+        for s in range(K):
+            flush.fill_(s & 0xFF)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2e_step()
+            secs += time.perf_counter() - t0
+        st = torch.tensor([secs], dtype=torch.float64, device="cuda")
+        if dist:
+            dist.all_reduce(st, op=dist.ReduceOp.MAX)
+        e2e = {"value": round(world * K / float(st.item()), 3), "unit": "frames/s",
+               "h2d_bytes_per_step": int(sc.volume.nbytes + tf.nbytes),
+               "d2h_bytes_per_step": int(H * W * 16)}
+
+    if rank != 0:
+        return
+    peaks, peak_kind = measured_peaks()
+    props = torch.cuda.get_device_properties(local)
+    sweep_s = statistics.mean(sweep_ms) / 1e3
+    march_s = statistics.mean(march_ms) / 1e3
+    n, R = sc.n_slices, sc.slice_res
+    sweep_bytes = sc.volume.nbytes + n * R * R * 4
+    sweep_roof = {"bound": "hbm", "achieved": round(sweep_bytes / sweep_s / 1e9, 1),
+                  "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                  "frac": round(sweep_bytes / sweep_s / 1e9 / peaks["hbm_gbs"], 4),
+                  "traffic": None, "kernel": "sweep_kernel",
+                  "peak_source": f"{peak_kind} HBM copy bandwidth"}
+    flops = samples * FLOPS_BASE + lit_samples * FLOPS_LIT[sc.mode]
+    fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * peaks["sm_max_mhz"] / 1e6
+    march_roof = {"bound": "alu", "achieved": round(flops / march_s / 1e12, 3),
+                  "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
+                  "frac": round(flops / march_s / 1e12 / fp32_peak, 4), "traffic": None,
+                  "kernel": "march_kernel",
+                  "peak_source": f"FP32 FMA rate: {props.multi_processor_count} SMs x "
+                                 f"{FP32_LANES_PER_SM} lanes x 2 x {peaks['sm_max_mhz']} MHz "
+                                 f"({peak_kind} max clock)"}
+    dominant, other = (march_roof, sweep_roof) if march_s >= sweep_s else (sweep_roof, march_roof)
+    frames = world * K
+    line = {
+        "metric": "frames/s", "value": round(frames / (max_total_ms / 1e3), 3),
+        "unit": "frames/s", "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": round(max_total_ms / K, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "volume": "256^3 uint16 (seed 2)",
+                   "stack": f"{n}x{R}x{R} FP32", "image": f"{W}x{H}",
+                   "l2": "flushed between steps (256 MiB write, outside the timed events)",
+                   "parallelism": f"replicas x{world} (independent frames)"},
+        "gsamples_per_s": round(samples * frames / (max_total_ms / 1e3) / 1e9, 3),
+        "march_gsamples_per_s": round(samples / march_s / 1e9, 3),
+        "samples_per_frame": samples, "lit_samples_per_frame": lit_samples,
+        "sweep_ms": round(sweep_s * 1e3, 4), "march_ms": round(march_s * 1e3, 4),
+        "wall_s": round(wall, 3),
+        "roofline": dominant, "roofline_other": other,
+        "gpu_launches": int(launches),
+        "clocks": clock,
+        "e2e": e2e,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(sc)
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gb300_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * vi.h -- C ABI of the GB300 (sm_103a) slice-based illuminated ray casting
+ * library: D. Luo, "Interactive volume illumination of slice-based ray
+ * casting", arXiv 2008.06134.
+ *
+ * The method has two passes (Section 3, Fig. 1):
+ *   1. vi_build_attenuation: a sweep from the light's viewpoint that builds one
+ *      illumination attenuation buffer per slice plane perpendicular to the
+ *      light, each formed from the previous one by the transfer-function
+ *      opacity (Section 3.2.1, Algorithm 1, Eq. 4, Eq. 8).
+ *   2. vi_render: an eye-space ray march that, per sample, reconstructs the
+ *      volume trilinearly, classifies it through an RGBA transfer function,
+ *      reads the attenuation buffers for a shadow (Section 3.2.2, Eq. 9, Eq. 10),
+ *      shell or cone scattering coefficient (Section 3.2.3, Eq. 11), weights the
+ *      emission by it (Eq. 7) and composites front to back (Eq. 2, Eq. 3) with
+ *      early ray termination.
+ *
+ * Conventions for every call:
+ *   - Every call returns VI_OK (0) or a negative vi_status.  No C++ exception
+ *     crosses this boundary.
+ *   - A context is bound to one CUDA device and one CUDA stream.  All device
+ *     work of a call is enqueued on that stream, in call order.  Calls on one
+ *     context must not run concurrently from several host threads.
+ *   - Geometry: the volume occupies the unit cube [0,1]^3; voxel (x, y, z) has
+ *     its centre at ((x + 1/2)/nx, (y + 1/2)/ny, (z + 1/2)/nz).
+ *   - An asynchronous device error is sticky: the next call, or vi_sync,
+ *     returns VI_ECUDA and clears it.
+ *   - Host input buffers are read by a copy enqueued on the stream.  A
+ *     pageable host buffer may be reused when the call returns; a page-locked
+ *     (pinned) one only after vi_sync.
+ *   - The library owns the device copies of the volume, the transfer function
+ *     and the attenuation stack.  The caller owns every buffer it passes.
+ */
+#ifndef VI_H
+#define VI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vi_ctx vi_ctx; /* opaque, library-owned */
+
+typedef enum {
+    VI_OK = 0,
+    VI_EINVAL = -1,   /* an argument is out of range, NULL where not allowed, or not finite */
+    VI_ENOMEM = -2,   /* the memory budget or the device refused an allocation */
+    VI_ESTATE = -3,   /* a required input is missing or the stack is stale */
+    VI_ECUDA = -4,    /* a CUDA runtime error (launch or asynchronous fault) */
+    VI_ETIMEOUT = -5  /* a bounded device-side wait gave up */
+} vi_status;
+
+enum { VI_U8 = 0, VI_U16 = 1 };                                  /* voxel types */
+enum { VI_NONE = 0, VI_SHADOW = 1, VI_SHELL = 2, VI_CONE = 3 };  /* coefficient modes */
+enum { VI_F32 = 0, VI_F16 = 1, VI_BF16 = 2, VI_UNORM16 = 3 };    /* stack storage */
+
+/* Options of the attenuation sweep.  NULL means the defaults shown. */
+typedef struct {
+    int format;                /* VI_F32 (default), VI_F16, VI_BF16 or VI_UNORM16 storage;
+                                  the transmittance product is always carried in FP32 */
+    float cone_half_angle_deg; /* cone scattering half angle phi (Section 3.2.3), default 15 */
+    float shell_radius_vox;    /* shell scattering radius r in voxels (Section 3.2.3), default 1 */
+    int opacity_correction;    /* 0 (default): the TF opacity is applied per slice as is;
+                                  1: alpha' = 1 - (1 - alpha)^(slice spacing in voxels) */
+    float comp_n;              /* darkening compensation (Section 4): each stored slice is
+                                  multiplied by (1 + alpha)^comp_n, clamped to 1; 0 = off */
+} vi_build_opts;
+
+/* A pinhole (perspective) or orthographic camera in unit-cube coordinates.
+   Row 0 of the image is its top; the camera's right vector is
+   normalize(forward x up). */
+typedef struct {
+    int perspective;         /* 1 perspective, 0 orthographic */
+    float eye[3];            /* eye (perspective) or centre of the image plane (orthographic) */
+    float target[3];         /* a point the view direction passes through */
+    float up[3];             /* must not be parallel to target - eye */
+    float fovy_deg;          /* perspective: vertical field of view, (0, 180) */
+    float ortho_half_height; /* orthographic: half height of the image plane, > 0 */
+} vi_camera;
+
+/* Options of the eye pass.  NULL means the defaults shown. */
+typedef struct {
+    float ert;              /* stop a ray once accumulated opacity > ert; default 2 (off) */
+    float bg[4];            /* background RGBA behind the remaining transparency, default 0 */
+    float ambient;          /* light factor = ambient + (1 - ambient) * coefficient, default 0 */
+    int opacity_correction; /* 1: alpha' = 1 - (1 - alpha)^step_vox; default 0 */
+    int32_t* sample_counts; /* optional device buffer of W*H int32: samples composited per
+                               pixel (row-major); NULL = not written */
+    int32_t* lit_counts;    /* optional device buffer of W*H int32: samples with opacity > 0,
+                               the ones that read the stack; NULL = not written */
+} vi_render_opts;
+
+/* Create a context on CUDA device `device` using `cuda_stream` (a cudaStream_t;
+   NULL = the legacy default stream).  *out receives the context. */
+int vi_create(vi_ctx** out, int device, void* cuda_stream);
+
+/* Free every device buffer of the context (after waiting for its stream). */
+int vi_destroy(vi_ctx* ctx);
+
+/* Cap on the device bytes this context may hold (volume + TF + stack + scratch);
+   0 = no cap (default).  An allocation above the cap fails with VI_ENOMEM and
+   leaves the previous state intact. */
+int vi_set_memory_budget(vi_ctx* ctx, size_t bytes);
+
+/* The volume (Section 3: a 3D array of voxels): nx*ny*nz voxels of `dtype`
+   (VI_U8 / VI_U16), layout data[z][y][x] with x fastest, each dimension in
+   [1, 65536].  data_on_device: 1 if `data` is a device pointer of this context's
+   device, 0 for host memory.  Marks the stack stale. */
+int vi_load_volume(vi_ctx* ctx, const void* data, int dtype, int nx, int ny, int nz,
+                   int data_on_device);
+
+/* RGBA transfer function (Section 2: the classification of data values): M
+   entries of straight (not premultiplied) RGBA float32 in host memory, M in
+   [2, 8192], evenly spaced over [vmin, vmax] (vmax > vmin), interpolated
+   linearly and clamped at both ends.  Marks the stack stale. */
+int vi_set_transfer_function(vi_ctx* ctx, const float* rgba, int M, float vmin, float vmax);
+
+/* Directional light (Section 3.2.1): dir is the direction the light travels
+   (any finite non-zero length); color multiplies the emission (Eq. 7; NULL =
+   white).  Marks the stack stale. */
+int vi_set_light(vi_ctx* ctx, const float dir[3], const float color[3]);
+
+/* Algorithm 1: build n_slices attenuation buffers of slice_res x slice_res
+   texels, slice 0 nearest the light at min of Eq. 8, spacing (max - min)/n.
+   Buffer k holds the light arriving at plane k: B_0 = 1,
+   B_k = prod_{j<k} (1 - alpha_j).  mode (VI_NONE, VI_SHADOW, VI_SHELL,
+   VI_CONE) selects the coefficient vi_render reads; VI_NONE builds nothing.
+   Needs a volume, a TF and a light (VI_ESTATE otherwise).  Asynchronous.
+   n_slices and slice_res must be >= 1 and n_slices * slice_res^2 <= 2^34. */
+int vi_build_attenuation(vi_ctx* ctx, int n_slices, int slice_res, int mode,
+                         const vi_build_opts* opts);
+
+/* Eye pass (Section 3.2.2, 3.2.3, 4): one ray per pixel centre, samples every
+   step_vox voxels from where the ray enters the unit cube (a voxel is
+   1/max(nx,ny,nz); step_vox in [1e-3, 1e3] and sqrt(3) max(nx,ny,nz) / step_vox
+   <= 2^24), front-to-back compositing with the mode's coefficient.
+   out_rgba: W*H*4 float32, row-major RGBA, caller-owned; a device pointer
+   (out_on_device = 1, written asynchronously) or host memory (0, filled when
+   the call returns).  W or H == 0 renders nothing.  VI_ESTATE if the volume
+   or TF is missing or the stack (modes other than VI_NONE) is stale. */
+int vi_render(vi_ctx* ctx, const vi_camera* camera, int W, int H, float step_vox,
+              float* out_rgba, int out_on_device, const vi_render_opts* opts);
+
+/* Wait for the context's stream; returns (and clears) a sticky error. */
+int vi_sync(vi_ctx* ctx);
+
+/* Static text for a vi_status code. */
+const char* vi_error_string(int status);
+
+/* ---- Inspection (tests and tools) ---------------------------------------- */
+
+/* Shape and storage of the current stack; any pointer may be NULL. */
+int vi_attenuation_info(vi_ctx* ctx, int* n_slices, int* slice_res, int* format,
+                        size_t* bytes);
+
+/* Copy the stack as stored ([n][R][R] of the storage format) into `out`
+   (out_bytes >= the stack's size); out_on_device as for vi_render.  Waits for
+   the copy. */
+int vi_get_attenuation(vi_ctx* ctx, void* out, size_t out_bytes, int out_on_device);
+
+/* Words per record written by vi_trace_pixel. */
+#define VI_TRACE_WORDS 40
+
+/* The integer decisions of one pixel's ray, sample by sample, for exact
+   comparison with an independent implementation: per sample VI_TRACE_WORDS
+   int32 = { i, bits(t_i), bits(lambda), bits(tu), bits(tv), voxel cell x,y,z,
+   own lookup cell (k, iu, iv), 8 neighbour cells (k, iu, iv), neighbour count,
+   unused }, unused words 0x7fffffff.  rec is host memory of max_rec records;
+   *n_rec receives the count.  Synchronous. */
+int vi_trace_pixel(vi_ctx* ctx, const vi_camera* camera, int W, int H, float step_vox,
+                   const vi_render_opts* opts, int x, int y, int32_t* rec, int max_rec,
+                   int* n_rec);
+
+/* Number of kernels this context has launched so far. */
+int vi_launch_count(vi_ctx* ctx, uint64_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VI_H */

@@ -101,6 +101,8 @@ def lib():
             P = C.POINTER
             L.orc_light_setup.argtypes = [P(C.c_float), C.c_int, C.c_int, P(Light)]
             L.orc_build_stack.argtypes = [P(Volume), P(TF), P(Light), P(BuildOpts), C.c_void_p]
+            L.orc_build_stack_rows.argtypes = [P(Volume), P(TF), P(Light), P(BuildOpts), C.c_int,
+                                               C.c_int, C.c_void_p]
             L.orc_frame_setup.argtypes = [P(Camera), C.c_int, C.c_int, C.c_float, C.c_int, P(Frame)]
             L.orc_ray_setup.argtypes = [P(Light), P(Frame), P(RenderOpts), C.c_int, C.c_int, P(Ray)]
             L.orc_point_light_coords.argtypes = [P(Light), P(C.c_float), P(C.c_float)]
@@ -183,6 +185,21 @@ def build_stack(vol: np.ndarray, tf: np.ndarray, vmin: float, vmax: float, light
     if rc:
         raise ValueError(f"orc_build_stack failed ({rc})")
     return B
+
+
+def build_stack_rows(vol, tf, vmin, vmax, light: Light, j0: int, j1: int, out: np.ndarray,
+                     opacity_correction: int = 0, comp_n: float = 0.0) -> np.ndarray:
+    """Algorithm 1 on texel rows [j0, j1) only, written into ``out`` (n, R, R)."""
+    V = volume(vol)
+    T = transfer_function(tf, vmin, vmax)
+    assert out.dtype == np.float64 and out.flags.c_contiguous
+    assert out.shape == (light.n, light.R, light.R)
+    opts = BuildOpts(int(opacity_correction), float(comp_n))
+    rc = lib().orc_build_stack_rows(C.byref(V.struct), C.byref(T.struct), C.byref(light),
+                                    C.byref(opts), int(j0), int(j1), out.ctypes.data)
+    if rc:
+        raise ValueError(f"orc_build_stack_rows failed ({rc})")
+    return out
 
 
 def camera(cam) -> Camera:

@@ -390,12 +390,13 @@ typedef struct {
     double* Bk;
     float sk;
     double spacing_vox;
+    int j0;
 } sweep_ctx;
 
-static void sweep_rows(void* p, long j0, long j1) {
+static void sweep_rows(void* p, long lo, long hi) {
     sweep_ctx* s = (sweep_ctx*)p;
     const int R = s->lt->R;
-    for (long j = j0; j < j1; ++j) {
+    for (long j = s->j0 + lo; j < s->j0 + hi; ++j) {
         for (int i = 0; i < R; ++i) {
             size_t t = (size_t)j * (size_t)R + (size_t)i;
             float P[3];
@@ -422,9 +423,12 @@ static void sweep_rows(void* p, long j0, long j1) {
     }
 }
 
-int orc_build_stack(const orc_volume* vol, const orc_tf* tf, const orc_light* lt,
-                    const orc_build_opts* opt, double* B) {
+/* Texel rows [j0, j1) of every slice (the rest of B is left untouched); the
+   CPU-baseline timing runs a band of rows. */
+int orc_build_stack_rows(const orc_volume* vol, const orc_tf* tf, const orc_light* lt,
+                         const orc_build_opts* opt, int j0, int j1, double* B) {
     if (!valid_inputs(vol, tf) || !lt || !B || lt->n < 1 || lt->R < 1) return ORC_EINVAL;
+    if (j0 < 0 || j1 > lt->R || j0 >= j1) return ORC_EINVAL;
     const size_t RR = (size_t)lt->R * (size_t)lt->R;
     double* T = (double*)malloc(RR * sizeof(double));
     if (!T) return ORC_ENOMEM;
@@ -436,14 +440,21 @@ int orc_build_stack(const orc_volume* vol, const orc_tf* tf, const orc_light* lt
     s.opt = opt;
     s.T = T;
     s.spacing_vox = (double)lt->dL * (double)vol_nmax(vol);
+    s.j0 = j0;
     /* For each slice, nearest to the light first: evaluate, store, blend. */
     for (int k = 0; k < lt->n; ++k) {
         s.sk = slice_offset(lt, k);
         s.Bk = B + (size_t)k * RR;
-        parallel_for(lt->R, 4, sweep_rows, &s);
+        parallel_for(j1 - j0, 4, sweep_rows, &s);
     }
     free(T);
     return ORC_OK;
+}
+
+int orc_build_stack(const orc_volume* vol, const orc_tf* tf, const orc_light* lt,
+                    const orc_build_opts* opt, double* B) {
+    if (!lt) return ORC_EINVAL;
+    return orc_build_stack_rows(vol, tf, lt, opt, 0, lt->R, B);
 }
 
 /* ------------------------------------------------------------------ */

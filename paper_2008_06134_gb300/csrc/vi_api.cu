@@ -1,0 +1,602 @@
+// vi_api.cu -- context, validation, device memory and the C ABI of vi.h.
+//
+// Host-side set-up of the light (Eq. 8, the Eq. 9 ratio, the Eq. 10 frame)
+// and of the camera runs in binary32 with the operation order documented in
+// vi_internal.h.  This file must be compiled with -ffp-contract=off for the
+// host compiler so that no a*b+c is fused behind our back.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "../../include/vi.h"
+#include "vi_internal.h"
+
+using vi::CameraFrame;
+using vi::LightFrame;
+using vi::MarchParams;
+using vi::SweepParams;
+
+struct vi_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sticky = VI_OK;
+    uint64_t launches = 0;
+
+    size_t budget = 0;  // 0 = unlimited
+    size_t used = 0;
+
+    void* vol = nullptr;
+    size_t vol_cap = 0;
+    int vtype = -1, nx = 0, ny = 0, nz = 0;
+
+    float4* tf = nullptr;
+    size_t tf_cap = 0;
+    int M = 0;
+    float vmin = 0.0f, vmax = 1.0f;
+
+    bool has_light = false;
+    float dir[3] = {0.0f, 0.0f, 1.0f};
+    float color[3] = {1.0f, 1.0f, 1.0f};
+
+    void* stack = nullptr;
+    size_t stack_cap = 0;
+    size_t stack_bytes = 0;
+    int mode = -1;          // mode of the last build; -1 = none yet
+    bool stack_valid = false;
+    vi_build_opts bopts{};
+    LightFrame lt{};
+    bool lt_valid = false;
+
+    float4* out = nullptr;  // staging for host-memory output
+    size_t out_cap = 0;
+    int32_t* trace = nullptr;
+    size_t trace_cap = 0;
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// binary32 index-path helpers (host).
+
+float dot3(const float a[3], const float b[3]) {
+    float p0 = a[0] * b[0];
+    float p1 = a[1] * b[1];
+    float p2 = a[2] * b[2];
+    float s = p0 + p1;
+    return s + p2;
+}
+
+void cross3(const float a[3], const float b[3], float o[3]) {
+    float p, q;
+    p = a[1] * b[2];
+    q = a[2] * b[1];
+    o[0] = p - q;
+    p = a[2] * b[0];
+    q = a[0] * b[2];
+    o[1] = p - q;
+    p = a[0] * b[1];
+    q = a[1] * b[0];
+    o[2] = p - q;
+}
+
+bool finite3(const float v[3]) {
+    return std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2]);
+}
+
+// Light frame for n slices of R x R texels (Eq. 8, Section 3.2.1, Eq. 9, Eq. 10).
+int light_frame(const float dir[3], int n, int R, LightFrame* o) {
+    float len = std::sqrt(dot3(dir, dir));
+    if (!(len > 0.0f) || !std::isfinite(len)) return VI_EINVAL;
+    std::memset(o, 0, sizeof(*o));
+    for (int a = 0; a < 3; ++a) o->L[a] = dir[a] / len;
+    // Eq. 8: the extreme vertices of [0,1]^3 take the negative (positive)
+    // components of L; the sum is formed in axis order.
+    float m[3], M[3];
+    for (int a = 0; a < 3; ++a) {
+        m[a] = o->L[a] < 0.0f ? o->L[a] : 0.0f;
+        M[a] = o->L[a] > 0.0f ? o->L[a] : 0.0f;
+    }
+    float mn = m[0] + m[1];
+    mn = mn + m[2];
+    float mx = M[0] + M[1];
+    mx = mx + M[2];
+    o->min = mn;
+    o->max = mx;
+    float span = mx - mn;
+    o->dL = span / (float)n;
+    o->kappa = (float)n / span;
+    const float c3[3] = {0.5f, 0.5f, 0.5f};
+    o->Lc = dot3(o->L, c3);
+    // Light view: U from the world axis least aligned with L, V = L x U.
+    int ax = 0;
+    if (std::fabs(o->L[1]) < std::fabs(o->L[ax])) ax = 1;
+    if (std::fabs(o->L[2]) < std::fabs(o->L[ax])) ax = 2;
+    float w[3];
+    for (int b = 0; b < 3; ++b) {
+        float e = (b == ax) ? 1.0f : 0.0f;
+        float p = o->L[ax] * o->L[b];
+        w[b] = e - p;
+    }
+    float wn = std::sqrt(dot3(w, w));
+    for (int b = 0; b < 3; ++b) o->U[b] = w[b] / wn;
+    cross3(o->L, o->U, o->V);
+    // Light projection: a square of half extent sqrt(3)/2 about the centre.
+    o->h = 0x1.bb67aep-1f;
+    float two_h = 2.0f * o->h;
+    o->sigma = (float)R / two_h;
+    o->rho0 = 0.5f * (float)(R - 1);
+    o->n = n;
+    o->R = R;
+    return VI_OK;
+}
+
+int camera_frame(const vi_camera* cam, int W, int H, float step_vox, int nmax, CameraFrame* c) {
+    if (!finite3(cam->eye) || !finite3(cam->target) || !finite3(cam->up)) return VI_EINVAL;
+    std::memset(c, 0, sizeof(*c));
+    float fw[3], r0[3];
+    for (int a = 0; a < 3; ++a) fw[a] = cam->target[a] - cam->eye[a];
+    float nf = std::sqrt(dot3(fw, fw));
+    if (!(nf > 0.0f) || !std::isfinite(nf)) return VI_EINVAL;
+    for (int a = 0; a < 3; ++a) c->f[a] = fw[a] / nf;
+    cross3(c->f, cam->up, r0);
+    float nr = std::sqrt(dot3(r0, r0));
+    if (!(nr > 0.0f) || !std::isfinite(nr)) return VI_EINVAL;
+    for (int a = 0; a < 3; ++a) c->r[a] = r0[a] / nr;
+    cross3(c->r, c->f, c->u);
+    for (int a = 0; a < 3; ++a) c->eye[a] = cam->eye[a];
+    float aspect = (float)W / (float)H;
+    if (cam->perspective) {
+        if (!(cam->fovy_deg > 0.0f && cam->fovy_deg < 180.0f)) return VI_EINVAL;
+        float th = (float)std::tan((double)cam->fovy_deg * (M_PI / 360.0));
+        c->sx = th * aspect;
+        c->sy = th;
+    } else {
+        if (!(cam->ortho_half_height > 0.0f) || !std::isfinite(cam->ortho_half_height))
+            return VI_EINVAL;
+        c->sx = cam->ortho_half_height * aspect;
+        c->sy = cam->ortho_half_height;
+    }
+    c->perspective = cam->perspective ? 1 : 0;
+    c->W = W;
+    c->H = H;
+    c->dt = step_vox / (float)nmax;
+    return VI_OK;
+}
+
+size_t voxel_bytes(int t) { return t == VI_U8 ? 1 : 2; }
+size_t format_bytes(int f) { return f == VI_F32 ? 4 : 2; }
+
+int nmax(const vi_ctx* c) { return std::max(c->nx, std::max(c->ny, c->nz)); }
+
+vi_build_opts default_build_opts() {
+    vi_build_opts o;
+    o.format = VI_F32;
+    o.cone_half_angle_deg = 15.0f;
+    o.shell_radius_vox = 1.0f;
+    o.opacity_correction = 0;
+    o.comp_n = 0.0f;
+    return o;
+}
+
+vi_render_opts default_render_opts() {
+    vi_render_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.ert = 2.0f;
+    return o;
+}
+
+int cuda_fail(vi_ctx* c, cudaError_t e) {
+    if (e == cudaSuccess) return VI_OK;
+    c->sticky = VI_ECUDA;
+    return VI_ECUDA;
+}
+
+// Grow a device buffer to `bytes` under the budget; keeps the old one on failure.
+int ensure(vi_ctx* c, void** p, size_t* cap, size_t bytes) {
+    if (bytes <= *cap && *p) return VI_OK;
+    size_t after = c->used - *cap + bytes;
+    if (c->budget && after > c->budget) return VI_ENOMEM;
+    void* q = nullptr;
+    if (cudaMalloc(&q, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return VI_ENOMEM;
+    }
+    if (*p) {
+        cudaStreamSynchronize(c->stream);
+        cudaFree(*p);
+    }
+    *p = q;
+    c->used = after;
+    *cap = bytes;
+    return VI_OK;
+}
+
+void release(vi_ctx* c, void** p, size_t* cap) {
+    if (*p) cudaFree(*p);
+    c->used -= *cap;
+    *p = nullptr;
+    *cap = 0;
+}
+
+// Common prologue of every call on a context.
+int enter(vi_ctx* c) {
+    if (!c) return VI_EINVAL;
+    if (c->sticky != VI_OK) return c->sticky;
+    if (cudaSetDevice(c->device) != cudaSuccess) {
+        cudaGetLastError();
+        return VI_ECUDA;
+    }
+    return VI_OK;
+}
+
+void mark_stale(vi_ctx* c) { c->stack_valid = false; }
+
+int fill_march_params(vi_ctx* c, const vi_camera* cam, int W, int H, float step_vox,
+                      const vi_render_opts* ro, MarchParams* p) {
+    std::memset(p, 0, sizeof(*p));
+    int rc = camera_frame(cam, W, H, step_vox, nmax(c), &p->cam);
+    if (rc) return rc;
+    p->vol.data = c->vol;
+    p->vol.nx = c->nx;
+    p->vol.ny = c->ny;
+    p->vol.nz = c->nz;
+    p->vol.fnx = (float)c->nx;
+    p->vol.fny = (float)c->ny;
+    p->vol.fnz = (float)c->nz;
+    p->tf = c->tf;
+    p->M = c->M;
+    p->tf_vmin = c->vmin;
+    p->tf_scale = (float)(c->M - 1) / (c->vmax - c->vmin);
+    if (c->lt_valid) p->lt = c->lt;  // else n = R = 0: no lookups
+    p->stack = c->stack;
+    const LightFrame& lt = p->lt;
+    if (c->mode == VI_SHELL && c->lt_valid) {
+        // The six points S +- r e_a as light-space offsets.
+        float r = c->bopts.shell_radius_vox / (float)nmax(c);
+        for (int a = 0; a < 3; ++a) {
+            float rl = r * lt.L[a];
+            float ru = r * lt.U[a];
+            float rv = r * lt.V[a];
+            float off[3] = {rl * lt.kappa, ru * lt.sigma, rv * lt.sigma};
+            for (int k = 0; k < 3; ++k) {
+                p->shell_off[2 * a][k] = off[k];
+                p->shell_off[2 * a + 1][k] = -off[k];
+            }
+        }
+    }
+    if (c->mode == VI_CONE && c->lt_valid) {
+        // Ring n sits n slice spacings towards the light; radius n dL tan(phi).
+        float tanphi = (float)std::tan((double)c->bopts.cone_half_angle_deg * (M_PI / 180.0));
+        for (int q = 0; q < 2; ++q) {
+            float dist = (float)(q + 1) * lt.dL;
+            float radw = dist * tanphi;
+            p->cone_rad[q] = radw * lt.sigma;
+        }
+        p->cone_thr = 1e-6f * lt.sigma;
+    }
+    p->ert = ro->ert;
+    for (int k = 0; k < 4; ++k) p->bg[k] = ro->bg[k];
+    for (int k = 0; k < 3; ++k) p->color[k] = c->color[k];
+    p->ambient = ro->ambient;
+    p->opacity_correction = ro->opacity_correction ? 1 : 0;
+    p->step_vox = step_vox;
+    p->counts = ro->sample_counts;
+    p->lit = ro->lit_counts;
+    return VI_OK;
+}
+
+int check_render_inputs(vi_ctx* c, const vi_camera* cam, int W, int H, float step_vox,
+                        const vi_render_opts* ro) {
+    if (!cam || W < 0 || H < 0) return VI_EINVAL;
+    if ((long long)W * (long long)H > 0x7fffffffLL) return VI_EINVAL;
+    if (!(step_vox >= 1e-3f && step_vox <= 1e3f)) return VI_EINVAL;
+    if (!std::isfinite(ro->ert) || !std::isfinite(ro->ambient)) return VI_EINVAL;
+    for (int k = 0; k < 4; ++k)
+        if (!std::isfinite(ro->bg[k])) return VI_EINVAL;
+    if (!c->vol || !c->tf || c->mode < 0) return VI_ESTATE;
+    if (c->mode != VI_NONE && !c->stack_valid) return VI_ESTATE;
+    // A ray crosses at most sqrt(3) of the cube: cap its sample count at 2^24.
+    if (1.7320509 * (double)nmax(c) / (double)step_vox > 16777216.0) return VI_EINVAL;
+    return VI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* vi_error_string(int status) {
+    switch (status) {
+        case VI_OK: return "ok";
+        case VI_EINVAL: return "invalid argument";
+        case VI_ENOMEM: return "out of memory (budget or device)";
+        case VI_ESTATE: return "missing input or stale attenuation stack";
+        case VI_ECUDA: return "CUDA error";
+        case VI_ETIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+int vi_create(vi_ctx** out, int device, void* cuda_stream) {
+    if (!out) return VI_EINVAL;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess) {
+        cudaGetLastError();
+        return VI_ECUDA;
+    }
+    if (device < 0 || device >= count) return VI_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return VI_ECUDA;
+    }
+    vi_ctx* c = new (std::nothrow) vi_ctx();
+    if (!c) return VI_ENOMEM;
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->bopts = default_build_opts();
+    *out = c;
+    return VI_OK;
+}
+
+int vi_destroy(vi_ctx* c) {
+    if (!c) return VI_EINVAL;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    cudaGetLastError();
+    release(c, &c->vol, &c->vol_cap);
+    release(c, reinterpret_cast<void**>(&c->tf), &c->tf_cap);
+    release(c, &c->stack, &c->stack_cap);
+    release(c, reinterpret_cast<void**>(&c->out), &c->out_cap);
+    release(c, reinterpret_cast<void**>(&c->trace), &c->trace_cap);
+    delete c;
+    return VI_OK;
+}
+
+int vi_set_memory_budget(vi_ctx* c, size_t bytes) {
+    if (!c) return VI_EINVAL;
+    c->budget = bytes;
+    return VI_OK;
+}
+
+int vi_load_volume(vi_ctx* c, const void* data, int dtype, int nx, int ny, int nz,
+                   int data_on_device) {
+    int rc = enter(c);
+    if (rc) return rc;
+    if (!data || (dtype != VI_U8 && dtype != VI_U16)) return VI_EINVAL;
+    if (nx < 1 || ny < 1 || nz < 1 || nx > 65536 || ny > 65536 || nz > 65536) return VI_EINVAL;
+    size_t bytes = (size_t)nx * (size_t)ny * (size_t)nz * voxel_bytes(dtype);
+    rc = ensure(c, &c->vol, &c->vol_cap, bytes);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(c->vol, data, bytes,
+                                    data_on_device ? cudaMemcpyDeviceToDevice
+                                                   : cudaMemcpyHostToDevice,
+                                    c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    c->vtype = dtype;
+    c->nx = nx;
+    c->ny = ny;
+    c->nz = nz;
+    mark_stale(c);
+    return VI_OK;
+}
+
+int vi_set_transfer_function(vi_ctx* c, const float* rgba, int M, float vmin, float vmax) {
+    int rc = enter(c);
+    if (rc) return rc;
+    if (!rgba || M < 2 || M > 8192) return VI_EINVAL;
+    if (!std::isfinite(vmin) || !std::isfinite(vmax) || !(vmax > vmin)) return VI_EINVAL;
+    if (!std::isfinite((vmax - vmin))) return VI_EINVAL;
+    for (int e = 0; e < M; ++e) {
+        for (int ch = 0; ch < 3; ++ch)
+            if (!std::isfinite(rgba[4 * e + ch])) return VI_EINVAL;
+        float a = rgba[4 * e + 3];
+        if (!(a >= 0.0f && a <= 1.0f)) return VI_EINVAL;
+    }
+    size_t bytes = (size_t)M * sizeof(float4);
+    rc = ensure(c, reinterpret_cast<void**>(&c->tf), &c->tf_cap, bytes);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(c->tf, rgba, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    c->M = M;
+    c->vmin = vmin;
+    c->vmax = vmax;
+    mark_stale(c);
+    return VI_OK;
+}
+
+int vi_set_light(vi_ctx* c, const float dir[3], const float color[3]) {
+    int rc = enter(c);
+    if (rc) return rc;
+    if (!dir || !finite3(dir)) return VI_EINVAL;
+    float len2 = dot3(dir, dir);
+    if (!(len2 > 0.0f) || !std::isfinite(len2)) return VI_EINVAL;
+    if (color && !finite3(color)) return VI_EINVAL;
+    for (int a = 0; a < 3; ++a) {
+        c->dir[a] = dir[a];
+        c->color[a] = color ? color[a] : 1.0f;
+    }
+    c->has_light = true;
+    mark_stale(c);
+    return VI_OK;
+}
+
+int vi_build_attenuation(vi_ctx* c, int n, int R, int mode, const vi_build_opts* opts) {
+    int rc = enter(c);
+    if (rc) return rc;
+    vi_build_opts o = opts ? *opts : default_build_opts();
+    if (n < 1 || R < 1 || R > 65536 || mode < VI_NONE || mode > VI_CONE) return VI_EINVAL;
+    if ((double)n * (double)R * (double)R > 17179869184.0) return VI_EINVAL;
+    if (o.format < VI_F32 || o.format > VI_UNORM16) return VI_EINVAL;
+    if (!(o.cone_half_angle_deg > 0.0f && o.cone_half_angle_deg < 90.0f)) return VI_EINVAL;
+    if (!(o.shell_radius_vox > 0.0f) || !std::isfinite(o.shell_radius_vox)) return VI_EINVAL;
+    if (!(o.comp_n >= 0.0f) || !std::isfinite(o.comp_n)) return VI_EINVAL;
+    if (!c->vol || !c->tf) return VI_ESTATE;
+    if (mode != VI_NONE && !c->has_light) return VI_ESTATE;
+
+    LightFrame lt{};
+    bool lt_ok = false;
+    if (c->has_light) {
+        rc = light_frame(c->dir, n, R, &lt);
+        if (rc) return rc;
+        lt_ok = true;
+    }
+    if (mode == VI_NONE) {
+        c->mode = VI_NONE;
+        c->bopts = o;
+        c->lt = lt;
+        c->lt_valid = lt_ok;
+        c->stack_valid = false;
+        return VI_OK;
+    }
+    size_t bytes = (size_t)n * (size_t)R * (size_t)R * format_bytes(o.format);
+    rc = ensure(c, &c->stack, &c->stack_cap, bytes);
+    if (rc) return rc;
+
+    SweepParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.vol.data = c->vol;
+    p.vol.nx = c->nx;
+    p.vol.ny = c->ny;
+    p.vol.nz = c->nz;
+    p.vol.fnx = (float)c->nx;
+    p.vol.fny = (float)c->ny;
+    p.vol.fnz = (float)c->nz;
+    p.tf = c->tf;
+    p.M = c->M;
+    p.tf_vmin = c->vmin;
+    p.tf_scale = (float)(c->M - 1) / (c->vmax - c->vmin);
+    p.lt = lt;
+    p.stack = c->stack;
+    p.opacity_correction = o.opacity_correction ? 1 : 0;
+    p.spacing_vox = lt.dL * (float)nmax(c);
+    p.comp_n = o.comp_n;
+    cudaError_t e = vi::launch_sweep(p, c->vtype, o.format, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    ++c->launches;
+    c->mode = mode;
+    c->bopts = o;
+    c->lt = lt;
+    c->lt_valid = true;
+    c->stack_bytes = bytes;
+    c->stack_valid = true;
+    return VI_OK;
+}
+
+int vi_render(vi_ctx* c, const vi_camera* cam, int W, int H, float step_vox, float* out,
+              int out_on_device, const vi_render_opts* opts) {
+    int rc = enter(c);
+    if (rc) return rc;
+    vi_render_opts ro = opts ? *opts : default_render_opts();
+    rc = check_render_inputs(c, cam, W, H, step_vox, &ro);
+    if (rc) return rc;
+    if (W == 0 || H == 0) return VI_OK;
+    if (!out) return VI_EINVAL;
+    MarchParams p;
+    rc = fill_march_params(c, cam, W, H, step_vox, &ro, &p);
+    if (rc) return rc;
+    size_t bytes = (size_t)W * (size_t)H * sizeof(float4);
+    if (out_on_device) {
+        p.out = reinterpret_cast<float4*>(out);
+    } else {
+        rc = ensure(c, reinterpret_cast<void**>(&c->out), &c->out_cap, bytes);
+        if (rc) return rc;
+        p.out = c->out;
+    }
+    cudaError_t e = vi::launch_march(p, c->vtype, c->bopts.format, c->mode, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    ++c->launches;
+    if (!out_on_device) {
+        e = cudaMemcpyAsync(out, c->out, bytes, cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+        e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+    }
+    return VI_OK;
+}
+
+int vi_sync(vi_ctx* c) {
+    if (!c) return VI_EINVAL;
+    if (cudaSetDevice(c->device) != cudaSuccess) {
+        cudaGetLastError();
+        return VI_ECUDA;
+    }
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    int s = c->sticky;
+    c->sticky = VI_OK;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return VI_ECUDA;
+    }
+    return s;
+}
+
+int vi_attenuation_info(vi_ctx* c, int* n, int* R, int* format, size_t* bytes) {
+    if (!c) return VI_EINVAL;
+    bool have = c->stack_valid;
+    if (n) *n = have ? c->lt.n : 0;
+    if (R) *R = have ? c->lt.R : 0;
+    if (format) *format = c->bopts.format;
+    if (bytes) *bytes = have ? c->stack_bytes : 0;
+    return VI_OK;
+}
+
+int vi_get_attenuation(vi_ctx* c, void* out, size_t out_bytes, int out_on_device) {
+    int rc = enter(c);
+    if (rc) return rc;
+    if (!c->stack_valid) return VI_ESTATE;
+    if (!out || out_bytes < c->stack_bytes) return VI_EINVAL;
+    cudaError_t e = cudaMemcpyAsync(out, c->stack, c->stack_bytes,
+                                    out_on_device ? cudaMemcpyDeviceToDevice
+                                                  : cudaMemcpyDeviceToHost,
+                                    c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    e = cudaStreamSynchronize(c->stream);
+    return cuda_fail(c, e);
+}
+
+int vi_trace_pixel(vi_ctx* c, const vi_camera* cam, int W, int H, float step_vox,
+                   const vi_render_opts* opts, int x, int y, int32_t* rec, int max_rec,
+                   int* n_rec) {
+    int rc = enter(c);
+    if (rc) return rc;
+    vi_render_opts ro = opts ? *opts : default_render_opts();
+    rc = check_render_inputs(c, cam, W, H, step_vox, &ro);
+    if (rc) return rc;
+    if (!rec || !n_rec || max_rec < 0 || max_rec > (1 << 22)) return VI_EINVAL;
+    if (x < 0 || y < 0 || x >= W || y >= H) return VI_EINVAL;
+    MarchParams p;
+    rc = fill_march_params(c, cam, W, H, step_vox, &ro, &p);
+    if (rc) return rc;
+    p.counts = nullptr;
+    p.lit = nullptr;
+    size_t bytes = ((size_t)max_rec * vi::kTraceWords + 1) * sizeof(int32_t);
+    rc = ensure(c, reinterpret_cast<void**>(&c->trace), &c->trace_cap, bytes);
+    if (rc) return rc;
+    int32_t* d_rec = c->trace + 1;
+    int* d_n = reinterpret_cast<int*>(c->trace);
+    cudaError_t e = vi::launch_trace(p, c->vtype, c->bopts.format, c->mode, x, y, d_rec, max_rec,
+                                     d_n, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    ++c->launches;
+    e = cudaMemcpyAsync(n_rec, d_n, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    if (*n_rec > 0) {
+        e = cudaMemcpyAsync(rec, d_rec, (size_t)(*n_rec) * vi::kTraceWords * sizeof(int32_t),
+                            cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+        e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+    }
+    return VI_OK;
+}
+
+int vi_launch_count(vi_ctx* c, uint64_t* count) {
+    if (!c || !count) return VI_EINVAL;
+    *count = c->launches;
+    return VI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,144 @@
+// vi_device.cuh -- device helpers shared by the sweep, march and trace kernels.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "vi_internal.h"
+
+namespace vi {
+
+// ---------------------------------------------------------------------------
+// Stack storage formats.  Accumulation is FP32; these only round at store.
+
+struct F32 {
+    using T = float;
+    static __device__ __forceinline__ T pack(float x) { return x; }
+    static __device__ __forceinline__ float load(const T* p) { return __ldg(p); }
+};
+struct F16 {
+    using T = __half;
+    static __device__ __forceinline__ T pack(float x) { return __float2half_rn(x); }
+    static __device__ __forceinline__ float load(const T* p) { return __half2float(__ldg(p)); }
+};
+struct BF16 {
+    using T = __nv_bfloat16;
+    static __device__ __forceinline__ T pack(float x) { return __float2bfloat16_rn(x); }
+    static __device__ __forceinline__ float load(const T* p) {
+        return __bfloat162float(__ldg(p));
+    }
+};
+// Fixed point on [0, 1] with 16 bits: x = q / 65535.
+struct UNORM16 {
+    using T = uint16_t;
+    static __device__ __forceinline__ T pack(float x) {
+        x = fminf(fmaxf(x, 0.0f), 1.0f);
+        return (T)__float2uint_rn(x * 65535.0f);
+    }
+    static __device__ __forceinline__ float load(const T* p) {
+        return (float)__ldg(p) * (1.0f / 65535.0f);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Index path (binary32, one rounding per operation, never contracted).
+
+__device__ __forceinline__ float dot3_rn(float a0, float a1, float a2, float b0, float b1,
+                                         float b2) {
+    float p0 = __fmul_rn(a0, b0);
+    float p1 = __fmul_rn(a1, b1);
+    float p2 = __fmul_rn(a2, b2);
+    return __fadd_rn(__fadd_rn(p0, p1), p2);
+}
+
+// floor(x) clamped to [lo, hi] as int.
+__device__ __forceinline__ int floor_clamp(float x, int lo, int hi) {
+    float f = floorf(x);
+    f = fminf(fmaxf(f, (float)lo), (float)hi);
+    return (int)f;
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
+
+// ---------------------------------------------------------------------------
+// Volume reconstruction: trilinear, voxel centres at (idx + 1/2) / N, clamp to
+// edge.  Cell indices come from the index path; weights are plain FP32.
+
+template <typename VoxT>
+__device__ __forceinline__ float trilinear(const VolumeView& v, float P0, float P1, float P2,
+                                           int* cell = nullptr) {
+    const VoxT* __restrict__ vol = static_cast<const VoxT*>(v.data);
+    float x = __fmaf_rn(P0, v.fnx, -0.5f);
+    float y = __fmaf_rn(P1, v.fny, -0.5f);
+    float z = __fmaf_rn(P2, v.fnz, -0.5f);
+    float flx = floorf(x), fly = floorf(y), flz = floorf(z);
+    int cx = floor_clamp(x, -1, v.nx), cy = floor_clamp(y, -1, v.ny), cz = floor_clamp(z, -1, v.nz);
+    if (cell) {
+        cell[0] = cx;
+        cell[1] = cy;
+        cell[2] = cz;
+    }
+    float wx = x - flx, wy = y - fly, wz = z - flz;
+    int x0 = clampi(cx, 0, v.nx - 1), x1 = clampi(cx + 1, 0, v.nx - 1);
+    int y0 = clampi(cy, 0, v.ny - 1), y1 = clampi(cy + 1, 0, v.ny - 1);
+    int z0 = clampi(cz, 0, v.nz - 1), z1 = clampi(cz + 1, 0, v.nz - 1);
+    const size_t sy = (size_t)v.nx, sz = (size_t)v.nx * (size_t)v.ny;
+    const VoxT* p00 = vol + z0 * sz + y0 * sy;
+    const VoxT* p01 = vol + z0 * sz + y1 * sy;
+    const VoxT* p10 = vol + z1 * sz + y0 * sy;
+    const VoxT* p11 = vol + z1 * sz + y1 * sy;
+    float c000 = (float)__ldg(p00 + x0), c001 = (float)__ldg(p00 + x1);
+    float c010 = (float)__ldg(p01 + x0), c011 = (float)__ldg(p01 + x1);
+    float c100 = (float)__ldg(p10 + x0), c101 = (float)__ldg(p10 + x1);
+    float c110 = (float)__ldg(p11 + x0), c111 = (float)__ldg(p11 + x1);
+    float c00 = fmaf(wx, c001 - c000, c000);
+    float c01 = fmaf(wx, c011 - c010, c010);
+    float c10 = fmaf(wx, c101 - c100, c100);
+    float c11 = fmaf(wx, c111 - c110, c110);
+    float c0 = fmaf(wy, c01 - c00, c00);
+    float c1 = fmaf(wy, c11 - c10, c10);
+    return fmaf(wz, c1 - c0, c0);
+}
+
+// Transfer function position of a value: x in [0, M - 1], entry i = floor(x)
+// (at most M - 2) and weight f = x - i.
+__device__ __forceinline__ void tf_coord(float v, float vmin, float scale, int M, int* i,
+                                         float* f) {
+    float x = (v - vmin) * scale;
+    x = fminf(fmaxf(x, 0.0f), (float)(M - 1));
+    int e = min((int)x, M - 2);
+    *i = e;
+    *f = x - (float)e;
+}
+
+// ---------------------------------------------------------------------------
+// Stack lookup (Eq. 9 slice, Eq. 10 UV): nearest slice k = clamp(floor(lambda
+// + 1/2), 0, n - 1), bilinear over texel centres at integer (tu, tv) with
+// clamp to edge.
+
+template <typename Fmt>
+__device__ __forceinline__ float stack_lookup(const typename Fmt::T* __restrict__ B, int n, int R,
+                                              float lam, float tu, float tv,
+                                              int* rec = nullptr) {
+    int k = floor_clamp(__fadd_rn(lam, 0.5f), 0, n - 1);
+    float fu = floorf(tu), fv = floorf(tv);
+    int iu = floor_clamp(tu, -1, R), iv = floor_clamp(tv, -1, R);
+    if (rec) {
+        rec[0] = k;
+        rec[1] = iu;
+        rec[2] = iv;
+    }
+    float wu = tu - fu, wv = tv - fv;
+    int i0 = clampi(iu, 0, R - 1), i1 = clampi(iu + 1, 0, R - 1);
+    int j0 = clampi(iv, 0, R - 1), j1 = clampi(iv + 1, 0, R - 1);
+    const typename Fmt::T* S = B + (size_t)k * (size_t)R * (size_t)R;
+    const typename Fmt::T* r0 = S + (size_t)j0 * R;
+    const typename Fmt::T* r1 = S + (size_t)j1 * R;
+    float b00 = Fmt::load(r0 + i0), b01 = Fmt::load(r0 + i1);
+    float b10 = Fmt::load(r1 + i0), b11 = Fmt::load(r1 + i1);
+    float top = fmaf(wu, b01 - b00, b00);
+    float bot = fmaf(wu, b11 - b10, b10);
+    return fmaf(wv, bot - top, top);
+}
+
+}  // namespace vi

@@ -1,0 +1,93 @@
+// vi_internal.h -- parameter blocks shared by the host runtime and the kernels.
+//
+// Every float here that feeds an integer decision (slice index, texel cell,
+// voxel cell, sample count, inside test) is computed on the host in binary32
+// with a fixed operation order and no contraction (the "index path"); the
+// kernels continue that path with __fmaf_rn / __fadd_rn / __fmul_rn /
+// __fdiv_rn / __fsqrt_rn so no compiler contraction or reassociation changes
+// a bit.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace vi {
+
+// Light set-up: Eq. 8 (min/max over the cube's vertices), the slice spacing and
+// the Eq. 9 ratio, and the light-space frame of Eq. 10 (orthographic light
+// view: basis U, V with V = L x U, a square of half extent h about the centre).
+struct LightFrame {
+    float L[3];
+    float min, max;
+    float dL;     // (max - min) / n
+    float kappa;  // n / (max - min)
+    float Lc;     // L . (1/2, 1/2, 1/2)
+    float U[3], V[3];
+    float h;      // sqrt(3)/2 as binary32
+    float sigma;  // R / (2 h): texels per world unit
+    float rho0;   // (R - 1) / 2
+    int n, R;
+};
+
+struct VolumeView {
+    const void* data;  // [nz][ny][nx], uint8 or uint16
+    int nx, ny, nz;
+    float fnx, fny, fnz;  // (float)nx ...
+};
+
+struct SweepParams {
+    VolumeView vol;
+    const float4* tf;  // M entries (alpha in .w)
+    int M;
+    float tf_vmin, tf_scale;  // x = (v - vmin) * scale, scale = (M - 1) / (vmax - vmin)
+    LightFrame lt;
+    void* stack;              // [n][R][R] of the storage format
+    int opacity_correction;
+    float spacing_vox;        // slice spacing in voxels (opacity correction exponent)
+    float comp_n;             // darkening compensation exponent, 0 = off
+};
+
+// Camera frame (binary32 index path): forward f, right r, up u, image-plane
+// half extents (sx, sy) at unit distance (perspective) or absolute (ortho).
+struct CameraFrame {
+    float eye[3], f[3], r[3], u[3];
+    float sx, sy;
+    int perspective;
+    int W, H;
+    float dt;  // step_vox / max(nx, ny, nz)
+};
+
+struct MarchParams {
+    VolumeView vol;
+    const float4* tf;
+    int M;
+    float tf_vmin, tf_scale;
+    LightFrame lt;
+    const void* stack;
+    CameraFrame cam;
+    float shell_off[6][3];  // light-space offsets of the six shell points
+    float cone_rad[2];      // ring radii in texels, rings 1 and 2
+    float cone_thr;         // 1e-6 * sigma: B_proj fallback threshold
+    float ert;
+    float bg[4];
+    float color[3];
+    float ambient;
+    int opacity_correction;
+    float step_vox;
+    float4* out;            // [H][W]
+    int32_t* counts;        // optional [H][W]: samples composited
+    int32_t* lit;           // optional [H][W]: samples with alpha > 0
+};
+
+enum { kTraceWords = 40, kTraceNone = 0x7fffffff };
+
+// Launchers (defined in vi_sweep.cu / vi_march.cu).  Return a cudaError_t.
+cudaError_t launch_sweep(const SweepParams& p, int voxel_type, int format, cudaStream_t s);
+cudaError_t launch_march(const MarchParams& p, int voxel_type, int format, int mode,
+                         cudaStream_t s);
+cudaError_t launch_trace(const MarchParams& p, int voxel_type, int format, int mode, int x,
+                         int y, int32_t* rec, int max_rec, int* n_rec, cudaStream_t s);
+
+}  // namespace vi

@@ -1,0 +1,334 @@
+// vi_march.cu -- the eye pass (Section 3.2.2, 3.2.3, 4).
+//
+// One thread per pixel; a warp covers an 8 x 4 pixel tile so its rays stay
+// close in the volume and in the attenuation stack.  Per sample: trilinear
+// reconstruction, RGBA transfer function (staged in shared memory), the light
+// coefficient from the stack (shadow: 1 bilinear lookup; shell: 6; cone: 8),
+// emission weighted by it (Eq. 7) and front-to-back compositing (Eq. 3).  The
+// warp leaves its sample loop when a ballot shows every lane has terminated
+// (early ray termination or exit).
+//
+// The same per-sample body runs in trace_kernel, which records every integer
+// decision of one ray for exact comparison with an independent implementation.
+#include "vi_device.cuh"
+
+namespace vi {
+
+namespace {
+
+constexpr int kMarchThreads = 256;  // 8 warps: a 16 x 16 pixel tile
+
+struct Ray {
+    float o[3], d[3];
+    float t0, t1;
+    float lo[3], ld[3];  // (lambda, tu, tv) at t = 0 and per unit t
+    float nbu[2], nbv[2];  // cone: ring radius times B_proj in (U, V) texel units
+    bool hit;
+};
+
+// Per-ray set-up, binary32 index path: pixel centre, direction, slab
+// intersection with [0,1]^3, light-space coordinates affine in t, and (cone)
+// B_proj = unit part of E - S (parallel to -d along the ray) orthogonal to L.
+template <int MODE>
+__device__ __forceinline__ void ray_setup(const MarchParams& p, int x, int y, Ray& r) {
+    const CameraFrame& c = p.cam;
+    float qx = __fdiv_rn((float)(2 * x + 1), (float)c.W);
+    float qy = __fdiv_rn((float)(2 * y + 1), (float)c.H);
+    float px = __fmul_rn(__fsub_rn(qx, 1.0f), c.sx);
+    float py = __fmul_rn(__fsub_rn(1.0f, qy), c.sy);
+    if (c.perspective) {
+        float w[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) w[a] = __fmaf_rn(py, c.u[a], __fmaf_rn(px, c.r[a], c.f[a]));
+        float nd = __fsqrt_rn(dot3_rn(w[0], w[1], w[2], w[0], w[1], w[2]));
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            r.o[a] = c.eye[a];
+            r.d[a] = __fdiv_rn(w[a], nd);
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            r.o[a] = __fmaf_rn(py, c.u[a], __fmaf_rn(px, c.r[a], c.eye[a]));
+            r.d[a] = c.f[a];
+        }
+    }
+    float t0 = 0.0f, t1 = __int_as_float(0x7f800000);
+    bool hit = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (r.d[a] != 0.0f) {
+            float ta = __fdiv_rn(__fsub_rn(0.0f, r.o[a]), r.d[a]);
+            float tb = __fdiv_rn(__fsub_rn(1.0f, r.o[a]), r.d[a]);
+            float tn = fminf(ta, tb), tx = fmaxf(ta, tb);
+            if (tn > t0) t0 = tn;
+            if (tx < t1) t1 = tx;
+        } else if (r.o[a] < 0.0f || r.o[a] > 1.0f) {
+            hit = false;
+        }
+    }
+    r.t0 = t0;
+    r.t1 = t1;
+    r.hit = hit && (t0 < t1);
+
+    const LightFrame& lt = p.lt;
+    float LO = dot3_rn(lt.L[0], lt.L[1], lt.L[2], r.o[0], r.o[1], r.o[2]);
+    r.lo[0] = __fmul_rn(__fsub_rn(LO, lt.min), lt.kappa);
+    r.ld[0] = __fmul_rn(dot3_rn(lt.L[0], lt.L[1], lt.L[2], r.d[0], r.d[1], r.d[2]), lt.kappa);
+    float oc0 = __fsub_rn(r.o[0], 0.5f), oc1 = __fsub_rn(r.o[1], 0.5f), oc2 = __fsub_rn(r.o[2], 0.5f);
+    r.lo[1] = __fmaf_rn(dot3_rn(oc0, oc1, oc2, lt.U[0], lt.U[1], lt.U[2]), lt.sigma, lt.rho0);
+    r.ld[1] = __fmul_rn(dot3_rn(r.d[0], r.d[1], r.d[2], lt.U[0], lt.U[1], lt.U[2]), lt.sigma);
+    r.lo[2] = __fmaf_rn(dot3_rn(oc0, oc1, oc2, lt.V[0], lt.V[1], lt.V[2]), lt.sigma, lt.rho0);
+    r.ld[2] = __fmul_rn(dot3_rn(r.d[0], r.d[1], r.d[2], lt.V[0], lt.V[1], lt.V[2]), lt.sigma);
+
+    if (MODE == 3) {
+        float bu0 = -r.ld[1], bv0 = -r.ld[2];
+        float nb = __fsqrt_rn(__fadd_rn(__fmul_rn(bu0, bu0), __fmul_rn(bv0, bv0)));
+        float bu = 1.0f, bv = 0.0f;  // view parallel to the light: B_proj = U
+        if (nb >= p.cone_thr) {
+            bu = __fdiv_rn(bu0, nb);
+            bv = __fdiv_rn(bv0, nb);
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            r.nbu[q] = __fmul_rn(p.cone_rad[q], bu);
+            r.nbv[q] = __fmul_rn(p.cone_rad[q], bv);
+        }
+    }
+}
+
+// Light-space cell of a lookup point, for the trace only.
+__device__ __forceinline__ void lookup_cell(int n, int R, float lam, float tu, float tv,
+                                            int32_t* rec) {
+    rec[0] = floor_clamp(__fadd_rn(lam, 0.5f), 0, n - 1);
+    rec[1] = floor_clamp(tu, -1, R);
+    rec[2] = floor_clamp(tv, -1, R);
+}
+
+enum { kEnded = 0, kContinue = 1, kStopped = 2 };
+
+// One sample i of a ray.  Returns kEnded if t_i is past the exit (nothing
+// done), kContinue after compositing, kStopped if early ray termination fired.
+template <typename VoxT, typename Fmt, int MODE, bool TRACE>
+__device__ __forceinline__ int march_sample(const MarchParams& p, const float4* s_tf,
+                                            const Ray& r, int i, float& C0, float& C1, float& C2,
+                                            float& A, int& count, int& lit, int32_t* rec) {
+    const float t = __fmaf_rn((float)i, p.cam.dt, r.t0);
+    if (!(t < r.t1)) return kEnded;
+    const float S0 = __fmaf_rn(t, r.d[0], r.o[0]);
+    const float S1 = __fmaf_rn(t, r.d[1], r.o[1]);
+    const float S2 = __fmaf_rn(t, r.d[2], r.o[2]);
+    int cell[3];
+    const float val = trilinear<VoxT>(p.vol, S0, S1, S2, TRACE ? cell : nullptr);
+    int e;
+    float f;
+    tf_coord(val, p.tf_vmin, p.tf_scale, p.M, &e, &f);
+    const float4 ta = s_tf[e], tb = s_tf[e + 1];
+    float alpha = fmaf(f, tb.w - ta.w, ta.w);
+    if (p.opacity_correction)
+        alpha = 1.0f - exp2f(p.step_vox * log2f(fmaxf(1.0f - alpha, 0.0f)));
+
+    if (TRACE) {
+        for (int w = 0; w < kTraceWords; ++w) rec[w] = kTraceNone;
+        rec[0] = i;
+        rec[1] = __float_as_int(t);
+        rec[5] = cell[0];
+        rec[6] = cell[1];
+        rec[7] = cell[2];
+        rec[35] = MODE == 2 ? 6 : (MODE == 3 ? 8 : 0);
+    }
+
+    float coef = 1.0f;
+    lit += alpha > 0.0f ? 1 : 0;
+    if ((MODE != 0 && alpha > 0.0f) || TRACE) {
+        const float l0 = __fmaf_rn(t, r.ld[0], r.lo[0]);
+        const float l1 = __fmaf_rn(t, r.ld[1], r.lo[1]);
+        const float l2 = __fmaf_rn(t, r.ld[2], r.lo[2]);
+        const typename Fmt::T* B = static_cast<const typename Fmt::T*>(p.stack);
+        const int n = p.lt.n, R = p.lt.R;
+        if (TRACE) {
+            rec[2] = __float_as_int(l0);
+            rec[3] = __float_as_int(l1);
+            rec[4] = __float_as_int(l2);
+            if (n > 0) lookup_cell(n, R, l0, l1, l2, rec + 8);
+        }
+        if (MODE == 1) {
+            coef = stack_lookup<Fmt>(B, n, R, l0, l1, l2);
+        } else if (MODE == 2) {
+            float sum = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                float q0 = __fadd_rn(l0, p.shell_off[q][0]);
+                float q1 = __fadd_rn(l1, p.shell_off[q][1]);
+                float q2 = __fadd_rn(l2, p.shell_off[q][2]);
+                sum += stack_lookup<Fmt>(B, n, R, q0, q1, q2, TRACE ? rec + 11 + 3 * q : nullptr);
+            }
+            coef = sum * (1.0f / 6.0f);
+        } else if (MODE == 3) {
+            float sum = 0.0f;
+#pragma unroll
+            for (int ring = 0; ring < 2; ++ring) {
+                const float q0 = __fadd_rn(l0, -(float)(ring + 1));
+                const float bu = r.nbu[ring], bv = r.nbv[ring];
+                // B_proj turned by m pi/2 about L: (bu, bv), (-bv, bu), (-bu, -bv), (bv, -bu).
+                const float du[4] = {bu, -bv, -bu, bv};
+                const float dv[4] = {bv, bu, -bv, -bu};
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    float q1 = __fadd_rn(l1, du[m]);
+                    float q2 = __fadd_rn(l2, dv[m]);
+                    sum += stack_lookup<Fmt>(B, n, R, q0, q1, q2,
+                                             TRACE ? rec + 11 + 3 * (ring * 4 + m) : nullptr);
+                }
+            }
+            coef = sum * 0.125f;
+        }
+    }
+
+    // Eq. 7 and Eq. 3: emission = light factor * light colour * alpha * rgb.
+    const float lf = fmaf(1.0f - p.ambient, coef, p.ambient);
+    const float w = (1.0f - A) * lf * alpha;
+    C0 = fmaf(w * p.color[0], fmaf(f, tb.x - ta.x, ta.x), C0);
+    C1 = fmaf(w * p.color[1], fmaf(f, tb.y - ta.y, ta.y), C1);
+    C2 = fmaf(w * p.color[2], fmaf(f, tb.z - ta.z, ta.z), C2);
+    A = fmaf(1.0f - A, alpha, A);
+    ++count;
+    return A > p.ert ? kStopped : kContinue;
+}
+
+__device__ __forceinline__ void load_tf(const MarchParams& p, float4* s_tf) {
+    for (int e = threadIdx.x; e < p.M; e += blockDim.x) s_tf[e] = p.tf[e];
+    __syncthreads();
+}
+
+template <typename VoxT, typename Fmt, int MODE>
+__global__ void __launch_bounds__(kMarchThreads) march_kernel(const MarchParams p) {
+    extern __shared__ float4 s_tf[];
+    load_tf(p, s_tf);
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int x = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
+    const int y = blockIdx.y * 16 + (warp >> 1) * 4 + (lane >> 3);
+    const bool valid = x < p.cam.W && y < p.cam.H;
+    Ray r;
+    r.hit = false;
+    if (valid) ray_setup<MODE>(p, x, y, r);
+
+    float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, A = 0.0f;
+    int count = 0, lit = 0;
+    bool active = valid && r.hit;
+    // All 32 lanes stay in the loop; it ends when the ballot finds none active.
+    for (int i = 0; __any_sync(0xffffffffu, active); ++i) {
+        if (active)
+            active = march_sample<VoxT, Fmt, MODE, false>(p, s_tf, r, i, C0, C1, C2, A, count,
+                                                          lit, nullptr) == kContinue;
+    }
+    if (valid) {
+        const size_t idx = (size_t)y * p.cam.W + x;
+        const float rem = 1.0f - A;
+        p.out[idx] = make_float4(fmaf(rem, p.bg[0], C0), fmaf(rem, p.bg[1], C1),
+                                 fmaf(rem, p.bg[2], C2), fmaf(rem, p.bg[3], A));
+        if (p.counts) p.counts[idx] = count;
+        if (p.lit) p.lit[idx] = lit;
+    }
+}
+
+template <typename VoxT, typename Fmt, int MODE>
+__global__ void trace_kernel(const MarchParams p, int x, int y, int32_t* rec, int max_rec,
+                             int* n_rec) {
+    extern __shared__ float4 s_tf[];
+    load_tf(p, s_tf);
+    if (threadIdx.x != 0) return;
+    Ray r;
+    ray_setup<MODE>(p, x, y, r);
+    float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, A = 0.0f;
+    int count = 0, lit = 0, nrec = 0;
+    int32_t scratch[kTraceWords];
+    if (r.hit) {
+        for (int i = 0;; ++i) {
+            int32_t* out = nrec < max_rec ? rec + (size_t)nrec * kTraceWords : scratch;
+            int st = march_sample<VoxT, Fmt, MODE, true>(p, s_tf, r, i, C0, C1, C2, A, count, lit,
+                                                         out);
+            if (st == kEnded) break;
+            if (nrec < max_rec) ++nrec;
+            if (st == kStopped) break;
+        }
+    }
+    *n_rec = nrec;
+}
+
+template <typename VoxT, typename Fmt, int MODE>
+cudaError_t launch_march_typed(const MarchParams& p, cudaStream_t s) {
+    const size_t smem = (size_t)p.M * sizeof(float4);
+    auto kern = march_kernel<VoxT, Fmt, MODE>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid((p.cam.W + 15) / 16, (p.cam.H + 15) / 16);
+    kern<<<grid, kMarchThreads, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <typename VoxT, typename Fmt, int MODE>
+cudaError_t launch_trace_typed(const MarchParams& p, int x, int y, int32_t* rec, int max_rec,
+                               int* n_rec, cudaStream_t s) {
+    const size_t smem = (size_t)p.M * sizeof(float4);
+    auto kern = trace_kernel<VoxT, Fmt, MODE>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<1, 32, smem, s>>>(p, x, y, rec, max_rec, n_rec);
+    return cudaGetLastError();
+}
+
+template <typename VoxT, typename Fmt>
+cudaError_t dispatch_mode(const MarchParams& p, int mode, bool trace, int x, int y, int32_t* rec,
+                          int max_rec, int* n_rec, cudaStream_t s) {
+    switch (mode) {
+        case 0:
+            return trace ? launch_trace_typed<VoxT, Fmt, 0>(p, x, y, rec, max_rec, n_rec, s)
+                         : launch_march_typed<VoxT, Fmt, 0>(p, s);
+        case 1:
+            return trace ? launch_trace_typed<VoxT, Fmt, 1>(p, x, y, rec, max_rec, n_rec, s)
+                         : launch_march_typed<VoxT, Fmt, 1>(p, s);
+        case 2:
+            return trace ? launch_trace_typed<VoxT, Fmt, 2>(p, x, y, rec, max_rec, n_rec, s)
+                         : launch_march_typed<VoxT, Fmt, 2>(p, s);
+        case 3:
+            return trace ? launch_trace_typed<VoxT, Fmt, 3>(p, x, y, rec, max_rec, n_rec, s)
+                         : launch_march_typed<VoxT, Fmt, 3>(p, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename VoxT>
+cudaError_t dispatch_fmt(const MarchParams& p, int format, int mode, bool trace, int x, int y,
+                         int32_t* rec, int max_rec, int* n_rec, cudaStream_t s) {
+    switch (format) {
+        case 0: return dispatch_mode<VoxT, F32>(p, mode, trace, x, y, rec, max_rec, n_rec, s);
+        case 1: return dispatch_mode<VoxT, F16>(p, mode, trace, x, y, rec, max_rec, n_rec, s);
+        case 2: return dispatch_mode<VoxT, BF16>(p, mode, trace, x, y, rec, max_rec, n_rec, s);
+        case 3: return dispatch_mode<VoxT, UNORM16>(p, mode, trace, x, y, rec, max_rec, n_rec, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t launch_march(const MarchParams& p, int voxel_type, int format, int mode,
+                         cudaStream_t s) {
+    if (voxel_type == 0) return dispatch_fmt<uint8_t>(p, format, mode, false, 0, 0, nullptr, 0, nullptr, s);
+    return dispatch_fmt<uint16_t>(p, format, mode, false, 0, 0, nullptr, 0, nullptr, s);
+}
+
+cudaError_t launch_trace(const MarchParams& p, int voxel_type, int format, int mode, int x, int y,
+                         int32_t* rec, int max_rec, int* n_rec, cudaStream_t s) {
+    if (voxel_type == 0) return dispatch_fmt<uint8_t>(p, format, mode, true, x, y, rec, max_rec, n_rec, s);
+    return dispatch_fmt<uint16_t>(p, format, mode, true, x, y, rec, max_rec, n_rec, s);
+}
+
+}  // namespace vi

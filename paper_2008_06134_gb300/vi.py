@@ -1,0 +1,270 @@
+"""Thin ctypes binding of the C ABI in ``include/vi.h``.
+
+Argument marshalling only: every step of the method runs in ``libvi.so``'s
+CUDA kernels.  Methods of :class:`Context` carry the C names without the
+``vi_`` prefix (``load_volume`` is ``vi_load_volume`` and so on).  Device
+buffers are passed as torch CUDA tensors (their ``data_ptr()``), host buffers
+as numpy arrays.  There is no CPU path: if ``libvi.so`` is missing, loading
+fails with an error that says how to build it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libvi.so")
+
+OK, EINVAL, ENOMEM, ESTATE, ECUDA, ETIMEOUT = 0, -1, -2, -3, -4, -5
+U8, U16 = 0, 1
+NONE, SHADOW, SHELL, CONE = 0, 1, 2, 3
+F32, F16, BF16, UNORM16 = 0, 1, 2, 3
+TRACE_WORDS = 40
+TRACE_NONE = 0x7FFFFFFF
+
+# Every symbol include/vi.h declares, in order.
+EXPORTS = ("vi_create", "vi_destroy", "vi_set_memory_budget", "vi_load_volume",
+           "vi_set_transfer_function", "vi_set_light", "vi_build_attenuation", "vi_render",
+           "vi_sync", "vi_error_string", "vi_attenuation_info", "vi_get_attenuation",
+           "vi_trace_pixel", "vi_launch_count")
+
+
+class ViError(RuntimeError):
+    def __init__(self, code: int, call: str):
+        self.code = code
+        super().__init__(f"{call}: {error_string(code)} ({code})")
+
+
+class BuildOpts(C.Structure):
+    _fields_ = [("format", C.c_int), ("cone_half_angle_deg", C.c_float),
+                ("shell_radius_vox", C.c_float), ("opacity_correction", C.c_int),
+                ("comp_n", C.c_float)]
+
+
+class Camera(C.Structure):
+    _fields_ = [("perspective", C.c_int), ("eye", C.c_float * 3), ("target", C.c_float * 3),
+                ("up", C.c_float * 3), ("fovy_deg", C.c_float), ("ortho_half_height", C.c_float)]
+
+
+class RenderOpts(C.Structure):
+    _fields_ = [("ert", C.c_float), ("bg", C.c_float * 4), ("ambient", C.c_float),
+                ("opacity_correction", C.c_int), ("sample_counts", C.c_void_p),
+                ("lit_counts", C.c_void_p)]
+
+
+_lib = None
+
+
+def library() -> C.CDLL:
+    """Load ``libvi.so`` (built by ``python -m paper_2008_06134_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(
+            f"{LIB_PATH} is not built; run `python -m paper_2008_06134_gb300.build` "
+            "(needs nvcc) -- there is no CPU fallback")
+    L = C.CDLL(LIB_PATH)
+    P, vp, i, f, sz = C.POINTER, C.c_void_p, C.c_int, C.c_float, C.c_size_t
+    L.vi_create.argtypes = [P(vp), i, vp]
+    L.vi_destroy.argtypes = [vp]
+    L.vi_set_memory_budget.argtypes = [vp, sz]
+    L.vi_load_volume.argtypes = [vp, vp, i, i, i, i, i]
+    L.vi_set_transfer_function.argtypes = [vp, vp, i, f, f]
+    L.vi_set_light.argtypes = [vp, vp, vp]
+    L.vi_build_attenuation.argtypes = [vp, i, i, i, P(BuildOpts)]
+    L.vi_render.argtypes = [vp, P(Camera), i, i, f, vp, i, P(RenderOpts)]
+    L.vi_sync.argtypes = [vp]
+    L.vi_error_string.argtypes = [i]
+    L.vi_error_string.restype = C.c_char_p
+    L.vi_attenuation_info.argtypes = [vp, P(i), P(i), P(i), P(sz)]
+    L.vi_get_attenuation.argtypes = [vp, vp, sz, i]
+    L.vi_trace_pixel.argtypes = [vp, P(Camera), i, i, f, P(RenderOpts), i, i, vp, i, P(i)]
+    L.vi_launch_count.argtypes = [vp, P(C.c_uint64)]
+    _lib = L
+    return L
+
+
+def error_string(code: int) -> str:
+    return library().vi_error_string(int(code)).decode()
+
+
+def _check(code: int, call: str) -> None:
+    if code != OK:
+        raise ViError(code, call)
+
+
+def _f3(v):
+    return (C.c_float * 3)(*[float(x) for x in v])
+
+
+def camera(cam) -> Camera:
+    """From a ``phantoms.Camera`` or an (eye, target, up, persp, fovy, half_height) tuple."""
+    t = cam.as_tuple() if hasattr(cam, "as_tuple") else cam
+    eye, target, up, persp, fovy, hh = t
+    return Camera(int(persp), _f3(eye), _f3(target), _f3(up), float(fovy), float(hh))
+
+
+def _ptr(buf):
+    """(pointer, on_device) of a torch tensor or numpy array."""
+    if hasattr(buf, "data_ptr"):
+        return buf.data_ptr(), int(buf.is_cuda)
+    return buf.ctypes.data, 0
+
+
+class Context:
+    """One ``vi_ctx``: a device, a stream and the resident volume / TF / stack."""
+
+    def __init__(self, device: int = 0, stream=None):
+        L = library()
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream(device).cuda_stream
+            except Exception:
+                stream = 0
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        self.stream = int(stream)
+        h = C.c_void_p()
+        _check(L.vi_create(C.byref(h), int(device), C.c_void_p(self.stream)), "vi_create")
+        self.h = h
+        self.L = L
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.L.vi_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_memory_budget(self, nbytes: int) -> None:
+        _check(self.L.vi_set_memory_budget(self.h, int(nbytes)), "vi_set_memory_budget")
+
+    def load_volume(self, vol, dtype: int | None = None) -> None:
+        """``vol``: [nz, ny, nx] uint8 / uint16, numpy (host) or torch (host or
+        device).  ``dtype`` (U8 / U16) overrides the element type, e.g. for a
+        torch int16 tensor holding uint16 bits."""
+        dt = str(vol.dtype)
+        if dtype is not None:
+            code = int(dtype)
+            size = vol.element_size() if hasattr(vol, "element_size") else vol.itemsize
+            if size != (1 if code == U8 else 2):
+                raise TypeError("element size does not match dtype")
+        elif dt.endswith("uint8"):
+            code = U8
+        elif dt.endswith("uint16"):
+            code = U16
+        else:
+            raise TypeError("volume must be uint8 or uint16")
+        if hasattr(vol, "is_contiguous") and not vol.is_contiguous():
+            raise ValueError("volume tensor must be contiguous")
+        if isinstance(vol, np.ndarray):
+            vol = np.ascontiguousarray(vol)
+        nz, ny, nx = vol.shape
+        p, dev = _ptr(vol)
+        _check(self.L.vi_load_volume(self.h, C.c_void_p(p), code, nx, ny, nz, dev),
+               "vi_load_volume")
+
+    def set_transfer_function(self, rgba, vmin: float, vmax: float) -> None:
+        rgba = np.ascontiguousarray(rgba, dtype=np.float32)
+        if rgba.ndim != 2 or rgba.shape[1] != 4:
+            raise ValueError("transfer function must be (M, 4)")
+        _check(self.L.vi_set_transfer_function(self.h, C.c_void_p(rgba.ctypes.data),
+                                               rgba.shape[0], float(vmin), float(vmax)),
+               "vi_set_transfer_function")
+
+    def set_light(self, direction, color=(1.0, 1.0, 1.0)) -> None:
+        _check(self.L.vi_set_light(self.h, _f3(direction), _f3(color)), "vi_set_light")
+
+    def build_attenuation(self, n_slices: int, slice_res: int, mode: int, format: int = F32,
+                          cone_half_angle_deg: float = 15.0, shell_radius_vox: float = 1.0,
+                          opacity_correction: int = 0, comp_n: float = 0.0) -> None:
+        o = BuildOpts(int(format), float(cone_half_angle_deg), float(shell_radius_vox),
+                      int(opacity_correction), float(comp_n))
+        _check(self.L.vi_build_attenuation(self.h, int(n_slices), int(slice_res), int(mode),
+                                           C.byref(o)), "vi_build_attenuation")
+
+    @staticmethod
+    def _render_opts(ert, bg, ambient, opacity_correction, sample_counts=None,
+                     lit_counts=None) -> RenderOpts:
+        ptrs = []
+        for buf in (sample_counts, lit_counts):
+            cp = None
+            if buf is not None:
+                cp, dev = _ptr(buf)
+                if not dev:
+                    raise ValueError("per-pixel counters must be device tensors")
+            ptrs.append(cp)
+        return RenderOpts(float(ert), (C.c_float * 4)(*map(float, bg)), float(ambient),
+                          int(opacity_correction), *ptrs)
+
+    def render(self, cam, W: int, H: int, step_vox: float, out=None, ert: float = 2.0,
+               bg=(0.0, 0.0, 0.0, 0.0), ambient: float = 0.0, opacity_correction: int = 0,
+               sample_counts=None, lit_counts=None):
+        """Render into ``out`` ((H, W, 4) float32; torch CUDA tensor or numpy /
+        pinned torch host tensor).  With ``out=None`` a torch CUDA tensor is
+        allocated and returned."""
+        if out is None:
+            import torch
+            out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+        p, dev = _ptr(out)
+        ro = self._render_opts(ert, bg, ambient, opacity_correction, sample_counts, lit_counts)
+        _check(self.L.vi_render(self.h, C.byref(camera(cam)), int(W), int(H), float(step_vox),
+                                C.c_void_p(p), dev, C.byref(ro)), "vi_render")
+        return out
+
+    def sync(self) -> None:
+        _check(self.L.vi_sync(self.h), "vi_sync")
+
+    def attenuation_info(self):
+        n, R, fmt, nb = C.c_int(), C.c_int(), C.c_int(), C.c_size_t()
+        _check(self.L.vi_attenuation_info(self.h, C.byref(n), C.byref(R), C.byref(fmt),
+                                          C.byref(nb)), "vi_attenuation_info")
+        return n.value, R.value, fmt.value, nb.value
+
+    def get_attenuation(self) -> np.ndarray:
+        """The stack as stored: (n, R, R) float32 / float16 / uint16 (bf16 as uint16 bits)."""
+        n, R, fmt, nb = self.attenuation_info()
+        dt = {F32: np.float32, F16: np.float16, BF16: np.uint16, UNORM16: np.uint16}[fmt]
+        out = np.empty((n, R, R), dtype=dt)
+        _check(self.L.vi_get_attenuation(self.h, C.c_void_p(out.ctypes.data), out.nbytes, 0),
+               "vi_get_attenuation")
+        return out
+
+    def trace_pixel(self, cam, W, H, step_vox, x, y, ert=2.0, bg=(0, 0, 0, 0), ambient=0.0,
+                    opacity_correction=0, max_rec=8192) -> np.ndarray:
+        rec = np.zeros((max_rec, TRACE_WORDS), dtype=np.int32)
+        n = C.c_int(0)
+        ro = self._render_opts(ert, bg, ambient, opacity_correction)
+        _check(self.L.vi_trace_pixel(self.h, C.byref(camera(cam)), int(W), int(H),
+                                     float(step_vox), C.byref(ro), int(x), int(y),
+                                     C.c_void_p(rec.ctypes.data), int(max_rec), C.byref(n)),
+               "vi_trace_pixel")
+        return rec[: n.value].copy()
+
+    def launch_count(self) -> int:
+        v = C.c_uint64(0)
+        _check(self.L.vi_launch_count(self.h, C.byref(v)), "vi_launch_count")
+        return int(v.value)
+
+
+def decode_stack(raw: np.ndarray, fmt: int) -> np.ndarray:
+    """Stored stack values as float64."""
+    if fmt == F32 or fmt == F16:
+        return raw.astype(np.float64)
+    if fmt == BF16:
+        return (raw.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    return raw.astype(np.float64) / 65535.0
