@@ -168,7 +168,8 @@ int vi_get_attenuation(vi_ctx* ctx, void* out, size_t out_bytes, int out_on_devi
    int32 = { i, bits(t_i), bits(lambda), bits(tu), bits(tv), voxel cell x,y,z,
    own lookup cell (k, iu, iv), 8 neighbour cells (k, iu, iv), neighbour count,
    unused }, unused words 0x7fffffff.  rec is host memory of max_rec records;
-   *n_rec receives the count.  Synchronous. */
+   recording stops after max_rec samples; *n_rec receives the count.
+   Synchronous. */
 int vi_trace_pixel(vi_ctx* ctx, const vi_camera* camera, int W, int H, float step_vox,
                    const vi_render_opts* opts, int x, int y, int32_t* rec, int max_rec,
                    int* n_rec);

@@ -243,14 +243,14 @@ __global__ void trace_kernel(const MarchParams p, int x, int y, int32_t* rec, in
     ray_setup<MODE>(p, x, y, r);
     float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, A = 0.0f;
     int count = 0, lit = 0, nrec = 0;
-    int32_t scratch[kTraceWords];
+    // Records the first max_rec samples of the ray.
     if (r.hit) {
-        for (int i = 0;; ++i) {
-            int32_t* out = nrec < max_rec ? rec + (size_t)nrec * kTraceWords : scratch;
+        for (int i = 0; nrec < max_rec; ++i) {
+            int32_t* out = rec + (size_t)nrec * kTraceWords;
             int st = march_sample<VoxT, Fmt, MODE, true>(p, s_tf, r, i, C0, C1, C2, A, count, lit,
                                                          out);
             if (st == kEnded) break;
-            if (nrec < max_rec) ++nrec;
+            ++nrec;
             if (st == kStopped) break;
         }
     }

@@ -107,8 +107,9 @@ def test_invalid_arguments(ctx, vi):
         (((0.5, 0.5, 3.0), (0.5, 0.5, 0.5), (0, 1, 0), 0, 40.0, -1.0), 4, 4, 0.5), # ortho < 0
         (good, -1, 4, 0.5), (good, 4, 4, 0.0), (good, 4, 4, float("nan")),
     ]:
+        buf = np.empty((4, 4, 4), np.float32)   # host buffer: the C ABI checks W, H itself
         with pytest.raises(vi.ViError) as e:
-            ctx.render(cam, W, H, step)
+            ctx.render(cam, W, H, step, out=buf)
         assert e.value.code == vi.EINVAL
     import torch
     empty = torch.empty((0, 5, 4), device="cuda")
