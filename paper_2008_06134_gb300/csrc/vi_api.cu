@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "../../include/vi.h"
 #include "vi_internal.h"
@@ -34,6 +35,17 @@ struct vi_ctx {
     size_t tf_cap = 0;
     int M = 0;
     float vmin = 0.0f, vmax = 1.0f;
+
+    // Brick occupancy (empty-space skipping): per-brick value range (from the
+    // volume), prefix count of TF entries with alpha > 0, per-brick flags.
+    uint32_t* brange = nullptr;
+    size_t brange_cap = 0;
+    int* tfcnt = nullptr;
+    size_t tfcnt_cap = 0;
+    uint8_t* bflags = nullptr;
+    size_t bflags_cap = 0;
+    int nbx = 0, nby = 0, nbz = 0;
+    bool flags_ok = false;  // bflags match the current volume and TF
 
     bool has_light = false;
     float dir[3] = {0.0f, 0.0f, 1.0f};
@@ -232,18 +244,49 @@ int enter(vi_ctx* c) {
 
 void mark_stale(vi_ctx* c) { c->stack_valid = false; }
 
+int nbricks(const vi_ctx* c) { return c->nbx * c->nby * c->nbz; }
+
+vi::VolumeView volume_view(const vi_ctx* c) {
+    vi::VolumeView v;
+    v.data = c->vol;
+    v.nx = c->nx;
+    v.ny = c->ny;
+    v.nz = c->nz;
+    v.fnx = (float)c->nx;
+    v.fny = (float)c->ny;
+    v.fnz = (float)c->nz;
+    return v;
+}
+
+vi::GridView grid_view(const vi_ctx* c) {
+    vi::GridView g;
+    g.flags = c->bflags;
+    g.nbx = c->nbx;
+    g.nby = c->nby;
+    return g;
+}
+
+// Brick flags from the current brick ranges and TF (both must be present).
+int refresh_flags(vi_ctx* c) {
+    c->flags_ok = false;
+    if (!c->brange || !c->tfcnt || !c->vol || !c->tf) return VI_OK;
+    int rc = ensure(c, reinterpret_cast<void**>(&c->bflags), &c->bflags_cap, (size_t)nbricks(c));
+    if (rc) return rc;
+    cudaError_t e = vi::launch_brick_flags(c->brange, nbricks(c), c->tfcnt, c->M, c->vmin,
+                                           c->vmax, c->bflags, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    ++c->launches;
+    c->flags_ok = true;
+    return VI_OK;
+}
+
 int fill_march_params(vi_ctx* c, const vi_camera* cam, int W, int H, float step_vox,
                       const vi_render_opts* ro, MarchParams* p) {
     std::memset(p, 0, sizeof(*p));
     int rc = camera_frame(cam, W, H, step_vox, nmax(c), &p->cam);
     if (rc) return rc;
-    p->vol.data = c->vol;
-    p->vol.nx = c->nx;
-    p->vol.ny = c->ny;
-    p->vol.nz = c->nz;
-    p->vol.fnx = (float)c->nx;
-    p->vol.fny = (float)c->ny;
-    p->vol.fnz = (float)c->nz;
+    p->vol = volume_view(c);
+    p->grid = grid_view(c);
     p->tf = c->tf;
     p->M = c->M;
     p->tf_vmin = c->vmin;
@@ -294,7 +337,7 @@ int check_render_inputs(vi_ctx* c, const vi_camera* cam, int W, int H, float ste
     if (!std::isfinite(ro->ert) || !std::isfinite(ro->ambient)) return VI_EINVAL;
     for (int k = 0; k < 4; ++k)
         if (!std::isfinite(ro->bg[k])) return VI_EINVAL;
-    if (!c->vol || !c->tf || c->mode < 0) return VI_ESTATE;
+    if (!c->vol || !c->tf || !c->flags_ok || c->mode < 0) return VI_ESTATE;
     if (c->mode != VI_NONE && !c->stack_valid) return VI_ESTATE;
     // A ray crosses at most sqrt(3) of the cube: cap its sample count at 2^24.
     if (1.7320509 * (double)nmax(c) / (double)step_vox > 16777216.0) return VI_EINVAL;
@@ -349,6 +392,9 @@ int vi_destroy(vi_ctx* c) {
     release(c, &c->stack, &c->stack_cap);
     release(c, reinterpret_cast<void**>(&c->out), &c->out_cap);
     release(c, reinterpret_cast<void**>(&c->trace), &c->trace_cap);
+    release(c, reinterpret_cast<void**>(&c->brange), &c->brange_cap);
+    release(c, reinterpret_cast<void**>(&c->tfcnt), &c->tfcnt_cap);
+    release(c, reinterpret_cast<void**>(&c->bflags), &c->bflags_cap);
     delete c;
     return VI_OK;
 }
@@ -368,6 +414,7 @@ int vi_load_volume(vi_ctx* c, const void* data, int dtype, int nx, int ny, int n
     size_t bytes = (size_t)nx * (size_t)ny * (size_t)nz * voxel_bytes(dtype);
     rc = ensure(c, &c->vol, &c->vol_cap, bytes);
     if (rc) return rc;
+    c->flags_ok = false;
     cudaError_t e = cudaMemcpyAsync(c->vol, data, bytes,
                                     data_on_device ? cudaMemcpyDeviceToDevice
                                                    : cudaMemcpyHostToDevice,
@@ -378,7 +425,17 @@ int vi_load_volume(vi_ctx* c, const void* data, int dtype, int nx, int ny, int n
     c->ny = ny;
     c->nz = nz;
     mark_stale(c);
-    return VI_OK;
+    constexpr int B = 1 << vi::kBrickShift;
+    c->nbx = (nx + B - 1) / B;
+    c->nby = (ny + B - 1) / B;
+    c->nbz = (nz + B - 1) / B;
+    rc = ensure(c, reinterpret_cast<void**>(&c->brange), &c->brange_cap,
+                (size_t)nbricks(c) * sizeof(uint32_t));
+    if (rc) return rc;
+    e = vi::launch_brick_range(volume_view(c), dtype, c->brange, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    ++c->launches;
+    return refresh_flags(c);
 }
 
 int vi_set_transfer_function(vi_ctx* c, const float* rgba, int M, float vmin, float vmax) {
@@ -396,13 +453,22 @@ int vi_set_transfer_function(vi_ctx* c, const float* rgba, int M, float vmin, fl
     size_t bytes = (size_t)M * sizeof(float4);
     rc = ensure(c, reinterpret_cast<void**>(&c->tf), &c->tf_cap, bytes);
     if (rc) return rc;
+    // Prefix count of entries with alpha > 0, for the brick flags.
+    std::vector<int> cnt((size_t)M + 1, 0);
+    for (int k = 0; k < M; ++k) cnt[k + 1] = cnt[k] + (rgba[4 * k + 3] > 0.0f ? 1 : 0);
+    rc = ensure(c, reinterpret_cast<void**>(&c->tfcnt), &c->tfcnt_cap, cnt.size() * sizeof(int));
+    if (rc) return rc;
     cudaError_t e = cudaMemcpyAsync(c->tf, rgba, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    // From pageable memory: the copy has left cnt by the time this returns.
+    e = cudaMemcpyAsync(c->tfcnt, cnt.data(), cnt.size() * sizeof(int), cudaMemcpyHostToDevice,
+                        c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e);
     c->M = M;
     c->vmin = vmin;
     c->vmax = vmax;
     mark_stale(c);
-    return VI_OK;
+    return refresh_flags(c);
 }
 
 int vi_set_light(vi_ctx* c, const float dir[3], const float color[3]) {
@@ -431,7 +497,7 @@ int vi_build_attenuation(vi_ctx* c, int n, int R, int mode, const vi_build_opts*
     if (!(o.cone_half_angle_deg > 0.0f && o.cone_half_angle_deg < 90.0f)) return VI_EINVAL;
     if (!(o.shell_radius_vox > 0.0f) || !std::isfinite(o.shell_radius_vox)) return VI_EINVAL;
     if (!(o.comp_n >= 0.0f) || !std::isfinite(o.comp_n)) return VI_EINVAL;
-    if (!c->vol || !c->tf) return VI_ESTATE;
+    if (!c->vol || !c->tf || !c->flags_ok) return VI_ESTATE;
     if (mode != VI_NONE && !c->has_light) return VI_ESTATE;
 
     LightFrame lt{};
@@ -455,13 +521,8 @@ int vi_build_attenuation(vi_ctx* c, int n, int R, int mode, const vi_build_opts*
 
     SweepParams p;
     std::memset(&p, 0, sizeof(p));
-    p.vol.data = c->vol;
-    p.vol.nx = c->nx;
-    p.vol.ny = c->ny;
-    p.vol.nz = c->nz;
-    p.vol.fnx = (float)c->nx;
-    p.vol.fny = (float)c->ny;
-    p.vol.fnz = (float)c->nz;
+    p.vol = volume_view(c);
+    p.grid = grid_view(c);
     p.tf = c->tf;
     p.M = c->M;
     p.tf_vmin = c->vmin;

@@ -64,40 +64,60 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v,
 // Volume reconstruction: trilinear, voxel centres at (idx + 1/2) / N, clamp to
 // edge.  Cell indices come from the index path; weights are plain FP32.
 
-template <typename VoxT>
-__device__ __forceinline__ float trilinear(const VolumeView& v, float P0, float P1, float P2,
-                                           int* cell = nullptr) {
-    const VoxT* __restrict__ vol = static_cast<const VoxT*>(v.data);
+struct VoxelCoord {
+    int cx, cy, cz;          // floor of the voxel coordinate, clamped to [-1, N]
+    int x0, x1, y0, y1, z0, z1;  // footprint corners, clamped to [0, N - 1]
+    float wx, wy, wz;        // weights of the upper corners
+};
+
+__device__ __forceinline__ VoxelCoord voxel_coord(const VolumeView& v, float P0, float P1,
+                                                  float P2) {
+    VoxelCoord c;
     float x = __fmaf_rn(P0, v.fnx, -0.5f);
     float y = __fmaf_rn(P1, v.fny, -0.5f);
     float z = __fmaf_rn(P2, v.fnz, -0.5f);
     float flx = floorf(x), fly = floorf(y), flz = floorf(z);
-    int cx = floor_clamp(x, -1, v.nx), cy = floor_clamp(y, -1, v.ny), cz = floor_clamp(z, -1, v.nz);
-    if (cell) {
-        cell[0] = cx;
-        cell[1] = cy;
-        cell[2] = cz;
-    }
-    float wx = x - flx, wy = y - fly, wz = z - flz;
-    int x0 = clampi(cx, 0, v.nx - 1), x1 = clampi(cx + 1, 0, v.nx - 1);
-    int y0 = clampi(cy, 0, v.ny - 1), y1 = clampi(cy + 1, 0, v.ny - 1);
-    int z0 = clampi(cz, 0, v.nz - 1), z1 = clampi(cz + 1, 0, v.nz - 1);
+    c.cx = (int)fminf(fmaxf(flx, -1.0f), (float)v.nx);
+    c.cy = (int)fminf(fmaxf(fly, -1.0f), (float)v.ny);
+    c.cz = (int)fminf(fmaxf(flz, -1.0f), (float)v.nz);
+    c.wx = x - flx;
+    c.wy = y - fly;
+    c.wz = z - flz;
+    c.x0 = clampi(c.cx, 0, v.nx - 1);
+    c.x1 = clampi(c.cx + 1, 0, v.nx - 1);
+    c.y0 = clampi(c.cy, 0, v.ny - 1);
+    c.y1 = clampi(c.cy + 1, 0, v.ny - 1);
+    c.z0 = clampi(c.cz, 0, v.nz - 1);
+    c.z1 = clampi(c.cz + 1, 0, v.nz - 1);
+    return c;
+}
+
+// Whether the brick holding the footprint's lower corner may yield alpha > 0.
+__device__ __forceinline__ bool brick_may_be_lit(const GridView& g, const VoxelCoord& c) {
+    const int b = ((c.z0 >> kBrickShift) * g.nby + (c.y0 >> kBrickShift)) * g.nbx +
+                  (c.x0 >> kBrickShift);
+    return __ldg(g.flags + b) != 0;
+}
+
+template <typename VoxT>
+__device__ __forceinline__ float trilinear_fetch(const VolumeView& v, const VoxelCoord& c) {
+    const VoxT* __restrict__ vol = static_cast<const VoxT*>(v.data);
     const size_t sy = (size_t)v.nx, sz = (size_t)v.nx * (size_t)v.ny;
-    const VoxT* p00 = vol + z0 * sz + y0 * sy;
-    const VoxT* p01 = vol + z0 * sz + y1 * sy;
-    const VoxT* p10 = vol + z1 * sz + y0 * sy;
-    const VoxT* p11 = vol + z1 * sz + y1 * sy;
-    float c000 = (float)__ldg(p00 + x0), c001 = (float)__ldg(p00 + x1);
-    float c010 = (float)__ldg(p01 + x0), c011 = (float)__ldg(p01 + x1);
-    float c100 = (float)__ldg(p10 + x0), c101 = (float)__ldg(p10 + x1);
-    float c110 = (float)__ldg(p11 + x0), c111 = (float)__ldg(p11 + x1);
-    float c00 = fmaf(wx, c001 - c000, c000);
-    float c01 = fmaf(wx, c011 - c010, c010);
-    float c10 = fmaf(wx, c101 - c100, c100);
-    float c11 = fmaf(wx, c111 - c110, c110);
-    float c0 = fmaf(wy, c01 - c00, c00);
-    float c1 = fmaf(wy, c11 - c10, c10);
-    return fmaf(wz, c1 - c0, c0);
+    const VoxT* p00 = vol + c.z0 * sz + c.y0 * sy;
+    const VoxT* p01 = vol + c.z0 * sz + c.y1 * sy;
+    const VoxT* p10 = vol + c.z1 * sz + c.y0 * sy;
+    const VoxT* p11 = vol + c.z1 * sz + c.y1 * sy;
+    float c000 = (float)__ldg(p00 + c.x0), c001 = (float)__ldg(p00 + c.x1);
+    float c010 = (float)__ldg(p01 + c.x0), c011 = (float)__ldg(p01 + c.x1);
+    float c100 = (float)__ldg(p10 + c.x0), c101 = (float)__ldg(p10 + c.x1);
+    float c110 = (float)__ldg(p11 + c.x0), c111 = (float)__ldg(p11 + c.x1);
+    float c00 = fmaf(c.wx, c001 - c000, c000);
+    float c01 = fmaf(c.wx, c011 - c010, c010);
+    float c10 = fmaf(c.wx, c101 - c100, c100);
+    float c11 = fmaf(c.wx, c111 - c110, c110);
+    float c0 = fmaf(c.wy, c01 - c00, c00);
+    float c1 = fmaf(c.wy, c11 - c10, c10);
+    return fmaf(c.wz, c1 - c0, c0);
 }
 
 // Transfer function position of a value: x in [0, M - 1], entry i = floor(x)

@@ -1,0 +1,86 @@
+// vi_grid.cu -- brick occupancy for exact empty-space skipping.
+//
+// The volume is cut into bricks of 8^3 voxels.  For each brick the value range
+// over its voxels plus a one-voxel apron on the high side (the voxels a
+// trilinear footprint whose lower corner lies in the brick can touch) is kept;
+// it changes only with the volume.  From it and the transfer function, a flag
+// says whether any value in that range can map to alpha > 0: the TF entries a
+// lookup of such a value can touch are a contiguous range, and a prefix count
+// of entries with alpha > 0 answers that in O(1).  A sample whose footprint
+// starts in an unflagged brick has alpha exactly 0 -- a trilinear value lies
+// within its corners' range, and a lerp of two zero entries is zero -- so the
+// sweep and the march skip its gather without changing any result.
+#include <cmath>
+
+#include "vi_device.cuh"
+
+namespace vi {
+
+namespace {
+
+template <typename VoxT>
+__global__ void brick_range_kernel(const VoxT* __restrict__ vol, int nx, int ny, int nz, int nbx,
+                                   int nby, int nbz, uint32_t* __restrict__ range) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbx * nby * nbz) return;
+    const int bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
+    const int x0 = bx << kBrickShift, y0 = by << kBrickShift, z0 = bz << kBrickShift;
+    const int x1 = min(x0 + (1 << kBrickShift), nx - 1);
+    const int y1 = min(y0 + (1 << kBrickShift), ny - 1);
+    const int z1 = min(z0 + (1 << kBrickShift), nz - 1);
+    uint32_t lo = 0xffffu, hi = 0u;
+    for (int z = z0; z <= z1; ++z)
+        for (int y = y0; y <= y1; ++y) {
+            const VoxT* row = vol + ((size_t)z * ny + y) * nx;
+            for (int x = x0; x <= x1; ++x) {
+                uint32_t v = row[x];
+                lo = min(lo, v);
+                hi = max(hi, v);
+            }
+        }
+    range[b] = (lo << 16) | hi;
+}
+
+__global__ void brick_flag_kernel(const uint32_t* __restrict__ range, int nbricks,
+                                  const int* __restrict__ lit_prefix, int M, double vmin,
+                                  double scale, uint8_t* __restrict__ flags) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbricks) return;
+    const double lo = (double)(range[b] >> 16), hi = (double)(range[b] & 0xffffu);
+    // Entries a lookup of a value in [lo, hi] can read, widened by one on each
+    // side to cover the binary32 rounding of the TF coordinate.
+    long e_lo = (long)floor((lo - vmin) * scale) - 1;
+    long e_hi = (long)floor((hi - vmin) * scale) + 2;
+    e_lo = e_lo < 0 ? 0 : (e_lo > M - 2 ? M - 2 : e_lo);
+    e_hi = e_hi < 1 ? 1 : (e_hi > M - 1 ? M - 1 : e_hi);
+    flags[b] = (lit_prefix[e_hi + 1] - lit_prefix[e_lo]) > 0 ? 1 : 0;
+}
+
+}  // namespace
+
+cudaError_t launch_brick_range(const VolumeView& v, int voxel_type, uint32_t* range,
+                               cudaStream_t s) {
+    const int nbx = (v.nx + (1 << kBrickShift) - 1) >> kBrickShift;
+    const int nby = (v.ny + (1 << kBrickShift) - 1) >> kBrickShift;
+    const int nbz = (v.nz + (1 << kBrickShift) - 1) >> kBrickShift;
+    const int n = nbx * nby * nbz;
+    const int threads = 128, blocks = (n + threads - 1) / threads;
+    if (voxel_type == 0)
+        brick_range_kernel<uint8_t><<<blocks, threads, 0, s>>>(
+            static_cast<const uint8_t*>(v.data), v.nx, v.ny, v.nz, nbx, nby, nbz, range);
+    else
+        brick_range_kernel<uint16_t><<<blocks, threads, 0, s>>>(
+            static_cast<const uint16_t*>(v.data), v.nx, v.ny, v.nz, nbx, nby, nbz, range);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_brick_flags(const uint32_t* range, int nbricks, const int* lit_prefix, int M,
+                               float vmin, float vmax, uint8_t* flags, cudaStream_t s) {
+    const double scale = (double)(M - 1) / ((double)vmax - (double)vmin);
+    const int threads = 256, blocks = (nbricks + threads - 1) / threads;
+    brick_flag_kernel<<<blocks, threads, 0, s>>>(range, nbricks, lit_prefix, M, (double)vmin,
+                                                 scale, flags);
+    return cudaGetLastError();
+}
+
+}  // namespace vi

@@ -37,8 +37,18 @@ struct VolumeView {
     float fnx, fny, fnz;  // (float)nx ...
 };
 
+// Bricks of 2^kBrickShift voxels per axis; flags[bz][by][bx] = 1 if a sample
+// whose trilinear footprint starts in the brick may have alpha > 0.
+constexpr int kBrickShift = 3;
+
+struct GridView {
+    const uint8_t* flags;
+    int nbx, nby;
+};
+
 struct SweepParams {
     VolumeView vol;
+    GridView grid;
     const float4* tf;  // M entries (alpha in .w)
     int M;
     float tf_vmin, tf_scale;  // x = (v - vmin) * scale, scale = (M - 1) / (vmax - vmin)
@@ -61,6 +71,7 @@ struct CameraFrame {
 
 struct MarchParams {
     VolumeView vol;
+    GridView grid;
     const float4* tf;
     int M;
     float tf_vmin, tf_scale;
@@ -89,5 +100,9 @@ cudaError_t launch_march(const MarchParams& p, int voxel_type, int format, int m
                          cudaStream_t s);
 cudaError_t launch_trace(const MarchParams& p, int voxel_type, int format, int mode, int x,
                          int y, int32_t* rec, int max_rec, int* n_rec, cudaStream_t s);
+cudaError_t launch_brick_range(const VolumeView& v, int voxel_type, uint32_t* range,
+                               cudaStream_t s);
+cudaError_t launch_brick_flags(const uint32_t* range, int nbricks, const int* lit_prefix, int M,
+                               float vmin, float vmax, uint8_t* flags, cudaStream_t s);
 
 }  // namespace vi

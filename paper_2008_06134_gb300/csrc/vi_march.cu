@@ -8,6 +8,11 @@
 // warp leaves its sample loop when a ballot shows every lane has terminated
 // (early ray termination or exit).
 //
+// Exact shortcuts: a sample whose footprint lies in a brick that cannot yield
+// alpha > 0 is counted and skipped before any gather; the TF's alpha is read
+// first, and the coefficient and the RGB only for samples with alpha > 0
+// (a transparent sample leaves C and A unchanged bit for bit).
+//
 // The same per-sample body runs in trace_kernel, which records every integer
 // decision of one ray for exact comparison with an independent implementation.
 #include "vi_device.cuh"
@@ -118,13 +123,18 @@ __device__ __forceinline__ int march_sample(const MarchParams& p, const float4* 
     const float S0 = __fmaf_rn(t, r.d[0], r.o[0]);
     const float S1 = __fmaf_rn(t, r.d[1], r.o[1]);
     const float S2 = __fmaf_rn(t, r.d[2], r.o[2]);
-    int cell[3];
-    const float val = trilinear<VoxT>(p.vol, S0, S1, S2, TRACE ? cell : nullptr);
+    const VoxelCoord vc = voxel_coord(p.vol, S0, S1, S2);
+    // A sample in a brick that cannot yield alpha > 0 composites nothing.
+    if (!TRACE && !brick_may_be_lit(p.grid, vc)) {
+        ++count;
+        return A > p.ert ? kStopped : kContinue;
+    }
+    const float val = trilinear_fetch<VoxT>(p.vol, vc);
     int e;
     float f;
     tf_coord(val, p.tf_vmin, p.tf_scale, p.M, &e, &f);
-    const float4 ta = s_tf[e], tb = s_tf[e + 1];
-    float alpha = fmaf(f, tb.w - ta.w, ta.w);
+    const float a0 = s_tf[e].w, a1 = s_tf[e + 1].w;
+    float alpha = fmaf(f, a1 - a0, a0);
     if (p.opacity_correction)
         alpha = 1.0f - exp2f(p.step_vox * log2f(fmaxf(1.0f - alpha, 0.0f)));
 
@@ -132,9 +142,9 @@ __device__ __forceinline__ int march_sample(const MarchParams& p, const float4* 
         for (int w = 0; w < kTraceWords; ++w) rec[w] = kTraceNone;
         rec[0] = i;
         rec[1] = __float_as_int(t);
-        rec[5] = cell[0];
-        rec[6] = cell[1];
-        rec[7] = cell[2];
+        rec[5] = vc.cx;
+        rec[6] = vc.cy;
+        rec[7] = vc.cz;
         rec[35] = MODE == 2 ? 6 : (MODE == 3 ? 8 : 0);
     }
 
@@ -186,13 +196,17 @@ __device__ __forceinline__ int march_sample(const MarchParams& p, const float4* 
     }
 
     // Eq. 7 and Eq. 3: emission = light factor * light colour * alpha * rgb.
-    const float lf = fmaf(1.0f - p.ambient, coef, p.ambient);
-    const float w = (1.0f - A) * lf * alpha;
-    C0 = fmaf(w * p.color[0], fmaf(f, tb.x - ta.x, ta.x), C0);
-    C1 = fmaf(w * p.color[1], fmaf(f, tb.y - ta.y, ta.y), C1);
-    C2 = fmaf(w * p.color[2], fmaf(f, tb.z - ta.z, ta.z), C2);
-    A = fmaf(1.0f - A, alpha, A);
+    // A sample with alpha = 0 leaves C and A unchanged, so it is skipped.
     ++count;
+    if (alpha > 0.0f) {
+        const float4 ta = s_tf[e], tb = s_tf[e + 1];
+        const float lf = fmaf(1.0f - p.ambient, coef, p.ambient);
+        const float w = (1.0f - A) * lf * alpha;
+        C0 = fmaf(w * p.color[0], fmaf(f, tb.x - ta.x, ta.x), C0);
+        C1 = fmaf(w * p.color[1], fmaf(f, tb.y - ta.y, ta.y), C1);
+        C2 = fmaf(w * p.color[2], fmaf(f, tb.z - ta.z, ta.z), C2);
+        A = fmaf(1.0f - A, alpha, A);
+    }
     return A > p.ert ? kStopped : kContinue;
 }
 

@@ -8,9 +8,11 @@
 // multi-slice-per-pass future work), with no framebuffer read-back.
 //
 // Memory: the volume is read through the read-only path (it fits in L2 for the
-// sizes this targets); each warp covers 32 consecutive texels of one row, so
-// every store of slice k is one 128-byte (FP32) or 64-byte (16-bit) line.  The
-// transfer function's alpha column is staged in shared memory.
+// sizes this targets).  A warp covers an 8 x 4 tile of texels, so its 32
+// sample points form a compact patch of the slice plane and its trilinear
+// footprints share sectors; each store of slice k writes four 32-byte row
+// segments (FP32).  A point in a brick that cannot yield alpha > 0 skips the
+// gather.  The transfer function's alpha column is staged in shared memory.
 #include "vi_device.cuh"
 
 namespace vi {
@@ -23,13 +25,16 @@ template <typename VoxT, typename Fmt>
 __global__ void __launch_bounds__(kSweepBX* kSweepBY)
     sweep_kernel(const SweepParams p) {
     extern __shared__ float s_alpha[];
-    const int tid = threadIdx.y * kSweepBX + threadIdx.x;
+    const int tid = threadIdx.x;
     for (int e = tid; e < p.M; e += kSweepBX * kSweepBY) s_alpha[e] = p.tf[e].w;
     __syncthreads();
 
+    // Block tile 32 x 8 texels; warp w covers columns 8 (w % 4) .. +7, rows
+    // 4 (w / 4) .. +3.
     const LightFrame& lt = p.lt;
-    const int i = blockIdx.x * kSweepBX + threadIdx.x;
-    const int j = blockIdx.y * kSweepBY + threadIdx.y;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int i = blockIdx.x * kSweepBX + (warp & 3) * 8 + (lane & 7);
+    const int j = blockIdx.y * kSweepBY + (warp >> 2) * 4 + (lane >> 3);
     if (i >= lt.R || j >= lt.R) return;
 
     // World position of texel (i, j) on the plane through the centre.
@@ -51,8 +56,10 @@ __global__ void __launch_bounds__(kSweepBX* kSweepBY)
         float P1 = __fmaf_rn(sk, lt.L[1], base1);
         float P2 = __fmaf_rn(sk, lt.L[2], base2);
         float alpha = 0.0f;
-        if (P0 >= 0.0f && P0 <= 1.0f && P1 >= 0.0f && P1 <= 1.0f && P2 >= 0.0f && P2 <= 1.0f) {
-            float val = trilinear<VoxT>(p.vol, P0, P1, P2);
+        VoxelCoord vc;
+        if (P0 >= 0.0f && P0 <= 1.0f && P1 >= 0.0f && P1 <= 1.0f && P2 >= 0.0f && P2 <= 1.0f &&
+            brick_may_be_lit(p.grid, vc = voxel_coord(p.vol, P0, P1, P2))) {
+            float val = trilinear_fetch<VoxT>(p.vol, vc);
             int e;
             float f;
             tf_coord(val, p.tf_vmin, p.tf_scale, p.M, &e, &f);
@@ -70,7 +77,7 @@ __global__ void __launch_bounds__(kSweepBX* kSweepBY)
 
 template <typename VoxT, typename Fmt>
 cudaError_t launch_typed(const SweepParams& p, cudaStream_t s) {
-    dim3 block(kSweepBX, kSweepBY);
+    dim3 block(kSweepBX * kSweepBY);
     dim3 grid((p.lt.R + kSweepBX - 1) / kSweepBX, (p.lt.R + kSweepBY - 1) / kSweepBY);
     size_t smem = (size_t)p.M * sizeof(float);
     sweep_kernel<VoxT, Fmt><<<grid, block, smem, s>>>(p);

@@ -180,3 +180,25 @@ def test_degenerate_cases_match_oracle(ctx, orc, case):
         sc.mode = 2
         sc.shell_radius_vox = 3.5
     check_against_oracle(ctx, orc, sc)
+
+
+def test_skip_flags_follow_tf_changes_and_clamped_values(ctx, orc):
+    """Empty-space skipping must never drop a sample that has alpha > 0: the TF
+    here is zero except at its two end entries, which only values clamped
+    below vmin / above vmax reach; then the TF changes without reloading the
+    volume."""
+    sc = small_scene(mode=1)
+    M = 64
+    tf = np.zeros((M, 4), np.float32)
+    tf[:, :3] = (0.9, 0.5, 0.2)
+    tf[0, 3] = 0.3
+    tf[-1, 3] = 0.05
+    sc.tf, sc.vmin, sc.vmax = tf, 60.0, 140.0   # blob values run 0..~220
+    check_against_oracle(ctx, orc, sc)
+    tf2 = np.zeros((M, 4), np.float32)
+    tf2[:, :3] = 1.0
+    tf2[30:34, 3] = 0.4                          # a narrow band in the middle
+    sc.tf = tf2
+    check_against_oracle(ctx, orc, sc)
+    sc.mode = 3
+    check_against_oracle(ctx, orc, sc)
