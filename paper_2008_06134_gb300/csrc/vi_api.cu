@@ -64,6 +64,8 @@ struct vi_ctx {
     size_t out_cap = 0;
     int32_t* trace = nullptr;
     size_t trace_cap = 0;
+    unsigned* counter = nullptr;  // tile counter of the persistent march kernel
+    size_t counter_cap = 0;
 };
 
 namespace {
@@ -395,6 +397,7 @@ int vi_destroy(vi_ctx* c) {
     release(c, reinterpret_cast<void**>(&c->brange), &c->brange_cap);
     release(c, reinterpret_cast<void**>(&c->tfcnt), &c->tfcnt_cap);
     release(c, reinterpret_cast<void**>(&c->bflags), &c->bflags_cap);
+    release(c, reinterpret_cast<void**>(&c->counter), &c->counter_cap);
     delete c;
     return VI_OK;
 }
@@ -556,6 +559,9 @@ int vi_render(vi_ctx* c, const vi_camera* cam, int W, int H, float step_vox, flo
     MarchParams p;
     rc = fill_march_params(c, cam, W, H, step_vox, &ro, &p);
     if (rc) return rc;
+    rc = ensure(c, reinterpret_cast<void**>(&c->counter), &c->counter_cap, 256);
+    if (rc) return rc;
+    p.tile_counter = c->counter;
     size_t bytes = (size_t)W * (size_t)H * sizeof(float4);
     if (out_on_device) {
         p.out = reinterpret_cast<float4*>(out);

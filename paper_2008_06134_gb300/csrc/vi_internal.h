@@ -90,6 +90,7 @@ struct MarchParams {
     float4* out;            // [H][W]
     int32_t* counts;        // optional [H][W]: samples composited
     int32_t* lit;           // optional [H][W]: samples with alpha > 0
+    unsigned* tile_counter; // work counter of the persistent march (zeroed per launch)
 };
 
 enum { kTraceWords = 40, kTraceNone = 0x7fffffff };

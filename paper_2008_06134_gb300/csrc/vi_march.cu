@@ -2,7 +2,8 @@
 //
 // One thread per pixel; a warp covers an 8 x 4 pixel tile so its rays stay
 // close in the volume and in the attenuation stack.  Per sample: trilinear
-// reconstruction, RGBA transfer function (staged in shared memory), the light
+// reconstruction, RGBA transfer function (alpha staged in shared memory, RGB
+// read through L1 only for samples with alpha > 0), the light
 // coefficient from the stack (shadow: 1 bilinear lookup; shell: 6; cone: 8),
 // emission weighted by it (Eq. 7) and front-to-back compositing (Eq. 3).  The
 // warp leaves its sample loop when a ballot shows every lane has terminated
@@ -21,7 +22,7 @@ namespace vi {
 
 namespace {
 
-constexpr int kMarchThreads = 256;  // 8 warps: a 16 x 16 pixel tile
+constexpr int kMarchThreads = 256;  // 8 warps per block
 
 struct Ray {
     float o[3], d[3];
@@ -115,7 +116,7 @@ enum { kEnded = 0, kContinue = 1, kStopped = 2 };
 // One sample i of a ray.  Returns kEnded if t_i is past the exit (nothing
 // done), kContinue after compositing, kStopped if early ray termination fired.
 template <typename VoxT, typename Fmt, int MODE, bool TRACE>
-__device__ __forceinline__ int march_sample(const MarchParams& p, const float4* s_tf,
+__device__ __forceinline__ int march_sample(const MarchParams& p, const float* s_alpha,
                                             const Ray& r, int i, float& C0, float& C1, float& C2,
                                             float& A, int& count, int& lit, int32_t* rec) {
     const float t = __fmaf_rn((float)i, p.cam.dt, r.t0);
@@ -133,7 +134,7 @@ __device__ __forceinline__ int march_sample(const MarchParams& p, const float4* 
     int e;
     float f;
     tf_coord(val, p.tf_vmin, p.tf_scale, p.M, &e, &f);
-    const float a0 = s_tf[e].w, a1 = s_tf[e + 1].w;
+    const float a0 = s_alpha[e], a1 = s_alpha[e + 1];
     float alpha = fmaf(f, a1 - a0, a0);
     if (p.opacity_correction)
         alpha = 1.0f - exp2f(p.step_vox * log2f(fmaxf(1.0f - alpha, 0.0f)));
@@ -199,7 +200,7 @@ __device__ __forceinline__ int march_sample(const MarchParams& p, const float4* 
     // A sample with alpha = 0 leaves C and A unchanged, so it is skipped.
     ++count;
     if (alpha > 0.0f) {
-        const float4 ta = s_tf[e], tb = s_tf[e + 1];
+        const float4 ta = __ldg(p.tf + e), tb = __ldg(p.tf + e + 1);
         const float lf = fmaf(1.0f - p.ambient, coef, p.ambient);
         const float w = (1.0f - A) * lf * alpha;
         C0 = fmaf(w * p.color[0], fmaf(f, tb.x - ta.x, ta.x), C0);
@@ -210,48 +211,59 @@ __device__ __forceinline__ int march_sample(const MarchParams& p, const float4* 
     return A > p.ert ? kStopped : kContinue;
 }
 
-__device__ __forceinline__ void load_tf(const MarchParams& p, float4* s_tf) {
-    for (int e = threadIdx.x; e < p.M; e += blockDim.x) s_tf[e] = p.tf[e];
+__device__ __forceinline__ void load_alpha(const MarchParams& p, float* s_alpha) {
+    for (int e = threadIdx.x; e < p.M; e += blockDim.x) s_alpha[e] = p.tf[e].w;
     __syncthreads();
 }
 
+// Persistent warps: each warp takes 8 x 4 pixel tiles, in raster order, from a
+// global counter until none are left, so warps whose rays end early pick up
+// more work instead of idling while others march through dense regions.
 template <typename VoxT, typename Fmt, int MODE>
 __global__ void __launch_bounds__(kMarchThreads) march_kernel(const MarchParams p) {
-    extern __shared__ float4 s_tf[];
-    load_tf(p, s_tf);
+    extern __shared__ float s_alpha[];
+    load_alpha(p, s_alpha);
 
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int x = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
-    const int y = blockIdx.y * 16 + (warp >> 1) * 4 + (lane >> 3);
-    const bool valid = x < p.cam.W && y < p.cam.H;
-    Ray r;
-    r.hit = false;
-    if (valid) ray_setup<MODE>(p, x, y, r);
+    const int lane = threadIdx.x & 31;
+    const unsigned tiles_x = (unsigned)(p.cam.W + 7) >> 3;
+    const unsigned ntiles = tiles_x * ((unsigned)(p.cam.H + 3) >> 2);
+    for (;;) {
+        unsigned tile = 0;
+        if (lane == 0) tile = atomicAdd(p.tile_counter, 1u);
+        tile = __shfl_sync(0xffffffffu, tile, 0);
+        if (tile >= ntiles) break;
+        const int x = (int)(tile % tiles_x) * 8 + (lane & 7);
+        const int y = (int)(tile / tiles_x) * 4 + (lane >> 3);
+        const bool valid = x < p.cam.W && y < p.cam.H;
+        Ray r;
+        r.hit = false;
+        if (valid) ray_setup<MODE>(p, x, y, r);
 
-    float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, A = 0.0f;
-    int count = 0, lit = 0;
-    bool active = valid && r.hit;
-    // All 32 lanes stay in the loop; it ends when the ballot finds none active.
-    for (int i = 0; __any_sync(0xffffffffu, active); ++i) {
-        if (active)
-            active = march_sample<VoxT, Fmt, MODE, false>(p, s_tf, r, i, C0, C1, C2, A, count,
-                                                          lit, nullptr) == kContinue;
-    }
-    if (valid) {
-        const size_t idx = (size_t)y * p.cam.W + x;
-        const float rem = 1.0f - A;
-        p.out[idx] = make_float4(fmaf(rem, p.bg[0], C0), fmaf(rem, p.bg[1], C1),
-                                 fmaf(rem, p.bg[2], C2), fmaf(rem, p.bg[3], A));
-        if (p.counts) p.counts[idx] = count;
-        if (p.lit) p.lit[idx] = lit;
+        float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, A = 0.0f;
+        int count = 0, lit = 0;
+        bool active = valid && r.hit;
+        // All 32 lanes stay in the loop; it ends when the ballot finds none active.
+        for (int i = 0; __any_sync(0xffffffffu, active); ++i) {
+            if (active)
+                active = march_sample<VoxT, Fmt, MODE, false>(p, s_alpha, r, i, C0, C1, C2, A,
+                                                              count, lit, nullptr) == kContinue;
+        }
+        if (valid) {
+            const size_t idx = (size_t)y * p.cam.W + x;
+            const float rem = 1.0f - A;
+            p.out[idx] = make_float4(fmaf(rem, p.bg[0], C0), fmaf(rem, p.bg[1], C1),
+                                     fmaf(rem, p.bg[2], C2), fmaf(rem, p.bg[3], A));
+            if (p.counts) p.counts[idx] = count;
+            if (p.lit) p.lit[idx] = lit;
+        }
     }
 }
 
 template <typename VoxT, typename Fmt, int MODE>
 __global__ void trace_kernel(const MarchParams p, int x, int y, int32_t* rec, int max_rec,
                              int* n_rec) {
-    extern __shared__ float4 s_tf[];
-    load_tf(p, s_tf);
+    extern __shared__ float s_alpha[];
+    load_alpha(p, s_alpha);
     if (threadIdx.x != 0) return;
     Ray r;
     ray_setup<MODE>(p, x, y, r);
@@ -261,8 +273,8 @@ __global__ void trace_kernel(const MarchParams p, int x, int y, int32_t* rec, in
     if (r.hit) {
         for (int i = 0; nrec < max_rec; ++i) {
             int32_t* out = rec + (size_t)nrec * kTraceWords;
-            int st = march_sample<VoxT, Fmt, MODE, true>(p, s_tf, r, i, C0, C1, C2, A, count, lit,
-                                                         out);
+            int st = march_sample<VoxT, Fmt, MODE, true>(p, s_alpha, r, i, C0, C1, C2, A, count,
+                                                         lit, out);
             if (st == kEnded) break;
             ++nrec;
             if (st == kStopped) break;
@@ -273,28 +285,29 @@ __global__ void trace_kernel(const MarchParams p, int x, int y, int32_t* rec, in
 
 template <typename VoxT, typename Fmt, int MODE>
 cudaError_t launch_march_typed(const MarchParams& p, cudaStream_t s) {
-    const size_t smem = (size_t)p.M * sizeof(float4);
+    const size_t smem = (size_t)p.M * sizeof(float);
     auto kern = march_kernel<VoxT, Fmt, MODE>;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    dim3 grid((p.cam.W + 15) / 16, (p.cam.H + 15) / 16);
-    kern<<<grid, kMarchThreads, smem, s>>>(p);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMarchThreads, smem);
+    if (e != cudaSuccess) return e;
+    // Enough warps to fill every SM once, never more than there are tiles.
+    const long long tiles = (long long)((p.cam.W + 7) / 8) * ((p.cam.H + 3) / 4);
+    long long blocks = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    blocks = blocks < (tiles + 7) / 8 ? blocks : (tiles + 7) / 8;
+    e = cudaMemsetAsync(p.tile_counter, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)blocks, kMarchThreads, smem, s>>>(p);
     return cudaGetLastError();
 }
 
 template <typename VoxT, typename Fmt, int MODE>
 cudaError_t launch_trace_typed(const MarchParams& p, int x, int y, int32_t* rec, int max_rec,
                                int* n_rec, cudaStream_t s) {
-    const size_t smem = (size_t)p.M * sizeof(float4);
+    const size_t smem = (size_t)p.M * sizeof(float);
     auto kern = trace_kernel<VoxT, Fmt, MODE>;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-    }
     kern<<<1, 32, smem, s>>>(p, x, y, rec, max_rec, n_rec);
     return cudaGetLastError();
 }
