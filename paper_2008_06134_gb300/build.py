@@ -30,6 +30,8 @@ def nvcc() -> str:
 def _flags(verbose: bool):
     f = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-ffp-contract=off,-O2",
                 "-I", os.path.join(HERE, "..", "include")]
+    # Optional tuning defines, e.g. VI_NVCC_DEFINES="-DVI_BRICK_SHIFT=2".
+    f += os.environ.get("VI_NVCC_DEFINES", "").split()
     if verbose:
         f += ["-Xptxas", "-v"]
     return f

@@ -27,7 +27,9 @@ struct vi_ctx {
     size_t budget = 0;  // 0 = unlimited
     size_t used = 0;
 
-    void* vol = nullptr;
+    void* raw = nullptr;  // the volume as loaded: [nz][ny][nx]
+    size_t raw_cap = 0;
+    void* vol = nullptr;  // footprint octets built from it (8 voxels per element)
     size_t vol_cap = 0;
     int vtype = -1, nx = 0, ny = 0, nz = 0;
 
@@ -389,6 +391,7 @@ int vi_destroy(vi_ctx* c) {
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     cudaGetLastError();
+    release(c, &c->raw, &c->raw_cap);
     release(c, &c->vol, &c->vol_cap);
     release(c, reinterpret_cast<void**>(&c->tf), &c->tf_cap);
     release(c, &c->stack, &c->stack_cap);
@@ -415,14 +418,20 @@ int vi_load_volume(vi_ctx* c, const void* data, int dtype, int nx, int ny, int n
     if (!data || (dtype != VI_U8 && dtype != VI_U16)) return VI_EINVAL;
     if (nx < 1 || ny < 1 || nz < 1 || nx > 65536 || ny > 65536 || nz > 65536) return VI_EINVAL;
     size_t bytes = (size_t)nx * (size_t)ny * (size_t)nz * voxel_bytes(dtype);
-    rc = ensure(c, &c->vol, &c->vol_cap, bytes);
+    rc = ensure(c, &c->raw, &c->raw_cap, bytes);
+    if (rc) return rc;
+    rc = ensure(c, &c->vol, &c->vol_cap, 8 * bytes);
     if (rc) return rc;
     c->flags_ok = false;
-    cudaError_t e = cudaMemcpyAsync(c->vol, data, bytes,
+    c->vtype = -1;
+    cudaError_t e = cudaMemcpyAsync(c->raw, data, bytes,
                                     data_on_device ? cudaMemcpyDeviceToDevice
                                                    : cudaMemcpyHostToDevice,
                                     c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e);
+    e = vi::launch_build_octets(c->raw, nx, ny, nz, dtype, c->vol, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    ++c->launches;
     c->vtype = dtype;
     c->nx = nx;
     c->ny = ny;
@@ -435,7 +444,7 @@ int vi_load_volume(vi_ctx* c, const void* data, int dtype, int nx, int ny, int n
     rc = ensure(c, reinterpret_cast<void**>(&c->brange), &c->brange_cap,
                 (size_t)nbricks(c) * sizeof(uint32_t));
     if (rc) return rc;
-    e = vi::launch_brick_range(volume_view(c), dtype, c->brange, c->stream);
+    e = vi::launch_brick_range(c->raw, nx, ny, nz, dtype, c->brange, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e);
     ++c->launches;
     return refresh_flags(c);

@@ -99,25 +99,55 @@ __device__ __forceinline__ bool brick_may_be_lit(const GridView& g, const VoxelC
     return __ldg(g.flags + b) != 0;
 }
 
+// Integer to float without the conversion pipe: v < 2^23 placed in the mantissa
+// of 2^23, then 2^23 subtracted (exact).
+__device__ __forceinline__ float u2f(unsigned v) {
+    return __uint_as_float(0x4b000000u | v) - 8388608.0f;
+}
+
+template <typename VoxT>
+struct Octet;
+template <>
+struct Octet<uint16_t> {
+    using V = uint4;
+    static __device__ __forceinline__ void unpack(const V q, float c[8]) {
+        c[0] = u2f(q.x & 0xffffu); c[1] = u2f(q.x >> 16);
+        c[2] = u2f(q.y & 0xffffu); c[3] = u2f(q.y >> 16);
+        c[4] = u2f(q.z & 0xffffu); c[5] = u2f(q.z >> 16);
+        c[6] = u2f(q.w & 0xffffu); c[7] = u2f(q.w >> 16);
+    }
+};
+template <>
+struct Octet<uint8_t> {
+    using V = uint2;
+    static __device__ __forceinline__ void unpack(const V q, float c[8]) {
+        c[0] = u2f(q.x & 0xffu); c[1] = u2f((q.x >> 8) & 0xffu);
+        c[2] = u2f((q.x >> 16) & 0xffu); c[3] = u2f(q.x >> 24);
+        c[4] = u2f(q.y & 0xffu); c[5] = u2f((q.y >> 8) & 0xffu);
+        c[6] = u2f((q.y >> 16) & 0xffu); c[7] = u2f(q.y >> 24);
+    }
+};
+
+// Trilinear from the octet at the footprint's lower corner.  The octet's upper
+// voxels are clamped copies at the high edges; at the low edges (cell -1) the
+// footprint collapses onto voxel 0, so the weight of the upper corner is 0.
 template <typename VoxT>
 __device__ __forceinline__ float trilinear_fetch(const VolumeView& v, const VoxelCoord& c) {
-    const VoxT* __restrict__ vol = static_cast<const VoxT*>(v.data);
-    const size_t sy = (size_t)v.nx, sz = (size_t)v.nx * (size_t)v.ny;
-    const VoxT* p00 = vol + c.z0 * sz + c.y0 * sy;
-    const VoxT* p01 = vol + c.z0 * sz + c.y1 * sy;
-    const VoxT* p10 = vol + c.z1 * sz + c.y0 * sy;
-    const VoxT* p11 = vol + c.z1 * sz + c.y1 * sy;
-    float c000 = (float)__ldg(p00 + c.x0), c001 = (float)__ldg(p00 + c.x1);
-    float c010 = (float)__ldg(p01 + c.x0), c011 = (float)__ldg(p01 + c.x1);
-    float c100 = (float)__ldg(p10 + c.x0), c101 = (float)__ldg(p10 + c.x1);
-    float c110 = (float)__ldg(p11 + c.x0), c111 = (float)__ldg(p11 + c.x1);
-    float c00 = fmaf(c.wx, c001 - c000, c000);
-    float c01 = fmaf(c.wx, c011 - c010, c010);
-    float c10 = fmaf(c.wx, c101 - c100, c100);
-    float c11 = fmaf(c.wx, c111 - c110, c110);
-    float c0 = fmaf(c.wy, c01 - c00, c00);
-    float c1 = fmaf(c.wy, c11 - c10, c10);
-    return fmaf(c.wz, c1 - c0, c0);
+    using O = Octet<VoxT>;
+    const typename O::V* oct = static_cast<const typename O::V*>(v.data);
+    const size_t idx = ((size_t)c.z0 * (size_t)v.ny + (size_t)c.y0) * (size_t)v.nx + (size_t)c.x0;
+    float q[8];
+    O::unpack(__ldg(oct + idx), q);
+    const float wx = c.cx < 0 ? 0.0f : c.wx;
+    const float wy = c.cy < 0 ? 0.0f : c.wy;
+    const float wz = c.cz < 0 ? 0.0f : c.wz;
+    float c00 = fmaf(wx, q[1] - q[0], q[0]);
+    float c01 = fmaf(wx, q[3] - q[2], q[2]);
+    float c10 = fmaf(wx, q[5] - q[4], q[4]);
+    float c11 = fmaf(wx, q[7] - q[6], q[6]);
+    float c0 = fmaf(wy, c01 - c00, c00);
+    float c1 = fmaf(wy, c11 - c10, c10);
+    return fmaf(wz, c1 - c0, c0);
 }
 
 // Transfer function position of a value: x in [0, M - 1], entry i = floor(x)
@@ -134,31 +164,46 @@ __device__ __forceinline__ void tf_coord(float v, float vmin, float scale, int M
 // ---------------------------------------------------------------------------
 // Stack lookup (Eq. 9 slice, Eq. 10 UV): nearest slice k = clamp(floor(lambda
 // + 1/2), 0, n - 1), bilinear over texel centres at integer (tu, tv) with
-// clamp to edge.
+// clamp to edge.  floor-to-int is one cvt.rmi; offsets inside a slice are
+// 32-bit (R <= 65536, so R^2 - 1 fits an unsigned int).
+
+__device__ __forceinline__ int slice_index(float lam, int n) {
+    return clampi(__float2int_rd(__fadd_rn(lam, 0.5f)), 0, n - 1);
+}
+
+template <typename Fmt>
+__device__ __forceinline__ float bilinear(const typename Fmt::T* __restrict__ S, int R, float tu,
+                                          float tv, int* rec = nullptr) {
+    const int iu = __float2int_rd(tu), iv = __float2int_rd(tv);
+    if (rec) {
+        rec[1] = clampi(iu, -1, R);
+        rec[2] = clampi(iv, -1, R);
+    }
+    const float wu = tu - (float)iu, wv = tv - (float)iv;
+    const unsigned i0 = (unsigned)clampi(iu, 0, R - 1), i1 = (unsigned)clampi(iu + 1, 0, R - 1);
+    const unsigned j0 = (unsigned)clampi(iv, 0, R - 1), j1 = (unsigned)clampi(iv + 1, 0, R - 1);
+    const typename Fmt::T* r0 = S + j0 * (unsigned)R;
+    const typename Fmt::T* r1 = S + j1 * (unsigned)R;
+    const float b00 = Fmt::load(r0 + i0), b01 = Fmt::load(r0 + i1);
+    const float b10 = Fmt::load(r1 + i0), b11 = Fmt::load(r1 + i1);
+    const float top = fmaf(wu, b01 - b00, b00);
+    const float bot = fmaf(wu, b11 - b10, b10);
+    return fmaf(wv, bot - top, top);
+}
+
+template <typename Fmt>
+__device__ __forceinline__ const typename Fmt::T* slice_ptr(const typename Fmt::T* B, int k,
+                                                            int R) {
+    return B + (size_t)k * ((size_t)R * (size_t)R);
+}
 
 template <typename Fmt>
 __device__ __forceinline__ float stack_lookup(const typename Fmt::T* __restrict__ B, int n, int R,
                                               float lam, float tu, float tv,
                                               int* rec = nullptr) {
-    int k = floor_clamp(__fadd_rn(lam, 0.5f), 0, n - 1);
-    float fu = floorf(tu), fv = floorf(tv);
-    int iu = floor_clamp(tu, -1, R), iv = floor_clamp(tv, -1, R);
-    if (rec) {
-        rec[0] = k;
-        rec[1] = iu;
-        rec[2] = iv;
-    }
-    float wu = tu - fu, wv = tv - fv;
-    int i0 = clampi(iu, 0, R - 1), i1 = clampi(iu + 1, 0, R - 1);
-    int j0 = clampi(iv, 0, R - 1), j1 = clampi(iv + 1, 0, R - 1);
-    const typename Fmt::T* S = B + (size_t)k * (size_t)R * (size_t)R;
-    const typename Fmt::T* r0 = S + (size_t)j0 * R;
-    const typename Fmt::T* r1 = S + (size_t)j1 * R;
-    float b00 = Fmt::load(r0 + i0), b01 = Fmt::load(r0 + i1);
-    float b10 = Fmt::load(r1 + i0), b11 = Fmt::load(r1 + i1);
-    float top = fmaf(wu, b01 - b00, b00);
-    float bot = fmaf(wu, b11 - b10, b10);
-    return fmaf(wv, bot - top, top);
+    const int k = slice_index(lam, n);
+    if (rec) rec[0] = k;
+    return bilinear<Fmt>(slice_ptr<Fmt>(B, k, R), R, tu, tv, rec);
 }
 
 }  // namespace vi

@@ -58,19 +58,60 @@ __global__ void brick_flag_kernel(const uint32_t* __restrict__ range, int nbrick
 
 }  // namespace
 
-cudaError_t launch_brick_range(const VolumeView& v, int voxel_type, uint32_t* range,
-                               cudaStream_t s) {
-    const int nbx = (v.nx + (1 << kBrickShift) - 1) >> kBrickShift;
-    const int nby = (v.ny + (1 << kBrickShift) - 1) >> kBrickShift;
-    const int nbz = (v.nz + (1 << kBrickShift) - 1) >> kBrickShift;
+cudaError_t launch_brick_range(const void* raw, int nx, int ny, int nz, int voxel_type,
+                               uint32_t* range, cudaStream_t s) {
+    const int nbx = (nx + (1 << kBrickShift) - 1) >> kBrickShift;
+    const int nby = (ny + (1 << kBrickShift) - 1) >> kBrickShift;
+    const int nbz = (nz + (1 << kBrickShift) - 1) >> kBrickShift;
     const int n = nbx * nby * nbz;
     const int threads = 128, blocks = (n + threads - 1) / threads;
     if (voxel_type == 0)
         brick_range_kernel<uint8_t><<<blocks, threads, 0, s>>>(
-            static_cast<const uint8_t*>(v.data), v.nx, v.ny, v.nz, nbx, nby, nbz, range);
+            static_cast<const uint8_t*>(raw), nx, ny, nz, nbx, nby, nbz, range);
     else
         brick_range_kernel<uint16_t><<<blocks, threads, 0, s>>>(
-            static_cast<const uint16_t*>(v.data), v.nx, v.ny, v.nz, nbx, nby, nbz, range);
+            static_cast<const uint16_t*>(raw), nx, ny, nz, nbx, nby, nbz, range);
+    return cudaGetLastError();
+}
+
+namespace {
+
+// One thread per voxel: gather its 2 x 2 x 2 footprint (clamped) into an octet.
+template <typename VoxT>
+__global__ void build_octets_kernel(const VoxT* __restrict__ raw, int nx, int ny, int nz,
+                                    typename Octet<VoxT>::V* __restrict__ oct) {
+    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t total = (size_t)nx * ny * nz;
+    if (id >= total) return;
+    const int x = (int)(id % nx), y = (int)((id / nx) % ny), z = (int)(id / ((size_t)nx * ny));
+    const int x1 = min(x + 1, nx - 1), y1 = min(y + 1, ny - 1), z1 = min(z + 1, nz - 1);
+    auto at = [&](int xx, int yy, int zz) -> unsigned {
+        return raw[((size_t)zz * ny + yy) * nx + xx];
+    };
+    const unsigned c000 = at(x, y, z), c001 = at(x1, y, z), c010 = at(x, y1, z), c011 = at(x1, y1, z);
+    const unsigned c100 = at(x, y, z1), c101 = at(x1, y, z1), c110 = at(x, y1, z1), c111 = at(x1, y1, z1);
+    if constexpr (sizeof(VoxT) == 2) {
+        oct[id] = make_uint4(c000 | (c001 << 16), c010 | (c011 << 16), c100 | (c101 << 16),
+                             c110 | (c111 << 16));
+    } else {
+        oct[id] = make_uint2(c000 | (c001 << 8) | (c010 << 16) | (c011 << 24),
+                             c100 | (c101 << 8) | (c110 << 16) | (c111 << 24));
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_build_octets(const void* raw, int nx, int ny, int nz, int voxel_type,
+                                void* octets, cudaStream_t s) {
+    const size_t total = (size_t)nx * ny * nz;
+    const unsigned threads = 256;
+    const size_t blocks = (total + threads - 1) / threads;
+    if (voxel_type == 0)
+        build_octets_kernel<uint8_t><<<(unsigned)blocks, threads, 0, s>>>(
+            static_cast<const uint8_t*>(raw), nx, ny, nz, static_cast<uint2*>(octets));
+    else
+        build_octets_kernel<uint16_t><<<(unsigned)blocks, threads, 0, s>>>(
+            static_cast<const uint16_t*>(raw), nx, ny, nz, static_cast<uint4*>(octets));
     return cudaGetLastError();
 }
 

@@ -31,15 +31,23 @@ struct LightFrame {
     int n, R;
 };
 
+// The volume as footprint octets: element (x, y, z) of [nz][ny][nx] holds the
+// eight voxels v(x + a, y + b, z + c), a, b, c in {0, 1} (indices clamped to
+// the volume), in the order c000 c001 c010 c011 c100 c101 c110 c111 (c{z}{y}{x});
+// 16 bytes for uint16 voxels, 8 for uint8.  One aligned vector load brings a
+// whole trilinear footprint.
 struct VolumeView {
-    const void* data;  // [nz][ny][nx], uint8 or uint16
+    const void* data;  // octets
     int nx, ny, nz;
     float fnx, fny, fnz;  // (float)nx ...
 };
 
 // Bricks of 2^kBrickShift voxels per axis; flags[bz][by][bx] = 1 if a sample
 // whose trilinear footprint starts in the brick may have alpha > 0.
-constexpr int kBrickShift = 3;
+#ifndef VI_BRICK_SHIFT
+#define VI_BRICK_SHIFT 3
+#endif
+constexpr int kBrickShift = VI_BRICK_SHIFT;
 
 struct GridView {
     const uint8_t* flags;
@@ -101,8 +109,10 @@ cudaError_t launch_march(const MarchParams& p, int voxel_type, int format, int m
                          cudaStream_t s);
 cudaError_t launch_trace(const MarchParams& p, int voxel_type, int format, int mode, int x,
                          int y, int32_t* rec, int max_rec, int* n_rec, cudaStream_t s);
-cudaError_t launch_brick_range(const VolumeView& v, int voxel_type, uint32_t* range,
-                               cudaStream_t s);
+cudaError_t launch_brick_range(const void* raw, int nx, int ny, int nz, int voxel_type,
+                               uint32_t* range, cudaStream_t s);
+cudaError_t launch_build_octets(const void* raw, int nx, int ny, int nz, int voxel_type,
+                                void* octets, cudaStream_t s);
 cudaError_t launch_brick_flags(const uint32_t* range, int nbricks, const int* lit_prefix, int M,
                                float vmin, float vmax, uint8_t* flags, cudaStream_t s);
 

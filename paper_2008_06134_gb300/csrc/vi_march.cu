@@ -179,17 +179,18 @@ __device__ __forceinline__ int march_sample(const MarchParams& p, const float* s
             float sum = 0.0f;
 #pragma unroll
             for (int ring = 0; ring < 2; ++ring) {
-                const float q0 = __fadd_rn(l0, -(float)(ring + 1));
+                // The ring's four points share lambda + offset, hence one slice.
+                const int k = slice_index(__fadd_rn(l0, -(float)(ring + 1)), n);
+                const typename Fmt::T* S = slice_ptr<Fmt>(B, k, R);
                 const float bu = r.nbu[ring], bv = r.nbv[ring];
                 // B_proj turned by m pi/2 about L: (bu, bv), (-bv, bu), (-bu, -bv), (bv, -bu).
                 const float du[4] = {bu, -bv, -bu, bv};
                 const float dv[4] = {bv, bu, -bv, -bu};
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
-                    float q1 = __fadd_rn(l1, du[m]);
-                    float q2 = __fadd_rn(l2, dv[m]);
-                    sum += stack_lookup<Fmt>(B, n, R, q0, q1, q2,
-                                             TRACE ? rec + 11 + 3 * (ring * 4 + m) : nullptr);
+                    int* rr = TRACE ? rec + 11 + 3 * (ring * 4 + m) : nullptr;
+                    if (TRACE) rr[0] = k;
+                    sum += bilinear<Fmt>(S, R, __fadd_rn(l1, du[m]), __fadd_rn(l2, dv[m]), rr);
                 }
             }
             coef = sum * 0.125f;

@@ -21,6 +21,17 @@ namespace {
 
 constexpr int kSweepBX = 32, kSweepBY = 8;
 
+// Whether the point of slice k on the column through (base) lies in [0,1]^3,
+// evaluated exactly as the sweep evaluates it.
+__device__ __forceinline__ bool texel_inside(const LightFrame& lt, int k, float base0,
+                                             float base1, float base2) {
+    const float sk = __fsub_rn(__fmaf_rn((float)k, lt.dL, lt.min), lt.Lc);
+    const float P0 = __fmaf_rn(sk, lt.L[0], base0);
+    const float P1 = __fmaf_rn(sk, lt.L[1], base1);
+    const float P2 = __fmaf_rn(sk, lt.L[2], base2);
+    return P0 >= 0.0f && P0 <= 1.0f && P1 >= 0.0f && P1 <= 1.0f && P2 >= 0.0f && P2 <= 1.0f;
+}
+
 template <typename VoxT, typename Fmt>
 __global__ void __launch_bounds__(kSweepBX* kSweepBY)
     sweep_kernel(const SweepParams p) {
@@ -48,17 +59,66 @@ __global__ void __launch_bounds__(kSweepBX* kSweepBY)
 
     typename Fmt::T* out = static_cast<typename Fmt::T*>(p.stack) + (size_t)j * lt.R + i;
     const size_t slice = (size_t)lt.R * (size_t)lt.R;
+
+    // Slices whose point lies in the cube form one interval [kin, kout]: every
+    // coordinate of P_k is monotone in k even after rounding (each step of the
+    // index path is a monotone rounding).  Estimate it in FP32 (FP64 is slow on
+    // this part), then settle it with the exact binary32 test.
+    int kin, kout;
+    {
+        float slo = -3.0e38f, shi = 3.0e38f;
+        const float b[3] = {base0, base1, base2};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float La = lt.L[a];
+            if (La != 0.0f) {
+                const float inv = 1.0f / La;
+                const float s0 = -b[a] * inv, s1 = (1.0f - b[a]) * inv;
+                slo = fmaxf(slo, fminf(s0, s1));
+                shi = fminf(shi, fmaxf(s0, s1));
+            } else if (b[a] < 0.0f || b[a] > 1.0f) {
+                slo = 3.0e38f;
+            }
+        }
+        const float inv_dL = 1.0f / lt.dL;
+        const float k0 = (lt.Lc - lt.min) * inv_dL;
+        const float klo = fmaf(slo, inv_dL, k0), khi = fmaf(shi, inv_dL, k0);
+        kin = (int)fminf(fmaxf(ceilf(klo), 0.0f), (float)lt.n);
+        kout = (int)fminf(fmaxf(floorf(khi), -1.0f), (float)(lt.n - 1));
+        if (kin > kout) {
+            // The estimate says the column misses the cube; a grazing column
+            // may still touch it within a slice or two of its closest approach.
+            const int kc = (int)fminf(fmaxf(floorf(0.5f * (klo + khi)), 0.0f), (float)(lt.n - 1));
+            kin = lt.n;
+            kout = -1;
+            for (int k = max(kc - 2, 0); k <= min(kc + 2, lt.n - 1); ++k)
+                if (texel_inside(lt, k, base0, base1, base2)) {
+                    kin = min(kin, k);
+                    kout = max(kout, k);
+                }
+        }
+        if (kin <= kout) {
+            while (kin > 0 && texel_inside(lt, kin - 1, base0, base1, base2)) --kin;
+            while (kin <= kout && !texel_inside(lt, kin, base0, base1, base2)) ++kin;
+            while (kout < lt.n - 1 && texel_inside(lt, kout + 1, base0, base1, base2)) ++kout;
+            while (kout >= kin && !texel_inside(lt, kout, base0, base1, base2)) --kout;
+        }
+    }
+
+    // Before the cube: full light.
+    const typename Fmt::T one = Fmt::pack(1.0f);
+    int k = 0;
+    for (; k < min(kin, lt.n); ++k) out[(size_t)k * slice] = one;
     float T = 1.0f;
-    for (int k = 0; k < lt.n; ++k) {
+    for (; k <= kout; ++k) {
         float dk = __fmaf_rn((float)k, lt.dL, lt.min);
         float sk = __fsub_rn(dk, lt.Lc);
         float P0 = __fmaf_rn(sk, lt.L[0], base0);
         float P1 = __fmaf_rn(sk, lt.L[1], base1);
         float P2 = __fmaf_rn(sk, lt.L[2], base2);
         float alpha = 0.0f;
-        VoxelCoord vc;
-        if (P0 >= 0.0f && P0 <= 1.0f && P1 >= 0.0f && P1 <= 1.0f && P2 >= 0.0f && P2 <= 1.0f &&
-            brick_may_be_lit(p.grid, vc = voxel_coord(p.vol, P0, P1, P2))) {
+        const VoxelCoord vc = voxel_coord(p.vol, P0, P1, P2);
+        if (brick_may_be_lit(p.grid, vc)) {
             float val = trilinear_fetch<VoxT>(p.vol, vc);
             int e;
             float f;
@@ -73,6 +133,9 @@ __global__ void __launch_bounds__(kSweepBX* kSweepBY)
         out[(size_t)k * slice] = Fmt::pack(stored);
         T *= (1.0f - alpha);
     }
+    // Past the cube: the light that left it.
+    const typename Fmt::T last = Fmt::pack(T);
+    for (; k < lt.n; ++k) out[(size_t)k * slice] = last;
 }
 
 template <typename VoxT, typename Fmt>
