@@ -92,6 +92,33 @@ __device__ __forceinline__ VoxelCoord voxel_coord(const VolumeView& v, float P0,
     return c;
 }
 
+// Brick coordinates of the footprint's lower corner.  Each is monotone in the
+// position along a ray or a light column, so two samples in one brick have
+// every sample between them in that brick too.
+__device__ __forceinline__ bool same_brick(const VoxelCoord& a, const VoxelCoord& b) {
+    return ((a.x0 ^ b.x0) >> kBrickShift) == 0 && ((a.y0 ^ b.y0) >> kBrickShift) == 0 &&
+           ((a.z0 ^ b.z0) >> kBrickShift) == 0;
+}
+
+// Parameter along P(s) = base + s dir at which the footprint's lower corner
+// leaves the brick of c (an estimate; callers verify with the exact path).
+__device__ __forceinline__ float brick_exit(const VolumeView& v, const VoxelCoord& c, float b0,
+                                            float b1, float b2, float d0, float d1, float d2) {
+    const float base[3] = {b0, b1, b2}, dir[3] = {d0, d1, d2};
+    const int lo[3] = {c.x0 >> kBrickShift, c.y0 >> kBrickShift, c.z0 >> kBrickShift};
+    const float N[3] = {v.fnx, v.fny, v.fnz};
+    float s_exit = 3.0e38f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        // Cells [8 b, 8 b + 7] <=> P in [(8 b + 0.5) / N, (8 b + 8.5) / N).
+        const float lo_p = __fdividef((float)(lo[a] << kBrickShift) + 0.5f, N[a]);
+        const float hi_p = __fdividef((float)((lo[a] + 1) << kBrickShift) + 0.5f, N[a]);
+        if (dir[a] > 0.0f) s_exit = fminf(s_exit, __fdividef(hi_p - base[a], dir[a]));
+        else if (dir[a] < 0.0f) s_exit = fminf(s_exit, __fdividef(lo_p - base[a], dir[a]));
+    }
+    return s_exit;
+}
+
 // Whether the brick holding the footprint's lower corner may yield alpha > 0.
 __device__ __forceinline__ bool brick_may_be_lit(const GridView& g, const VoxelCoord& c) {
     const int b = ((c.z0 >> kBrickShift) * g.nby + (c.y0 >> kBrickShift)) * g.nbx +
@@ -174,15 +201,18 @@ __device__ __forceinline__ int slice_index(float lam, int n) {
 template <typename Fmt>
 __device__ __forceinline__ float bilinear(const typename Fmt::T* __restrict__ S, int R, float tu,
                                           float tv, int* rec = nullptr) {
-    const int iu = __float2int_rd(tu), iv = __float2int_rd(tv);
     if (rec) {
-        rec[1] = clampi(iu, -1, R);
-        rec[2] = clampi(iv, -1, R);
+        rec[1] = clampi(__float2int_rd(tu), -1, R);
+        rec[2] = clampi(__float2int_rd(tv), -1, R);
     }
-    const float wu = tu - (float)iu, wv = tv - (float)iv;
-    const unsigned i0 = (unsigned)clampi(iu, 0, R - 1), i1 = (unsigned)clampi(iu + 1, 0, R - 1);
-    const unsigned j0 = (unsigned)clampi(iv, 0, R - 1), j1 = (unsigned)clampi(iv + 1, 0, R - 1);
-    const typename Fmt::T* r0 = S + j0 * (unsigned)R;
+    // Clamping the coordinate to [0, R - 1] first gives the clamp-to-edge
+    // result bit for bit: outside, the weight of the far texel becomes 0.
+    const float cu = fminf(fmaxf(tu, 0.0f), (float)(R - 1));
+    const float cv = fminf(fmaxf(tv, 0.0f), (float)(R - 1));
+    const int i0 = __float2int_rd(cu), j0 = __float2int_rd(cv);
+    const float wu = cu - (float)i0, wv = cv - (float)j0;
+    const unsigned i1 = (unsigned)min(i0 + 1, R - 1), j1 = (unsigned)min(j0 + 1, R - 1);
+    const typename Fmt::T* r0 = S + (unsigned)j0 * (unsigned)R;
     const typename Fmt::T* r1 = S + j1 * (unsigned)R;
     const float b00 = Fmt::load(r0 + i0), b01 = Fmt::load(r0 + i1);
     const float b10 = Fmt::load(r1 + i0), b11 = Fmt::load(r1 + i1);

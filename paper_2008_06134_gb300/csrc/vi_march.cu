@@ -115,19 +115,45 @@ enum { kEnded = 0, kContinue = 1, kStopped = 2 };
 
 // One sample i of a ray.  Returns kEnded if t_i is past the exit (nothing
 // done), kContinue after compositing, kStopped if early ray termination fired.
+// Footprint cell of sample i (index path).
+__device__ __forceinline__ VoxelCoord sample_cell(const MarchParams& p, const Ray& r, int i,
+                                                  float* t_out) {
+    const float t = __fmaf_rn((float)i, p.cam.dt, r.t0);
+    *t_out = t;
+    return voxel_coord(p.vol, __fmaf_rn(t, r.d[0], r.o[0]), __fmaf_rn(t, r.d[1], r.o[1]),
+                       __fmaf_rn(t, r.d[2], r.o[2]));
+}
+
+// Last sample j >= i of the ray still in the brick of sample i (whose cell is
+// vc), or i itself if the estimate does not verify.  Samples i..j all lie in
+// that brick because each brick coordinate is monotone in the sample index.
+__device__ __forceinline__ int last_in_brick(const MarchParams& p, const Ray& r, int i, float t,
+                                             const VoxelCoord& vc) {
+    const float t_exit = brick_exit(p.vol, vc, r.o[0], r.o[1], r.o[2], r.d[0], r.d[1], r.d[2]);
+    const float steps = (fminf(t_exit, r.t1) - t) / p.cam.dt;
+    if (!(steps >= 2.0f)) return i;
+    const int j = i + (int)fminf(steps, 1.0e7f) - 1;
+    float tj;
+    const VoxelCoord cj = sample_cell(p, r, j, &tj);
+    return (tj < r.t1 && same_brick(vc, cj)) ? j : i;
+}
+
+// One sample i of a ray (i advances past what was consumed).  Returns kEnded
+// if t_i is past the exit (nothing done), kContinue after compositing,
+// kStopped if early ray termination fired.
 template <typename VoxT, typename Fmt, int MODE, bool TRACE>
 __device__ __forceinline__ int march_sample(const MarchParams& p, const float* s_alpha,
-                                            const Ray& r, int i, float& C0, float& C1, float& C2,
+                                            const Ray& r, int& i, float& C0, float& C1, float& C2,
                                             float& A, int& count, int& lit, int32_t* rec) {
-    const float t = __fmaf_rn((float)i, p.cam.dt, r.t0);
+    float t;
+    const VoxelCoord vc = sample_cell(p, r, i, &t);
     if (!(t < r.t1)) return kEnded;
-    const float S0 = __fmaf_rn(t, r.d[0], r.o[0]);
-    const float S1 = __fmaf_rn(t, r.d[1], r.o[1]);
-    const float S2 = __fmaf_rn(t, r.d[2], r.o[2]);
-    const VoxelCoord vc = voxel_coord(p.vol, S0, S1, S2);
-    // A sample in a brick that cannot yield alpha > 0 composites nothing.
+    // Samples in a brick that cannot yield alpha > 0 composite nothing: count
+    // the run of them in this brick and move past it.
     if (!TRACE && !brick_may_be_lit(p.grid, vc)) {
-        ++count;
+        const int j = last_in_brick(p, r, i, t, vc);
+        count += j - i + 1;
+        i = j + 1;
         return A > p.ert ? kStopped : kContinue;
     }
     const float val = trilinear_fetch<VoxT>(p.vol, vc);
@@ -200,6 +226,7 @@ __device__ __forceinline__ int march_sample(const MarchParams& p, const float* s
     // Eq. 7 and Eq. 3: emission = light factor * light colour * alpha * rgb.
     // A sample with alpha = 0 leaves C and A unchanged, so it is skipped.
     ++count;
+    ++i;
     if (alpha > 0.0f) {
         const float4 ta = __ldg(p.tf + e), tb = __ldg(p.tf + e + 1);
         const float lf = fmaf(1.0f - p.ambient, coef, p.ambient);
@@ -241,10 +268,10 @@ __global__ void __launch_bounds__(kMarchThreads) march_kernel(const MarchParams 
         if (valid) ray_setup<MODE>(p, x, y, r);
 
         float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, A = 0.0f;
-        int count = 0, lit = 0;
+        int count = 0, lit = 0, i = 0;
         bool active = valid && r.hit;
         // All 32 lanes stay in the loop; it ends when the ballot finds none active.
-        for (int i = 0; __any_sync(0xffffffffu, active); ++i) {
+        while (__any_sync(0xffffffffu, active)) {
             if (active)
                 active = march_sample<VoxT, Fmt, MODE, false>(p, s_alpha, r, i, C0, C1, C2, A,
                                                               count, lit, nullptr) == kContinue;
@@ -272,7 +299,7 @@ __global__ void trace_kernel(const MarchParams p, int x, int y, int32_t* rec, in
     int count = 0, lit = 0, nrec = 0;
     // Records the first max_rec samples of the ray.
     if (r.hit) {
-        for (int i = 0; nrec < max_rec; ++i) {
+        for (int i = 0; nrec < max_rec;) {
             int32_t* out = rec + (size_t)nrec * kTraceWords;
             int st = march_sample<VoxT, Fmt, MODE, true>(p, s_alpha, r, i, C0, C1, C2, A, count,
                                                          lit, out);
