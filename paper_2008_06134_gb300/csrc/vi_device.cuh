@@ -155,26 +155,47 @@ struct Octet<uint8_t> {
     }
 };
 
-// Trilinear from the octet at the footprint's lower corner.  The octet's upper
-// voxels are clamped copies at the high edges; at the low edges (cell -1) the
-// footprint collapses onto voxel 0, so the weight of the upper corner is 0.
+// What a trilinear fetch needs: the octet holding the footprint and the
+// weights of its upper corners.  The octet's upper voxels are clamped copies
+// at the high edges; at the low edges (cell -1) the footprint collapses onto
+// voxel 0, so the upper corner's weight is 0 there.
+struct OctetRef {
+    size_t idx;
+    float wx, wy, wz;
+};
+
+__device__ __forceinline__ OctetRef octet_ref(const VolumeView& v, const VoxelCoord& c) {
+    OctetRef o;
+    o.idx = ((size_t)c.z0 * (size_t)v.ny + (size_t)c.y0) * (size_t)v.nx + (size_t)c.x0;
+    o.wx = c.cx < 0 ? 0.0f : c.wx;
+    o.wy = c.cy < 0 ? 0.0f : c.wy;
+    o.wz = c.cz < 0 ? 0.0f : c.wz;
+    return o;
+}
+
+template <typename VoxT>
+__device__ __forceinline__ typename Octet<VoxT>::V octet_load(const VolumeView& v, size_t idx) {
+    return __ldg(static_cast<const typename Octet<VoxT>::V*>(v.data) + idx);
+}
+
+template <typename VoxT>
+__device__ __forceinline__ float trilinear_octet(const typename Octet<VoxT>::V oct,
+                                                 const OctetRef& o) {
+    float q[8];
+    Octet<VoxT>::unpack(oct, q);
+    float c00 = fmaf(o.wx, q[1] - q[0], q[0]);
+    float c01 = fmaf(o.wx, q[3] - q[2], q[2]);
+    float c10 = fmaf(o.wx, q[5] - q[4], q[4]);
+    float c11 = fmaf(o.wx, q[7] - q[6], q[6]);
+    float c0 = fmaf(o.wy, c01 - c00, c00);
+    float c1 = fmaf(o.wy, c11 - c10, c10);
+    return fmaf(o.wz, c1 - c0, c0);
+}
+
 template <typename VoxT>
 __device__ __forceinline__ float trilinear_fetch(const VolumeView& v, const VoxelCoord& c) {
-    using O = Octet<VoxT>;
-    const typename O::V* oct = static_cast<const typename O::V*>(v.data);
-    const size_t idx = ((size_t)c.z0 * (size_t)v.ny + (size_t)c.y0) * (size_t)v.nx + (size_t)c.x0;
-    float q[8];
-    O::unpack(__ldg(oct + idx), q);
-    const float wx = c.cx < 0 ? 0.0f : c.wx;
-    const float wy = c.cy < 0 ? 0.0f : c.wy;
-    const float wz = c.cz < 0 ? 0.0f : c.wz;
-    float c00 = fmaf(wx, q[1] - q[0], q[0]);
-    float c01 = fmaf(wx, q[3] - q[2], q[2]);
-    float c10 = fmaf(wx, q[5] - q[4], q[4]);
-    float c11 = fmaf(wx, q[7] - q[6], q[6]);
-    float c0 = fmaf(wy, c01 - c00, c00);
-    float c1 = fmaf(wy, c11 - c10, c10);
-    return fmaf(wz, c1 - c0, c0);
+    const OctetRef o = octet_ref(v, c);
+    return trilinear_octet<VoxT>(octet_load<VoxT>(v, o.idx), o);
 }
 
 // Transfer function position of a value: x in [0, M - 1], entry i = floor(x)

@@ -138,22 +138,23 @@ __device__ __forceinline__ int last_in_brick(const MarchParams& p, const Ray& r,
     return (tj < r.t1 && same_brick(vc, cj)) ? j : i;
 }
 
-// One sample i of a ray (i advances past what was consumed).  Returns kEnded
-// if t_i is past the exit (nothing done), kContinue after compositing,
-// kStopped if early ray termination fired.
+// One sample i of a ray.  Returns kEnded if t_i is past the exit (nothing
+// done), kContinue after compositing, kStopped if early ray termination
+// fired.  *empty_to receives the index after the last sample of this ray that
+// is known to be transparent: the end of the run in an empty brick, or i + 1.
 template <typename VoxT, typename Fmt, int MODE, bool TRACE>
 __device__ __forceinline__ int march_sample(const MarchParams& p, const float* s_alpha,
-                                            const Ray& r, int& i, float& C0, float& C1, float& C2,
-                                            float& A, int& count, int& lit, int32_t* rec) {
+                                            const Ray& r, int i, float& C0, float& C1, float& C2,
+                                            float& A, int& count, int& lit, int32_t* rec,
+                                            int* empty_to) {
     float t;
     const VoxelCoord vc = sample_cell(p, r, i, &t);
+    *empty_to = i + 1;
     if (!(t < r.t1)) return kEnded;
-    // Samples in a brick that cannot yield alpha > 0 composite nothing: count
-    // the run of them in this brick and move past it.
+    // A sample in a brick that cannot yield alpha > 0 composites nothing; the
+    // caller may skip the rest of the run in that brick.
     if (!TRACE && !brick_may_be_lit(p.grid, vc)) {
-        const int j = last_in_brick(p, r, i, t, vc);
-        count += j - i + 1;
-        i = j + 1;
+        *empty_to = last_in_brick(p, r, i, t, vc) + 1;
         return A > p.ert ? kStopped : kContinue;
     }
     const float val = trilinear_fetch<VoxT>(p.vol, vc);
@@ -226,7 +227,6 @@ __device__ __forceinline__ int march_sample(const MarchParams& p, const float* s
     // Eq. 7 and Eq. 3: emission = light factor * light colour * alpha * rgb.
     // A sample with alpha = 0 leaves C and A unchanged, so it is skipped.
     ++count;
-    ++i;
     if (alpha > 0.0f) {
         const float4 ta = __ldg(p.tf + e), tb = __ldg(p.tf + e + 1);
         const float lf = fmaf(1.0f - p.ambient, coef, p.ambient);
@@ -268,13 +268,26 @@ __global__ void __launch_bounds__(kMarchThreads) march_kernel(const MarchParams 
         if (valid) ray_setup<MODE>(p, x, y, r);
 
         float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, A = 0.0f;
-        int count = 0, lit = 0, i = 0;
+        int count = 0, lit = 0;
         bool active = valid && r.hit;
-        // All 32 lanes stay in the loop; it ends when the ballot finds none active.
-        while (__any_sync(0xffffffffu, active)) {
-            if (active)
-                active = march_sample<VoxT, Fmt, MODE, false>(p, s_alpha, r, i, C0, C1, C2, A,
-                                                              count, lit, nullptr) == kContinue;
+        // The warp's rays advance in lockstep (same sample index), which keeps
+        // their gathers coherent.  All 32 lanes stay in the loop; it ends when
+        // the ballot finds none active.  When every active lane sits in a run
+        // of transparent samples, the warp skips to the end of the shortest run.
+        for (int i = 0; __any_sync(0xffffffffu, active);) {
+            int next = 0x7fffffff;
+            if (active) {
+                const int c0 = count;
+                const int st = march_sample<VoxT, Fmt, MODE, false>(p, s_alpha, r, i, C0, C1, C2,
+                                                                    A, count, lit, nullptr, &next);
+                if (count == c0 && st != kEnded) ++count;  // transparent: counted below
+                active = st == kContinue;
+                if (!active) next = 0x7fffffff;
+            }
+            const int to = __reduce_min_sync(0xffffffffu, next);
+            if (to == 0x7fffffff) break;
+            if (active) count += to - i - 1;  // the rest of this lane's transparent run
+            i = to;
         }
         if (valid) {
             const size_t idx = (size_t)y * p.cam.W + x;
@@ -299,10 +312,11 @@ __global__ void trace_kernel(const MarchParams p, int x, int y, int32_t* rec, in
     int count = 0, lit = 0, nrec = 0;
     // Records the first max_rec samples of the ray.
     if (r.hit) {
-        for (int i = 0; nrec < max_rec;) {
+        for (int i = 0; nrec < max_rec; ++i) {
             int32_t* out = rec + (size_t)nrec * kTraceWords;
+            int next;
             int st = march_sample<VoxT, Fmt, MODE, true>(p, s_alpha, r, i, C0, C1, C2, A, count,
-                                                         lit, out);
+                                                         lit, out, &next);
             if (st == kEnded) break;
             ++nrec;
             if (st == kStopped) break;

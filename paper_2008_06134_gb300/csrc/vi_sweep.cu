@@ -11,11 +11,10 @@
 // sizes this targets).  A warp covers an 8 x 4 tile of texels, so its 32
 // sample points form a compact patch of the slice plane and its trilinear
 // footprints share sectors; each store of slice k writes four 32-byte row
-// segments (FP32).  Slices outside the cube, and runs of slices inside a brick
-// that cannot yield alpha > 0, only store; the run's end is found from the
-// brick exit and confirmed with the exact index path (each brick coordinate is
-// monotone in k).  The transfer function's alpha column is staged in shared
-// memory.
+// segments (FP32).  Slices outside the cube only store (the inside slices of a
+// column form one interval, found exactly); inside, a point in a brick that
+// cannot yield alpha > 0 skips the gather.  The transfer function's alpha
+// column is staged in shared memory.
 #include "vi_device.cuh"
 
 namespace vi {
@@ -23,6 +22,7 @@ namespace vi {
 namespace {
 
 constexpr int kSweepBX = 32, kSweepBY = 8;
+constexpr int kBatch = 4;  // slices whose loads are issued together
 
 // Whether the point of slice k on the column through (base) lies in [0,1]^3,
 // evaluated exactly as the sweep evaluates it.
@@ -112,47 +112,47 @@ __global__ void __launch_bounds__(kSweepBX* kSweepBY)
     const typename Fmt::T one = Fmt::pack(1.0f);
     int k = 0;
     for (; k < min(kin, lt.n); ++k) out[(size_t)k * slice] = one;
+    // Inside the cube, four slices at a time: their positions, brick flags and
+    // octets do not depend on T, so the loads of a batch are issued together
+    // and their latencies overlap; T then runs through the batch in order.
     float T = 1.0f;
-    while (k <= kout) {
-        float dk = __fmaf_rn((float)k, lt.dL, lt.min);
-        float sk = __fsub_rn(dk, lt.Lc);
-        float P0 = __fmaf_rn(sk, lt.L[0], base0);
-        float P1 = __fmaf_rn(sk, lt.L[1], base1);
-        float P2 = __fmaf_rn(sk, lt.L[2], base2);
-        const VoxelCoord vc = voxel_coord(p.vol, P0, P1, P2);
-        if (!brick_may_be_lit(p.grid, vc)) {
-            // A run of slices in a brick that cannot yield alpha > 0: T is
-            // unchanged there (with compensation too: (1 + 0)^c = 1).
-            int kl = k;
-            const float s_exit = brick_exit(p.vol, vc, base0, base1, base2, lt.L[0], lt.L[1],
-                                            lt.L[2]);
-            const float kf = fminf((s_exit + lt.Lc - lt.min) / lt.dL, (float)kout + 1.0f);
-            if (kf >= (float)k + 2.0f) {
-                const int cand = (int)kf - 1;
-                const float sc = __fsub_rn(__fmaf_rn((float)cand, lt.dL, lt.min), lt.Lc);
-                const VoxelCoord vcand = voxel_coord(p.vol, __fmaf_rn(sc, lt.L[0], base0),
-                                                     __fmaf_rn(sc, lt.L[1], base1),
-                                                     __fmaf_rn(sc, lt.L[2], base2));
-                if (same_brick(vc, vcand)) kl = cand;
-            }
-            const typename Fmt::T st = Fmt::pack(T);
-            for (; k <= kl; ++k) out[(size_t)k * slice] = st;
-            continue;
+    for (; k <= kout; k += kBatch) {
+        OctetRef ref[kBatch];
+        bool lit[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const float sk = __fsub_rn(__fmaf_rn((float)(k + u), lt.dL, lt.min), lt.Lc);
+            const VoxelCoord vc = voxel_coord(p.vol, __fmaf_rn(sk, lt.L[0], base0),
+                                              __fmaf_rn(sk, lt.L[1], base1),
+                                              __fmaf_rn(sk, lt.L[2], base2));
+            ref[u] = octet_ref(p.vol, vc);
+            lit[u] = k + u <= kout && brick_may_be_lit(p.grid, vc);
         }
-        float val = trilinear_fetch<VoxT>(p.vol, vc);
-        int e;
-        float f;
-        tf_coord(val, p.tf_vmin, p.tf_scale, p.M, &e, &f);
-        float a0 = s_alpha[e];
-        float alpha = fmaf(f, s_alpha[e + 1] - a0, a0);
-        if (p.opacity_correction)
-            alpha = 1.0f - exp2f(p.spacing_vox * log2f(fmaxf(1.0f - alpha, 0.0f)));
-        float stored = T;
-        if (p.comp_n != 0.0f) stored = fminf(1.0f, T * powf(1.0f + alpha, p.comp_n));
-        out[(size_t)k * slice] = Fmt::pack(stored);
-        T *= (1.0f - alpha);
-        ++k;
+        typename Octet<VoxT>::V oct[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u)
+            if (lit[u]) oct[u] = octet_load<VoxT>(p.vol, ref[u].idx);
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            if (k + u > kout) break;
+            float alpha = 0.0f;
+            if (lit[u]) {
+                int e;
+                float f;
+                tf_coord(trilinear_octet<VoxT>(oct[u], ref[u]), p.tf_vmin, p.tf_scale, p.M, &e,
+                         &f);
+                const float a0 = s_alpha[e];
+                alpha = fmaf(f, s_alpha[e + 1] - a0, a0);
+                if (p.opacity_correction)
+                    alpha = 1.0f - exp2f(p.spacing_vox * log2f(fmaxf(1.0f - alpha, 0.0f)));
+            }
+            float stored = T;
+            if (p.comp_n != 0.0f) stored = fminf(1.0f, T * powf(1.0f + alpha, p.comp_n));
+            out[(size_t)(k + u) * slice] = Fmt::pack(stored);
+            T *= (1.0f - alpha);
+        }
     }
+    k = max(k, kout + 1);
     // Past the cube: the light that left it.
     const typename Fmt::T last = Fmt::pack(T);
     for (; k < lt.n; ++k) out[(size_t)k * slice] = last;
