@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(kSweepBX* kSweepBY)
             T *= (1.0f - alpha);
         }
     }
-    k = max(k, kout + 1);
+    if (kin <= kout) k = kout + 1;  // the last batch may have run past kout
     // Past the cube: the light that left it.
     const typename Fmt::T last = Fmt::pack(T);
     for (; k < lt.n; ++k) out[(size_t)k * slice] = last;
