@@ -111,7 +111,7 @@ __device__ __forceinline__ void lookup_cell(int n, int R, float lam, float tu, f
     rec[2] = floor_clamp(tv, -1, R);
 }
 
-enum { kEnded = 0, kContinue = 1, kStopped = 2 };
+enum { kEnded = 0, kContinue = 1, kStopped = 2, kEmpty = 3 };
 
 // One sample i of a ray.  Returns kEnded if t_i is past the exit (nothing
 // done), kContinue after compositing, kStopped if early ray termination fired.
@@ -139,23 +139,19 @@ __device__ __forceinline__ int last_in_brick(const MarchParams& p, const Ray& r,
 }
 
 // One sample i of a ray.  Returns kEnded if t_i is past the exit (nothing
-// done), kContinue after compositing, kStopped if early ray termination
-// fired.  *empty_to receives the index after the last sample of this ray that
-// is known to be transparent: the end of the run in an empty brick, or i + 1.
+// done), kStopped if early ray termination fired, kEmpty if the sample lies in
+// a brick that cannot yield alpha > 0 (counted, nothing composited), else
+// kContinue.
 template <typename VoxT, typename Fmt, int MODE, bool TRACE>
 __device__ __forceinline__ int march_sample(const MarchParams& p, const float* s_alpha,
                                             const Ray& r, int i, float& C0, float& C1, float& C2,
-                                            float& A, int& count, int& lit, int32_t* rec,
-                                            int* empty_to) {
+                                            float& A, int& count, int& lit, int32_t* rec) {
     float t;
     const VoxelCoord vc = sample_cell(p, r, i, &t);
-    *empty_to = i + 1;
     if (!(t < r.t1)) return kEnded;
-    // A sample in a brick that cannot yield alpha > 0 composites nothing; the
-    // caller may skip the rest of the run in that brick.
     if (!TRACE && !brick_may_be_lit(p.grid, vc)) {
-        *empty_to = last_in_brick(p, r, i, t, vc) + 1;
-        return A > p.ert ? kStopped : kContinue;
+        ++count;
+        return A > p.ert ? kStopped : kEmpty;
     }
     const float val = trilinear_fetch<VoxT>(p.vol, vc);
     int e;
@@ -272,21 +268,28 @@ __global__ void __launch_bounds__(kMarchThreads) march_kernel(const MarchParams 
         bool active = valid && r.hit;
         // The warp's rays advance in lockstep (same sample index), which keeps
         // their gathers coherent.  All 32 lanes stay in the loop; it ends when
-        // the ballot finds none active.  When every active lane sits in a run
-        // of transparent samples, the warp skips to the end of the shortest run.
+        // the ballot finds none active.  When every active lane sits in a brick
+        // that cannot yield alpha > 0, the warp skips together to the end of
+        // the shortest such run (each lane's run is verified exactly).
         for (int i = 0; __any_sync(0xffffffffu, active);) {
-            int next = 0x7fffffff;
-            if (active) {
-                const int c0 = count;
-                const int st = march_sample<VoxT, Fmt, MODE, false>(p, s_alpha, r, i, C0, C1, C2,
-                                                                    A, count, lit, nullptr, &next);
-                if (count == c0 && st != kEnded) ++count;  // transparent: counted below
-                active = st == kContinue;
-                if (!active) next = 0x7fffffff;
+            int st = kEnded;
+            if (active)
+                st = march_sample<VoxT, Fmt, MODE, false>(p, s_alpha, r, i, C0, C1, C2, A, count,
+                                                          lit, nullptr);
+            active = active && (st == kContinue || st == kEmpty);
+            const unsigned act = __ballot_sync(0xffffffffu, active);
+            const unsigned emp = __ballot_sync(0xffffffffu, active && st == kEmpty);
+            int to = i + 1;
+            if (act != 0u && emp == act) {
+                int next = 0x7fffffff;
+                if (active) {
+                    float t;
+                    const VoxelCoord vc = sample_cell(p, r, i, &t);
+                    next = last_in_brick(p, r, i, t, vc) + 1;
+                }
+                to = __reduce_min_sync(0xffffffffu, next);
+                if (active) count += to - i - 1;  // the rest of the run: transparent
             }
-            const int to = __reduce_min_sync(0xffffffffu, next);
-            if (to == 0x7fffffff) break;
-            if (active) count += to - i - 1;  // the rest of this lane's transparent run
             i = to;
         }
         if (valid) {
@@ -314,9 +317,8 @@ __global__ void trace_kernel(const MarchParams p, int x, int y, int32_t* rec, in
     if (r.hit) {
         for (int i = 0; nrec < max_rec; ++i) {
             int32_t* out = rec + (size_t)nrec * kTraceWords;
-            int next;
             int st = march_sample<VoxT, Fmt, MODE, true>(p, s_alpha, r, i, C0, C1, C2, A, count,
-                                                         lit, out, &next);
+                                                         lit, out);
             if (st == kEnded) break;
             ++nrec;
             if (st == kStopped) break;
