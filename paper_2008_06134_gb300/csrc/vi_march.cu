@@ -113,8 +113,6 @@ __device__ __forceinline__ void lookup_cell(int n, int R, float lam, float tu, f
 
 enum { kEnded = 0, kContinue = 1, kStopped = 2, kEmpty = 3 };
 
-// One sample i of a ray.  Returns kEnded if t_i is past the exit (nothing
-// done), kContinue after compositing, kStopped if early ray termination fired.
 // Footprint cell of sample i (index path).
 __device__ __forceinline__ VoxelCoord sample_cell(const MarchParams& p, const Ray& r, int i,
                                                   float* t_out) {
@@ -124,18 +122,34 @@ __device__ __forceinline__ VoxelCoord sample_cell(const MarchParams& p, const Ra
                        __fmaf_rn(t, r.d[2], r.o[2]));
 }
 
-// Last sample j >= i of the ray still in the brick of sample i (whose cell is
-// vc), or i itself if the estimate does not verify.  Samples i..j all lie in
-// that brick because each brick coordinate is monotone in the sample index.
-__device__ __forceinline__ int last_in_brick(const MarchParams& p, const Ray& r, int i, float t,
-                                             const VoxelCoord& vc) {
-    const float t_exit = brick_exit(p.vol, vc, r.o[0], r.o[1], r.o[2], r.d[0], r.d[1], r.d[2]);
-    const float steps = (fminf(t_exit, r.t1) - t) / p.cam.dt;
-    if (!(steps >= 2.0f)) return i;
-    const int j = i + (int)fminf(steps, 1.0e7f) - 1;
-    float tj;
-    const VoxelCoord cj = sample_cell(p, r, j, &tj);
-    return (tj < r.t1 && same_brick(vc, cj)) ? j : i;
+// Last sample j >= i such that samples i..j all lie in bricks that cannot
+// yield alpha > 0 (sample i, at t with cell vc, is in one).  Walks up to
+// kWalk bricks along the ray: in each, the last sample is estimated from the
+// brick exit and confirmed with the exact index path (each brick coordinate
+// is monotone in the sample index, so samples between two confirmed ones
+// share their brick).  The walk stops at a brick that may be lit or at the
+// ray's exit.
+constexpr int kWalk = 8;
+
+__device__ __forceinline__ int last_transparent(const MarchParams& p, const Ray& r, int i, float t,
+                                                VoxelCoord vc) {
+    int s = i;
+    for (int w = 0; w < kWalk; ++w) {
+        int end = s;
+        const float t_exit = brick_exit(p.vol, vc, r.o[0], r.o[1], r.o[2], r.d[0], r.d[1], r.d[2]);
+        const float steps = (fminf(t_exit, r.t1) - t) / p.cam.dt;
+        if (steps >= 2.0f) {
+            const int j = s + (int)fminf(steps, 1.0e7f) - 1;
+            float tj;
+            const VoxelCoord cj = sample_cell(p, r, j, &tj);
+            if (tj < r.t1 && same_brick(vc, cj)) end = j;
+        }
+        // The sample after the run: past the exit, or in a brick that may be lit.
+        vc = sample_cell(p, r, end + 1, &t);
+        if (!(t < r.t1) || brick_may_be_lit(p.grid, vc)) return end;
+        s = end + 1;  // transparent as well: the walk goes on from here
+    }
+    return s;
 }
 
 // One sample i of a ray.  Returns kEnded if t_i is past the exit (nothing
@@ -285,7 +299,7 @@ __global__ void __launch_bounds__(kMarchThreads) march_kernel(const MarchParams 
                 if (active) {
                     float t;
                     const VoxelCoord vc = sample_cell(p, r, i, &t);
-                    next = last_in_brick(p, r, i, t, vc) + 1;
+                    next = last_transparent(p, r, i, t, vc) + 1;
                 }
                 to = __reduce_min_sync(0xffffffffu, next);
                 if (active) count += to - i - 1;  // the rest of the run: transparent
