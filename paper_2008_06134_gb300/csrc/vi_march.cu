@@ -257,8 +257,15 @@ __device__ __forceinline__ void load_alpha(const MarchParams& p, float* s_alpha)
 // Persistent warps: each warp takes 8 x 4 pixel tiles, in raster order, from a
 // global counter until none are left, so warps whose rays end early pick up
 // more work instead of idling while others march through dense regions.
+// Resident blocks per SM the register allocation is fitted to (4 x 256
+// threads = 32 warps by default).
+#ifndef VI_MARCH_MIN_BLOCKS
+#define VI_MARCH_MIN_BLOCKS 4
+#endif
+
 template <typename VoxT, typename Fmt, int MODE>
-__global__ void __launch_bounds__(kMarchThreads) march_kernel(const MarchParams p) {
+__global__ void __launch_bounds__(kMarchThreads, VI_MARCH_MIN_BLOCKS)
+    march_kernel(const MarchParams p) {
     extern __shared__ float s_alpha[];
     load_alpha(p, s_alpha);
 
