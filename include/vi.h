@@ -177,6 +177,36 @@ int vi_trace_pixel(vi_ctx* ctx, const vi_camera* camera, int W, int H, float ste
 /* Number of kernels this context has launched so far. */
 int vi_launch_count(vi_ctx* ctx, uint64_t* count);
 
+/* ---- Rendering without allocation ----------------------------------------- */
+
+/* Largest frame vi_render_host_noalloc takes: 512 x 512 pixels. */
+#define VI_NOALLOC_MAX_PIXELS 262144
+
+/* vi_render for callers that cannot allocate device memory -- a plug-in whose
+   host application owns the GPU's memory, a process under a hard device-memory
+   cap, a real-time loop where an allocation's latency is not acceptable.  The
+   paper has no counterpart; it is a deployment variant of the eye pass.
+
+   It renders with the context's resident volume, TF and stack exactly as
+   vi_render does (same kernel, same result) into the caller's host buffer
+   out_rgba (W*H*4 float32, row-major RGBA), and allocates nothing: no
+   cudaMalloc, no cudaFree, no library-owned growth.  The march's work counter
+   and the frame's staging live in one fixed device array inside the library
+   (256 B + VI_NOALLOC_MAX_PIXELS * 16 B, about 4 MiB), which every GPU that
+   loads the library holds until the process exits.
+     - W * H above VI_NOALLOC_MAX_PIXELS returns VI_EINVAL (nothing runs).
+     - The first call on a device looks up that array's device address; make
+       it before any stream capture.
+     - Every call on every context of a device shares the array: the counter
+       is cleared on the stream at each call, the staged frame is overwritten
+       (the array keeps the last call's contents), and calls whose GPU work
+       overlaps -- two streams, two contexts, two threads -- race on it and
+       must be ordered by the caller.
+   Synchronous: returns when the frame is in out_rgba.  Other arguments,
+   states and errors as vi_render. */
+int vi_render_host_noalloc(vi_ctx* ctx, const vi_camera* camera, int W, int H, float step_vox,
+                           float* out_rgba, const vi_render_opts* opts);
+
 #ifdef __cplusplus
 }
 #endif

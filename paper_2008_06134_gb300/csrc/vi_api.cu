@@ -669,6 +669,35 @@ int vi_trace_pixel(vi_ctx* c, const vi_camera* cam, int W, int H, float step_vox
     return VI_OK;
 }
 
+int vi_render_host_noalloc(vi_ctx* c, const vi_camera* cam, int W, int H, float step_vox,
+                           float* out, const vi_render_opts* opts) {
+    int rc = enter(c);
+    if (rc) return rc;
+    vi_render_opts ro = opts ? *opts : default_render_opts();
+    rc = check_render_inputs(c, cam, W, H, step_vox, &ro);
+    if (rc) return rc;
+    if ((size_t)W * (size_t)H > vi::kNoallocMaxPixels) return VI_EINVAL;
+    if (W == 0 || H == 0) return VI_OK;
+    if (!out) return VI_EINVAL;
+    MarchParams p;
+    rc = fill_march_params(c, cam, W, H, step_vox, &ro, &p);
+    if (rc) return rc;
+    unsigned* counter = nullptr;
+    float4* image = nullptr;
+    cudaError_t e = vi::noalloc_scratch(&counter, &image);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    p.tile_counter = counter;  // zeroed on the stream by the launch
+    p.out = image;
+    e = vi::launch_march(p, c->vtype, c->bopts.format, c->mode, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    ++c->launches;
+    e = cudaMemcpyAsync(out, image, (size_t)W * (size_t)H * sizeof(float4),
+                        cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    e = cudaStreamSynchronize(c->stream);
+    return cuda_fail(c, e);
+}
+
 int vi_launch_count(vi_ctx* c, uint64_t* count) {
     if (!c || !count) return VI_EINVAL;
     *count = c->launches;

@@ -16,6 +16,8 @@
 //
 // The same per-sample body runs in trace_kernel, which records every integer
 // decision of one ray for exact comparison with an independent implementation.
+#include <mutex>
+
 #include "vi_device.cuh"
 
 namespace vi {
@@ -421,6 +423,46 @@ cudaError_t launch_trace(const MarchParams& p, int voxel_type, int format, int m
                          int32_t* rec, int max_rec, int* n_rec, cudaStream_t s) {
     if (voxel_type == 0) return dispatch_fmt<uint8_t>(p, format, mode, true, x, y, rec, max_rec, n_rec, s);
     return dispatch_fmt<uint16_t>(p, format, mode, true, x, y, rec, max_rec, n_rec, s);
+}
+
+// ---------------------------------------------------------------------------
+// Fixed device scratch for vi_render_host_noalloc, for callers that cannot
+// allocate device memory.  The first 256 bytes hold the march's work counter,
+// the rest stages a frame of up to kNoallocMaxPixels RGBA float pixels before
+// it is copied to the caller's host buffer.  It is a file-scope device array:
+// every GPU that loads the library holds it until the process exits, and
+// every call shares it.
+
+namespace {
+
+constexpr size_t kNoallocCounterBytes = 256;
+__device__ __align__(256) static unsigned char
+    g_noalloc_scratch[kNoallocCounterBytes + kNoallocMaxPixels * sizeof(float4)];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoallocMaxDevices] = {};
+
+}  // namespace
+
+cudaError_t noalloc_scratch(unsigned** counter, float4** image) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNoallocMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        // A host-side reference to the array is a stand-in, not a device
+        // address: look the address up once per device, with it current.
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev] = p;
+    }
+    unsigned char* base = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+    *counter = reinterpret_cast<unsigned*>(base);
+    *image = reinterpret_cast<float4*>(base + kNoallocCounterBytes);
+    return cudaSuccess;
 }
 
 }  // namespace vi

@@ -22,13 +22,14 @@ U8, U16 = 0, 1
 NONE, SHADOW, SHELL, CONE = 0, 1, 2, 3
 F32, F16, BF16, UNORM16 = 0, 1, 2, 3
 TRACE_WORDS = 40
+NOALLOC_MAX_PIXELS = 512 * 512
 TRACE_NONE = 0x7FFFFFFF
 
 # Every symbol include/vi.h declares, in order.
 EXPORTS = ("vi_create", "vi_destroy", "vi_set_memory_budget", "vi_load_volume",
            "vi_set_transfer_function", "vi_set_light", "vi_build_attenuation", "vi_render",
            "vi_sync", "vi_error_string", "vi_attenuation_info", "vi_get_attenuation",
-           "vi_trace_pixel", "vi_launch_count")
+           "vi_trace_pixel", "vi_launch_count", "vi_render_host_noalloc")
 
 
 class ViError(RuntimeError):
@@ -83,6 +84,7 @@ def library() -> C.CDLL:
     L.vi_get_attenuation.argtypes = [vp, vp, sz, i]
     L.vi_trace_pixel.argtypes = [vp, P(Camera), i, i, f, P(RenderOpts), i, i, vp, i, P(i)]
     L.vi_launch_count.argtypes = [vp, P(C.c_uint64)]
+    L.vi_render_host_noalloc.argtypes = [vp, P(Camera), i, i, f, vp, P(RenderOpts)]
     _lib = L
     return L
 
@@ -254,6 +256,19 @@ class Context:
                                      C.c_void_p(rec.ctypes.data), int(max_rec), C.byref(n)),
                "vi_trace_pixel")
         return rec[: n.value].copy()
+
+    def render_host_noalloc(self, cam, W: int, H: int, step_vox: float, out=None,
+                            ert: float = 2.0, bg=(0.0, 0.0, 0.0, 0.0), ambient: float = 0.0,
+                            opacity_correction: int = 0) -> np.ndarray:
+        """vi_render_host_noalloc: the frame into a host (H, W, 4) float32 array,
+        with no device allocation (W * H <= NOALLOC_MAX_PIXELS)."""
+        if out is None:
+            out = np.empty((H, W, 4), dtype=np.float32)
+        ro = self._render_opts(ert, bg, ambient, opacity_correction)
+        _check(self.L.vi_render_host_noalloc(self.h, C.byref(camera(cam)), int(W), int(H),
+                                             float(step_vox), C.c_void_p(out.ctypes.data),
+                                             C.byref(ro)), "vi_render_host_noalloc")
+        return out
 
     def launch_count(self) -> int:
         v = C.c_uint64(0)
