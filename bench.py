@@ -40,6 +40,27 @@ FP32_LANES_PER_SM = 128
 FLOPS_BASE = 8 + 6 + 21 + 14 + 15
 FLOPS_LIT = {0: 0, 1: 6 + 2 + 12, 2: 6 + 2 + 6 * 12 + 7, 3: 6 + 2 + 8 * 12 + 9}
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture of this workload, summarised in profiles/<kernel>_ct256*.md.  Each
+# entry holds for the kernel sources it was taken from (hash of the files that
+# define the kernel); once they change the figure is stale and reported as null.
+NCU_TRAFFIC = {
+    "march_kernel": (("vi_march.cu", "vi_device.cuh", "vi_internal.h"), "429b6002c659682c",
+                     78_973_440),
+    "sweep_kernel": (("vi_sweep.cu", "vi_device.cuh", "vi_internal.h"), "6f5fef12bb7b3574",
+                     288_918_016),
+}
+
+
+def ncu_traffic(kernel: str):
+    import hashlib
+    files, digest, nbytes = NCU_TRAFFIC[kernel]
+    m = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2008_06134_gb300", "csrc", f), "rb") as fh:
+            m.update(fh.read())
+    return nbytes if m.hexdigest()[:16] == digest else None
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -329,13 +350,15 @@ def gb300_arm(args):
     sweep_roof = {"bound": "hbm", "achieved": round(sweep_bytes / sweep_s / 1e9, 1),
                   "peak": peaks["hbm_gbs"], "unit": "GB/s",
                   "frac": round(sweep_bytes / sweep_s / 1e9 / peaks["hbm_gbs"], 4),
-                  "traffic": None, "kernel": "sweep_kernel",
+                  "traffic": ncu_traffic("sweep_kernel"), "algorithmic_bytes": int(sweep_bytes),
+                  "kernel": "sweep_kernel",
                   "peak_source": f"{peak_kind} HBM copy bandwidth"}
     flops = samples * FLOPS_BASE + lit_samples * FLOPS_LIT[sc.mode]
     fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * peaks["sm_max_mhz"] / 1e6
     march_roof = {"bound": "alu", "achieved": round(flops / march_s / 1e12, 3),
                   "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
-                  "frac": round(flops / march_s / 1e12 / fp32_peak, 4), "traffic": None,
+                  "frac": round(flops / march_s / 1e12 / fp32_peak, 4),
+                  "traffic": ncu_traffic("march_kernel"), "algorithmic_flops": int(flops),
                   "kernel": "march_kernel",
                   "peak_source": f"FP32 FMA rate: {props.multi_processor_count} SMs x "
                                  f"{FP32_LANES_PER_SM} lanes x 2 x {peaks['sm_max_mhz']} MHz "
