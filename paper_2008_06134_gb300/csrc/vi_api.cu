@@ -53,9 +53,14 @@ struct vi_ctx {
     float dir[3] = {0.0f, 0.0f, 1.0f};
     float color[3] = {1.0f, 1.0f, 1.0f};
 
-    void* stack = nullptr;
+    void* stack_mem = nullptr;   // allocation; the stack starts at the next 512-byte boundary
     size_t stack_cap = 0;
-    size_t stack_bytes = 0;
+    void* stack = nullptr;
+    size_t stack_bytes = 0;      // dense size n R^2 element bytes, as vi_get_attenuation returns
+    size_t row_pitch = 0;        // bytes per stack row (pitched layout, R + 1 rows per slice)
+    vi::StackView sview{};       // texture views of the stack
+    int ntex = 0;
+    int stack_valid_shape_n = 0; // slice count the texture views were made for
     int mode = -1;          // mode of the last build; -1 = none yet
     bool stack_valid = false;
     vi_build_opts bopts{};
@@ -248,6 +253,74 @@ int enter(vi_ctx* c) {
 
 void mark_stale(vi_ctx* c) { c->stack_valid = false; }
 
+void destroy_stack_textures(vi_ctx* c) {
+    for (int g = 0; g < c->ntex; ++g) cudaDestroyTextureObject(c->sview.tex[g]);
+    c->ntex = 0;
+}
+
+// Pitched stack for n slices of R x R texels of format fmt, and its texture
+// views (rebuilt only when the shape, format or buffer changes).
+int setup_stack(vi_ctx* c, int n, int R, int fmt) {
+    const size_t esize = format_bytes(fmt);
+    const size_t pitch = (R * esize + 511) / 512 * 512;
+    int max_h = 0, max_w = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&max_h, cudaDevAttrMaxTexture2DLinearHeight, c->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&max_w, cudaDevAttrMaxTexture2DLinearWidth, c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    if (R > max_w || R + 1 > max_h) return VI_EINVAL;
+    int spt_log2 = 0;
+    while (spt_log2 < 30 && ((size_t)2 << spt_log2) * (size_t)(R + 1) <= (size_t)max_h &&
+           (1 << (spt_log2 + 1)) <= n)
+        ++spt_log2;
+    const int spt = 1 << spt_log2;
+    const int ntex = (n + spt - 1) / spt;
+    if (ntex > vi::kMaxStackTextures) return VI_EINVAL;
+    const size_t bytes = (size_t)n * (size_t)(R + 1) * pitch + 512;
+    void* before = c->stack_mem;
+    int rc = ensure(c, &c->stack_mem, &c->stack_cap, bytes);
+    if (rc) return rc;
+    void* base = reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(c->stack_mem) + 511) &
+                                         ~(uintptr_t)511);
+    const bool same = before == c->stack_mem && c->stack == base && c->row_pitch == pitch &&
+                      c->ntex == ntex && c->sview.spt_log2 == spt_log2 && c->lt.R == R &&
+                      c->bopts.format == fmt && c->stack_valid_shape_n == n;
+    c->stack = base;
+    c->row_pitch = pitch;
+    if (same) return VI_OK;
+    destroy_stack_textures(c);
+    cudaChannelFormatDesc ch = fmt == VI_F32 ? cudaCreateChannelDesc<float>()
+                                             : cudaCreateChannelDesc<unsigned short>();
+    for (int g = 0; g < ntex; ++g) {
+        const int slices = (g + 1) * spt <= n ? spt : n - g * spt;
+        cudaResourceDesc res;
+        std::memset(&res, 0, sizeof(res));
+        res.resType = cudaResourceTypePitch2D;
+        res.res.pitch2D.devPtr = static_cast<char*>(base) + (size_t)g * spt * (R + 1) * pitch;
+        res.res.pitch2D.desc = ch;
+        res.res.pitch2D.width = (size_t)R;
+        res.res.pitch2D.height = (size_t)slices * (R + 1);
+        res.res.pitch2D.pitchInBytes = pitch;
+        cudaTextureDesc td;
+        std::memset(&td, 0, sizeof(td));
+        td.addressMode[0] = cudaAddressModeClamp;
+        td.addressMode[1] = cudaAddressModeClamp;
+        td.filterMode = cudaFilterModePoint;
+        td.readMode = cudaReadModeElementType;
+        td.normalizedCoords = 0;
+        e = cudaCreateTextureObject(&c->sview.tex[g], &res, &td, nullptr);
+        if (e != cudaSuccess) {
+            c->ntex = g;
+            destroy_stack_textures(c);
+            return cuda_fail(c, e);
+        }
+        c->ntex = g + 1;
+    }
+    c->sview.spt_log2 = spt_log2;
+    c->stack_valid_shape_n = n;
+    return VI_OK;
+}
+
 int nbricks(const vi_ctx* c) { return c->nbx * c->nby * c->nbz; }
 
 vi::VolumeView volume_view(const vi_ctx* c) {
@@ -296,7 +369,7 @@ int fill_march_params(vi_ctx* c, const vi_camera* cam, int W, int H, float step_
     p->tf_vmin = c->vmin;
     p->tf_scale = (float)(c->M - 1) / (c->vmax - c->vmin);
     if (c->lt_valid) p->lt = c->lt;  // else n = R = 0: no lookups
-    p->stack = c->stack;
+    p->stack = c->sview;
     const LightFrame& lt = p->lt;
     if (c->mode == VI_SHELL && c->lt_valid) {
         // The six points S +- r e_a as light-space offsets.
@@ -394,7 +467,8 @@ int vi_destroy(vi_ctx* c) {
     release(c, &c->raw, &c->raw_cap);
     release(c, &c->vol, &c->vol_cap);
     release(c, reinterpret_cast<void**>(&c->tf), &c->tf_cap);
-    release(c, &c->stack, &c->stack_cap);
+    destroy_stack_textures(c);
+    release(c, &c->stack_mem, &c->stack_cap);
     release(c, reinterpret_cast<void**>(&c->out), &c->out_cap);
     release(c, reinterpret_cast<void**>(&c->trace), &c->trace_cap);
     release(c, reinterpret_cast<void**>(&c->brange), &c->brange_cap);
@@ -528,7 +602,8 @@ int vi_build_attenuation(vi_ctx* c, int n, int R, int mode, const vi_build_opts*
         return VI_OK;
     }
     size_t bytes = (size_t)n * (size_t)R * (size_t)R * format_bytes(o.format);
-    rc = ensure(c, &c->stack, &c->stack_cap, bytes);
+    c->stack_valid = false;
+    rc = setup_stack(c, n, R, o.format);
     if (rc) return rc;
 
     SweepParams p;
@@ -541,6 +616,7 @@ int vi_build_attenuation(vi_ctx* c, int n, int R, int mode, const vi_build_opts*
     p.tf_scale = (float)(c->M - 1) / (c->vmax - c->vmin);
     p.lt = lt;
     p.stack = c->stack;
+    p.row_pitch = c->row_pitch;
     p.opacity_correction = o.opacity_correction ? 1 : 0;
     p.spacing_vox = lt.dL * (float)nmax(c);
     p.comp_n = o.comp_n;
@@ -622,12 +698,17 @@ int vi_get_attenuation(vi_ctx* c, void* out, size_t out_bytes, int out_on_device
     if (rc) return rc;
     if (!c->stack_valid) return VI_ESTATE;
     if (!out || out_bytes < c->stack_bytes) return VI_EINVAL;
-    cudaError_t e = cudaMemcpyAsync(out, c->stack, c->stack_bytes,
-                                    out_on_device ? cudaMemcpyDeviceToDevice
-                                                  : cudaMemcpyDeviceToHost,
-                                    c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e);
-    e = cudaStreamSynchronize(c->stream);
+    const int n = c->lt.n, R = c->lt.R;
+    const size_t row = (size_t)R * format_bytes(c->bopts.format);
+    for (int k = 0; k < n; ++k) {
+        cudaError_t e = cudaMemcpy2DAsync(
+            static_cast<char*>(out) + (size_t)k * R * row, row,
+            static_cast<const char*>(c->stack) + (size_t)k * (R + 1) * c->row_pitch, c->row_pitch,
+            row, (size_t)R, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+            c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+    }
+    cudaError_t e = cudaStreamSynchronize(c->stream);
     return cuda_fail(c, e);
 }
 

@@ -11,21 +11,48 @@ namespace vi {
 // ---------------------------------------------------------------------------
 // Stack storage formats.  Accumulation is FP32; these only round at store.
 
+// gather() fetches the 2 x 2 footprint whose lower-left texel is (i0, j0) from
+// a pitched 2D texture, given x = i0 + 1, y = j0 + 1 (exact integers, so the
+// footprint choice is exact); texture gather returns (i0, j0+1), (i0+1, j0+1),
+// (i0+1, j0), (i0, j0) in x, y, z, w.  Raw texels, no filtering: the weights
+// are applied in FP32 by the caller.
 struct F32 {
     using T = float;
     static __device__ __forceinline__ T pack(float x) { return x; }
     static __device__ __forceinline__ float load(const T* p) { return __ldg(p); }
+    static __device__ __forceinline__ void gather(cudaTextureObject_t t, float x, float y,
+                                                  float& b00, float& b01, float& b10,
+                                                  float& b11) {
+        const float4 g = tex2Dgather<float4>(t, x, y, 0);
+        b00 = g.w; b01 = g.z; b10 = g.x; b11 = g.y;
+    }
 };
 struct F16 {
     using T = __half;
     static __device__ __forceinline__ T pack(float x) { return __float2half_rn(x); }
     static __device__ __forceinline__ float load(const T* p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ void gather(cudaTextureObject_t t, float x, float y,
+                                                  float& b00, float& b01, float& b10,
+                                                  float& b11) {
+        const uint4 g = tex2Dgather<uint4>(t, x, y, 0);  // raw binary16 bits
+        b00 = __half2float(__ushort_as_half((unsigned short)g.w));
+        b01 = __half2float(__ushort_as_half((unsigned short)g.z));
+        b10 = __half2float(__ushort_as_half((unsigned short)g.x));
+        b11 = __half2float(__ushort_as_half((unsigned short)g.y));
+    }
 };
 struct BF16 {
     using T = __nv_bfloat16;
     static __device__ __forceinline__ T pack(float x) { return __float2bfloat16_rn(x); }
     static __device__ __forceinline__ float load(const T* p) {
         return __bfloat162float(__ldg(p));
+    }
+    static __device__ __forceinline__ void gather(cudaTextureObject_t t, float x, float y,
+                                                  float& b00, float& b01, float& b10,
+                                                  float& b11) {
+        const uint4 g = tex2Dgather<uint4>(t, x, y, 0);  // raw bfloat16 bits
+        b00 = __uint_as_float(g.w << 16); b01 = __uint_as_float(g.z << 16);
+        b10 = __uint_as_float(g.x << 16); b11 = __uint_as_float(g.y << 16);
     }
 };
 // Fixed point on [0, 1] with 16 bits: x = q / 65535.
@@ -37,6 +64,13 @@ struct UNORM16 {
     }
     static __device__ __forceinline__ float load(const T* p) {
         return (float)__ldg(p) * (1.0f / 65535.0f);
+    }
+    static __device__ __forceinline__ void gather(cudaTextureObject_t t, float x, float y,
+                                                  float& b00, float& b01, float& b10,
+                                                  float& b11) {
+        const uint4 g = tex2Dgather<uint4>(t, x, y, 0);
+        constexpr float s = 1.0f / 65535.0f;
+        b00 = (float)g.w * s; b01 = (float)g.z * s; b10 = (float)g.x * s; b11 = (float)g.y * s;
     }
 };
 
@@ -219,9 +253,14 @@ __device__ __forceinline__ int slice_index(float lam, int n) {
     return clampi(__float2int_rd(__fadd_rn(lam, 0.5f)), 0, n - 1);
 }
 
+// Bilinear lookup in slice k of the stack through its texture view.  Slice k
+// is rows [row0, row0 + R) of texture stack_tex[k >> spt_log2] with row0 =
+// (k & (2^spt_log2 - 1)) (R + 1); the extra row R repeats row R - 1, so the
+// footprint of the last row stays inside the slice, and the texture's clamp
+// addressing covers the last column.
 template <typename Fmt>
-__device__ __forceinline__ float bilinear(const typename Fmt::T* __restrict__ S, int R, float tu,
-                                          float tv, int* rec = nullptr) {
+__device__ __forceinline__ float bilinear(const StackView& sv, int k, int R, float tu, float tv,
+                                          int* rec = nullptr) {
     if (rec) {
         rec[1] = clampi(__float2int_rd(tu), -1, R);
         rec[2] = clampi(__float2int_rd(tv), -1, R);
@@ -232,29 +271,21 @@ __device__ __forceinline__ float bilinear(const typename Fmt::T* __restrict__ S,
     const float cv = fminf(fmaxf(tv, 0.0f), (float)(R - 1));
     const int i0 = __float2int_rd(cu), j0 = __float2int_rd(cv);
     const float wu = cu - (float)i0, wv = cv - (float)j0;
-    const unsigned i1 = (unsigned)min(i0 + 1, R - 1), j1 = (unsigned)min(j0 + 1, R - 1);
-    const typename Fmt::T* r0 = S + (unsigned)j0 * (unsigned)R;
-    const typename Fmt::T* r1 = S + j1 * (unsigned)R;
-    const float b00 = Fmt::load(r0 + i0), b01 = Fmt::load(r0 + i1);
-    const float b10 = Fmt::load(r1 + i0), b11 = Fmt::load(r1 + i1);
+    const int row0 = (k & ((1 << sv.spt_log2) - 1)) * (R + 1);
+    float b00, b01, b10, b11;
+    Fmt::gather(sv.tex[k >> sv.spt_log2], (float)(i0 + 1), (float)(row0 + j0 + 1), b00, b01, b10,
+                b11);
     const float top = fmaf(wu, b01 - b00, b00);
     const float bot = fmaf(wu, b11 - b10, b10);
     return fmaf(wv, bot - top, top);
 }
 
 template <typename Fmt>
-__device__ __forceinline__ const typename Fmt::T* slice_ptr(const typename Fmt::T* B, int k,
-                                                            int R) {
-    return B + (size_t)k * ((size_t)R * (size_t)R);
-}
-
-template <typename Fmt>
-__device__ __forceinline__ float stack_lookup(const typename Fmt::T* __restrict__ B, int n, int R,
-                                              float lam, float tu, float tv,
-                                              int* rec = nullptr) {
+__device__ __forceinline__ float stack_lookup(const StackView& sv, int n, int R, float lam, float tu,
+                                              float tv, int* rec = nullptr) {
     const int k = slice_index(lam, n);
     if (rec) rec[0] = k;
-    return bilinear<Fmt>(slice_ptr<Fmt>(B, k, R), R, tu, tv, rec);
+    return bilinear<Fmt>(sv, k, R, tu, tv, rec);
 }
 
 }  // namespace vi

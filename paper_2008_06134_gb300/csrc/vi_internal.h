@@ -54,6 +54,18 @@ struct GridView {
     int nbx, nby;
 };
 
+// The attenuation stack in device memory.  Slice k, row j (0 <= j <= R) starts
+// at byte k (R + 1) row_pitch + j row_pitch; row R repeats row R - 1.  Texture g
+// views slices [g 2^spt_log2, (g + 1) 2^spt_log2) as one pitched 2D texture, R
+// texels wide and 2^spt_log2 (R + 1) rows high (2D linear textures are limited
+// in height, so a deep stack needs several).
+constexpr int kMaxStackTextures = 128;
+
+struct StackView {
+    int spt_log2;  // slices per texture = 2^spt_log2
+    cudaTextureObject_t tex[kMaxStackTextures];
+};
+
 struct SweepParams {
     VolumeView vol;
     GridView grid;
@@ -61,7 +73,8 @@ struct SweepParams {
     int M;
     float tf_vmin, tf_scale;  // x = (v - vmin) * scale, scale = (M - 1) / (vmax - vmin)
     LightFrame lt;
-    void* stack;              // [n][R][R] of the storage format
+    void* stack;              // pitched: see StackView
+    size_t row_pitch;         // bytes
     int opacity_correction;
     float spacing_vox;        // slice spacing in voxels (opacity correction exponent)
     float comp_n;             // darkening compensation exponent, 0 = off
@@ -84,7 +97,7 @@ struct MarchParams {
     int M;
     float tf_vmin, tf_scale;
     LightFrame lt;
-    const void* stack;
+    StackView stack;
     CameraFrame cam;
     float shell_off[6][3];  // light-space offsets of the six shell points
     float cone_rad[2];      // ring radii in texels, rings 1 and 2

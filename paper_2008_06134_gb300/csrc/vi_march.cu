@@ -194,7 +194,6 @@ __device__ __forceinline__ int march_sample(const MarchParams& p, const float* s
         const float l0 = __fmaf_rn(t, r.ld[0], r.lo[0]);
         const float l1 = __fmaf_rn(t, r.ld[1], r.lo[1]);
         const float l2 = __fmaf_rn(t, r.ld[2], r.lo[2]);
-        const typename Fmt::T* B = static_cast<const typename Fmt::T*>(p.stack);
         const int n = p.lt.n, R = p.lt.R;
         if (TRACE) {
             rec[2] = __float_as_int(l0);
@@ -203,7 +202,7 @@ __device__ __forceinline__ int march_sample(const MarchParams& p, const float* s
             if (n > 0) lookup_cell(n, R, l0, l1, l2, rec + 8);
         }
         if (MODE == 1) {
-            coef = stack_lookup<Fmt>(B, n, R, l0, l1, l2);
+            coef = stack_lookup<Fmt>(p.stack, n, R, l0, l1, l2);
         } else if (MODE == 2) {
             float sum = 0.0f;
 #pragma unroll
@@ -211,7 +210,8 @@ __device__ __forceinline__ int march_sample(const MarchParams& p, const float* s
                 float q0 = __fadd_rn(l0, p.shell_off[q][0]);
                 float q1 = __fadd_rn(l1, p.shell_off[q][1]);
                 float q2 = __fadd_rn(l2, p.shell_off[q][2]);
-                sum += stack_lookup<Fmt>(B, n, R, q0, q1, q2, TRACE ? rec + 11 + 3 * q : nullptr);
+                sum += stack_lookup<Fmt>(p.stack, n, R, q0, q1, q2,
+                                         TRACE ? rec + 11 + 3 * q : nullptr);
             }
             coef = sum * (1.0f / 6.0f);
         } else if (MODE == 3) {
@@ -220,7 +220,6 @@ __device__ __forceinline__ int march_sample(const MarchParams& p, const float* s
             for (int ring = 0; ring < 2; ++ring) {
                 // The ring's four points share lambda + offset, hence one slice.
                 const int k = slice_index(__fadd_rn(l0, -(float)(ring + 1)), n);
-                const typename Fmt::T* S = slice_ptr<Fmt>(B, k, R);
                 const float bu = r.nbu[ring], bv = r.nbv[ring];
                 // B_proj turned by m pi/2 about L: (bu, bv), (-bv, bu), (-bu, -bv), (bv, -bu).
                 const float du[4] = {bu, -bv, -bu, bv};
@@ -229,7 +228,8 @@ __device__ __forceinline__ int march_sample(const MarchParams& p, const float* s
                 for (int m = 0; m < 4; ++m) {
                     int* rr = TRACE ? rec + 11 + 3 * (ring * 4 + m) : nullptr;
                     if (TRACE) rr[0] = k;
-                    sum += bilinear<Fmt>(S, R, __fadd_rn(l1, du[m]), __fadd_rn(l2, dv[m]), rr);
+                    sum += bilinear<Fmt>(p.stack, k, R, __fadd_rn(l1, du[m]), __fadd_rn(l2, dv[m]),
+                                         rr);
                 }
             }
             coef = sum * 0.125f;

@@ -60,8 +60,12 @@ __global__ void __launch_bounds__(kSweepBX* kSweepBY)
     float base1 = __fmaf_rn(v, lt.V[1], __fmaf_rn(u, lt.U[1], 0.5f));
     float base2 = __fmaf_rn(v, lt.V[2], __fmaf_rn(u, lt.U[2], 0.5f));
 
-    typename Fmt::T* out = static_cast<typename Fmt::T*>(p.stack) + (size_t)j * lt.R + i;
-    const size_t slice = (size_t)lt.R * (size_t)lt.R;
+    // Pitched stack: slice k, row j at byte (k (R + 1) + j) row_pitch.  The last
+    // row (j = R - 1) is written twice, its copy being row R.
+    const size_t slice = (size_t)(lt.R + 1) * p.row_pitch / sizeof(typename Fmt::T);
+    typename Fmt::T* out = reinterpret_cast<typename Fmt::T*>(static_cast<char*>(p.stack) +
+                                                              (size_t)j * p.row_pitch) + i;
+    const size_t dup = j == lt.R - 1 ? p.row_pitch / sizeof(typename Fmt::T) : 0;
 
     // Slices whose point lies in the cube form one interval [kin, kout]: every
     // coordinate of P_k is monotone in k even after rounding (each step of the
@@ -111,7 +115,10 @@ __global__ void __launch_bounds__(kSweepBX* kSweepBY)
     // Before the cube: full light.
     const typename Fmt::T one = Fmt::pack(1.0f);
     int k = 0;
-    for (; k < min(kin, lt.n); ++k) out[(size_t)k * slice] = one;
+    for (; k < min(kin, lt.n); ++k) {
+        out[(size_t)k * slice] = one;
+        if (dup) out[(size_t)k * slice + dup] = one;
+    }
     // Inside the cube, four slices at a time: their positions, brick flags and
     // octets do not depend on T, so the loads of a batch are issued together
     // and their latencies overlap; T then runs through the batch in order.
@@ -148,14 +155,19 @@ __global__ void __launch_bounds__(kSweepBX* kSweepBY)
             }
             float stored = T;
             if (p.comp_n != 0.0f) stored = fminf(1.0f, T * powf(1.0f + alpha, p.comp_n));
-            out[(size_t)(k + u) * slice] = Fmt::pack(stored);
+            const typename Fmt::T q = Fmt::pack(stored);
+            out[(size_t)(k + u) * slice] = q;
+            if (dup) out[(size_t)(k + u) * slice + dup] = q;
             T *= (1.0f - alpha);
         }
     }
     if (kin <= kout) k = kout + 1;  // the last batch may have run past kout
     // Past the cube: the light that left it.
     const typename Fmt::T last = Fmt::pack(T);
-    for (; k < lt.n; ++k) out[(size_t)k * slice] = last;
+    for (; k < lt.n; ++k) {
+        out[(size_t)k * slice] = last;
+        if (dup) out[(size_t)k * slice + dup] = last;
+    }
 }
 
 template <typename VoxT, typename Fmt>
