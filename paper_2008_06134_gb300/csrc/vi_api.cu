@@ -280,6 +280,7 @@ int setup_stack(vi_ctx* c, int n, int R, int fmt) {
     void* before = c->stack_mem;
     int rc = ensure(c, &c->stack_mem, &c->stack_cap, bytes);
     if (rc) return rc;
+    if (before != c->stack_mem) c->stack_valid = false;
     void* base = reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(c->stack_mem) + 511) &
                                          ~(uintptr_t)511);
     const bool same = before == c->stack_mem && c->stack == base && c->row_pitch == pitch &&
@@ -288,6 +289,7 @@ int setup_stack(vi_ctx* c, int n, int R, int fmt) {
     c->stack = base;
     c->row_pitch = pitch;
     if (same) return VI_OK;
+    c->stack_valid = false;
     destroy_stack_textures(c);
     cudaChannelFormatDesc ch = fmt == VI_F32 ? cudaCreateChannelDesc<float>()
                                              : cudaCreateChannelDesc<unsigned short>();
@@ -602,9 +604,9 @@ int vi_build_attenuation(vi_ctx* c, int n, int R, int mode, const vi_build_opts*
         return VI_OK;
     }
     size_t bytes = (size_t)n * (size_t)R * (size_t)R * format_bytes(o.format);
-    c->stack_valid = false;
-    rc = setup_stack(c, n, R, o.format);
+    rc = setup_stack(c, n, R, o.format);  // a refusal leaves the previous stack usable
     if (rc) return rc;
+    c->stack_valid = false;
 
     SweepParams p;
     std::memset(&p, 0, sizeof(p));
