@@ -265,16 +265,20 @@ __device__ __forceinline__ float bilinear(const StackView& sv, int k, int R, flo
         rec[1] = clampi(__float2int_rd(tu), -1, R);
         rec[2] = clampi(__float2int_rd(tv), -1, R);
     }
-    // Clamping the coordinate to [0, R - 1] first gives the clamp-to-edge
-    // result bit for bit: outside, the weight of the far texel becomes 0.
-    const float cu = fminf(fmaxf(tu, 0.0f), (float)(R - 1));
+    // Columns: the texture's clamp addressing turns a footprint that reaches
+    // past either edge into two copies of the edge texel, which is exactly the
+    // clamp-to-edge result.  Rows: slices are stacked in one texture, so the
+    // row coordinate is clamped to the slice first (the guard row R covers the
+    // footprint of row R - 1).
+    const float fu = floorf(tu);
+    const float wu = tu - fu;
     const float cv = fminf(fmaxf(tv, 0.0f), (float)(R - 1));
-    const int i0 = __float2int_rd(cu), j0 = __float2int_rd(cv);
-    const float wu = cu - (float)i0, wv = cv - (float)j0;
-    const int row0 = (k & ((1 << sv.spt_log2) - 1)) * (R + 1);
+    const float fv = floorf(cv);
+    const float wv = cv - fv;
+    // Gather takes the footprint's lower-left texel plus one (exact integers).
+    const float row0 = (float)((k & ((1 << sv.spt_log2) - 1)) * (R + 1) + 1);
     float b00, b01, b10, b11;
-    Fmt::gather(sv.tex[k >> sv.spt_log2], (float)(i0 + 1), (float)(row0 + j0 + 1), b00, b01, b10,
-                b11);
+    Fmt::gather(sv.tex[k >> sv.spt_log2], fu + 1.0f, fv + row0, b00, b01, b10, b11);
     const float top = fmaf(wu, b01 - b00, b00);
     const float bot = fmaf(wu, b11 - b10, b10);
     return fmaf(wv, bot - top, top);
