@@ -154,51 +154,22 @@ __device__ __forceinline__ int last_transparent(const MarchParams& p, const Ray&
     return s;
 }
 
-// Sample i as far as it goes before shading: its t, whether it is on the ray,
-// whether its brick may yield alpha > 0, and then its octet load (in flight
-// until shade_sample uses it, so a warp can fetch sample i + 1 while it shades
-// sample i).
-template <typename VoxT>
-struct Fetched {
-    float t;
-    bool on_ray, maybe_lit;
-    OctetRef ref;
-    typename Octet<VoxT>::V oct;
-};
-
-template <typename VoxT, bool TRACE>
-__device__ __forceinline__ Fetched<VoxT> fetch_sample(const MarchParams& p, const Ray& r, int i,
-                                                      int* cell = nullptr) {
-    Fetched<VoxT> f;
-    const VoxelCoord vc = sample_cell(p, r, i, &f.t);
-    f.on_ray = f.t < r.t1;
-    f.maybe_lit = f.on_ray && (TRACE || brick_may_be_lit(p.grid, vc));
-    f.ref = octet_ref(p.vol, vc);
-    if (f.maybe_lit) f.oct = octet_load<VoxT>(p.vol, f.ref.idx);
-    if (TRACE) {
-        cell[0] = vc.cx;
-        cell[1] = vc.cy;
-        cell[2] = vc.cz;
-    }
-    return f;
-}
-
-// Shades sample i from what fetch_sample brought.  Returns kEnded if t_i is
-// past the exit (nothing done), kStopped if early ray termination fired, kEmpty
-// if the sample lies in a brick that cannot yield alpha > 0 (counted, nothing
-// composited), else kContinue.
+// One sample i of a ray.  Returns kEnded if t_i is past the exit (nothing
+// done), kStopped if early ray termination fired, kEmpty if the sample lies in
+// a brick that cannot yield alpha > 0 (counted, nothing composited), else
+// kContinue.
 template <typename VoxT, typename Fmt, int MODE, bool TRACE>
-__device__ __forceinline__ int shade_sample(const MarchParams& p, const float* s_alpha,
-                                            const Ray& r, int i, const Fetched<VoxT>& fs,
-                                            float& C0, float& C1, float& C2, float& A, int& count,
-                                            int& lit, int32_t* rec, const int* cell = nullptr) {
-    if (!fs.on_ray) return kEnded;
-    if (!fs.maybe_lit) {
+__device__ __forceinline__ int march_sample(const MarchParams& p, const float* s_alpha,
+                                            const Ray& r, int i, float& C0, float& C1, float& C2,
+                                            float& A, int& count, int& lit, int32_t* rec) {
+    float t;
+    const VoxelCoord vc = sample_cell(p, r, i, &t);
+    if (!(t < r.t1)) return kEnded;
+    if (!TRACE && !brick_may_be_lit(p.grid, vc)) {
         ++count;
         return A > p.ert ? kStopped : kEmpty;
     }
-    const float t = fs.t;
-    const float val = trilinear_octet<VoxT>(fs.oct, fs.ref);
+    const float val = trilinear_fetch<VoxT>(p.vol, vc);
     int e;
     float f;
     tf_coord(val, p.tf_vmin, p.tf_scale, p.M, &e, &f);
@@ -211,9 +182,9 @@ __device__ __forceinline__ int shade_sample(const MarchParams& p, const float* s
         for (int w = 0; w < kTraceWords; ++w) rec[w] = kTraceNone;
         rec[0] = i;
         rec[1] = __float_as_int(t);
-        rec[5] = cell[0];
-        rec[6] = cell[1];
-        rec[7] = cell[2];
+        rec[5] = vc.cx;
+        rec[6] = vc.cy;
+        rec[7] = vc.cz;
         rec[35] = MODE == 2 ? 6 : (MODE == 3 ? 8 : 0);
     }
 
@@ -323,16 +294,11 @@ __global__ void __launch_bounds__(kMarchThreads, VI_MARCH_MIN_BLOCKS)
         // the ballot finds none active.  When every active lane sits in a brick
         // that cannot yield alpha > 0, the warp skips together to the end of
         // the shortest such run (each lane's run is verified exactly).
-        Fetched<VoxT> cur;
-        if (active) cur = fetch_sample<VoxT, false>(p, r, 0);
         for (int i = 0; __any_sync(0xffffffffu, active);) {
             int st = kEnded;
-            Fetched<VoxT> nxt;
-            if (active) {
-                nxt = fetch_sample<VoxT, false>(p, r, i + 1);  // in flight while i is shaded
-                st = shade_sample<VoxT, Fmt, MODE, false>(p, s_alpha, r, i, cur, C0, C1, C2, A,
-                                                          count, lit, nullptr);
-            }
+            if (active)
+                st = march_sample<VoxT, Fmt, MODE, false>(p, s_alpha, r, i, C0, C1, C2, A, count,
+                                                          lit, nullptr);
             active = active && (st == kContinue || st == kEmpty);
             const unsigned act = __ballot_sync(0xffffffffu, active);
             const unsigned emp = __ballot_sync(0xffffffffu, active && st == kEmpty);
@@ -347,7 +313,6 @@ __global__ void __launch_bounds__(kMarchThreads, VI_MARCH_MIN_BLOCKS)
                 to = __reduce_min_sync(0xffffffffu, next);
                 if (active) count += to - i - 1;  // the rest of the run: transparent
             }
-            if (active) cur = to == i + 1 ? nxt : fetch_sample<VoxT, false>(p, r, to);
             i = to;
         }
         if (valid) {
@@ -375,10 +340,8 @@ __global__ void trace_kernel(const MarchParams p, int x, int y, int32_t* rec, in
     if (r.hit) {
         for (int i = 0; nrec < max_rec; ++i) {
             int32_t* out = rec + (size_t)nrec * kTraceWords;
-            int cell[3];
-            const Fetched<VoxT> fs = fetch_sample<VoxT, true>(p, r, i, cell);
-            int st = shade_sample<VoxT, Fmt, MODE, true>(p, s_alpha, r, i, fs, C0, C1, C2, A, count,
-                                                         lit, out, cell);
+            int st = march_sample<VoxT, Fmt, MODE, true>(p, s_alpha, r, i, C0, C1, C2, A, count,
+                                                         lit, out);
             if (st == kEnded) break;
             ++nrec;
             if (st == kStopped) break;
