@@ -70,6 +70,11 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="ct256-cone",
+                    choices=["ct256-cone", "precision", "scalability"],
+                    help="ct256-cone: the headline frame; precision: storage formats on the "
+                         "512^3 blob scene vs the FP64 oracle; scalability: slice count x "
+                         "slice resolution grid")
     return ap.parse_args()
 
 
@@ -390,10 +395,133 @@ def gb300_arm(args):
     ctx.close()
 
 
+def timed_frames(ctx, build, render, flush, steps):
+    """Mean sweep and march ms over `steps` frames (CUDA events, L2 flushed)."""
+    import torch
+    sw, ma = [], []
+    for s in range(steps):
+        flush.fill_(s & 0xFF)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
+        build()
+        e[1].record()
+        render()
+        e[2].record()
+        torch.cuda.synchronize()
+        sw.append(e[0].elapsed_time(e[1]))
+        ma.append(e[1].elapsed_time(e[2]))
+    return statistics.mean(sw), statistics.mean(ma)
+
+
+def precision_workload(args):
+    """Storage formats FP32 / FP16 / BF16 / UNORM16 on the 512^3 blob scene:
+    frames/s of each and its per-channel error against the FP64 oracle on the
+    centred 256x144 crop (the oracle builds its own FP64 stack)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2008_06134_gb300 import build, phantoms as ph, vi
+    build.build()
+    oracle.build()
+    sc = ph.blob512_precision()
+    W, H = sc.width, sc.height
+    x0, y0 = (W - 256) // 2, (H - 144) // 2
+    ys, xs = np.mgrid[y0:y0 + 144, x0:x0 + 256]
+    t0 = time.perf_counter()
+    light = oracle.light_setup(sc.light_dir, sc.n_slices, sc.slice_res)
+    ref_stack = oracle.build_stack(sc.volume, sc.tf, sc.vmin, sc.vmax, light)
+    refs = {}
+    for mode in (vi.SHELL, vi.CONE):
+        ro = oracle.render_opts(mode, sc.step_vox, sc.ert, sc.bg, sc.light_color,
+                                cone_half_angle_deg=sc.cone_half_angle_deg)
+        refs[mode] = oracle.render_pixels(sc.volume, sc.tf, sc.vmin, sc.vmax, light, ref_stack,
+                                          sc.camera, W, H, ro, xs.ravel(), ys.ravel())[0]
+    oracle_s = time.perf_counter() - t0
+    del ref_stack
+    ctx = vi.Context(0)
+    ctx.load_volume(torch.from_numpy(sc.volume.view(np.int16)).cuda(), dtype=vi.U16)
+    ctx.set_transfer_function(sc.tf, sc.vmin, sc.vmax)
+    ctx.set_light(sc.light_dir, sc.light_color)
+    out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    names = {vi.F32: "f32", vi.F16: "f16", vi.BF16: "bf16", vi.UNORM16: "unorm16"}
+    rows = {}
+    for mode, mname in ((vi.SHELL, "shell"), (vi.CONE, "cone")):
+        for fmt in (vi.F32, vi.F16, vi.BF16, vi.UNORM16):
+            def bld():
+                ctx.build_attenuation(sc.n_slices, sc.slice_res, mode, format=fmt)
+
+            def rnd():
+                ctx.render(sc.camera, W, H, sc.step_vox, out=out, ert=sc.ert, bg=sc.bg)
+            for _ in range(args.warmup):
+                bld()
+                rnd()
+            sweep_ms, march_ms = timed_frames(ctx, bld, rnd, flush, args.steps)
+            img = out.cpu().numpy().astype(np.float64)[y0:y0 + 144, x0:x0 + 256].reshape(-1, 4)
+            err = np.abs(img - refs[mode])
+            rows[f"{mname}-{names[fmt]}"] = {
+                "frames_per_s": round(1000.0 / (sweep_ms + march_ms), 2),
+                "sweep_ms": round(sweep_ms, 4), "march_ms": round(march_ms, 4),
+                "max_abs_err_rgba": [float(f"{v:.3g}") for v in err.max(axis=0)],
+                "mean_abs_err_rgba": [float(f"{v:.3g}") for v in err.mean(axis=0)]}
+        base = rows[f"{mname}-f32"]["frames_per_s"]
+        for fmt in names.values():
+            rows[f"{mname}-{fmt}"]["gain_vs_f32"] = round(rows[f"{mname}-{fmt}"]["frames_per_s"]
+                                                          / base, 3)
+    print(json.dumps({"workload": "precision", "metric": "frames/s", "unit": "frames/s",
+                      "scene": sc.name, "steps": args.steps, "warmup": args.warmup,
+                      "error_reference": "FP64 oracle, centred 256x144 crop "
+                                         f"({oracle_s:.1f} s on {oracle.threads()} cores)",
+                      "results": rows}), flush=True)
+    ctx.close()
+
+
+def scalability_workload(args):
+    """Frame cost over slice counts {64, 128, 256} x slice resolutions {128, 256,
+    512}^2 on the 256^3 CT phantom at a 512x512 viewport, shell and cone."""
+    import numpy as np
+    import torch
+
+    from paper_2008_06134_gb300 import build, phantoms as ph, vi
+    build.build()
+    sc = ph.ct256_cone()
+    ctx = vi.Context(0)
+    ctx.load_volume(torch.from_numpy(sc.volume.view(np.int16)).cuda(), dtype=vi.U16)
+    ctx.set_transfer_function(sc.tf, sc.vmin, sc.vmax)
+    ctx.set_light(sc.light_dir, sc.light_color)
+    W = H = 512
+    out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    rows = []
+    for mode, mname in ((vi.SHELL, "shell"), (vi.CONE, "cone")):
+        for n in (64, 128, 256):
+            for R in (128, 256, 512):
+                def bld():
+                    ctx.build_attenuation(n, R, mode)
+
+                def rnd():
+                    ctx.render(sc.camera, W, H, sc.step_vox, out=out, ert=sc.ert, bg=sc.bg)
+                for _ in range(args.warmup):
+                    bld()
+                    rnd()
+                sweep_ms, march_ms = timed_frames(ctx, bld, rnd, flush, args.steps)
+                rows.append({"mode": mname, "slices": n, "slice_res": R,
+                             "sweep_ms": round(sweep_ms, 4), "march_ms": round(march_ms, 4),
+                             "frame_ms": round(sweep_ms + march_ms, 4)})
+    print(json.dumps({"workload": "scalability", "scene": "ct256-u16, 512x512 perspective, "
+                      "step 0.5, ERT 0.99", "steps": args.steps, "rows": rows}), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         reference_arm(args)
+    elif args.workload == "precision":
+        precision_workload(args)
+    elif args.workload == "scalability":
+        scalability_workload(args)
     else:
         gb300_arm(args)
 

@@ -43,12 +43,15 @@ __global__ void __launch_bounds__(kSweepBX* kSweepBY)
     for (int e = tid; e < p.M; e += kSweepBX * kSweepBY) s_alpha[e] = p.tf[e].w;
     __syncthreads();
 
-    // Block tile 32 x 8 texels; warp w covers columns 8 (w % 4) .. +7, rows
-    // 4 (w / 4) .. +3.
+    // Block tile 32 x 8 texels.  A warp covers TW x (32 / TW) texels, TW chosen
+    // so one row of its store is a whole 32-byte sector: 8 x 4 for FP32, 16 x 2
+    // for the 16-bit formats.
+    constexpr int TW = sizeof(typename Fmt::T) == 2 ? 16 : 8;
+    constexpr int TH = 32 / TW;
     const LightFrame& lt = p.lt;
     const int lane = tid & 31, warp = tid >> 5;
-    const int i = blockIdx.x * kSweepBX + (warp & 3) * 8 + (lane & 7);
-    const int j = blockIdx.y * kSweepBY + (warp >> 2) * 4 + (lane >> 3);
+    const int i = blockIdx.x * kSweepBX + (warp % (kSweepBX / TW)) * TW + (lane % TW);
+    const int j = blockIdx.y * kSweepBY + (warp / (kSweepBX / TW)) * TH + (lane / TW);
     if (i >= lt.R || j >= lt.R) return;
 
     // World position of texel (i, j) on the plane through the centre.

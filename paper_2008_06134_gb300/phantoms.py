@@ -255,6 +255,20 @@ def ct256_cone(seed: int = 2, n: int = 256, ert: float = 0.99) -> Scene:
                  (1.0, 1.0, 1.0), 256, 512, MODE_CONE, cam, 1024, 1024, 0.5, ert)
 
 
+def blob512_precision(seed: int = 3, n: int = 512, mode: int = MODE_CONE) -> Scene:
+    """512^3 uint16 Gaussian-blob phantom (the 64^3 generator scaled: sigma x 8,
+    centres in [0, 512), values x 256), the 256-entry random TF over [0, 65535],
+    512 light slices of 1024x1024, 1920x1080 perspective, step 0.5 voxel."""
+    vol = gaussian_blobs(n, seed, sigma_scale=n / 64.0, dtype=np.uint16, value_scale=256.0)
+    tf = tf_random_pl(256, seed)
+    drng = _child(seed, 2)
+    light = random_direction(drng)
+    view = random_direction(drng)
+    cam = orbit_camera(view, perspective=True, distance=2.6, fovy_deg=40.0)
+    return Scene(f"blob{n}-u16 512x1024^2 1920x1080-persp", vol, tf, 0.0, 65535.0, light,
+                 (1.0, 1.0, 1.0), 512, 1024, mode, cam, 1920, 1080, 0.5, 2.0)
+
+
 def unit(v) -> np.ndarray:
     v = np.asarray(v, dtype=np.float64)
     return v / math.sqrt(float(v @ v))
