@@ -71,10 +71,15 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="ct256-cone",
-                    choices=["ct256-cone", "precision", "scalability"],
+                    choices=["ct256-cone", "precision", "scalability", "serving"],
                     help="ct256-cone: the headline frame; precision: storage formats on the "
                          "512^3 blob scene vs the FP64 oracle; scalability: slice count x "
-                         "slice resolution grid")
+                         "slice resolution grid; serving: the render server on a stream of "
+                         "mixed requests")
+    ap.add_argument("--requests", type=int, default=512, help="serving: request count")
+    ap.add_argument("--rate", type=float, default=300.0, help="serving: arrivals per second")
+    ap.add_argument("--slots", type=int, default=8, help="serving: concurrent render slots")
+    ap.add_argument("--budget-gib", type=float, default=8.0, help="serving: HBM budget")
     return ap.parse_args()
 
 
@@ -514,6 +519,99 @@ def scalability_workload(args):
     ctx.close()
 
 
+def serving_workload(args):
+    """The render server on the serving mix: 8 registered volumes ({128, 256,
+    512}^3, uint8 blobs and uint16 CT ellipsoids) with at most 6 resident under
+    a fixed HBM budget, and a seeded stream of requests (256^2 to 1920x1080,
+    64-512 slices of 256^2 or 512^2, shadow / shell / cone, light and view
+    uniform on the sphere).  Runs: one slot with FP32 stacks (one frame at a
+    time: the plain path), and `--slots` concurrent slots with FP32 and with
+    FP16 stacks, each under Poisson arrivals at `--rate` and as one burst.
+    Reports per run frames/s and request latency (submission to completion)
+    percentiles; the FP32 served frames are compared with the plain ones."""
+    import numpy as np
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+
+    from paper_2008_06134_gb300 import build, phantoms as ph, vi
+    build.build()
+    specs = ph.serving_volumes()
+    t_gen = time.perf_counter()
+    with ThreadPoolExecutor(len(specs)) as ex:
+        arrays = list(ex.map(lambda v: v.generate(), specs))
+    t_gen = time.perf_counter() - t_gen
+    host = [torch.from_numpy(a.view(np.int16) if a.dtype == np.uint16 else a).pin_memory()
+            for a in arrays]
+    codes = [vi.U8 if a.dtype == np.uint8 else vi.U16 for a in arrays]
+    reqs = ph.serving_requests(len(specs), args.requests, args.rate)
+    budget = int(args.budget_gib * (1 << 30))
+
+    def submit(s, vids, q, out, fmt):
+        v = specs[q["volume"]]
+        return s.submit(vids[q["volume"]], v.tf, v.vmin, v.vmax, q["light_dir"], q["n_slices"],
+                        q["slice_res"], q["mode"], q["camera"], q["width"], q["height"],
+                        q["step_vox"], out, format=fmt, ert=q["ert"])
+
+    def run(slots, fmt, burst):
+        outs = [torch.empty((q["height"], q["width"], 4), device="cuda") for q in reqs]
+        with vi.Server(0, slots=slots, memory_budget=budget, max_resident_volumes=6) as s:
+            vids = [s.add_volume(h, c) for h, c in zip(host, codes)]
+            warm = torch.empty((64, 64, 4), device="cuda")
+            for i in range(len(specs)):           # untimed: load every volume once
+                q = dict(reqs[i % len(reqs)], volume=i, width=64, height=64)
+                assert s.wait(submit(s, vids, q, warm, fmt), 600000.0)[0] == vi.REQ_DONE
+            torch.cuda.synchronize()
+            base = s.stats()
+            t0 = time.perf_counter()
+            tickets = []
+            for q, out in zip(reqs, outs):
+                if not burst:
+                    delay = t0 + q["arrival_s"] - time.perf_counter()
+                    if delay > 0:
+                        time.sleep(delay)
+                tickets.append(submit(s, vids, q, out, fmt))
+            results = [s.wait(t, 600000.0) for t in tickets]
+            times = np.array([s.timing(t) for t in tickets])
+            st = s.stats()
+        failed = sum(r != (vi.REQ_DONE, vi.OK) for r in results)
+        lat = times[:, 2] - times[:, 0]
+        span_s = (times[:, 2].max() - times[:, 0].min()) / 1000.0
+        row = {"frames_per_s": round(len(reqs) / span_s, 1),
+               "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 3),
+                              "p99": round(float(np.percentile(lat, 99)), 3),
+                              "mean": round(float(lat.mean()), 3),
+                              "max": round(float(lat.max()), 3)},
+               "queue_wait_ms_p50": round(float(np.percentile(times[:, 1] - times[:, 0], 50)), 3),
+               "failed": failed,
+               "volume_loads": st["volume_loads"] - base["volume_loads"],
+               "volume_evictions": st["volume_evictions"] - base["volume_evictions"],
+               "stack_reuses": st["stack_reuses"] - base["stack_reuses"],
+               "peak_bytes": st["peak_bytes"]}
+        return row, outs
+
+    runs = {}
+    plain, plain_outs = run(1, vi.F32, burst=False)
+    runs["plain-f32-1slot-poisson"] = plain
+    for fmt, fname in ((vi.F32, "f32"), (vi.F16, "f16")):
+        row, outs = run(args.slots, fmt, burst=False)
+        if fmt == vi.F32:
+            row["frames_identical_to_plain"] = sum(bool(torch.equal(a, b))
+                                                   for a, b in zip(outs, plain_outs))
+        else:
+            row["max_abs_err_vs_plain_f32"] = float(f"{max(float((a - b).abs().max()) for a, b in zip(outs, plain_outs)):.3g}")
+        runs[f"served-{fname}-{args.slots}slots-poisson"] = row
+        del outs
+    for slots, name in ((1, "plain-f32-1slot-burst"), (args.slots, f"served-f32-{args.slots}slots-burst")):
+        runs[name] = run(slots, vi.F32, burst=True)[0]
+    print(json.dumps({"workload": "serving", "metric": "frames/s", "unit": "frames/s",
+                      "requests": len(reqs), "rate_per_s": args.rate, "slots": args.slots,
+                      "budget_bytes": budget, "max_resident_volumes": 6,
+                      "volumes": [v.name for v in specs],
+                      "mix": "256^2..1920x1080 perspective, 64-512 slices of 256^2/512^2, "
+                             "shadow/shell/cone, light and view uniform, step 0.5, ERT 0.99",
+                      "volume_generation_s": round(t_gen, 1), "runs": runs}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -522,6 +620,8 @@ def main():
         precision_workload(args)
     elif args.workload == "scalability":
         scalability_workload(args)
+    elif args.workload == "serving":
+        serving_workload(args)
     else:
         gb300_arm(args)
 

@@ -207,6 +207,92 @@ int vi_launch_count(vi_ctx* ctx, uint64_t* count);
 int vi_render_host_noalloc(vi_ctx* ctx, const vi_camera* camera, int W, int H, float step_vox,
                            float* out_rgba, const vi_render_opts* opts);
 
+/* ---- Serving: continuous batching of render requests ---------------------- */
+
+/* A render server on one device.  It is not in the paper (which renders one
+   frame at a time): requests arrive at any time and are admitted in arrival
+   order into `slots` concurrent render slots (each a context on its own CUDA
+   stream) whenever a slot is free and the device memory they need fits the
+   budget, so frames of different requests run on the GPU together.  Volumes
+   are registered once and kept resident (octets and brick ranges) up to
+   max_resident_volumes (0 = no count limit) and memory_budget bytes in total
+   with the slots' buffers (0 = no byte limit); the least recently used idle
+   volume is evicted when room is needed and reloaded from the caller's host
+   copy when next requested.  A request that can never fit fails with
+   VI_ENOMEM; others wait.  All host-side waits are bounded.
+   Each slot keeps the attenuation stack of its last request.  A request with
+   the same volume, TF (entries and range), light, stack shape, mode and build
+   options as a free slot's last one is placed on that slot and renders from
+   its stack without a new sweep (a new view of an unchanged scene). */
+typedef struct vi_server vi_server;
+
+enum { VI_REQ_QUEUED = 0, VI_REQ_RUNNING = 1, VI_REQ_DONE = 2, VI_REQ_FAILED = 3,
+       VI_REQ_CANCELLED = 4 };
+
+/* One frame: the same inputs as vi_set_transfer_function, vi_set_light,
+   vi_build_attenuation and vi_render on a registered volume.  The TF is
+   copied at submission; out_rgba (W*H*4 float32) must stay valid until the
+   request finishes (device memory, or host memory -- page-locked to overlap). */
+typedef struct {
+    int volume_id;
+    const float* tf_rgba;
+    int tf_entries;
+    float tf_vmin, tf_vmax;
+    float light_dir[3];
+    float light_color[3];
+    int n_slices, slice_res, mode;
+    vi_build_opts build;
+    vi_camera camera;
+    int width, height;
+    float step_vox;
+    vi_render_opts render;
+    float* out_rgba;
+    int out_on_device;
+} vi_request;
+
+typedef struct {
+    uint64_t submitted, completed, failed, cancelled;
+    uint64_t volume_loads, volume_evictions;
+    int queued, running, resident_volumes;
+    size_t bytes_in_use, peak_bytes;
+    uint64_t stack_reuses;  /* requests that rendered from a slot's kept stack */
+} vi_server_stats;
+
+/* Create / destroy a server (destroy cancels queued requests, lets running
+   ones finish, and frees everything). */
+int vi_server_create(vi_server** out, int device, int slots, size_t memory_budget,
+                     int max_resident_volumes);
+int vi_server_destroy(vi_server* server);
+
+/* Register a volume (as vi_load_volume: data[z][y][x], VI_U8 / VI_U16).  The
+   host data must stay valid and unchanged while the server lives: it is
+   (re)loaded from it on demand, and kept stacks built from it are reused.
+   *volume_id receives its id. */
+int vi_server_add_volume(vi_server* server, const void* host_data, int dtype, int nx, int ny,
+                         int nz, int* volume_id);
+
+/* Queue a request; *ticket names it.  Malformed requests return VI_EINVAL
+   and are not queued. */
+int vi_server_submit(vi_server* server, const vi_request* request, uint64_t* ticket);
+
+/* Wait up to timeout_ms for the request to finish (VI_ETIMEOUT otherwise);
+   *status receives a VI_REQ_* state and *result its vi_status. */
+int vi_server_wait(vi_server* server, uint64_t ticket, double timeout_ms, int* status,
+                   int* result);
+
+/* Cancel a request that is still queued (VI_ESTATE once it has started). */
+int vi_server_cancel(vi_server* server, uint64_t ticket);
+
+/* Milliseconds since server creation at which the request was submitted,
+   started on a slot, and finished (0 until then). */
+int vi_server_timing(vi_server* server, uint64_t ticket, double* submit_ms, double* start_ms,
+                     double* end_ms);
+
+/* Forget a finished request (VI_ESTATE if it has not finished). */
+int vi_server_release(vi_server* server, uint64_t ticket);
+
+int vi_server_get_stats(vi_server* server, vi_server_stats* stats);
+
 #ifdef __cplusplus
 }
 #endif

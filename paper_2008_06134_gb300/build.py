@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvi.so")
-SOURCES = ["vi_api.cu", "vi_sweep.cu", "vi_march.cu", "vi_grid.cu"]
+SOURCES = ["vi_api.cu", "vi_sweep.cu", "vi_march.cu", "vi_grid.cu", "vi_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

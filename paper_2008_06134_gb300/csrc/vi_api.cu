@@ -10,70 +10,12 @@
 #include <new>
 #include <vector>
 
-#include "../../include/vi.h"
-#include "vi_internal.h"
+#include "vi_context.h"
 
 using vi::CameraFrame;
 using vi::LightFrame;
 using vi::MarchParams;
 using vi::SweepParams;
-
-struct vi_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    int sticky = VI_OK;
-    uint64_t launches = 0;
-
-    size_t budget = 0;  // 0 = unlimited
-    size_t used = 0;
-
-    void* raw = nullptr;  // the volume as loaded: [nz][ny][nx]
-    size_t raw_cap = 0;
-    void* vol = nullptr;  // footprint octets built from it (8 voxels per element)
-    size_t vol_cap = 0;
-    int vtype = -1, nx = 0, ny = 0, nz = 0;
-
-    float4* tf = nullptr;
-    size_t tf_cap = 0;
-    int M = 0;
-    float vmin = 0.0f, vmax = 1.0f;
-
-    // Brick occupancy (empty-space skipping): per-brick value range (from the
-    // volume), prefix count of TF entries with alpha > 0, per-brick flags.
-    uint32_t* brange = nullptr;
-    size_t brange_cap = 0;
-    int* tfcnt = nullptr;
-    size_t tfcnt_cap = 0;
-    uint8_t* bflags = nullptr;
-    size_t bflags_cap = 0;
-    int nbx = 0, nby = 0, nbz = 0;
-    bool flags_ok = false;  // bflags match the current volume and TF
-
-    bool has_light = false;
-    float dir[3] = {0.0f, 0.0f, 1.0f};
-    float color[3] = {1.0f, 1.0f, 1.0f};
-
-    void* stack_mem = nullptr;   // allocation; the stack starts at the next 512-byte boundary
-    size_t stack_cap = 0;
-    void* stack = nullptr;
-    size_t stack_bytes = 0;      // dense size n R^2 element bytes, as vi_get_attenuation returns
-    size_t row_pitch = 0;        // bytes per stack row (pitched layout, R + 1 rows per slice)
-    vi::StackView sview{};       // texture views of the stack
-    int ntex = 0;
-    int stack_valid_shape_n = 0; // slice count the texture views were made for
-    int mode = -1;          // mode of the last build; -1 = none yet
-    bool stack_valid = false;
-    vi_build_opts bopts{};
-    LightFrame lt{};
-    bool lt_valid = false;
-
-    float4* out = nullptr;  // staging for host-memory output
-    size_t out_cap = 0;
-    int32_t* trace = nullptr;
-    size_t trace_cap = 0;
-    unsigned* counter = nullptr;  // tile counter of the persistent march kernel
-    size_t counter_cap = 0;
-};
 
 namespace {
 
@@ -188,7 +130,7 @@ int camera_frame(const vi_camera* cam, int W, int H, float step_vox, int nmax, C
 size_t voxel_bytes(int t) { return t == VI_U8 ? 1 : 2; }
 size_t format_bytes(int f) { return f == VI_F32 ? 4 : 2; }
 
-int nmax(const vi_ctx* c) { return std::max(c->nx, std::max(c->ny, c->nz)); }
+int nmax(const vi_ctx* c) { return std::max(c->vr->nx, std::max(c->vr->ny, c->vr->nz)); }
 
 vi_build_opts default_build_opts() {
     vi_build_opts o;
@@ -213,32 +155,12 @@ int cuda_fail(vi_ctx* c, cudaError_t e) {
     return VI_ECUDA;
 }
 
-// Grow a device buffer to `bytes` under the budget; keeps the old one on failure.
+// Grow a device buffer to `bytes` under the context's budget.
 int ensure(vi_ctx* c, void** p, size_t* cap, size_t bytes) {
-    if (bytes <= *cap && *p) return VI_OK;
-    size_t after = c->used - *cap + bytes;
-    if (c->budget && after > c->budget) return VI_ENOMEM;
-    void* q = nullptr;
-    if (cudaMalloc(&q, bytes) != cudaSuccess) {
-        cudaGetLastError();
-        return VI_ENOMEM;
-    }
-    if (*p) {
-        cudaStreamSynchronize(c->stream);
-        cudaFree(*p);
-    }
-    *p = q;
-    c->used = after;
-    *cap = bytes;
-    return VI_OK;
+    return vi_detail::ensure_mem(&c->used, c->budget, p, cap, bytes, c->stream);
 }
 
-void release(vi_ctx* c, void** p, size_t* cap) {
-    if (*p) cudaFree(*p);
-    c->used -= *cap;
-    *p = nullptr;
-    *cap = 0;
-}
+void release(vi_ctx* c, void** p, size_t* cap) { vi_detail::release_mem(&c->used, p, cap); }
 
 // Common prologue of every call on a context.
 int enter(vi_ctx* c) {
@@ -323,35 +245,36 @@ int setup_stack(vi_ctx* c, int n, int R, int fmt) {
     return VI_OK;
 }
 
-int nbricks(const vi_ctx* c) { return c->nbx * c->nby * c->nbz; }
+int nbricks(const vi_ctx* c) { return c->vr->nbx * c->vr->nby * c->vr->nbz; }
 
 vi::VolumeView volume_view(const vi_ctx* c) {
+    const VolumeRes* r = c->vr;
     vi::VolumeView v;
-    v.data = c->vol;
-    v.nx = c->nx;
-    v.ny = c->ny;
-    v.nz = c->nz;
-    v.fnx = (float)c->nx;
-    v.fny = (float)c->ny;
-    v.fnz = (float)c->nz;
+    v.data = r->oct;
+    v.nx = r->nx;
+    v.ny = r->ny;
+    v.nz = r->nz;
+    v.fnx = (float)r->nx;
+    v.fny = (float)r->ny;
+    v.fnz = (float)r->nz;
     return v;
 }
 
 vi::GridView grid_view(const vi_ctx* c) {
     vi::GridView g;
     g.flags = c->bflags;
-    g.nbx = c->nbx;
-    g.nby = c->nby;
+    g.nbx = c->vr->nbx;
+    g.nby = c->vr->nby;
     return g;
 }
 
 // Brick flags from the current brick ranges and TF (both must be present).
 int refresh_flags(vi_ctx* c) {
     c->flags_ok = false;
-    if (!c->brange || !c->tfcnt || !c->vol || !c->tf) return VI_OK;
+    if (!c->vr->brange || !c->tfcnt || c->vr->vtype < 0 || !c->tf) return VI_OK;
     int rc = ensure(c, reinterpret_cast<void**>(&c->bflags), &c->bflags_cap, (size_t)nbricks(c));
     if (rc) return rc;
-    cudaError_t e = vi::launch_brick_flags(c->brange, nbricks(c), c->tfcnt, c->M, c->vmin,
+    cudaError_t e = vi::launch_brick_flags(c->vr->brange, nbricks(c), c->tfcnt, c->M, c->vmin,
                                            c->vmax, c->bflags, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e);
     ++c->launches;
@@ -416,7 +339,7 @@ int check_render_inputs(vi_ctx* c, const vi_camera* cam, int W, int H, float ste
     if (!std::isfinite(ro->ert) || !std::isfinite(ro->ambient)) return VI_EINVAL;
     for (int k = 0; k < 4; ++k)
         if (!std::isfinite(ro->bg[k])) return VI_EINVAL;
-    if (!c->vol || !c->tf || !c->flags_ok || c->mode < 0) return VI_ESTATE;
+    if (c->vr->vtype < 0 || !c->tf || !c->flags_ok || c->mode < 0) return VI_ESTATE;
     if (c->mode != VI_NONE && !c->stack_valid) return VI_ESTATE;
     // A ray crosses at most sqrt(3) of the cube: cap its sample count at 2^24.
     if (1.7320509 * (double)nmax(c) / (double)step_vox > 16777216.0) return VI_EINVAL;
@@ -424,6 +347,139 @@ int check_render_inputs(vi_ctx* c, const vi_camera* cam, int W, int H, float ste
 }
 
 }  // namespace
+
+namespace vi_detail {
+
+int ensure_mem(size_t* used, size_t budget, void** p, size_t* cap, size_t bytes, cudaStream_t s) {
+    if (bytes <= *cap && *p) return VI_OK;
+    size_t after = *used - *cap + bytes;
+    if (budget && after > budget) return VI_ENOMEM;
+    void* q = nullptr;
+    if (cudaMalloc(&q, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return VI_ENOMEM;
+    }
+    if (*p) {
+        cudaStreamSynchronize(s);
+        cudaFree(*p);
+    }
+    *p = q;
+    *used = after;
+    *cap = bytes;
+    return VI_OK;
+}
+
+void release_mem(size_t* used, void** p, size_t* cap) {
+    if (*p) cudaFree(*p);
+    *used -= *cap;
+    *p = nullptr;
+    *cap = 0;
+}
+
+size_t volume_bytes(int dtype, int nx, int ny, int nz) {
+    constexpr int B = 1 << vi::kBrickShift;
+    const size_t raw = (size_t)nx * (size_t)ny * (size_t)nz * voxel_bytes(dtype);
+    const size_t bricks = (size_t)((nx + B - 1) / B) * ((ny + B - 1) / B) * ((nz + B - 1) / B);
+    return raw + 8 * raw + bricks * sizeof(uint32_t);
+}
+
+int volume_load(VolumeRes* v, size_t* used, size_t budget, const void* data, int dtype, int nx,
+                int ny, int nz, int data_on_device, cudaStream_t s, uint64_t* launches) {
+    const size_t bytes = (size_t)nx * (size_t)ny * (size_t)nz * voxel_bytes(dtype);
+    constexpr int B = 1 << vi::kBrickShift;
+    const int nbx = (nx + B - 1) / B, nby = (ny + B - 1) / B, nbz = (nz + B - 1) / B;
+    // Check the whole footprint first, so a refusal leaves the old volume intact.
+    const size_t have = std::max(v->raw_cap, bytes) - v->raw_cap +
+                        std::max(v->oct_cap, 8 * bytes) - v->oct_cap +
+                        std::max(v->brange_cap, (size_t)nbx * nby * nbz * sizeof(uint32_t)) -
+                        v->brange_cap;
+    if (budget && *used + have > budget) return VI_ENOMEM;
+    int rc = ensure_mem(used, budget, &v->raw, &v->raw_cap, bytes, s);
+    if (rc) return rc;
+    rc = ensure_mem(used, budget, &v->oct, &v->oct_cap, 8 * bytes, s);
+    if (rc) return rc;
+    rc = ensure_mem(used, budget, reinterpret_cast<void**>(&v->brange), &v->brange_cap,
+                    (size_t)nbx * nby * nbz * sizeof(uint32_t), s);
+    if (rc) return rc;
+    v->vtype = -1;
+    cudaError_t e = cudaMemcpyAsync(v->raw, data, bytes,
+                                    data_on_device ? cudaMemcpyDeviceToDevice
+                                                   : cudaMemcpyHostToDevice,
+                                    s);
+    if (e == cudaSuccess) e = vi::launch_build_octets(v->raw, nx, ny, nz, dtype, v->oct, s);
+    if (e == cudaSuccess) e = vi::launch_brick_range(v->raw, nx, ny, nz, dtype, v->brange, s);
+    if (e != cudaSuccess) return VI_ECUDA;
+    if (launches) *launches += 2;
+    v->vtype = dtype;
+    v->nx = nx;
+    v->ny = ny;
+    v->nz = nz;
+    v->nbx = nbx;
+    v->nby = nby;
+    v->nbz = nbz;
+    return VI_OK;
+}
+
+void volume_release(VolumeRes* v, size_t* used) {
+    release_mem(used, &v->raw, &v->raw_cap);
+    release_mem(used, &v->oct, &v->oct_cap);
+    release_mem(used, reinterpret_cast<void**>(&v->brange), &v->brange_cap);
+    v->vtype = -1;
+}
+
+int ctx_bind_volume(vi_ctx* c, VolumeRes* v, bool keep_stack) {
+    int rc = enter(c);
+    if (rc) return rc;
+    if (!v || v->vtype < 0) return VI_EINVAL;
+    if (!keep_stack || c->vr != v) mark_stale(c);
+    c->vr = v;
+    c->flags_ok = false;
+    return refresh_flags(c);
+}
+
+void ctx_trim(vi_ctx* c) {
+    cudaStreamSynchronize(c->stream);
+    destroy_stack_textures(c);
+    release(c, &c->stack_mem, &c->stack_cap);
+    release(c, reinterpret_cast<void**>(&c->out), &c->out_cap);
+    c->stack = nullptr;
+    mark_stale(c);
+}
+
+int ctx_render_async(vi_ctx* c, const vi_camera* cam, int W, int H, float step_vox, float* out,
+                     int out_on_device, const vi_render_opts* opts) {
+    int rc = enter(c);
+    if (rc) return rc;
+    vi_render_opts ro = opts ? *opts : default_render_opts();
+    rc = check_render_inputs(c, cam, W, H, step_vox, &ro);
+    if (rc) return rc;
+    if (W == 0 || H == 0) return VI_OK;
+    if (!out) return VI_EINVAL;
+    MarchParams p;
+    rc = fill_march_params(c, cam, W, H, step_vox, &ro, &p);
+    if (rc) return rc;
+    rc = ensure(c, reinterpret_cast<void**>(&c->counter), &c->counter_cap, 256);
+    if (rc) return rc;
+    p.tile_counter = c->counter;
+    size_t bytes = (size_t)W * (size_t)H * sizeof(float4);
+    if (out_on_device) {
+        p.out = reinterpret_cast<float4*>(out);
+    } else {
+        rc = ensure(c, reinterpret_cast<void**>(&c->out), &c->out_cap, bytes);
+        if (rc) return rc;
+        p.out = c->out;
+    }
+    cudaError_t e = vi::launch_march(p, c->vr->vtype, c->bopts.format, c->mode, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    ++c->launches;
+    if (!out_on_device) {
+        e = cudaMemcpyAsync(out, c->out, bytes, cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+    }
+    return VI_OK;
+}
+
+}  // namespace vi_detail
 
 extern "C" {
 
@@ -466,14 +522,12 @@ int vi_destroy(vi_ctx* c) {
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     cudaGetLastError();
-    release(c, &c->raw, &c->raw_cap);
-    release(c, &c->vol, &c->vol_cap);
+    vi_detail::volume_release(&c->own, &c->used);
     release(c, reinterpret_cast<void**>(&c->tf), &c->tf_cap);
     destroy_stack_textures(c);
     release(c, &c->stack_mem, &c->stack_cap);
     release(c, reinterpret_cast<void**>(&c->out), &c->out_cap);
     release(c, reinterpret_cast<void**>(&c->trace), &c->trace_cap);
-    release(c, reinterpret_cast<void**>(&c->brange), &c->brange_cap);
     release(c, reinterpret_cast<void**>(&c->tfcnt), &c->tfcnt_cap);
     release(c, reinterpret_cast<void**>(&c->bflags), &c->bflags_cap);
     release(c, reinterpret_cast<void**>(&c->counter), &c->counter_cap);
@@ -493,36 +547,13 @@ int vi_load_volume(vi_ctx* c, const void* data, int dtype, int nx, int ny, int n
     if (rc) return rc;
     if (!data || (dtype != VI_U8 && dtype != VI_U16)) return VI_EINVAL;
     if (nx < 1 || ny < 1 || nz < 1 || nx > 65536 || ny > 65536 || nz > 65536) return VI_EINVAL;
-    size_t bytes = (size_t)nx * (size_t)ny * (size_t)nz * voxel_bytes(dtype);
-    rc = ensure(c, &c->raw, &c->raw_cap, bytes);
-    if (rc) return rc;
-    rc = ensure(c, &c->vol, &c->vol_cap, 8 * bytes);
-    if (rc) return rc;
+    rc = vi_detail::volume_load(&c->own, &c->used, c->budget, data, dtype, nx, ny, nz,
+                                data_on_device, c->stream, &c->launches);
+    if (rc == VI_ECUDA) c->sticky = VI_ECUDA;
+    if (rc) return rc;  // a budget refusal leaves the previous volume in place
+    c->vr = &c->own;
     c->flags_ok = false;
-    c->vtype = -1;
-    cudaError_t e = cudaMemcpyAsync(c->raw, data, bytes,
-                                    data_on_device ? cudaMemcpyDeviceToDevice
-                                                   : cudaMemcpyHostToDevice,
-                                    c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e);
-    e = vi::launch_build_octets(c->raw, nx, ny, nz, dtype, c->vol, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e);
-    ++c->launches;
-    c->vtype = dtype;
-    c->nx = nx;
-    c->ny = ny;
-    c->nz = nz;
     mark_stale(c);
-    constexpr int B = 1 << vi::kBrickShift;
-    c->nbx = (nx + B - 1) / B;
-    c->nby = (ny + B - 1) / B;
-    c->nbz = (nz + B - 1) / B;
-    rc = ensure(c, reinterpret_cast<void**>(&c->brange), &c->brange_cap,
-                (size_t)nbricks(c) * sizeof(uint32_t));
-    if (rc) return rc;
-    e = vi::launch_brick_range(c->raw, nx, ny, nz, dtype, c->brange, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e);
-    ++c->launches;
     return refresh_flags(c);
 }
 
@@ -585,7 +616,7 @@ int vi_build_attenuation(vi_ctx* c, int n, int R, int mode, const vi_build_opts*
     if (!(o.cone_half_angle_deg > 0.0f && o.cone_half_angle_deg < 90.0f)) return VI_EINVAL;
     if (!(o.shell_radius_vox > 0.0f) || !std::isfinite(o.shell_radius_vox)) return VI_EINVAL;
     if (!(o.comp_n >= 0.0f) || !std::isfinite(o.comp_n)) return VI_EINVAL;
-    if (!c->vol || !c->tf || !c->flags_ok) return VI_ESTATE;
+    if (c->vr->vtype < 0 || !c->tf || !c->flags_ok) return VI_ESTATE;
     if (mode != VI_NONE && !c->has_light) return VI_ESTATE;
 
     LightFrame lt{};
@@ -622,7 +653,7 @@ int vi_build_attenuation(vi_ctx* c, int n, int R, int mode, const vi_build_opts*
     p.opacity_correction = o.opacity_correction ? 1 : 0;
     p.spacing_vox = lt.dL * (float)nmax(c);
     p.comp_n = o.comp_n;
-    cudaError_t e = vi::launch_sweep(p, c->vtype, o.format, c->stream);
+    cudaError_t e = vi::launch_sweep(p, c->vr->vtype, o.format, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e);
     ++c->launches;
     c->mode = mode;
@@ -636,37 +667,9 @@ int vi_build_attenuation(vi_ctx* c, int n, int R, int mode, const vi_build_opts*
 
 int vi_render(vi_ctx* c, const vi_camera* cam, int W, int H, float step_vox, float* out,
               int out_on_device, const vi_render_opts* opts) {
-    int rc = enter(c);
-    if (rc) return rc;
-    vi_render_opts ro = opts ? *opts : default_render_opts();
-    rc = check_render_inputs(c, cam, W, H, step_vox, &ro);
-    if (rc) return rc;
-    if (W == 0 || H == 0) return VI_OK;
-    if (!out) return VI_EINVAL;
-    MarchParams p;
-    rc = fill_march_params(c, cam, W, H, step_vox, &ro, &p);
-    if (rc) return rc;
-    rc = ensure(c, reinterpret_cast<void**>(&c->counter), &c->counter_cap, 256);
-    if (rc) return rc;
-    p.tile_counter = c->counter;
-    size_t bytes = (size_t)W * (size_t)H * sizeof(float4);
-    if (out_on_device) {
-        p.out = reinterpret_cast<float4*>(out);
-    } else {
-        rc = ensure(c, reinterpret_cast<void**>(&c->out), &c->out_cap, bytes);
-        if (rc) return rc;
-        p.out = c->out;
-    }
-    cudaError_t e = vi::launch_march(p, c->vtype, c->bopts.format, c->mode, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e);
-    ++c->launches;
-    if (!out_on_device) {
-        e = cudaMemcpyAsync(out, c->out, bytes, cudaMemcpyDeviceToHost, c->stream);
-        if (e != cudaSuccess) return cuda_fail(c, e);
-        e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) return cuda_fail(c, e);
-    }
-    return VI_OK;
+    int rc = vi_detail::ctx_render_async(c, cam, W, H, step_vox, out, out_on_device, opts);
+    if (rc || out_on_device || W == 0 || H == 0) return rc;
+    return cuda_fail(c, cudaStreamSynchronize(c->stream));
 }
 
 int vi_sync(vi_ctx* c) {
@@ -734,7 +737,7 @@ int vi_trace_pixel(vi_ctx* c, const vi_camera* cam, int W, int H, float step_vox
     if (rc) return rc;
     int32_t* d_rec = c->trace + 1;
     int* d_n = reinterpret_cast<int*>(c->trace);
-    cudaError_t e = vi::launch_trace(p, c->vtype, c->bopts.format, c->mode, x, y, d_rec, max_rec,
+    cudaError_t e = vi::launch_trace(p, c->vr->vtype, c->bopts.format, c->mode, x, y, d_rec, max_rec,
                                      d_n, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e);
     ++c->launches;
@@ -771,7 +774,7 @@ int vi_render_host_noalloc(vi_ctx* c, const vi_camera* cam, int W, int H, float 
     if (e != cudaSuccess) return cuda_fail(c, e);
     p.tile_counter = counter;  // zeroed on the stream by the launch
     p.out = image;
-    e = vi::launch_march(p, c->vtype, c->bopts.format, c->mode, c->stream);
+    e = vi::launch_march(p, c->vr->vtype, c->bopts.format, c->mode, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e);
     ++c->launches;
     e = cudaMemcpyAsync(out, image, (size_t)W * (size_t)H * sizeof(float4),

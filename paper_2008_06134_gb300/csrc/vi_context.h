@@ -1,0 +1,103 @@
+// vi_context.h -- the context behind vi_ctx and the pieces of it the server
+// shares; internal to the library.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/vi.h"
+#include "vi_internal.h"
+
+// A loaded volume: the voxels as given ([nz][ny][nx]), their footprint octets
+// and the per-brick value ranges.  A context owns one (vi_load_volume); a
+// server owns several and lends them to its render slots.
+struct VolumeRes {
+    void* raw = nullptr;
+    size_t raw_cap = 0;
+    void* oct = nullptr;  // footprint octets (8 voxels per element)
+    size_t oct_cap = 0;
+    uint32_t* brange = nullptr;
+    size_t brange_cap = 0;
+    int vtype = -1, nx = 0, ny = 0, nz = 0;
+    int nbx = 0, nby = 0, nbz = 0;
+};
+
+struct vi_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int sticky = VI_OK;
+    uint64_t launches = 0;
+
+    size_t budget = 0;  // 0 = unlimited
+    size_t used = 0;
+
+    VolumeRes own;          // the volume vi_load_volume loads
+    VolumeRes* vr = &own;   // the volume in use: own, or one a server shares
+
+    float4* tf = nullptr;
+    size_t tf_cap = 0;
+    int M = 0;
+    float vmin = 0.0f, vmax = 1.0f;
+
+    // Brick occupancy (empty-space skipping): prefix count of TF entries with
+    // alpha > 0 and per-brick flags (the value ranges belong to the volume).
+    int* tfcnt = nullptr;
+    size_t tfcnt_cap = 0;
+    uint8_t* bflags = nullptr;
+    size_t bflags_cap = 0;
+    bool flags_ok = false;  // bflags match the current volume and TF
+
+    bool has_light = false;
+    float dir[3] = {0.0f, 0.0f, 1.0f};
+    float color[3] = {1.0f, 1.0f, 1.0f};
+
+    void* stack_mem = nullptr;   // allocation; the stack starts at the next 512-byte boundary
+    size_t stack_cap = 0;
+    void* stack = nullptr;
+    size_t stack_bytes = 0;      // dense size n R^2 element bytes, as vi_get_attenuation returns
+    size_t row_pitch = 0;        // bytes per stack row (pitched layout, R + 1 rows per slice)
+    vi::StackView sview{};       // texture views of the stack
+    int ntex = 0;
+    int stack_valid_shape_n = 0; // slice count the texture views were made for
+    int mode = -1;          // mode of the last build; -1 = none yet
+    bool stack_valid = false;
+    vi_build_opts bopts{};
+    vi::LightFrame lt{};
+    bool lt_valid = false;
+
+    float4* out = nullptr;  // staging for host-memory output
+    size_t out_cap = 0;
+    int32_t* trace = nullptr;
+    size_t trace_cap = 0;
+    unsigned* counter = nullptr;  // tile counter of the persistent march kernel
+    size_t counter_cap = 0;
+};
+
+namespace vi_detail {
+
+// Device allocation under a byte budget (0 = none) with a usage counter; keeps
+// the old buffer on failure.  Frees the old one after `s` drains.
+int ensure_mem(size_t* used, size_t budget, void** p, size_t* cap, size_t bytes, cudaStream_t s);
+void release_mem(size_t* used, void** p, size_t* cap);
+
+// Loads nx*ny*nz voxels into v (octets and brick ranges built on stream s).
+int volume_load(VolumeRes* v, size_t* used, size_t budget, const void* data, int dtype, int nx,
+                int ny, int nz, int data_on_device, cudaStream_t s, uint64_t* launches);
+void volume_release(VolumeRes* v, size_t* used);
+size_t volume_bytes(int dtype, int nx, int ny, int nz);
+
+// Points the context at a volume it does not own and refreshes the brick
+// flags.  The stack goes stale unless keep_stack is set and the context was
+// already on v (the caller vouches that v holds the same voxels).
+int ctx_bind_volume(vi_ctx* c, VolumeRes* v, bool keep_stack);
+
+// Frees the stack and the output staging of an idle context (its next build
+// allocates them again).
+void ctx_trim(vi_ctx* c);
+
+// vi_render without waiting: host output is copied asynchronously (a pinned
+// buffer overlaps; a pageable one makes the copy synchronous).
+int ctx_render_async(vi_ctx* c, const vi_camera* cam, int W, int H, float step_vox, float* out,
+                     int out_on_device, const vi_render_opts* opts);
+
+}  // namespace vi_detail

@@ -272,3 +272,71 @@ def blob512_precision(seed: int = 3, n: int = 512, mode: int = MODE_CONE) -> Sce
 def unit(v) -> np.ndarray:
     v = np.asarray(v, dtype=np.float64)
     return v / math.sqrt(float(v @ v))
+
+
+# ---- Serving mix: many volumes, a stream of requests -------------------------
+
+SERVING_SIZES = ((256, 256), (512, 512), (1024, 768), (1280, 720), (1920, 1080))
+
+
+@dataclasses.dataclass
+class ServedVolume:
+    """One registered volume of the serving mix with its transfer function."""
+    name: str
+    n: int
+    kind: str          # "blob-u8" or "ellipsoid-u16"
+    seed: int
+    tf: np.ndarray
+    vmin: float
+    vmax: float
+
+    def generate(self) -> np.ndarray:
+        if self.kind == "blob-u8":
+            return gaussian_blobs(self.n, self.seed, sigma_scale=self.n / 64.0)
+        return ct_phantom(self.n, self.seed)
+
+
+def serving_volumes(seed: int = 4) -> list:
+    """The volumes of the serving mix: {128, 256, 512}^3 x {uint8 Gaussian
+    blobs with a 256-entry random TF, uint16 CT ellipsoids with the 4096-entry
+    CT TF}, plus a second 128^3 blob and 256^3 ellipsoid (8 volumes, so that a
+    residency limit of 6 forces evictions).  Volumes are generated on demand
+    (``generate``); each has its own seed derived from ``seed``."""
+    out = []
+    specs = [(128, "blob-u8"), (128, "ellipsoid-u16"), (256, "blob-u8"), (256, "ellipsoid-u16"),
+             (512, "blob-u8"), (512, "ellipsoid-u16"), (128, "blob-u8"), (256, "ellipsoid-u16")]
+    for i, (n, kind) in enumerate(specs):
+        s = 100 * seed + i
+        if kind == "blob-u8":
+            out.append(ServedVolume(f"blob{n}-u8#{i}", n, kind, s, tf_random_pl(256, s), 0.0,
+                                    255.0))
+        else:
+            out.append(ServedVolume(f"ct{n}-u16#{i}", n, kind, s, tf_ct(4096, s), 0.0, 4095.0))
+    return out
+
+
+def serving_requests(n_volumes: int, count: int = 512, rate_per_s: float = 300.0,
+                     seed: int = 4) -> list:
+    """``count`` render requests with Poisson arrivals at ``rate_per_s``.
+
+    Each request draws, in this order: the inter-arrival gap ~ Exp(rate), the
+    volume uniformly, the image size from SERVING_SIZES, the slice count from
+    {64, 128, 256, 512}, the slice resolution from {256, 512}, the mode from
+    {shadow, shell, cone}, and the light and view directions uniformly on the
+    sphere (perspective camera 2.6 from the centre, fovy 40 deg).  Step 0.5
+    voxel, early ray termination at 0.99."""
+    rng = _child(seed, 3)
+    t = 0.0
+    reqs = []
+    for _ in range(count):
+        t += float(rng.exponential(1.0 / rate_per_s))
+        vol = int(rng.integers(n_volumes))
+        W, H = SERVING_SIZES[int(rng.integers(len(SERVING_SIZES)))]
+        n = int((64, 128, 256, 512)[rng.integers(4)])
+        R = int((256, 512)[rng.integers(2)])
+        mode = int((MODE_SHADOW, MODE_SHELL, MODE_CONE)[rng.integers(3)])
+        light = random_direction(rng)
+        cam = orbit_camera(random_direction(rng), perspective=True, distance=2.6, fovy_deg=40.0)
+        reqs.append(dict(arrival_s=t, volume=vol, width=W, height=H, n_slices=n, slice_res=R,
+                         mode=mode, light_dir=light, camera=cam, step_vox=0.5, ert=0.99))
+    return reqs

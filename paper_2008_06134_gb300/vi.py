@@ -29,7 +29,10 @@ TRACE_NONE = 0x7FFFFFFF
 EXPORTS = ("vi_create", "vi_destroy", "vi_set_memory_budget", "vi_load_volume",
            "vi_set_transfer_function", "vi_set_light", "vi_build_attenuation", "vi_render",
            "vi_sync", "vi_error_string", "vi_attenuation_info", "vi_get_attenuation",
-           "vi_trace_pixel", "vi_launch_count", "vi_render_host_noalloc")
+           "vi_trace_pixel", "vi_launch_count", "vi_render_host_noalloc", "vi_server_create",
+           "vi_server_destroy", "vi_server_add_volume", "vi_server_submit", "vi_server_wait",
+           "vi_server_cancel", "vi_server_timing", "vi_server_release", "vi_server_get_stats")
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = 0, 1, 2, 3, 4
 
 
 class ViError(RuntimeError):
@@ -53,6 +56,23 @@ class RenderOpts(C.Structure):
     _fields_ = [("ert", C.c_float), ("bg", C.c_float * 4), ("ambient", C.c_float),
                 ("opacity_correction", C.c_int), ("sample_counts", C.c_void_p),
                 ("lit_counts", C.c_void_p)]
+
+
+class Request(C.Structure):
+    _fields_ = [("volume_id", C.c_int), ("tf_rgba", C.c_void_p), ("tf_entries", C.c_int),
+                ("tf_vmin", C.c_float), ("tf_vmax", C.c_float), ("light_dir", C.c_float * 3),
+                ("light_color", C.c_float * 3), ("n_slices", C.c_int), ("slice_res", C.c_int),
+                ("mode", C.c_int), ("build", BuildOpts), ("camera", Camera), ("width", C.c_int),
+                ("height", C.c_int), ("step_vox", C.c_float), ("render", RenderOpts),
+                ("out_rgba", C.c_void_p), ("out_on_device", C.c_int)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
+                ("cancelled", C.c_uint64), ("volume_loads", C.c_uint64),
+                ("volume_evictions", C.c_uint64), ("queued", C.c_int), ("running", C.c_int),
+                ("resident_volumes", C.c_int), ("bytes_in_use", C.c_size_t),
+                ("peak_bytes", C.c_size_t), ("stack_reuses", C.c_uint64)]
 
 
 _lib = None
@@ -85,6 +105,16 @@ def library() -> C.CDLL:
     L.vi_trace_pixel.argtypes = [vp, P(Camera), i, i, f, P(RenderOpts), i, i, vp, i, P(i)]
     L.vi_launch_count.argtypes = [vp, P(C.c_uint64)]
     L.vi_render_host_noalloc.argtypes = [vp, P(Camera), i, i, f, vp, P(RenderOpts)]
+    d, u64 = C.c_double, C.c_uint64
+    L.vi_server_create.argtypes = [P(vp), i, i, sz, i]
+    L.vi_server_destroy.argtypes = [vp]
+    L.vi_server_add_volume.argtypes = [vp, vp, i, i, i, i, P(i)]
+    L.vi_server_submit.argtypes = [vp, P(Request), P(u64)]
+    L.vi_server_wait.argtypes = [vp, u64, d, P(i), P(i)]
+    L.vi_server_cancel.argtypes = [vp, u64]
+    L.vi_server_timing.argtypes = [vp, u64, P(d), P(d), P(d)]
+    L.vi_server_release.argtypes = [vp, u64]
+    L.vi_server_get_stats.argtypes = [vp, P(ServerStats)]
     _lib = L
     return L
 
@@ -283,3 +313,99 @@ def decode_stack(raw: np.ndarray, fmt: int) -> np.ndarray:
     if fmt == BF16:
         return (raw.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
     return raw.astype(np.float64) / 65535.0
+
+
+class Server:
+    """A vi_server: continuous batching of render requests over resident volumes."""
+
+    def __init__(self, device: int = 0, slots: int = 4, memory_budget: int = 0,
+                 max_resident_volumes: int = 0):
+        L = library()
+        h = C.c_void_p()
+        _check(L.vi_server_create(C.byref(h), int(device), int(slots), int(memory_budget),
+                                  int(max_resident_volumes)), "vi_server_create")
+        self.h, self.L = h, L
+        self._keep = {}   # host volumes and outputs the server reads or writes later
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.L.vi_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_volume(self, vol, dtype: int | None = None) -> int:
+        """Register a (nz, ny, nx) volume: a uint8 / uint16 numpy array, or a
+        contiguous host torch tensor (page-locked, so reloads after eviction
+        copy at full speed) whose 16-bit data is taken as VI_U16 unless
+        ``dtype`` says otherwise.  The server keeps a reference to it."""
+        if hasattr(vol, "data_ptr"):
+            if vol.is_cuda or not vol.is_contiguous() or vol.dim() != 3:
+                raise ValueError("volume must be a contiguous 3-D host tensor")
+            code = dtype if dtype is not None else (U8 if vol.element_size() == 1 else U16)
+            ptr = vol.data_ptr()
+        else:
+            vol = np.ascontiguousarray(vol)
+            code = dtype if dtype is not None else (U8 if vol.dtype == np.uint8 else U16)
+            ptr = vol.ctypes.data
+        nz, ny, nx = vol.shape
+        vid = C.c_int(-1)
+        _check(self.L.vi_server_add_volume(self.h, C.c_void_p(ptr), int(code), nx, ny, nz,
+                                           C.byref(vid)), "vi_server_add_volume")
+        self._keep[("vol", vid.value)] = vol
+        return vid.value
+
+    def submit(self, volume_id, tf, vmin, vmax, light_dir, n_slices, slice_res, mode, cam, W, H,
+               step_vox, out, light_color=(1.0, 1.0, 1.0), format=F32,
+               cone_half_angle_deg=15.0, shell_radius_vox=1.0, ert=2.0,
+               bg=(0.0, 0.0, 0.0, 0.0)) -> int:
+        tf = np.ascontiguousarray(tf, dtype=np.float32)
+        p, dev = _ptr(out)
+        q = Request(int(volume_id), C.c_void_p(tf.ctypes.data), tf.shape[0], float(vmin),
+                    float(vmax), _f3(light_dir), _f3(light_color), int(n_slices),
+                    int(slice_res), int(mode),
+                    BuildOpts(int(format), float(cone_half_angle_deg), float(shell_radius_vox),
+                              0, 0.0),
+                    camera(cam), int(W), int(H), float(step_vox),
+                    Context._render_opts(ert, bg, 0.0, 0), C.c_void_p(p), dev)
+        t = C.c_uint64(0)
+        _check(self.L.vi_server_submit(self.h, C.byref(q), C.byref(t)), "vi_server_submit")
+        self._keep[("out", t.value)] = out
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: float = 60000.0):
+        """(status, result) of a request; raises ViError(ETIMEOUT) on timeout."""
+        st, res = C.c_int(0), C.c_int(0)
+        rc = self.L.vi_server_wait(self.h, C.c_uint64(ticket), float(timeout_ms), C.byref(st),
+                                   C.byref(res))
+        if rc != OK:
+            raise ViError(rc, "vi_server_wait")
+        return st.value, res.value
+
+    def cancel(self, ticket: int) -> int:
+        return int(self.L.vi_server_cancel(self.h, C.c_uint64(ticket)))
+
+    def timing(self, ticket: int):
+        a, b, c = C.c_double(), C.c_double(), C.c_double()
+        _check(self.L.vi_server_timing(self.h, C.c_uint64(ticket), C.byref(a), C.byref(b),
+                                       C.byref(c)), "vi_server_timing")
+        return a.value, b.value, c.value
+
+    def release(self, ticket: int) -> None:
+        _check(self.L.vi_server_release(self.h, C.c_uint64(ticket)), "vi_server_release")
+        self._keep.pop(("out", ticket), None)
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(self.L.vi_server_get_stats(self.h, C.byref(st)), "vi_server_get_stats")
+        return {name: getattr(st, name) for name, _ in ServerStats._fields_}

@@ -70,3 +70,22 @@ def test_binding_does_not_import_the_oracle():
     assert "oracle" not in re.sub(r'""".*?"""', "", src, flags=re.S)
     for f in os.listdir(os.path.join(ROOT, "paper_2008_06134_gb300", "csrc")):
         assert "oracle" not in open(os.path.join(ROOT, "paper_2008_06134_gb300", "csrc", f)).read()
+
+
+def test_server_calls_reject_bad_arguments_without_cuda(lib):
+    from paper_2008_06134_gb300 import vi
+    null = C.c_void_p(None)
+    st, res = C.c_int(), C.c_int()
+    assert lib.vi_server_destroy(null) == vi.EINVAL
+    assert lib.vi_server_submit(null, None, None) == vi.EINVAL
+    assert lib.vi_server_wait(null, 1, 0.0, C.byref(st), C.byref(res)) == vi.EINVAL
+    assert lib.vi_server_cancel(null, 1) == vi.EINVAL
+    assert lib.vi_server_get_stats(null, None) == vi.EINVAL
+    assert lib.vi_server_create(None, 0, 4, 0, 0) == vi.EINVAL
+    h = C.c_void_p()
+    assert lib.vi_server_create(C.byref(h), 0, 0, 0, 0) == vi.EINVAL      # no slots
+    rc = lib.vi_server_create(C.byref(h), 0, 2, 0, 0)
+    if rc == vi.OK:          # a GPU is present: clean up
+        assert lib.vi_server_destroy(h) == vi.OK
+    else:                    # no GPU here: a clean error, no crash
+        assert rc in (vi.ECUDA, vi.EINVAL)

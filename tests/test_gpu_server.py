@@ -1,0 +1,191 @@
+"""The render server (continuous batching): every result is the same alone and
+in the mix; memory and residency limits, malformed requests, bounded waits and
+cancellation behave as documented.  Failures are made on the host (budgets,
+bad arguments, queued work), never by faulting the GPU."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2008_06134_gb300 import build, phantoms as ph, vi
+    build.build()
+    vols = [ph.gaussian_blobs(32, 11), ph.ct_phantom(48, 12),
+            ph.gaussian_blobs(40, 13)[:28, :36, :40].copy()]
+    tfs = [(ph.tf_random_pl(256, 11), 0.0, 255.0), (ph.tf_ct(512, 12), 0.0, 4095.0),
+           (ph.tf_random_pl(64, 13), 0.0, 255.0)]
+    return torch, ph, vi, vols, tfs
+
+
+def make_requests(ph, vi, count, seed=0):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for q in range(count):
+        v = int(rng.integers(3))
+        W, H = [(32, 24), (48, 40), (64, 64), (57, 31)][int(rng.integers(4))]
+        reqs.append(dict(
+            vol=v, light=ph.random_direction(rng),
+            cam=ph.orbit_camera(ph.random_direction(rng), bool(rng.integers(2)), 2.4),
+            n=int([8, 16, 33][rng.integers(3)]), R=int([16, 24, 45][rng.integers(3)]),
+            mode=int(rng.integers(1, 4)), fmt=int([vi.F32, vi.F16, vi.UNORM16][rng.integers(3)]),
+            W=W, H=H, ert=float([2.0, 0.95][rng.integers(2)])))
+    return reqs
+
+
+def run(env, reqs, slots, together, budget=0, max_resident=0):
+    torch, ph, vi, vols, tfs = env
+    with vi.Server(0, slots=slots, memory_budget=budget, max_resident_volumes=max_resident) as s:
+        vids = [s.add_volume(v) for v in vols]
+        outs, tickets = [], []
+        for q in reqs:
+            out = torch.full((q["H"], q["W"], 4), float("nan"), device="cuda")
+            tf, vmin, vmax = tfs[q["vol"]]
+            t = s.submit(vids[q["vol"]], tf, vmin, vmax, q["light"], q["n"], q["R"], q["mode"],
+                         q["cam"], q["W"], q["H"], 0.5, out, format=q["fmt"], ert=q["ert"])
+            outs.append(out)
+            tickets.append(t)
+            if not together:
+                assert s.wait(t) == (vi.REQ_DONE, vi.OK)
+        for t in tickets:
+            assert s.wait(t) == (vi.REQ_DONE, vi.OK)
+        stats = s.stats()
+    torch.cuda.synchronize()
+    return [o.cpu().numpy() for o in outs], stats
+
+
+def test_results_are_identical_alone_and_in_the_mix(env):
+    torch, ph, vi, vols, tfs = env
+    reqs = make_requests(ph, vi, 16)
+    alone, _ = run(env, reqs, slots=1, together=False)
+    mixed, stats = run(env, reqs, slots=4, together=True)
+    for a, b in zip(alone, mixed):
+        assert np.isfinite(a).all()
+        assert np.array_equal(a, b)
+    assert stats["completed"] == 16 and stats["failed"] == 0
+
+
+def test_server_frame_equals_context_frame(env):
+    """A served frame is the frame a plain context renders from the same inputs."""
+    torch, ph, vi, vols, tfs = env
+    q = make_requests(ph, vi, 1, seed=5)[0]
+    (served,), _ = run(env, [q], slots=2, together=True)
+    tf, vmin, vmax = tfs[q["vol"]]
+    with vi.Context(0) as c:
+        c.load_volume(vols[q["vol"]])
+        c.set_transfer_function(tf, vmin, vmax)
+        c.set_light(q["light"])
+        c.build_attenuation(q["n"], q["R"], q["mode"], format=q["fmt"])
+        ref = c.render(q["cam"], q["W"], q["H"], 0.5, ert=q["ert"]).cpu().numpy()
+    assert np.array_equal(served, ref)
+
+
+def test_residency_limit_evicts_and_reloads(env):
+    torch, ph, vi, vols, tfs = env
+    reqs = make_requests(ph, vi, 12, seed=3)
+    alone, _ = run(env, reqs, slots=1, together=False)
+    mixed, stats = run(env, reqs, slots=2, together=True, max_resident=1)
+    for a, b in zip(alone, mixed):
+        assert np.array_equal(a, b)
+    assert stats["volume_evictions"] > 0 and stats["volume_loads"] > 3
+    assert stats["resident_volumes"] <= 1
+
+
+def test_request_beyond_the_budget_fails_and_others_finish(env):
+    torch, ph, vi, vols, tfs = env
+    budget = 64 << 20
+    with vi.Server(0, slots=2, memory_budget=budget) as s:
+        vid = s.add_volume(vols[0])
+        tf, vmin, vmax = tfs[0]
+        cam = ph.orbit_camera(np.array([0.3, 0.4, -0.8]), True, 2.4)
+        big = torch.empty((16, 16, 4), device="cuda")
+        small = torch.empty((16, 16, 4), device="cuda")
+        t_big = s.submit(vid, tf, vmin, vmax, (0, 0, 1), 512, 1024, vi.CONE, cam, 16, 16, 0.5, big)
+        t_small = s.submit(vid, tf, vmin, vmax, (0, 0, 1), 16, 32, vi.CONE, cam, 16, 16, 0.5, small)
+        assert s.wait(t_big) == (vi.REQ_FAILED, vi.ENOMEM)
+        assert s.wait(t_small) == (vi.REQ_DONE, vi.OK)
+        assert s.stats()["peak_bytes"] <= budget
+
+
+def test_malformed_requests_are_refused(env):
+    torch, ph, vi, vols, tfs = env
+    with vi.Server(0, slots=1) as s:
+        vid = s.add_volume(vols[0])
+        tf, vmin, vmax = tfs[0]
+        cam = ph.orbit_camera(np.array([0.3, 0.4, -0.8]), True, 2.4)
+        out = torch.empty((8, 8, 4), device="cuda")
+        bad_tf = tf.copy()
+        bad_tf[3, 3] = 2.0
+        for kw in (dict(volume_id=99), dict(tf=bad_tf), dict(light_dir=(0, 0, 0)),
+                   dict(n_slices=0), dict(mode=9), dict(vmax=-1.0)):
+            args = dict(volume_id=vid, tf=tf, vmin=vmin, vmax=vmax, light_dir=(0, 0, 1),
+                        n_slices=8, slice_res=8, mode=vi.SHADOW, cam=cam, W=8, H=8,
+                        step_vox=0.5, out=out)
+            args.update(kw)
+            with pytest.raises(vi.ViError) as e:
+                s.submit(**args)
+            assert e.value.code == vi.EINVAL
+        assert s.stats()["submitted"] == 0
+
+
+def test_bounded_wait_cancel_and_shutdown(env):
+    torch, ph, vi, vols, tfs = env
+    s = vi.Server(0, slots=1)
+    vid = s.add_volume(vols[1])
+    tf, vmin, vmax = tfs[1]
+    cam = ph.orbit_camera(np.array([0.3, 0.4, -0.8]), True, 2.4)
+    outs = [torch.empty((1024, 1024, 4), device="cuda") for _ in range(3)]
+    ts = [s.submit(vid, tf, vmin, vmax, (0.2, 0.1, 1.0), 256, 512, vi.CONE, cam, 1024, 1024,
+                   0.25, o) for o in outs]
+    with pytest.raises(vi.ViError) as e:     # the last one is still queued behind the others
+        s.wait(ts[2], timeout_ms=0.0)
+    assert e.value.code == vi.ETIMEOUT
+    rc = s.cancel(ts[2])
+    assert rc in (vi.OK, vi.ESTATE)
+    status, result = s.wait(ts[2])
+    assert status == (vi.REQ_CANCELLED if rc == vi.OK else vi.REQ_DONE)
+    assert s.wait(ts[0]) == (vi.REQ_DONE, vi.OK)
+    t_last = s.submit(vid, tf, vmin, vmax, (0.2, 0.1, 1.0), 256, 512, vi.CONE, cam, 1024, 1024,
+                      0.25, outs[2])
+    s.close()                                 # cancels what is queued, finishes what runs
+    assert s.h is None
+    del t_last
+
+
+def test_kept_stack_serves_a_new_view_of_the_same_scene(env):
+    """A second request with the same volume, TF, light and stack but a new
+    camera renders from the slot's kept stack: no sweep, same frame as a fresh
+    context builds and renders."""
+    torch, ph, vi, vols, tfs = env
+    tf, vmin, vmax = tfs[1]
+    light = (0.3, -0.2, 0.9)
+    cams = [ph.orbit_camera(np.array(d), True, 2.4) for d in ((0.3, 0.4, -0.8), (-0.6, 0.1, 0.5))]
+    outs = []
+    with vi.Server(0, slots=2) as s:
+        vid = s.add_volume(vols[1])
+        for cam in cams:
+            out = torch.empty((40, 48, 4), device="cuda")
+            t = s.submit(vid, tf, vmin, vmax, light, 24, 40, vi.CONE, cam, 48, 40, 0.5, out,
+                         format=vi.F16, ert=0.95)
+            assert s.wait(t) == (vi.REQ_DONE, vi.OK)
+            outs.append(out.cpu().numpy())
+        assert s.stats()["stack_reuses"] == 1
+        # A different TF must not reuse the stack.
+        tf2 = tf.copy()
+        tf2[:, 3] *= 0.5
+        out = torch.empty((40, 48, 4), device="cuda")
+        t = s.submit(vid, tf2, vmin, vmax, light, 24, 40, vi.CONE, cams[0], 48, 40, 0.5, out,
+                     format=vi.F16, ert=0.95)
+        assert s.wait(t) == (vi.REQ_DONE, vi.OK)
+        assert s.stats()["stack_reuses"] == 1
+    with vi.Context(0) as c:
+        c.load_volume(vols[1])
+        for cam, got, t_f in ((cams[0], outs[0], tf), (cams[1], outs[1], tf), (cams[0], out.cpu().numpy(), tf2)):
+            c.set_transfer_function(t_f, vmin, vmax)
+            c.set_light(light)
+            c.build_attenuation(24, 40, vi.CONE, format=vi.F16)
+            ref = c.render(cam, 48, 40, 0.5, ert=0.95).cpu().numpy()
+            assert np.array_equal(got, ref)
