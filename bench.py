@@ -77,7 +77,8 @@ def parse():
                          "slice resolution grid; serving: the render server on a stream of "
                          "mixed requests")
     ap.add_argument("--requests", type=int, default=512, help="serving: request count")
-    ap.add_argument("--rate", type=float, default=300.0, help="serving: arrivals per second")
+    ap.add_argument("--rate", default="300,800",
+                    help="serving: Poisson arrival rates per second (comma-separated)")
     ap.add_argument("--slots", type=int, default=8, help="serving: concurrent render slots")
     ap.add_argument("--budget-gib", type=float, default=8.0, help="serving: HBM budget")
     return ap.parse_args()
@@ -543,7 +544,8 @@ def serving_workload(args):
     host = [torch.from_numpy(a.view(np.int16) if a.dtype == np.uint16 else a).pin_memory()
             for a in arrays]
     codes = [vi.U8 if a.dtype == np.uint8 else vi.U16 for a in arrays]
-    reqs = ph.serving_requests(len(specs), args.requests, args.rate)
+    rates = [float(r) for r in str(args.rate).split(",")]
+    mixes = {r: ph.serving_requests(len(specs), args.requests, r) for r in rates}
     budget = int(args.budget_gib * (1 << 30))
 
     def submit(s, vids, q, out, fmt):
@@ -552,7 +554,7 @@ def serving_workload(args):
                         q["slice_res"], q["mode"], q["camera"], q["width"], q["height"],
                         q["step_vox"], out, format=fmt, ert=q["ert"])
 
-    def run(slots, fmt, burst):
+    def run(slots, fmt, burst, reqs):
         outs = [torch.empty((q["height"], q["width"], 4), device="cuda") for q in reqs]
         with vi.Server(0, slots=slots, memory_budget=budget, max_resident_volumes=6) as s:
             vids = [s.add_volume(h, c) for h, c in zip(host, codes)]
@@ -582,6 +584,8 @@ def serving_workload(args):
                               "mean": round(float(lat.mean()), 3),
                               "max": round(float(lat.max()), 3)},
                "queue_wait_ms_p50": round(float(np.percentile(times[:, 1] - times[:, 0], 50)), 3),
+               "service_ms": {"p50": round(float(np.percentile(times[:, 2] - times[:, 1], 50)), 3),
+                              "p99": round(float(np.percentile(times[:, 2] - times[:, 1], 99)), 3)},
                "failed": failed,
                "volume_loads": st["volume_loads"] - base["volume_loads"],
                "volume_evictions": st["volume_evictions"] - base["volume_evictions"],
@@ -590,21 +594,27 @@ def serving_workload(args):
         return row, outs
 
     runs = {}
-    plain, plain_outs = run(1, vi.F32, burst=False)
-    runs["plain-f32-1slot-poisson"] = plain
-    for fmt, fname in ((vi.F32, "f32"), (vi.F16, "f16")):
-        row, outs = run(args.slots, fmt, burst=False)
-        if fmt == vi.F32:
-            row["frames_identical_to_plain"] = sum(bool(torch.equal(a, b))
-                                                   for a, b in zip(outs, plain_outs))
-        else:
-            row["max_abs_err_vs_plain_f32"] = float(f"{max(float((a - b).abs().max()) for a, b in zip(outs, plain_outs)):.3g}")
-        runs[f"served-{fname}-{args.slots}slots-poisson"] = row
-        del outs
-    for slots, name in ((1, "plain-f32-1slot-burst"), (args.slots, f"served-f32-{args.slots}slots-burst")):
-        runs[name] = run(slots, vi.F32, burst=True)[0]
+    for rate in rates:
+        reqs = mixes[rate]
+        plain, plain_outs = run(1, vi.F32, False, reqs)
+        runs[f"plain-f32-1slot-poisson{rate:g}"] = plain
+        for fmt, fname in ((vi.F32, "f32"), (vi.F16, "f16")):
+            row, outs = run(args.slots, fmt, False, reqs)
+            if fmt == vi.F32:
+                row["frames_identical_to_plain"] = sum(bool(torch.equal(a, b))
+                                                       for a, b in zip(outs, plain_outs))
+            else:
+                err = max(float((a - b).abs().max()) for a, b in zip(outs, plain_outs))
+                row["max_abs_err_vs_plain_f32"] = float(f"{err:.3g}")
+            runs[f"served-{fname}-{args.slots}slots-poisson{rate:g}"] = row
+            del outs
+        del plain_outs
+    # Capacity: every request of the first mix submitted at once.
+    for slots, name in ((1, "plain-f32-1slot-burst"),
+                        (args.slots, f"served-f32-{args.slots}slots-burst")):
+        runs[name] = run(slots, vi.F32, True, mixes[rates[0]])[0]
     print(json.dumps({"workload": "serving", "metric": "frames/s", "unit": "frames/s",
-                      "requests": len(reqs), "rate_per_s": args.rate, "slots": args.slots,
+                      "requests": args.requests, "rates_per_s": rates, "slots": args.slots,
                       "budget_bytes": budget, "max_resident_volumes": 6,
                       "volumes": [v.name for v in specs],
                       "mix": "256^2..1920x1080 perspective, 64-512 slices of 256^2/512^2, "

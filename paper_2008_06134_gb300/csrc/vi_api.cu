@@ -157,10 +157,12 @@ int cuda_fail(vi_ctx* c, cudaError_t e) {
 
 // Grow a device buffer to `bytes` under the context's budget.
 int ensure(vi_ctx* c, void** p, size_t* cap, size_t bytes) {
-    return vi_detail::ensure_mem(&c->used, c->budget, p, cap, bytes, c->stream);
+    return vi_detail::ensure_mem(&c->used, c->budget, p, cap, bytes, c->stream, c->pool);
 }
 
-void release(vi_ctx* c, void** p, size_t* cap) { vi_detail::release_mem(&c->used, p, cap); }
+void release(vi_ctx* c, void** p, size_t* cap) {
+    vi_detail::release_mem(&c->used, p, cap, c->stream, c->pool);
+}
 
 // Common prologue of every call on a context.
 int enter(vi_ctx* c) {
@@ -350,18 +352,24 @@ int check_render_inputs(vi_ctx* c, const vi_camera* cam, int W, int H, float ste
 
 namespace vi_detail {
 
-int ensure_mem(size_t* used, size_t budget, void** p, size_t* cap, size_t bytes, cudaStream_t s) {
+int ensure_mem(size_t* used, size_t budget, void** p, size_t* cap, size_t bytes, cudaStream_t s,
+               cudaMemPool_t pool) {
     if (bytes <= *cap && *p) return VI_OK;
     size_t after = *used - *cap + bytes;
     if (budget && after > budget) return VI_ENOMEM;
     void* q = nullptr;
-    if (cudaMalloc(&q, bytes) != cudaSuccess) {
+    const cudaError_t e = pool ? cudaMallocFromPoolAsync(&q, bytes, pool, s) : cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
         cudaGetLastError();
         return VI_ENOMEM;
     }
     if (*p) {
-        cudaStreamSynchronize(s);
-        cudaFree(*p);
+        if (pool) {
+            cudaFreeAsync(*p, s);
+        } else {
+            cudaStreamSynchronize(s);
+            cudaFree(*p);
+        }
     }
     *p = q;
     *used = after;
@@ -369,8 +377,11 @@ int ensure_mem(size_t* used, size_t budget, void** p, size_t* cap, size_t bytes,
     return VI_OK;
 }
 
-void release_mem(size_t* used, void** p, size_t* cap) {
-    if (*p) cudaFree(*p);
+void release_mem(size_t* used, void** p, size_t* cap, cudaStream_t s, cudaMemPool_t pool) {
+    if (*p) {
+        if (pool) cudaFreeAsync(*p, s);
+        else cudaFree(*p);
+    }
     *used -= *cap;
     *p = nullptr;
     *cap = 0;
@@ -394,12 +405,12 @@ int volume_load(VolumeRes* v, size_t* used, size_t budget, const void* data, int
                         std::max(v->brange_cap, (size_t)nbx * nby * nbz * sizeof(uint32_t)) -
                         v->brange_cap;
     if (budget && *used + have > budget) return VI_ENOMEM;
-    int rc = ensure_mem(used, budget, &v->raw, &v->raw_cap, bytes, s);
+    int rc = ensure_mem(used, budget, &v->raw, &v->raw_cap, bytes, s, v->pool);
     if (rc) return rc;
-    rc = ensure_mem(used, budget, &v->oct, &v->oct_cap, 8 * bytes, s);
+    rc = ensure_mem(used, budget, &v->oct, &v->oct_cap, 8 * bytes, s, v->pool);
     if (rc) return rc;
     rc = ensure_mem(used, budget, reinterpret_cast<void**>(&v->brange), &v->brange_cap,
-                    (size_t)nbx * nby * nbz * sizeof(uint32_t), s);
+                    (size_t)nbx * nby * nbz * sizeof(uint32_t), s, v->pool);
     if (rc) return rc;
     v->vtype = -1;
     cudaError_t e = cudaMemcpyAsync(v->raw, data, bytes,
@@ -420,10 +431,10 @@ int volume_load(VolumeRes* v, size_t* used, size_t budget, const void* data, int
     return VI_OK;
 }
 
-void volume_release(VolumeRes* v, size_t* used) {
-    release_mem(used, &v->raw, &v->raw_cap);
-    release_mem(used, &v->oct, &v->oct_cap);
-    release_mem(used, reinterpret_cast<void**>(&v->brange), &v->brange_cap);
+void volume_release(VolumeRes* v, size_t* used, cudaStream_t s) {
+    release_mem(used, &v->raw, &v->raw_cap, s, v->pool);
+    release_mem(used, &v->oct, &v->oct_cap, s, v->pool);
+    release_mem(used, reinterpret_cast<void**>(&v->brange), &v->brange_cap, s, v->pool);
     v->vtype = -1;
 }
 
@@ -522,7 +533,7 @@ int vi_destroy(vi_ctx* c) {
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     cudaGetLastError();
-    vi_detail::volume_release(&c->own, &c->used);
+    vi_detail::volume_release(&c->own, &c->used, c->stream);
     release(c, reinterpret_cast<void**>(&c->tf), &c->tf_cap);
     destroy_stack_textures(c);
     release(c, &c->stack_mem, &c->stack_cap);

@@ -20,6 +20,7 @@ struct VolumeRes {
     size_t brange_cap = 0;
     int vtype = -1, nx = 0, ny = 0, nz = 0;
     int nbx = 0, nby = 0, nbz = 0;
+    cudaMemPool_t pool = nullptr;  // stream-ordered pool its buffers come from (null: cudaMalloc)
 };
 
 struct vi_ctx {
@@ -30,6 +31,7 @@ struct vi_ctx {
 
     size_t budget = 0;  // 0 = unlimited
     size_t used = 0;
+    cudaMemPool_t pool = nullptr;  // stream-ordered pool for its buffers (null: cudaMalloc)
 
     VolumeRes own;          // the volume vi_load_volume loads
     VolumeRes* vr = &own;   // the volume in use: own, or one a server shares
@@ -76,14 +78,19 @@ struct vi_ctx {
 namespace vi_detail {
 
 // Device allocation under a byte budget (0 = none) with a usage counter; keeps
-// the old buffer on failure.  Frees the old one after `s` drains.
-int ensure_mem(size_t* used, size_t budget, void** p, size_t* cap, size_t bytes, cudaStream_t s);
-void release_mem(size_t* used, void** p, size_t* cap);
+// the old buffer on failure.  Without a pool: cudaMalloc, and the old buffer is
+// freed after `s` drains.  With a pool: allocation and free are ordered on `s`
+// (no device-wide synchronisation; freed blocks are reused by the pool).
+int ensure_mem(size_t* used, size_t budget, void** p, size_t* cap, size_t bytes, cudaStream_t s,
+               cudaMemPool_t pool);
+// Frees a buffer: cudaFree, or a free ordered on `s` when it came from `pool`.
+void release_mem(size_t* used, void** p, size_t* cap, cudaStream_t s, cudaMemPool_t pool);
 
 // Loads nx*ny*nz voxels into v (octets and brick ranges built on stream s).
 int volume_load(VolumeRes* v, size_t* used, size_t budget, const void* data, int dtype, int nx,
                 int ny, int nz, int data_on_device, cudaStream_t s, uint64_t* launches);
-void volume_release(VolumeRes* v, size_t* used);
+// Frees the volume's buffers (ordered on `s` when they came from a pool).
+void volume_release(VolumeRes* v, size_t* used, cudaStream_t s);
 size_t volume_bytes(int dtype, int nx, int ny, int nz);
 
 // Points the context at a volume it does not own and refreshes the brick

@@ -34,6 +34,7 @@ struct ServerVolume {
     bool resident = false;
     int pins = 0;           // slots rendering from it
     uint64_t last_use = 0;  // admission counter at last use
+    cudaEvent_t ready = nullptr;  // recorded after its last load; every reader's stream waits on it
 };
 
 struct Request {
@@ -97,6 +98,9 @@ struct vi_server {
     std::condition_variable done;  // waiters: a request finished
     std::thread worker;
     bool stop = false;
+    // Stream-ordered pool for every device buffer of the server (volumes and
+    // slots): evictions and reloads reuse blocks without cudaMalloc / cudaFree.
+    cudaMemPool_t pool = nullptr;
 };
 
 namespace {
@@ -140,6 +144,16 @@ size_t slot_growth(const Slot* sl, const Request* r, const ServerVolume* v) {
            grow(out, c->out_cap) + grow(256, c->counter_cap);
 }
 
+// Frees an idle volume's buffers, ordered on `stream`: no device-wide
+// synchronisation, and the pool hands the blocks to the next allocations.
+// Past the byte budget the pool returns its unused blocks to the device.
+void evict(vi_server* s, ServerVolume* v, cudaStream_t stream) {
+    vi_detail::volume_release(&v->res, &v->used, stream);
+    v->resident = false;
+    ++s->stats.volume_evictions;
+    if (s->budget) cudaMemPoolTrimTo(s->pool, s->budget);
+}
+
 // Makes room for `extra` bytes: first frees the stacks of idle slots other
 // than `target`, then evicts idle volumes (least recently used first, never
 // `keep`); true if the budget now allows it.
@@ -160,9 +174,7 @@ bool make_room(vi_server* s, size_t extra, const Slot* target, int keep) {
             if (!victim || v->last_use < victim->last_use) victim = v;
         }
         if (!victim) return false;
-        vi_detail::volume_release(&victim->res, &victim->used);
-        victim->resident = false;
-        ++s->stats.volume_evictions;
+        evict(s, victim, target->stream);
     }
     return true;
 }
@@ -183,7 +195,8 @@ int start(vi_server* s, Slot* sl, Request* r, bool reuse) {
     const vi_request& q = r->req;
     ServerVolume* v = s->vols[q.volume_id];
     vi_ctx* c = sl->ctx;
-    int rc = vi_detail::ctx_bind_volume(c, &v->res, reuse);
+    int rc = cudaStreamWaitEvent(sl->stream, v->ready, 0) == cudaSuccess ? VI_OK : VI_ECUDA;
+    if (!rc) rc = vi_detail::ctx_bind_volume(c, &v->res, reuse);
     if (!reuse) {
         sl->has_stack = false;
         if (!rc)
@@ -255,9 +268,7 @@ void schedule(vi_server* s) {
                     if (!victim || o->last_use < victim->last_use) victim = o;
                 }
                 if (!victim) break;
-                vi_detail::volume_release(&victim->res, &victim->used);
-                victim->resident = false;
-                ++s->stats.volume_evictions;
+                evict(s, victim, sl->stream);
                 --resident;
             }
             if (resident >= s->max_resident) {
@@ -271,10 +282,11 @@ void schedule(vi_server* s) {
         if (!v->resident) {
             int rc = vi_detail::volume_load(&v->res, &v->used, 0, v->host, v->dtype, v->nx,
                                                   v->ny, v->nz, 0, sl->stream, nullptr);
-            // Other slots' streams may read this volume next: let its octets
-            // and brick ranges finish before anyone is admitted on it.
-            if (!rc && cudaStreamSynchronize(sl->stream) != cudaSuccess) rc = VI_ECUDA;
+            // Slots on other streams may read this volume next: they wait on
+            // this event (octets and brick ranges built) before they do.
+            if (!rc && cudaEventRecord(v->ready, sl->stream) != cudaSuccess) rc = VI_ECUDA;
             if (rc) {
+                vi_detail::volume_release(&v->res, &v->used, sl->stream);  // a partial load
                 finish(s, r, VI_REQ_FAILED, rc);
                 continue;
             }
@@ -342,6 +354,19 @@ int vi_server_create(vi_server** out, int device, int slots, size_t memory_budge
     s->budget = memory_budget;
     s->max_resident = max_resident_volumes;
     s->t0 = Clock::now();
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    uint64_t keep = UINT64_MAX;  // freed blocks stay in the pool (trimmed to the budget)
+    if (cudaMemPoolCreate(&s->pool, &props) != cudaSuccess ||
+        cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+        cudaGetLastError();
+        if (s->pool) cudaMemPoolDestroy(s->pool);
+        delete s;
+        return VI_ECUDA;
+    }
     for (int i = 0; i < slots; ++i) {
         Slot* sl = new Slot();
         sl->server = s;
@@ -354,9 +379,11 @@ int vi_server_create(vi_server** out, int device, int slots, size_t memory_budge
                 cudaStreamDestroy(o->stream);
                 delete o;
             }
+            cudaMemPoolDestroy(s->pool);
             delete s;
             return VI_ECUDA;
         }
+        sl->ctx->pool = s->pool;
         s->slots.push_back(sl);
     }
     s->worker = std::thread(worker_main, s);
@@ -383,9 +410,12 @@ int vi_server_destroy(vi_server* s) {
         delete sl;
     }
     for (ServerVolume* v : s->vols) {
-        vi_detail::volume_release(&v->res, &v->used);
+        vi_detail::volume_release(&v->res, &v->used, nullptr);
+        cudaEventDestroy(v->ready);
         delete v;
     }
+    cudaDeviceSynchronize();
+    cudaMemPoolDestroy(s->pool);
     for (auto& kv : s->reqs) delete kv.second;
     delete s;
     return VI_OK;
@@ -400,11 +430,18 @@ int vi_server_add_volume(vi_server* s, const void* host_data, int dtype, int nx,
     std::lock_guard<std::mutex> lk(s->mu);
     ServerVolume* v = new (std::nothrow) ServerVolume();
     if (!v) return VI_ENOMEM;
+    if (cudaSetDevice(s->device) != cudaSuccess ||
+        cudaEventCreateWithFlags(&v->ready, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        delete v;
+        return VI_ECUDA;
+    }
     v->host = host_data;
     v->dtype = dtype;
     v->nx = nx;
     v->ny = ny;
     v->nz = nz;
+    v->res.pool = s->pool;
     *volume_id = (int)s->vols.size();
     s->vols.push_back(v);
     return VI_OK;
