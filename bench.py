@@ -45,10 +45,10 @@ FLOPS_LIT = {0: 0, 1: 6 + 2 + 12, 2: 6 + 2 + 6 * 12 + 7, 3: 6 + 2 + 8 * 12 + 9}
 # entry holds for the kernel sources it was taken from (hash of the files that
 # define the kernel); once they change the figure is stale and reported as null.
 NCU_TRAFFIC = {
-    "march_kernel": (("vi_march.cu", "vi_device.cuh", "vi_internal.h"), "429b6002c659682c",
-                     78_973_440),
-    "sweep_kernel": (("vi_sweep.cu", "vi_device.cuh", "vi_internal.h"), "6f5fef12bb7b3574",
-                     288_918_016),
+    "march_kernel": (("vi_march.cu", "vi_device.cuh", "vi_internal.h"), "7539b5dd9069b74f",
+                     83_350_528),
+    "sweep_kernel": (("vi_sweep.cu", "vi_device.cuh", "vi_internal.h"), "aaf51e2d5456c23a",
+                     306_188_800),
 }
 
 
