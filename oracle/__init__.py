@@ -27,6 +27,11 @@ _lib = None
 TRACE_WORDS = 40
 TRACE_NONE = 0x7FFFFFFF
 NONE, SHADOW, SHELL, CONE = 0, 1, 2, 3
+TRANSMITTANCE, OPTICAL_DEPTH = 0, 1      # what the attenuation buffer holds
+SLICE_NEAREST, SLICE_LINEAR = 0, 1      # slice filtering of a lookup
+DEPTH_MAX = 64.0                         # cap of a stored optical depth
+MAX_SHELLS = 4
+MAX_NB = 6 * MAX_SHELLS
 
 
 def build(force: bool = False) -> str:
@@ -62,7 +67,7 @@ class Light(C.Structure):
 
 
 class BuildOpts(C.Structure):
-    _fields_ = [("opacity_correction", C.c_int), ("comp_n", C.c_float)]
+    _fields_ = [("opacity_correction", C.c_int), ("comp_n", C.c_float), ("quantity", C.c_int)]
 
 
 class Camera(C.Structure):
@@ -75,7 +80,8 @@ class RenderOpts(C.Structure):
     _fields_ = [("mode", C.c_int), ("ert", C.c_float), ("bg", C.c_float * 4),
                 ("color", C.c_float * 3), ("ambient", C.c_float), ("step_vox", C.c_float),
                 ("opacity_correction", C.c_int), ("cone_half_angle_deg", C.c_float),
-                ("shell_radius_vox", C.c_float), ("ert_band", C.c_double)]
+                ("shell_radius_vox", C.c_float), ("ert_band", C.c_double),
+                ("quantity", C.c_int), ("slice_filter", C.c_int), ("shell_count", C.c_int)]
 
 
 class Frame(C.Structure):
@@ -87,7 +93,7 @@ class Frame(C.Structure):
 class Ray(C.Structure):
     _fields_ = [("hit", C.c_int), ("o", C.c_float * 3), ("d", C.c_float * 3),
                 ("t0", C.c_float), ("t1", C.c_float), ("lo", C.c_float * 3),
-                ("ld", C.c_float * 3), ("nnb", C.c_int), ("nb", (C.c_float * 3) * 8)]
+                ("ld", C.c_float * 3), ("nnb", C.c_int), ("nb", (C.c_float * 3) * MAX_NB)]
 
 
 def lib():
@@ -124,6 +130,9 @@ def lib():
             L.orc_stack_lookup.argtypes = [C.c_void_p, P(Light), C.c_float, C.c_float, C.c_float,
                                            P(C.c_int)]
             L.orc_stack_lookup.restype = C.c_double
+            L.orc_light_lookup.argtypes = [C.c_void_p, P(Light), P(RenderOpts), C.c_float,
+                                           C.c_float, C.c_float, P(C.c_int)]
+            L.orc_light_lookup.restype = C.c_double
             L.orc_set_threads.argtypes = [C.c_int]
             _lib = L
     return _lib
@@ -174,12 +183,14 @@ def light_setup(direction, n: int, R: int) -> Light:
 
 
 def build_stack(vol: np.ndarray, tf: np.ndarray, vmin: float, vmax: float, light: Light,
-                opacity_correction: int = 0, comp_n: float = 0.0) -> np.ndarray:
-    """Algorithm 1: the (n, R, R) attenuation buffer, binary64."""
+                opacity_correction: int = 0, comp_n: float = 0.0,
+                quantity: int = TRANSMITTANCE) -> np.ndarray:
+    """Algorithm 1: the (n, R, R) attenuation buffer, binary64 (transmittances,
+    or optical depths with ``quantity=OPTICAL_DEPTH``)."""
     V = volume(vol)
     T = transfer_function(tf, vmin, vmax)
     B = np.empty((light.n, light.R, light.R), dtype=np.float64)
-    opts = BuildOpts(int(opacity_correction), float(comp_n))
+    opts = BuildOpts(int(opacity_correction), float(comp_n), int(quantity))
     rc = lib().orc_build_stack(C.byref(V.struct), C.byref(T.struct), C.byref(light),
                                C.byref(opts), B.ctypes.data)
     if rc:
@@ -188,13 +199,14 @@ def build_stack(vol: np.ndarray, tf: np.ndarray, vmin: float, vmax: float, light
 
 
 def build_stack_rows(vol, tf, vmin, vmax, light: Light, j0: int, j1: int, out: np.ndarray,
-                     opacity_correction: int = 0, comp_n: float = 0.0) -> np.ndarray:
+                     opacity_correction: int = 0, comp_n: float = 0.0,
+                     quantity: int = TRANSMITTANCE) -> np.ndarray:
     """Algorithm 1 on texel rows [j0, j1) only, written into ``out`` (n, R, R)."""
     V = volume(vol)
     T = transfer_function(tf, vmin, vmax)
     assert out.dtype == np.float64 and out.flags.c_contiguous
     assert out.shape == (light.n, light.R, light.R)
-    opts = BuildOpts(int(opacity_correction), float(comp_n))
+    opts = BuildOpts(int(opacity_correction), float(comp_n), int(quantity))
     rc = lib().orc_build_stack_rows(C.byref(V.struct), C.byref(T.struct), C.byref(light),
                                     C.byref(opts), int(j0), int(j1), out.ctypes.data)
     if rc:
@@ -212,10 +224,12 @@ def camera(cam) -> Camera:
 def render_opts(mode: int, step_vox: float, ert: float = 2.0, bg=(0, 0, 0, 0),
                 color=(1, 1, 1), ambient: float = 0.0, opacity_correction: int = 0,
                 cone_half_angle_deg: float = 15.0, shell_radius_vox: float = 1.0,
-                ert_band: float = 1e-5) -> RenderOpts:
+                ert_band: float = 1e-5, quantity: int = 0, slice_filter: int = 0,
+                shell_count: int = 1) -> RenderOpts:
     return RenderOpts(int(mode), float(ert), (C.c_float * 4)(*map(float, bg)),
                       _f3(color), float(ambient), float(step_vox), int(opacity_correction),
-                      float(cone_half_angle_deg), float(shell_radius_vox), float(ert_band))
+                      float(cone_half_angle_deg), float(shell_radius_vox), float(ert_band),
+                      int(quantity), int(slice_filter), int(shell_count))
 
 
 def render_pixels(vol, tf, vmin, vmax, light: Light, stack, cam, W: int, H: int,
@@ -319,6 +333,15 @@ def tf_lookup(tf: np.ndarray, vmin: float, vmax: float, v: float) -> np.ndarray:
     out = (C.c_double * 4)()
     lib().orc_tf_lookup(C.byref(T.struct), float(v), out)
     return np.array(out[:])
+
+
+def light_lookup(stack, light: Light, ro: RenderOpts, lam, tu, tv):
+    """One lookup's light factor under ``ro``'s slice filter and buffer quantity."""
+    stack = np.ascontiguousarray(stack, dtype=np.float64)
+    rec = (C.c_int * 3)()
+    v = lib().orc_light_lookup(stack.ctypes.data, C.byref(light), C.byref(ro), float(lam),
+                               float(tu), float(tv), rec)
+    return v, tuple(rec[:])
 
 
 def stack_lookup(stack, light: Light, lam, tu, tv):

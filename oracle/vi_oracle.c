@@ -24,6 +24,15 @@
  *   Eq. 1        -- exact transmittance exp(-integral of kappa) along the
  *                   light ray (orc_transmittance_bruteforce, convergence pin).
  *
+ * Variants (all off by default):
+ *   Eq. 5-6      -- extinction form: the buffer holds the optical depth
+ *                   D_k = sum_{j<k} tau_j, tau_j = -ln(1 - alpha_j), capped at
+ *                   ORC_DEPTH_MAX; a lookup's light factor is exp(-D).
+ *   slice_filter -- linear interpolation in lambda between the two slices
+ *                   bracketing a sample instead of the nearest slice.
+ *   shell_count  -- several shells (Section 3.2.3: the number and size of
+ *                   the shells can vary) at radii r, 2r, ..., equal weights.
+ *
  * Precision.  Everything whose rounding decides an integer -- the light and
  * camera set-up, sample positions t_i and the count of samples on a ray, the
  * slice index k, the texel cell, the voxel cell and the inside-the-cube test of
@@ -50,6 +59,15 @@
 enum { ORC_U8 = 0, ORC_U16 = 1 };
 enum { ORC_NONE = 0, ORC_SHADOW = 1, ORC_SHELL = 2, ORC_CONE = 3 };
 enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_ENOMEM = -2 };
+enum { ORC_TRANSMITTANCE = 0, ORC_OPTICAL_DEPTH = 1 };
+enum { ORC_SLICE_NEAREST = 0, ORC_SLICE_LINEAR = 1 };
+
+/* Cap of the stored optical depth: exp(-64) < 2e-28, zero for every purpose,
+   and the cap keeps an opaque texel (tau = infinity) finite for
+   interpolation. */
+#define ORC_DEPTH_MAX 64.0
+#define ORC_MAX_SHELLS 4
+#define ORC_MAX_NB (6 * ORC_MAX_SHELLS)
 
 #define ORC_TRACE_WORDS 40
 #define ORC_TRACE_NONE 0x7fffffff
@@ -84,6 +102,7 @@ typedef struct {
 typedef struct {
     int opacity_correction; /* alpha' = 1 - (1 - alpha)^(slice spacing in voxels) */
     float comp_n;           /* darkening compensation exponent, 0 = off */
+    int quantity;           /* ORC_TRANSMITTANCE or ORC_OPTICAL_DEPTH */
 } orc_build_opts;
 
 typedef struct {
@@ -104,6 +123,9 @@ typedef struct {
     float cone_half_angle_deg;  /* cone half angle phi */
     float shell_radius_vox;     /* shell radius r in voxels */
     double ert_band;            /* |A - ert| <= band marks an ERT-ambiguous pixel */
+    int quantity;               /* what the buffer holds: ORC_TRANSMITTANCE / ORC_OPTICAL_DEPTH */
+    int slice_filter;           /* ORC_SLICE_NEAREST or ORC_SLICE_LINEAR */
+    int shell_count;            /* shells at r, 2r, ...; 0 means 1 */
 } orc_render_opts;
 
 /* Camera frame (index path, binary32). */
@@ -121,7 +143,7 @@ typedef struct {
     float t0, t1;
     float lo[3], ld[3]; /* (lambda, tu, tv) at t = 0 and their rate per unit t */
     int nnb;
-    float nb[8][3];     /* neighbour offsets in (lambda, tu, tv) */
+    float nb[ORC_MAX_NB][3]; /* neighbour offsets in (lambda, tu, tv) */
 } orc_ray;
 
 /* ------------------------------------------------------------------ */
@@ -411,14 +433,27 @@ static void sweep_rows(void* p, long lo, long hi) {
                 if (s->opt && s->opt->opacity_correction)
                     alpha = 1.0 - pow(1.0 - alpha, s->spacing_vox);
             }
+            const int depth = s->opt && s->opt->quantity == ORC_OPTICAL_DEPTH;
             double stored = s->T[t];
             if (s->opt && s->opt->comp_n != 0.0f) {
-                /* Darkening compensation: scale the slice by (1 + alpha)^n. */
-                stored = stored * pow(1.0 + alpha, (double)s->opt->comp_n);
-                if (stored > 1.0) stored = 1.0;
+                /* Darkening compensation: scale the slice by (1 + alpha)^n
+                   (in depth form: subtract n ln(1 + alpha)). */
+                if (depth) {
+                    stored = stored - (double)s->opt->comp_n * log1p(alpha);
+                    if (stored < 0.0) stored = 0.0;
+                } else {
+                    stored = stored * pow(1.0 + alpha, (double)s->opt->comp_n);
+                    if (stored > 1.0) stored = 1.0;
+                }
             }
             s->Bk[t] = stored;
-            s->T[t] = s->T[t] * (1.0 - alpha);
+            if (depth) {
+                /* Eq. 5-6: extinctions add; tau = -ln(1 - alpha). */
+                double D = s->T[t] + (-log1p(-alpha));
+                s->T[t] = D < ORC_DEPTH_MAX ? D : ORC_DEPTH_MAX;
+            } else {
+                s->T[t] = s->T[t] * (1.0 - alpha);
+            }
         }
     }
 }
@@ -432,7 +467,13 @@ int orc_build_stack_rows(const orc_volume* vol, const orc_tf* tf, const orc_ligh
     const size_t RR = (size_t)lt->R * (size_t)lt->R;
     double* T = (double*)malloc(RR * sizeof(double));
     if (!T) return ORC_ENOMEM;
-    for (size_t t = 0; t < RR; ++t) T[t] = 1.0; /* LightBuffer initialised to full light */
+    if (opt && opt->quantity != ORC_TRANSMITTANCE && opt->quantity != ORC_OPTICAL_DEPTH) {
+        free(T);
+        return ORC_EINVAL;
+    }
+    /* LightBuffer initialised to full light: T = 1, or optical depth 0. */
+    const double full = (opt && opt->quantity == ORC_OPTICAL_DEPTH) ? 0.0 : 1.0;
+    for (size_t t = 0; t < RR; ++t) T[t] = full;
     sweep_ctx s;
     s.vol = vol;
     s.tf = tf;
@@ -521,6 +562,7 @@ static void quarter_turn(int m, float bu, float bv, float* cu, float* cv) {
 int orc_ray_setup(const orc_light* lt, const orc_frame* fr, const orc_render_opts* ro,
                   int x, int y, orc_ray* ray) {
     if (!lt || !fr || !ro || !ray) return ORC_EINVAL;
+    if (ro->shell_count < 0 || ro->shell_count > ORC_MAX_SHELLS) return ORC_EINVAL;
     memset(ray, 0, sizeof(*ray));
     /* Pixel centre (x + 1/2, y + 1/2); row 0 at the top. */
     float qx = (float)(2 * x + 1) / (float)fr->W;
@@ -571,16 +613,21 @@ int orc_ray_setup(const orc_light* lt, const orc_frame* fr, const orc_render_opt
     ray->ld[2] = dot3f(ray->d, lt->V) * lt->sigma;
 
     if (ro->mode == ORC_SHELL) {
-        /* Shell: the six points S +- r e_a, r one voxel (Section 3.2.3). */
-        float r = ro->shell_radius_vox / (float)fr->Nmax;
-        ray->nnb = 6;
-        for (int a = 0; a < 3; ++a) {
-            float rl = r * lt->L[a];
-            float ru = r * lt->U[a];
-            float rv = r * lt->V[a];
-            float off[3] = {rl * lt->kappa, ru * lt->sigma, rv * lt->sigma};
-            for (int s = 0; s < 2; ++s)
-                for (int c = 0; c < 3; ++c) ray->nb[2 * a + s][c] = s ? -off[c] : off[c];
+        /* Shells (Section 3.2.3): shell q = 1..Q holds the six points
+           S +- q r e_a, r = shell_radius_vox voxels. */
+        const int Q = ro->shell_count > 0 ? ro->shell_count : 1;
+        ray->nnb = 6 * Q;
+        for (int q = 1; q <= Q; ++q) {
+            float r = ((float)q * ro->shell_radius_vox) / (float)fr->Nmax;
+            for (int a = 0; a < 3; ++a) {
+                float rl = r * lt->L[a];
+                float ru = r * lt->U[a];
+                float rv = r * lt->V[a];
+                float off[3] = {rl * lt->kappa, ru * lt->sigma, rv * lt->sigma};
+                for (int s = 0; s < 2; ++s)
+                    for (int c = 0; c < 3; ++c)
+                        ray->nb[6 * (q - 1) + 2 * a + s][c] = s ? -off[c] : off[c];
+            }
         }
     } else if (ro->mode == ORC_CONE) {
         /* Cone: apex S, axis towards the light.  Ring n (n = 1, 2) is centred
@@ -621,11 +668,9 @@ int orc_ray_setup(const orc_light* lt, const orc_frame* fr, const orc_render_opt
 /* Bilinear lookup in slice k of the buffer (Eq. 9 for k, Eq. 10 for UV):
    k = clamp(floor(lambda + 1/2), 0, n - 1); texel centres at integer (tu, tv),
    clamp to edge. */
-static double stack_lookup(const double* B, const orc_light* lt, float lam, float tu, float tv,
-                           int* rec) {
+static double bilinear_slice(const double* B, const orc_light* lt, int k, float tu, float tv,
+                             int* rec) {
     const int R = lt->R;
-    float lh = lam + 0.5f;
-    int k = floor_clamp(lh, 0, lt->n - 1);
     int iu = floor_clamp(tu, -1, R);
     int iv = floor_clamp(tv, -1, R);
     if (rec) {
@@ -642,6 +687,37 @@ static double stack_lookup(const double* B, const orc_light* lt, float lam, floa
     double top = (1.0 - fu) * S[(size_t)j0 * R + i0] + fu * S[(size_t)j0 * R + i1];
     double bot = (1.0 - fu) * S[(size_t)j1 * R + i0] + fu * S[(size_t)j1 * R + i1];
     return (1.0 - fv) * top + fv * bot;
+}
+
+static double stack_lookup(const double* B, const orc_light* lt, float lam, float tu, float tv,
+                           int* rec) {
+    float lh = lam + 0.5f;
+    int k = floor_clamp(lh, 0, lt->n - 1);
+    return bilinear_slice(B, lt, k, tu, tv, rec);
+}
+
+/* Light factor of one lookup point: the buffer value at (lambda, tu, tv),
+   from the nearest slice (as stack_lookup) or, with linear slice filtering,
+   interpolated between slices k0 = clamp(floor(lambda), 0, n - 1) and
+   min(k0 + 1, n - 1) with weight lambda - k0 clamped to [0, 1]; then, for an
+   optical-depth buffer, the transmittance exp(-D) (Eq. 5-6). */
+static double light_lookup(const double* B, const orc_light* lt, const orc_render_opts* ro,
+                           float lam, float tu, float tv, int* rec) {
+    double v;
+    if (ro->slice_filter == ORC_SLICE_LINEAR) {
+        int k0 = floor_clamp(lam, 0, lt->n - 1);
+        int k1 = k0 + 1 < lt->n ? k0 + 1 : k0;
+        double w = (double)lam - (double)k0;
+        if (w < 0.0) w = 0.0;
+        if (w > 1.0) w = 1.0;
+        double b0 = bilinear_slice(B, lt, k0, tu, tv, rec);
+        double b1 = bilinear_slice(B, lt, k1, tu, tv, NULL);
+        v = (1.0 - w) * b0 + w * b1;
+    } else {
+        v = stack_lookup(B, lt, lam, tu, tv, rec);
+    }
+    if (!B) return 1.0;
+    return ro->quantity == ORC_OPTICAL_DEPTH ? exp(-v) : v;
 }
 
 /* ------------------------------------------------------------------ */
@@ -717,16 +793,18 @@ static void march_one(const march_ctx* s, long p) {
             /* Attenuation coefficient a_s of the sample (Eq. 7). */
             double coef = 1.0;
             if (ro->mode == ORC_SHADOW) {
-                coef = stack_lookup(s->B, s->lt, l[0], l[1], l[2], rec ? rec + 8 : NULL);
+                coef = light_lookup(s->B, s->lt, ro, l[0], l[1], l[2], rec ? rec + 8 : NULL);
             } else {
-                if (rec) stack_lookup(NULL, s->lt, l[0], l[1], l[2], rec + 8);
+                if (rec) light_lookup(NULL, s->lt, ro, l[0], l[1], l[2], rec + 8);
                 if (ro->mode == ORC_SHELL || ro->mode == ORC_CONE) {
                     double sum = 0.0;
                     for (int j = 0; j < ray.nnb; ++j) {
                         float q0 = l[0] + ray.nb[j][0];
                         float q1 = l[1] + ray.nb[j][1];
                         float q2 = l[2] + ray.nb[j][2];
-                        sum += stack_lookup(s->B, s->lt, q0, q1, q2, rec ? rec + 11 + 3 * j : NULL);
+                        /* The record has room for the first 8 neighbours. */
+                        int* nrec = (rec && j < 8) ? rec + 11 + 3 * j : NULL;
+                        sum += light_lookup(s->B, s->lt, ro, q0, q1, q2, nrec);
                     }
                     coef = sum / (double)ray.nnb;
                 }
@@ -795,6 +873,10 @@ static int render_common(const orc_volume* vol, const orc_tf* tf, const orc_ligh
     if (!valid_inputs(vol, tf) || !lt || !cam || !ro || !out || !xs || !ys) return ORC_EINVAL;
     if (ro->mode < ORC_NONE || ro->mode > ORC_CONE) return ORC_EINVAL;
     if (ro->mode != ORC_NONE && !B) return ORC_EINVAL;
+    if (ro->quantity != ORC_TRANSMITTANCE && ro->quantity != ORC_OPTICAL_DEPTH) return ORC_EINVAL;
+    if (ro->slice_filter != ORC_SLICE_NEAREST && ro->slice_filter != ORC_SLICE_LINEAR)
+        return ORC_EINVAL;
+    if (ro->shell_count < 0 || ro->shell_count > ORC_MAX_SHELLS) return ORC_EINVAL;
     orc_frame fr;
     int rc = orc_frame_setup(cam, W, H, ro->step_vox, vol_nmax(vol), &fr);
     if (rc) return rc;
@@ -902,4 +984,9 @@ int orc_texel_world(const orc_light* lt, int i, int j, int k, float P[3]) {
 double orc_stack_lookup(const double* B, const orc_light* lt, float lam, float tu, float tv,
                         int rec[3]) {
     return stack_lookup(B, lt, lam, tu, tv, rec);
+}
+
+double orc_light_lookup(const double* B, const orc_light* lt, const orc_render_opts* ro,
+                        float lam, float tu, float tv, int rec[3]) {
+    return light_lookup(B, lt, ro, lam, tu, tv, rec);
 }

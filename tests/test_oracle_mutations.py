@@ -28,8 +28,20 @@ MUTATIONS = {
     "cone-away-from-light": ("o[0] = -(float)ring;", "o[0] = (float)ring;"),
     "cone-rotation-sign": ("case 1: *cu = -bv; *cv = bu; break;", "case 1: *cu = bv; *cv = bu; break;"),
     "cone-radius-dropped-tan": ("float radw = dist * tanphi;", "float radw = dist;"),
-    "shell-radius-units": ("float r = ro->shell_radius_vox / (float)fr->Nmax;",
-                           "float r = ro->shell_radius_vox / (float)(2 * fr->Nmax);"),
+    "shell-radius-units": ("float r = ((float)q * ro->shell_radius_vox) / (float)fr->Nmax;",
+                           "float r = ((float)q * ro->shell_radius_vox) / (float)(2 * fr->Nmax);"),
+    "shells-same-radius": ("float r = ((float)q * ro->shell_radius_vox) / (float)fr->Nmax;",
+                           "float r = ro->shell_radius_vox / (float)fr->Nmax;"),
+    "depth-extinction-sign": ("double D = s->T[t] + (-log1p(-alpha));",
+                              "double D = s->T[t] + log1p(alpha);"),
+    "depth-cap-lower": ("#define ORC_DEPTH_MAX 64.0", "#define ORC_DEPTH_MAX 16.0"),
+    "depth-exp-sign": ("return ro->quantity == ORC_OPTICAL_DEPTH ? exp(-v) : v;",
+                       "return ro->quantity == ORC_OPTICAL_DEPTH ? exp(v) : v;"),
+    "depth-comp-n-sign": ("stored = stored - (double)s->opt->comp_n * log1p(alpha);",
+                          "stored = stored + (double)s->opt->comp_n * log1p(alpha);"),
+    "slice-lerp-weights-swapped": ("v = (1.0 - w) * b0 + w * b1;", "v = w * b0 + (1.0 - w) * b1;"),
+    "slice-lerp-nearest-base": ("int k0 = floor_clamp(lam, 0, lt->n - 1);",
+                                "int k0 = floor_clamp(lam + 0.5f, 0, lt->n - 1);"),
     "sample-count-le": ("if (!(t < ray.t1)) break;", "if (!(t <= ray.t1)) break;"),
     "opacity-correction-exponent": ("alpha = 1.0 - pow(1.0 - alpha, s->spacing_vox);",
                                     "alpha = 1.0 - pow(1.0 - alpha, 1.0 / s->spacing_vox);"),

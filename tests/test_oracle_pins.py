@@ -601,3 +601,192 @@ def test_oracle_rejects_invalid_input(orc):
         orc.light_setup((np.nan, 0, 1), 4, 4)
     with pytest.raises(ValueError):
         orc.light_setup((0, 0, 1), 0, 4)
+
+
+# --------------------------------------------------------------------------
+# Variants: the extinction form of the buffer (Eq. 5-6), linear filtering
+# between slices, several shells (Section 3.2.3).
+
+def test_depth_buffer_is_summed_extinction_on_slab(orc):
+    """Eq. 5-6: the buffer holds D_k = m_k (-ln(1 - a)), m_k the slab planes
+    before plane k; exp(-D_k) is T1's geometric series."""
+    a = f32(0.3)
+    vol, tf, N, z_lo, z_hi = slab_scene(a)
+    n, R = 50, 24
+    lt = orc.light_setup((0, 0, 1), n, R)
+    D = orc.build_stack(vol, tf, 0, 255, lt, quantity=orc.OPTICAL_DEPTH)
+    d = np.arange(n) / n
+    in_slab = (d >= z_lo / N) & (d <= (z_hi + 1) / N)
+    m = np.concatenate([[0], np.cumsum(in_slab)[:-1]])
+    tau = -math.log(1.0 - a)
+    col = D[:, R // 2, R // 2]
+    assert np.abs(col - m * tau).max() < 1e-12
+    assert np.abs(np.exp(-col) - (1 - a) ** m).max() < 1e-12
+    assert D[0].max() == 0.0                     # slice 0: no medium before it
+    corner = D[:, 0, 0]                          # a column that misses the cube
+    assert np.all(corner == 0.0)
+
+
+def test_depth_buffer_caps_opaque_layers(orc):
+    """An opaque layer (alpha = 1, tau infinite) leaves exactly the cap 64
+    behind it; depth never decreases, and exp(-D) is the transmittance 0 to
+    within exp(-64)."""
+    N = 16
+    vol = np.zeros((N, N, N), np.uint8)
+    vol[4:12] = 255
+    tf = step_tf(256, [(128, 256, (1, 1, 1, 1.0))])
+    n, R = 32, 8
+    lt = orc.light_setup((0, 0, 1), n, R)
+    D = orc.build_stack(vol, tf, 0, 255, lt, quantity=orc.OPTICAL_DEPTH)
+    T = orc.build_stack(vol, tf, 0, 255, lt)
+    col = D[:, R // 2, R // 2]
+    assert col[0] == 0.0 and np.all(col[: int(0.2 * n)] == 0.0)   # before the layer
+    assert np.all(col[int(0.8 * n):] == orc.DEPTH_MAX)               # behind it: capped
+    assert np.all(np.diff(col) >= 0.0) and col.max() == orc.DEPTH_MAX
+    assert np.isfinite(D).all()
+    assert np.abs(np.exp(-D) - T).max() < 1e-27
+
+
+def test_depth_comp_n_subtracts_log_compensation(orc):
+    """(1 + alpha)^c compensation in depth form: D' = max(0, D - c ln(1 + alpha))."""
+    a, c = f32(0.3), 2.0
+    vol, tf, N, z_lo, z_hi = slab_scene(a)
+    n, R = 50, 8
+    lt = orc.light_setup((0, 0, 1), n, R)
+    D = orc.build_stack(vol, tf, 0, 255, lt, comp_n=c, quantity=orc.OPTICAL_DEPTH)
+    d = np.arange(n) / n
+    in_slab = (d >= z_lo / N) & (d <= (z_hi + 1) / N)
+    m = np.concatenate([[0], np.cumsum(in_slab)[:-1]])
+    want = np.maximum(0.0, m * -math.log(1 - a) - c * np.log1p(a * in_slab))
+    assert np.abs(D[:, R // 2, R // 2] - want).max() < 1e-12
+
+
+def test_depth_and_transmittance_buffers_agree_at_texel_centres(orc):
+    """exp(-sum of -ln(1 - alpha)) = prod(1 - alpha) on an arbitrary volume and light."""
+    vol, tf, vmin, vmax = blob_scene()
+    tf[:, 3] *= 6.0                              # up to alpha 0.48 per sample
+    lt = orc.light_setup((0.3, -0.5, 0.81), 40, 20)
+    T = orc.build_stack(vol, tf, vmin, vmax, lt)
+    D = orc.build_stack(vol, tf, vmin, vmax, lt, quantity=orc.OPTICAL_DEPTH)
+    assert T.min() < 0.5                         # the light is really attenuated
+    assert np.abs(np.exp(-D) - T).max() < 1e-12
+
+
+def linear_field(n, R):
+    k, j, i = np.meshgrid(np.arange(n), np.arange(R), np.arange(R), indexing="ij")
+    return 0.1 + 0.01 * i + 0.001 * j + 0.0001 * k
+
+
+@pytest.mark.parametrize("quantity", ["transmittance", "depth"])
+@pytest.mark.parametrize("slices", ["nearest", "linear"])
+def test_light_lookup_reproduces_linear_field(orc, quantity, slices):
+    """Bilinear in (tu, tv), nearest or linear in lambda, clamped at every edge;
+    an optical-depth buffer returns exp(-value)."""
+    n, R = 5, 10
+    B = linear_field(n, R)
+    lt = orc.light_setup((0.2, 0.3, 0.9), n, R)
+    q = orc.OPTICAL_DEPTH if quantity == "depth" else orc.TRANSMITTANCE
+    sf = orc.SLICE_LINEAR if slices == "linear" else orc.SLICE_NEAREST
+    ro = orc.render_opts(orc.SHADOW, 0.5, quantity=q, slice_filter=sf)
+    rng = np.random.default_rng(7)
+    for _ in range(300):
+        lam, tu, tv = (np.float32(x) for x in (rng.uniform(-1.5, n + 0.5), rng.uniform(-2, R + 1),
+                                               rng.uniform(-2, R + 1)))
+        if slices == "linear":
+            kk = int(min(max(np.floor(lam), 0), n - 1))
+            lam_eff = min(max(float(lam), 0.0), n - 1.0)
+        else:
+            kk = int(min(max(np.floor(np.float32(lam + np.float32(0.5))), 0), n - 1))
+            lam_eff = kk
+        v = (0.1 + 0.01 * np.clip(float(tu), 0, R - 1) + 0.001 * np.clip(float(tv), 0, R - 1)
+             + 0.0001 * lam_eff)
+        want = math.exp(-v) if quantity == "depth" else v
+        got, rec = orc.light_lookup(B, lt, ro, lam, tu, tv)
+        assert got == pytest.approx(want, abs=1e-12)
+        assert rec[0] == kk
+
+
+@pytest.mark.parametrize("quantity", ["transmittance", "depth"])
+def test_T7_multi_shell_on_homogeneous_medium(orc, quantity):
+    """Two shells of radius 1 and 2 voxels (12 points, equal weights) on a
+    homogeneous cube under light +z, in either buffer form: the coefficient is
+    the mean of (1 - a)^k over the points' nearest slices."""
+    N, a = 32, f32(0.1)
+    vol = np.full((N, N, N), 200, np.uint8)
+    tf = step_tf(256, [(100, 256, (1, 1, 1, a))])
+    n, R = 50, 64
+    q = orc.OPTICAL_DEPTH if quantity == "depth" else orc.TRANSMITTANCE
+    lt = orc.light_setup((0, 0, 1), n, R)
+    B = orc.build_stack(vol, tf, 0, 255, lt, quantity=q)
+    c = cam((0.5, 0.5, 2.0), (0.5, 0.5, 0.5), (0, 1, 0), False, 40, 0.25)
+    ro = orc.render_opts(orc.SHELL, 0.5, quantity=q, shell_count=2)
+    img, *_ = orc.render_image(vol, tf, 0, 255, lt, B, c, 4, 4, ro)
+    z = 1 - np.arange(64) / 64
+    ks = lambda lam: np.clip(np.floor(lam + 0.5), 0, n - 1)
+    lam = n * z
+    r = n / N
+    coef = (8 * (1 - a) ** ks(lam) + (1 - a) ** ks(lam + r) + (1 - a) ** ks(lam - r)
+            + (1 - a) ** ks(lam + 2 * r) + (1 - a) ** ks(lam - 2 * r)) / 12
+    C = np.sum(a * (1 - a) ** np.arange(64) * coef)
+    assert np.allclose(img[..., :3], C, atol=1e-12)
+
+
+def test_linear_slice_filter_shadow_on_homogeneous_medium(orc):
+    """Light +z through a homogeneous cube (B_k = (1 - a)^k), a vertical eye ray,
+    shadow mode with linear slice filtering: the coefficient at lambda is
+    (1 - w)(1 - a)^k0 + w (1 - a)^(k0 + 1), k0 = floor(lambda), w = lambda - k0."""
+    N, a = 32, f32(0.1)
+    vol = np.full((N, N, N), 200, np.uint8)
+    tf = step_tf(256, [(100, 256, (1, 1, 1, a))])
+    n, R = 50, 64
+    lt = orc.light_setup((0, 0, 1), n, R)
+    B = orc.build_stack(vol, tf, 0, 255, lt)
+    c = cam((0.5, 0.5, 2.0), (0.5, 0.5, 0.5), (0, 1, 0), False, 40, 0.25)
+    ro = orc.render_opts(orc.SHADOW, 0.5, slice_filter=orc.SLICE_LINEAR)
+    img, *_ = orc.render_image(vol, tf, 0, 255, lt, B, c, 4, 4, ro)
+    lam = np.clip(n * (1 - np.arange(64) / 64), 0, n - 1)
+    k0 = np.floor(lam)
+    k1 = np.minimum(k0 + 1, n - 1)
+    w = lam - k0
+    coef = (1 - w) * (1 - a) ** k0 + w * (1 - a) ** k1
+    C = np.sum(a * (1 - a) ** np.arange(64) * coef)
+    assert np.allclose(img[..., :3], C, atol=1e-12)
+    # Linear filtering differs from the nearest slice here (lambda is not on a plane).
+    ref, *_ = orc.render_image(vol, tf, 0, 255, lt, B, c, 4, 4, orc.render_opts(orc.SHADOW, 0.5))
+    assert np.abs(img - ref).max() > 1e-5
+
+
+def test_shell_points_of_several_shells(orc):
+    """Shell q of Q holds the axis neighbours at q r."""
+    rng = np.random.default_rng(71)
+    d = rng.normal(size=3)
+    n, R, Nmax = 64, 128, 48
+    lt = orc.light_setup(d, n, R)
+    L, U, V = (np.array(x[:], dtype=np.float64) for x in (lt.L, lt.U, lt.V))
+    ro = orc.render_opts(orc.SHELL, 0.5, shell_radius_vox=1.25, shell_count=3)
+    c = cam((2, 2, 2), (0.5, 0.5, 0.5), (0, 0, 1), True, 40, 0.5)
+    fr = orc.frame_setup(c, 4, 4, 0.5, Nmax)
+    ray = orc.ray_setup(lt, fr, ro, 1, 2)
+    assert ray.nnb == 18
+    for q in (1, 2, 3):
+        r = q * 1.25 / Nmax
+        for a in range(3):
+            for s, sign in enumerate((1.0, -1.0)):
+                w = np.zeros(3)
+                w[a] = sign * r
+                want = np.array([lt.kappa * (L @ w), lt.sigma * (U @ w), lt.sigma * (V @ w)])
+                got = np.array(ray.nb[6 * (q - 1) + 2 * a + s][:], float)
+                assert np.allclose(got, want, atol=1e-5)
+
+
+def test_variant_options_are_validated(orc):
+    vol = np.zeros((4, 4, 4), np.uint8)
+    tf = step_tf(16, [(1, 16, (1, 1, 1, 0.1))])
+    lt = orc.light_setup((0, 0, 1), 4, 4)
+    with pytest.raises(ValueError):
+        orc.build_stack(vol, tf, 0, 255, lt, quantity=2)
+    B = orc.build_stack(vol, tf, 0, 255, lt)
+    c = cam((0.5, 0.5, 2.0), (0.5, 0.5, 0.5), (0, 1, 0), False, 40, 0.5)
+    for kw in (dict(quantity=2), dict(slice_filter=2), dict(shell_count=5), dict(shell_count=-1)):
+        with pytest.raises(ValueError):
+            orc.render_image(vol, tf, 0, 255, lt, B, c, 2, 2, orc.render_opts(orc.SHELL, 0.5, **kw))
