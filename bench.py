@@ -443,8 +443,17 @@ def precision_workload(args):
                                 cone_half_angle_deg=sc.cone_half_angle_deg)
         refs[mode] = oracle.render_pixels(sc.volume, sc.tf, sc.vmin, sc.vmax, light, ref_stack,
                                           sc.camera, W, H, ro, xs.ravel(), ys.ravel())[0]
-    oracle_s = time.perf_counter() - t0
     del ref_stack
+    # The extinction form (Eq. 5-6) against the oracle's own optical-depth frame.
+    depth_stack = oracle.build_stack(sc.volume, sc.tf, sc.vmin, sc.vmax, light,
+                                     quantity=oracle.OPTICAL_DEPTH)
+    ro = oracle.render_opts(vi.CONE, sc.step_vox, sc.ert, sc.bg, sc.light_color,
+                            cone_half_angle_deg=sc.cone_half_angle_deg,
+                            quantity=oracle.OPTICAL_DEPTH)
+    depth_ref = oracle.render_pixels(sc.volume, sc.tf, sc.vmin, sc.vmax, light, depth_stack,
+                                     sc.camera, W, H, ro, xs.ravel(), ys.ravel())[0]
+    del depth_stack
+    oracle_s = time.perf_counter() - t0
     ctx = vi.Context(0)
     ctx.load_volume(torch.from_numpy(sc.volume.view(np.int16)).cuda(), dtype=vi.U16)
     ctx.set_transfer_function(sc.tf, sc.vmin, sc.vmax)
@@ -453,28 +462,34 @@ def precision_workload(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     names = {vi.F32: "f32", vi.F16: "f16", vi.BF16: "bf16", vi.UNORM16: "unorm16"}
     rows = {}
-    for mode, mname in ((vi.SHELL, "shell"), (vi.CONE, "cone")):
-        for fmt in (vi.F32, vi.F16, vi.BF16, vi.UNORM16):
-            def bld():
-                ctx.build_attenuation(sc.n_slices, sc.slice_res, mode, format=fmt)
+    cases = [(mode, mname, fmt, vi.TRANSMITTANCE) for mode, mname in
+             ((vi.SHELL, "shell"), (vi.CONE, "cone"))
+             for fmt in (vi.F32, vi.F16, vi.BF16, vi.UNORM16)]
+    cases += [(vi.CONE, "cone-depth", fmt, vi.OPTICAL_DEPTH) for fmt in (vi.F32, vi.F16, vi.BF16)]
+    for mode, mname, fmt, quantity in cases:
+        def bld():
+            ctx.build_attenuation(sc.n_slices, sc.slice_res, mode, format=fmt,
+                                  quantity=quantity)
 
-            def rnd():
-                ctx.render(sc.camera, W, H, sc.step_vox, out=out, ert=sc.ert, bg=sc.bg)
-            for _ in range(args.warmup):
-                bld()
-                rnd()
-            sweep_ms, march_ms = timed_frames(ctx, bld, rnd, flush, args.steps)
-            img = out.cpu().numpy().astype(np.float64)[y0:y0 + 144, x0:x0 + 256].reshape(-1, 4)
-            err = np.abs(img - refs[mode])
-            rows[f"{mname}-{names[fmt]}"] = {
-                "frames_per_s": round(1000.0 / (sweep_ms + march_ms), 2),
-                "sweep_ms": round(sweep_ms, 4), "march_ms": round(march_ms, 4),
-                "max_abs_err_rgba": [float(f"{v:.3g}") for v in err.max(axis=0)],
-                "mean_abs_err_rgba": [float(f"{v:.3g}") for v in err.mean(axis=0)]}
+        def rnd():
+            ctx.render(sc.camera, W, H, sc.step_vox, out=out, ert=sc.ert, bg=sc.bg)
+        for _ in range(args.warmup):
+            bld()
+            rnd()
+        sweep_ms, march_ms = timed_frames(ctx, bld, rnd, flush, args.steps)
+        img = out.cpu().numpy().astype(np.float64)[y0:y0 + 144, x0:x0 + 256].reshape(-1, 4)
+        err = np.abs(img - (depth_ref if quantity == vi.OPTICAL_DEPTH else refs[mode]))
+        rows[f"{mname}-{names[fmt]}"] = {
+            "frames_per_s": round(1000.0 / (sweep_ms + march_ms), 2),
+            "sweep_ms": round(sweep_ms, 4), "march_ms": round(march_ms, 4),
+            "max_abs_err_rgba": [float(f"{v:.3g}") for v in err.max(axis=0)],
+            "mean_abs_err_rgba": [float(f"{v:.3g}") for v in err.mean(axis=0)]}
+    for mname in ("shell", "cone", "cone-depth"):
         base = rows[f"{mname}-f32"]["frames_per_s"]
         for fmt in names.values():
-            rows[f"{mname}-{fmt}"]["gain_vs_f32"] = round(rows[f"{mname}-{fmt}"]["frames_per_s"]
-                                                          / base, 3)
+            if f"{mname}-{fmt}" in rows:
+                rows[f"{mname}-{fmt}"]["gain_vs_f32"] = round(
+                    rows[f"{mname}-{fmt}"]["frames_per_s"] / base, 3)
     print(json.dumps({"workload": "precision", "metric": "frames/s", "unit": "frames/s",
                       "scene": sc.name, "steps": args.steps, "warmup": args.warmup,
                       "error_reference": "FP64 oracle, centred 256x144 crop "

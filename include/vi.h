@@ -55,6 +55,10 @@ typedef enum {
 enum { VI_U8 = 0, VI_U16 = 1 };                                  /* voxel types */
 enum { VI_NONE = 0, VI_SHADOW = 1, VI_SHELL = 2, VI_CONE = 3 };  /* coefficient modes */
 enum { VI_F32 = 0, VI_F16 = 1, VI_BF16 = 2, VI_UNORM16 = 3 };    /* stack storage */
+enum { VI_TRANSMITTANCE = 0, VI_OPTICAL_DEPTH = 1 };             /* what the stack holds */
+enum { VI_SLICE_NEAREST = 0, VI_SLICE_LINEAR = 1 };              /* slice filtering */
+#define VI_DEPTH_MAX 64.0f  /* cap of a stored optical depth: exp(-64) < 2e-28 */
+#define VI_MAX_SHELLS 4
 
 /* Options of the attenuation sweep.  NULL means the defaults shown. */
 typedef struct {
@@ -66,6 +70,16 @@ typedef struct {
                                   1: alpha' = 1 - (1 - alpha)^(slice spacing in voxels) */
     float comp_n;              /* darkening compensation (Section 4): each stored slice is
                                   multiplied by (1 + alpha)^comp_n, clamped to 1; 0 = off */
+    int quantity;              /* VI_TRANSMITTANCE (default): B_k = prod_{j<k} (1 - alpha_j),
+                                  Eq. 4 in product form.  VI_OPTICAL_DEPTH: the extinction form
+                                  of Eq. 5-6, B_k = sum_{j<k} -ln(1 - alpha_j) carried in FP32
+                                  and capped at VI_DEPTH_MAX; a lookup's light factor is then
+                                  exp(-B) of the interpolated depth, and comp_n subtracts
+                                  comp_n ln(1 + alpha) (floored at 0).  Not with VI_UNORM16. */
+    int shell_count;           /* VI_SHELL: shells at radii r, 2r, ... (Section 3.2.3: the
+                                  number and size of the shells can vary), six points each,
+                                  equal weights; 0 or 1 (default) = one shell, at most
+                                  VI_MAX_SHELLS */
 } vi_build_opts;
 
 /* A pinhole (perspective) or orthographic camera in unit-cube coordinates.
@@ -90,6 +104,9 @@ typedef struct {
                                pixel (row-major); NULL = not written */
     int32_t* lit_counts;    /* optional device buffer of W*H int32: samples with opacity > 0,
                                the ones that read the stack; NULL = not written */
+    int slice_filter;       /* VI_SLICE_NEAREST (default): the slice of Eq. 9 rounded to the
+                               nearest plane; VI_SLICE_LINEAR: linear in lambda between slices
+                               k0 = clamp(floor(lambda), 0, n - 1) and min(k0 + 1, n - 1) */
 } vi_render_opts;
 
 /* Create a context on CUDA device `device` using `cuda_stream` (a cudaStream_t;

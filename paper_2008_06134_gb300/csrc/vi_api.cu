@@ -132,6 +132,9 @@ size_t format_bytes(int f) { return f == VI_F32 ? 4 : 2; }
 
 int nmax(const vi_ctx* c) { return std::max(c->vr->nx, std::max(c->vr->ny, c->vr->nz)); }
 
+static_assert(vi::kMaxShells == VI_MAX_SHELLS, "shell limit differs between header and kernels");
+static_assert(vi::kDepthMax == VI_DEPTH_MAX, "depth cap differs between header and kernels");
+
 vi_build_opts default_build_opts() {
     vi_build_opts o;
     o.format = VI_F32;
@@ -139,6 +142,8 @@ vi_build_opts default_build_opts() {
     o.shell_radius_vox = 1.0f;
     o.opacity_correction = 0;
     o.comp_n = 0.0f;
+    o.quantity = VI_TRANSMITTANCE;
+    o.shell_count = 1;
     return o;
 }
 
@@ -298,20 +303,25 @@ int fill_march_params(vi_ctx* c, const vi_camera* cam, int W, int H, float step_
     if (c->lt_valid) p->lt = c->lt;  // else n = R = 0: no lookups
     p->stack = c->sview;
     const LightFrame& lt = p->lt;
+    p->shells = c->bopts.shell_count > 1 ? c->bopts.shell_count : 1;
     if (c->mode == VI_SHELL && c->lt_valid) {
-        // The six points S +- r e_a as light-space offsets.
-        float r = c->bopts.shell_radius_vox / (float)nmax(c);
-        for (int a = 0; a < 3; ++a) {
-            float rl = r * lt.L[a];
-            float ru = r * lt.U[a];
-            float rv = r * lt.V[a];
-            float off[3] = {rl * lt.kappa, ru * lt.sigma, rv * lt.sigma};
-            for (int k = 0; k < 3; ++k) {
-                p->shell_off[2 * a][k] = off[k];
-                p->shell_off[2 * a + 1][k] = -off[k];
+        // Shell q holds the six points S +- q r e_a, as light-space offsets.
+        for (int q = 1; q <= p->shells; ++q) {
+            float r = ((float)q * c->bopts.shell_radius_vox) / (float)nmax(c);
+            for (int a = 0; a < 3; ++a) {
+                float rl = r * lt.L[a];
+                float ru = r * lt.U[a];
+                float rv = r * lt.V[a];
+                float off[3] = {rl * lt.kappa, ru * lt.sigma, rv * lt.sigma};
+                for (int k = 0; k < 3; ++k) {
+                    p->shell_off[q - 1][2 * a][k] = off[k];
+                    p->shell_off[q - 1][2 * a + 1][k] = -off[k];
+                }
             }
         }
     }
+    p->depth = c->bopts.quantity == VI_OPTICAL_DEPTH ? 1 : 0;
+    p->slice_linear = ro->slice_filter == VI_SLICE_LINEAR ? 1 : 0;
     if (c->mode == VI_CONE && c->lt_valid) {
         // Ring n sits n slice spacings towards the light; radius n dL tan(phi).
         float tanphi = (float)std::tan((double)c->bopts.cone_half_angle_deg * (M_PI / 180.0));
@@ -339,6 +349,8 @@ int check_render_inputs(vi_ctx* c, const vi_camera* cam, int W, int H, float ste
     if ((long long)W * (long long)H > 0x7fffffffLL) return VI_EINVAL;
     if (!(step_vox >= 1e-3f && step_vox <= 1e3f)) return VI_EINVAL;
     if (!std::isfinite(ro->ert) || !std::isfinite(ro->ambient)) return VI_EINVAL;
+    if (ro->slice_filter != VI_SLICE_NEAREST && ro->slice_filter != VI_SLICE_LINEAR)
+        return VI_EINVAL;
     for (int k = 0; k < 4; ++k)
         if (!std::isfinite(ro->bg[k])) return VI_EINVAL;
     if (c->vr->vtype < 0 || !c->tf || !c->flags_ok || c->mode < 0) return VI_ESTATE;
@@ -627,6 +639,9 @@ int vi_build_attenuation(vi_ctx* c, int n, int R, int mode, const vi_build_opts*
     if (!(o.cone_half_angle_deg > 0.0f && o.cone_half_angle_deg < 90.0f)) return VI_EINVAL;
     if (!(o.shell_radius_vox > 0.0f) || !std::isfinite(o.shell_radius_vox)) return VI_EINVAL;
     if (!(o.comp_n >= 0.0f) || !std::isfinite(o.comp_n)) return VI_EINVAL;
+    if (o.quantity != VI_TRANSMITTANCE && o.quantity != VI_OPTICAL_DEPTH) return VI_EINVAL;
+    if (o.quantity == VI_OPTICAL_DEPTH && o.format == VI_UNORM16) return VI_EINVAL;
+    if (o.shell_count < 0 || o.shell_count > VI_MAX_SHELLS) return VI_EINVAL;
     if (c->vr->vtype < 0 || !c->tf || !c->flags_ok) return VI_ESTATE;
     if (mode != VI_NONE && !c->has_light) return VI_ESTATE;
 
@@ -664,6 +679,7 @@ int vi_build_attenuation(vi_ctx* c, int n, int R, int mode, const vi_build_opts*
     p.opacity_correction = o.opacity_correction ? 1 : 0;
     p.spacing_vox = lt.dL * (float)nmax(c);
     p.comp_n = o.comp_n;
+    p.depth = o.quantity == VI_OPTICAL_DEPTH ? 1 : 0;
     cudaError_t e = vi::launch_sweep(p, c->vr->vtype, o.format, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e);
     ++c->launches;

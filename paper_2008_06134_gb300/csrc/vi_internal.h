@@ -78,7 +78,12 @@ struct SweepParams {
     int opacity_correction;
     float spacing_vox;        // slice spacing in voxels (opacity correction exponent)
     float comp_n;             // darkening compensation exponent, 0 = off
+    int depth;                // 1: store optical depth (Eq. 5-6), else transmittance
 };
+
+// Cap of a stored optical depth (exp(-64) < 2e-28) and the most shells.
+constexpr float kDepthMax = 64.0f;
+constexpr int kMaxShells = 4;
 
 // Camera frame (binary32 index path): forward f, right r, up u, image-plane
 // half extents (sx, sy) at unit distance (perspective) or absolute (ortho).
@@ -99,7 +104,10 @@ struct MarchParams {
     LightFrame lt;
     StackView stack;
     CameraFrame cam;
-    float shell_off[6][3];  // light-space offsets of the six shell points
+    float shell_off[kMaxShells][6][3];  // light-space offsets of the shell points, per shell
+    int shells;             // shells in use (1 .. kMaxShells)
+    int depth;              // 1: the stack holds optical depth; light factor exp(-value)
+    int slice_linear;       // 1: linear filtering between slices
     float cone_rad[2];      // ring radii in texels, rings 1 and 2
     float cone_thr;         // 1e-6 * sigma: B_proj fallback threshold
     float ert;

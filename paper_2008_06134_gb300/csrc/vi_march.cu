@@ -105,12 +105,41 @@ __device__ __forceinline__ void ray_setup(const MarchParams& p, int x, int y, Ra
     }
 }
 
-// Light-space cell of a lookup point, for the trace only.
+// Light-space cell of a lookup point, for the trace only: the nearest slice,
+// or with linear slice filtering the lower of the two bracketing slices.
 __device__ __forceinline__ void lookup_cell(int n, int R, float lam, float tu, float tv,
-                                            int32_t* rec) {
-    rec[0] = floor_clamp(__fadd_rn(lam, 0.5f), 0, n - 1);
+                                            bool slice_linear, int32_t* rec) {
+    rec[0] = slice_linear ? floor_clamp(lam, 0, n - 1) : floor_clamp(__fadd_rn(lam, 0.5f), 0, n - 1);
     rec[1] = floor_clamp(tu, -1, R);
     rec[2] = floor_clamp(tv, -1, R);
+}
+
+// Stack value at a lookup point under the extended options: the nearest
+// slice, or linear in lambda between k0 = clamp(floor(lambda), 0, n - 1) and
+// min(k0 + 1, n - 1) (weight lambda - k0, exact in binary32, clamped to
+// [0, 1]).
+template <typename Fmt>
+__device__ __forceinline__ float slice_value(const MarchParams& p, int n, int R, float lam,
+                                             float tu, float tv, int* rec) {
+    if (p.slice_linear) {
+        const int k0 = floor_clamp(lam, 0, n - 1);
+        const int k1 = min(k0 + 1, n - 1);
+        const float w = fminf(fmaxf(__fsub_rn(lam, (float)k0), 0.0f), 1.0f);
+        if (rec) rec[0] = k0;
+        const float b0 = bilinear<Fmt>(p.stack, k0, R, tu, tv, rec);
+        const float b1 = bilinear<Fmt>(p.stack, k1, R, tu, tv);
+        return fmaf(w, b1 - b0, b0);
+    }
+    return stack_lookup<Fmt>(p.stack, n, R, lam, tu, tv, rec);
+}
+
+// Light factor of one lookup point: the stack value, or exp(-value) for an
+// optical-depth stack (Eq. 5-6).
+template <typename Fmt>
+__device__ __forceinline__ float light_factor(const MarchParams& p, int n, int R, float lam,
+                                              float tu, float tv, int* rec) {
+    const float v = slice_value<Fmt>(p, n, R, lam, tu, tv, rec);
+    return p.depth ? __expf(-v) : v;
 }
 
 enum { kEnded = 0, kContinue = 1, kStopped = 2, kEmpty = 3 };
@@ -158,7 +187,9 @@ __device__ __forceinline__ int last_transparent(const MarchParams& p, const Ray&
 // done), kStopped if early ray termination fired, kEmpty if the sample lies in
 // a brick that cannot yield alpha > 0 (counted, nothing composited), else
 // kContinue.
-template <typename VoxT, typename Fmt, int MODE, bool TRACE>
+// EXT enables the variant options (optical-depth stack, linear slice
+// filtering, several shells); the default kernels compile without them.
+template <typename VoxT, typename Fmt, int MODE, bool TRACE, bool EXT>
 __device__ __forceinline__ int march_sample(const MarchParams& p, const float* s_alpha,
                                             const Ray& r, int i, float& C0, float& C1, float& C2,
                                             float& A, int& count, int& lit, int32_t* rec) {
@@ -185,7 +216,7 @@ __device__ __forceinline__ int march_sample(const MarchParams& p, const float* s
         rec[5] = vc.cx;
         rec[6] = vc.cy;
         rec[7] = vc.cz;
-        rec[35] = MODE == 2 ? 6 : (MODE == 3 ? 8 : 0);
+        rec[35] = MODE == 2 ? 6 * (EXT ? p.shells : 1) : (MODE == 3 ? 8 : 0);
     }
 
     float coef = 1.0f;
@@ -199,37 +230,73 @@ __device__ __forceinline__ int march_sample(const MarchParams& p, const float* s
             rec[2] = __float_as_int(l0);
             rec[3] = __float_as_int(l1);
             rec[4] = __float_as_int(l2);
-            if (n > 0) lookup_cell(n, R, l0, l1, l2, rec + 8);
+            if (n > 0) lookup_cell(n, R, l0, l1, l2, EXT && p.slice_linear, rec + 8);
         }
         if (MODE == 1) {
-            coef = stack_lookup<Fmt>(p.stack, n, R, l0, l1, l2);
+            coef = EXT ? light_factor<Fmt>(p, n, R, l0, l1, l2, nullptr)
+                       : stack_lookup<Fmt>(p.stack, n, R, l0, l1, l2);
         } else if (MODE == 2) {
             float sum = 0.0f;
+            const int shells = EXT ? p.shells : 1;
+            if (EXT) {
+                // One point at a time: the variants' lookups are heavier, and
+                // keeping all of them in flight would spill.
+#pragma unroll 1
+                for (int j = 0; j < 6 * shells; ++j) {
+                    const int sh = j / 6, q = j - 6 * sh;
+                    float q0 = __fadd_rn(l0, p.shell_off[sh][q][0]);
+                    float q1 = __fadd_rn(l1, p.shell_off[sh][q][1]);
+                    float q2 = __fadd_rn(l2, p.shell_off[sh][q][2]);
+                    // The record has room for the first 8 neighbours.
+                    int* rr = (TRACE && j < 8) ? rec + 11 + 3 * j : nullptr;
+                    sum += light_factor<Fmt>(p, n, R, q0, q1, q2, rr);
+                }
+            } else {
 #pragma unroll
-            for (int q = 0; q < 6; ++q) {
-                float q0 = __fadd_rn(l0, p.shell_off[q][0]);
-                float q1 = __fadd_rn(l1, p.shell_off[q][1]);
-                float q2 = __fadd_rn(l2, p.shell_off[q][2]);
-                sum += stack_lookup<Fmt>(p.stack, n, R, q0, q1, q2,
-                                         TRACE ? rec + 11 + 3 * q : nullptr);
+                for (int q = 0; q < 6; ++q) {
+                    float q0 = __fadd_rn(l0, p.shell_off[0][q][0]);
+                    float q1 = __fadd_rn(l1, p.shell_off[0][q][1]);
+                    float q2 = __fadd_rn(l2, p.shell_off[0][q][2]);
+                    sum += stack_lookup<Fmt>(p.stack, n, R, q0, q1, q2,
+                                             TRACE ? rec + 11 + 3 * q : nullptr);
+                }
             }
-            coef = sum * (1.0f / 6.0f);
+            coef = EXT ? sum * (1.0f / (float)(6 * shells)) : sum * (1.0f / 6.0f);
         } else if (MODE == 3) {
             float sum = 0.0f;
+            if (EXT) {
+                // One point at a time (see the shell case).  Point j is ring
+                // j / 4, quarter turn m = j % 4 of B_proj about L.
+#pragma unroll 1
+                for (int j = 0; j < 8; ++j) {
+                    const int ring = j >> 2, m = j & 3;
+                    const float lr = __fadd_rn(l0, -(float)(ring + 1));
+                    const float bu = ring ? r.nbu[1] : r.nbu[0];
+                    const float bv = ring ? r.nbv[1] : r.nbv[0];
+                    float cu = (m & 1) ? -bv : bu, cv = (m & 1) ? bu : bv;
+                    if (m & 2) {
+                        cu = -cu;
+                        cv = -cv;
+                    }
+                    int* rr = TRACE ? rec + 11 + 3 * j : nullptr;
+                    sum += light_factor<Fmt>(p, n, R, lr, __fadd_rn(l1, cu), __fadd_rn(l2, cv), rr);
+                }
+            } else {
 #pragma unroll
-            for (int ring = 0; ring < 2; ++ring) {
-                // The ring's four points share lambda + offset, hence one slice.
-                const int k = slice_index(__fadd_rn(l0, -(float)(ring + 1)), n);
-                const float bu = r.nbu[ring], bv = r.nbv[ring];
-                // B_proj turned by m pi/2 about L: (bu, bv), (-bv, bu), (-bu, -bv), (bv, -bu).
-                const float du[4] = {bu, -bv, -bu, bv};
-                const float dv[4] = {bv, bu, -bv, -bu};
+                for (int ring = 0; ring < 2; ++ring) {
+                    // The ring's four points share lambda + offset, hence one slice.
+                    const int k = slice_index(__fadd_rn(l0, -(float)(ring + 1)), n);
+                    const float bu = r.nbu[ring], bv = r.nbv[ring];
+                    // B_proj turned by m pi/2 about L: (bu, bv), (-bv, bu), (-bu, -bv), (bv, -bu).
+                    const float du[4] = {bu, -bv, -bu, bv};
+                    const float dv[4] = {bv, bu, -bv, -bu};
 #pragma unroll
-                for (int m = 0; m < 4; ++m) {
-                    int* rr = TRACE ? rec + 11 + 3 * (ring * 4 + m) : nullptr;
-                    if (TRACE) rr[0] = k;
-                    sum += bilinear<Fmt>(p.stack, k, R, __fadd_rn(l1, du[m]), __fadd_rn(l2, dv[m]),
-                                         rr);
+                    for (int m = 0; m < 4; ++m) {
+                        int* rr = TRACE ? rec + 11 + 3 * (ring * 4 + m) : nullptr;
+                        if (TRACE) rr[0] = k;
+                        sum += bilinear<Fmt>(p.stack, k, R, __fadd_rn(l1, du[m]),
+                                             __fadd_rn(l2, dv[m]), rr);
+                    }
                 }
             }
             coef = sum * 0.125f;
@@ -265,7 +332,7 @@ __device__ __forceinline__ void load_alpha(const MarchParams& p, float* s_alpha)
 #define VI_MARCH_MIN_BLOCKS 4
 #endif
 
-template <typename VoxT, typename Fmt, int MODE>
+template <typename VoxT, typename Fmt, int MODE, bool EXT>
 __global__ void __launch_bounds__(kMarchThreads, VI_MARCH_MIN_BLOCKS)
     march_kernel(const MarchParams p) {
     extern __shared__ float s_alpha[];
@@ -297,8 +364,8 @@ __global__ void __launch_bounds__(kMarchThreads, VI_MARCH_MIN_BLOCKS)
         for (int i = 0; __any_sync(0xffffffffu, active);) {
             int st = kEnded;
             if (active)
-                st = march_sample<VoxT, Fmt, MODE, false>(p, s_alpha, r, i, C0, C1, C2, A, count,
-                                                          lit, nullptr);
+                st = march_sample<VoxT, Fmt, MODE, false, EXT>(p, s_alpha, r, i, C0, C1, C2, A,
+                                                               count, lit, nullptr);
             active = active && (st == kContinue || st == kEmpty);
             const unsigned act = __ballot_sync(0xffffffffu, active);
             const unsigned emp = __ballot_sync(0xffffffffu, active && st == kEmpty);
@@ -340,8 +407,8 @@ __global__ void trace_kernel(const MarchParams p, int x, int y, int32_t* rec, in
     if (r.hit) {
         for (int i = 0; nrec < max_rec; ++i) {
             int32_t* out = rec + (size_t)nrec * kTraceWords;
-            int st = march_sample<VoxT, Fmt, MODE, true>(p, s_alpha, r, i, C0, C1, C2, A, count,
-                                                         lit, out);
+            int st = march_sample<VoxT, Fmt, MODE, true, true>(p, s_alpha, r, i, C0, C1, C2, A,
+                                                               count, lit, out);
             if (st == kEnded) break;
             ++nrec;
             if (st == kStopped) break;
@@ -350,10 +417,10 @@ __global__ void trace_kernel(const MarchParams p, int x, int y, int32_t* rec, in
     *n_rec = nrec;
 }
 
-template <typename VoxT, typename Fmt, int MODE>
+template <typename VoxT, typename Fmt, int MODE, bool EXT>
 cudaError_t launch_march_typed(const MarchParams& p, cudaStream_t s) {
     const size_t smem = (size_t)p.M * sizeof(float);
-    auto kern = march_kernel<VoxT, Fmt, MODE>;
+    auto kern = march_kernel<VoxT, Fmt, MODE, EXT>;
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -379,22 +446,25 @@ cudaError_t launch_trace_typed(const MarchParams& p, int x, int y, int32_t* rec,
     return cudaGetLastError();
 }
 
+template <typename VoxT, typename Fmt, int MODE>
+cudaError_t dispatch_ext(const MarchParams& p, bool trace, int x, int y, int32_t* rec,
+                         int max_rec, int* n_rec, cudaStream_t s) {
+    if (trace) return launch_trace_typed<VoxT, Fmt, MODE>(p, x, y, rec, max_rec, n_rec, s);
+    const bool ext = p.depth || p.slice_linear || p.shells > 1;
+    return ext ? launch_march_typed<VoxT, Fmt, MODE, true>(p, s)
+               : launch_march_typed<VoxT, Fmt, MODE, false>(p, s);
+}
+
 template <typename VoxT, typename Fmt>
 cudaError_t dispatch_mode(const MarchParams& p, int mode, bool trace, int x, int y, int32_t* rec,
                           int max_rec, int* n_rec, cudaStream_t s) {
     switch (mode) {
-        case 0:
+        case 0:  // no lookups: the options that change lookups do not apply
             return trace ? launch_trace_typed<VoxT, Fmt, 0>(p, x, y, rec, max_rec, n_rec, s)
-                         : launch_march_typed<VoxT, Fmt, 0>(p, s);
-        case 1:
-            return trace ? launch_trace_typed<VoxT, Fmt, 1>(p, x, y, rec, max_rec, n_rec, s)
-                         : launch_march_typed<VoxT, Fmt, 1>(p, s);
-        case 2:
-            return trace ? launch_trace_typed<VoxT, Fmt, 2>(p, x, y, rec, max_rec, n_rec, s)
-                         : launch_march_typed<VoxT, Fmt, 2>(p, s);
-        case 3:
-            return trace ? launch_trace_typed<VoxT, Fmt, 3>(p, x, y, rec, max_rec, n_rec, s)
-                         : launch_march_typed<VoxT, Fmt, 3>(p, s);
+                         : launch_march_typed<VoxT, Fmt, 0, false>(p, s);
+        case 1: return dispatch_ext<VoxT, Fmt, 1>(p, trace, x, y, rec, max_rec, n_rec, s);
+        case 2: return dispatch_ext<VoxT, Fmt, 2>(p, trace, x, y, rec, max_rec, n_rec, s);
+        case 3: return dispatch_ext<VoxT, Fmt, 3>(p, trace, x, y, rec, max_rec, n_rec, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -72,7 +72,8 @@ bool stack_matches(const Slot* sl, const Request* r) {
               a.n_slices == b.n_slices && a.slice_res == b.slice_res && a.mode == b.mode &&
               x.format == y.format && same_bits(x.cone_half_angle_deg, y.cone_half_angle_deg) &&
               same_bits(x.shell_radius_vox, y.shell_radius_vox) &&
-              x.opacity_correction == y.opacity_correction && same_bits(x.comp_n, y.comp_n);
+              x.opacity_correction == y.opacity_correction && same_bits(x.comp_n, y.comp_n) &&
+              x.quantity == y.quantity && x.shell_count == y.shell_count;
     for (int i = 0; eq && i < 3; ++i)
         eq = same_bits(a.light_dir[i], b.light_dir[i]) &&
              same_bits(a.light_color[i], b.light_color[i]);
@@ -462,6 +463,13 @@ int vi_server_submit(vi_server* s, const vi_request* q, uint64_t* ticket) {
     if (q->light_dir[0] == 0.0f && q->light_dir[1] == 0.0f && q->light_dir[2] == 0.0f)
         return VI_EINVAL;
     if (q->n_slices < 1 || q->slice_res < 1 || q->mode < VI_NONE || q->mode > VI_CONE)
+        return VI_EINVAL;
+    if (q->build.format < VI_F32 || q->build.format > VI_UNORM16) return VI_EINVAL;
+    if (q->build.quantity != VI_TRANSMITTANCE && q->build.quantity != VI_OPTICAL_DEPTH)
+        return VI_EINVAL;
+    if (q->build.quantity == VI_OPTICAL_DEPTH && q->build.format == VI_UNORM16) return VI_EINVAL;
+    if (q->build.shell_count < 0 || q->build.shell_count > VI_MAX_SHELLS) return VI_EINVAL;
+    if (q->render.slice_filter != VI_SLICE_NEAREST && q->render.slice_filter != VI_SLICE_LINEAR)
         return VI_EINVAL;
     if (q->width < 0 || q->height < 0 || (q->width * (long long)q->height > 0 && !q->out_rgba))
         return VI_EINVAL;

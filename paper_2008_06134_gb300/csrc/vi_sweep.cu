@@ -5,7 +5,9 @@
 // FP32 register: it stores T into buffer k (the light arriving at plane k),
 // then applies the back-to-front blend of Eq. 4 to a scalar transmittance,
 // T <- T (1 - alpha_k).  All n slices come out of one launch (the paper's
-// multi-slice-per-pass future work), with no framebuffer read-back.
+// multi-slice-per-pass future work), with no framebuffer read-back.  In the
+// extinction form of Eq. 5-6 (DEPTH) the column carries the optical depth
+// D <- D + tau_k, tau_k = -ln(1 - alpha_k), capped at kDepthMax, and stores D.
 //
 // Memory: the volume is read through the read-only path (it fits in L2 for the
 // sizes this targets).  A warp covers an 8 x 4 tile of texels, so its 32
@@ -35,7 +37,7 @@ __device__ __forceinline__ bool texel_inside(const LightFrame& lt, int k, float 
     return P0 >= 0.0f && P0 <= 1.0f && P1 >= 0.0f && P1 <= 1.0f && P2 >= 0.0f && P2 <= 1.0f;
 }
 
-template <typename VoxT, typename Fmt>
+template <typename VoxT, typename Fmt, bool DEPTH>
 __global__ void __launch_bounds__(kSweepBX* kSweepBY)
     sweep_kernel(const SweepParams p) {
     extern __shared__ float s_alpha[];
@@ -115,8 +117,8 @@ __global__ void __launch_bounds__(kSweepBX* kSweepBY)
         }
     }
 
-    // Before the cube: full light.
-    const typename Fmt::T one = Fmt::pack(1.0f);
+    // Before the cube: full light (transmittance 1, optical depth 0).
+    const typename Fmt::T one = Fmt::pack(DEPTH ? 0.0f : 1.0f);
     int k = 0;
     for (; k < min(kin, lt.n); ++k) {
         out[(size_t)k * slice] = one;
@@ -125,7 +127,7 @@ __global__ void __launch_bounds__(kSweepBX* kSweepBY)
     // Inside the cube, four slices at a time: their positions, brick flags and
     // octets do not depend on T, so the loads of a batch are issued together
     // and their latencies overlap; T then runs through the batch in order.
-    float T = 1.0f;
+    float T = DEPTH ? 0.0f : 1.0f;  // transmittance, or optical depth
     for (; k <= kout; k += kBatch) {
         OctetRef ref[kBatch];
         bool lit[kBatch];
@@ -157,11 +159,16 @@ __global__ void __launch_bounds__(kSweepBX* kSweepBY)
                     alpha = 1.0f - exp2f(p.spacing_vox * log2f(fmaxf(1.0f - alpha, 0.0f)));
             }
             float stored = T;
-            if (p.comp_n != 0.0f) stored = fminf(1.0f, T * powf(1.0f + alpha, p.comp_n));
+            if (p.comp_n != 0.0f)
+                stored = DEPTH ? fmaxf(0.0f, T - p.comp_n * log1pf(alpha))
+                               : fminf(1.0f, T * powf(1.0f + alpha, p.comp_n));
             const typename Fmt::T q = Fmt::pack(stored);
             out[(size_t)(k + u) * slice] = q;
             if (dup) out[(size_t)(k + u) * slice + dup] = q;
-            T *= (1.0f - alpha);
+            if (DEPTH)
+                T = fminf(T - log1pf(-alpha), kDepthMax);  // alpha = 1: tau = inf, capped
+            else
+                T *= (1.0f - alpha);
         }
     }
     if (kin <= kout) k = kout + 1;  // the last batch may have run past kout
@@ -173,22 +180,30 @@ __global__ void __launch_bounds__(kSweepBX* kSweepBY)
     }
 }
 
-template <typename VoxT, typename Fmt>
+template <typename VoxT, typename Fmt, bool DEPTH>
 cudaError_t launch_typed(const SweepParams& p, cudaStream_t s) {
     dim3 block(kSweepBX * kSweepBY);
     dim3 grid((p.lt.R + kSweepBX - 1) / kSweepBX, (p.lt.R + kSweepBY - 1) / kSweepBY);
     size_t smem = (size_t)p.M * sizeof(float);
-    sweep_kernel<VoxT, Fmt><<<grid, block, smem, s>>>(p);
+    sweep_kernel<VoxT, Fmt, DEPTH><<<grid, block, smem, s>>>(p);
     return cudaGetLastError();
 }
 
 template <typename VoxT>
 cudaError_t launch_fmt(const SweepParams& p, int format, cudaStream_t s) {
+    if (p.depth) {  // optical depth: not in UNORM16 (its range is [0, 1])
+        switch (format) {
+            case 0: return launch_typed<VoxT, F32, true>(p, s);
+            case 1: return launch_typed<VoxT, F16, true>(p, s);
+            case 2: return launch_typed<VoxT, BF16, true>(p, s);
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (format) {
-        case 0: return launch_typed<VoxT, F32>(p, s);
-        case 1: return launch_typed<VoxT, F16>(p, s);
-        case 2: return launch_typed<VoxT, BF16>(p, s);
-        case 3: return launch_typed<VoxT, UNORM16>(p, s);
+        case 0: return launch_typed<VoxT, F32, false>(p, s);
+        case 1: return launch_typed<VoxT, F16, false>(p, s);
+        case 2: return launch_typed<VoxT, BF16, false>(p, s);
+        case 3: return launch_typed<VoxT, UNORM16, false>(p, s);
     }
     return cudaErrorInvalidValue;
 }

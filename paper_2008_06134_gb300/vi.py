@@ -21,6 +21,10 @@ OK, EINVAL, ENOMEM, ESTATE, ECUDA, ETIMEOUT = 0, -1, -2, -3, -4, -5
 U8, U16 = 0, 1
 NONE, SHADOW, SHELL, CONE = 0, 1, 2, 3
 F32, F16, BF16, UNORM16 = 0, 1, 2, 3
+TRANSMITTANCE, OPTICAL_DEPTH = 0, 1   # what the stack holds
+SLICE_NEAREST, SLICE_LINEAR = 0, 1    # slice filtering of a lookup
+DEPTH_MAX = 64.0
+MAX_SHELLS = 4
 TRACE_WORDS = 40
 NOALLOC_MAX_PIXELS = 512 * 512
 TRACE_NONE = 0x7FFFFFFF
@@ -44,7 +48,7 @@ class ViError(RuntimeError):
 class BuildOpts(C.Structure):
     _fields_ = [("format", C.c_int), ("cone_half_angle_deg", C.c_float),
                 ("shell_radius_vox", C.c_float), ("opacity_correction", C.c_int),
-                ("comp_n", C.c_float)]
+                ("comp_n", C.c_float), ("quantity", C.c_int), ("shell_count", C.c_int)]
 
 
 class Camera(C.Structure):
@@ -55,7 +59,7 @@ class Camera(C.Structure):
 class RenderOpts(C.Structure):
     _fields_ = [("ert", C.c_float), ("bg", C.c_float * 4), ("ambient", C.c_float),
                 ("opacity_correction", C.c_int), ("sample_counts", C.c_void_p),
-                ("lit_counts", C.c_void_p)]
+                ("lit_counts", C.c_void_p), ("slice_filter", C.c_int)]
 
 
 class Request(C.Structure):
@@ -223,15 +227,16 @@ class Context:
 
     def build_attenuation(self, n_slices: int, slice_res: int, mode: int, format: int = F32,
                           cone_half_angle_deg: float = 15.0, shell_radius_vox: float = 1.0,
-                          opacity_correction: int = 0, comp_n: float = 0.0) -> None:
+                          opacity_correction: int = 0, comp_n: float = 0.0,
+                          quantity: int = TRANSMITTANCE, shell_count: int = 1) -> None:
         o = BuildOpts(int(format), float(cone_half_angle_deg), float(shell_radius_vox),
-                      int(opacity_correction), float(comp_n))
+                      int(opacity_correction), float(comp_n), int(quantity), int(shell_count))
         _check(self.L.vi_build_attenuation(self.h, int(n_slices), int(slice_res), int(mode),
                                            C.byref(o)), "vi_build_attenuation")
 
     @staticmethod
     def _render_opts(ert, bg, ambient, opacity_correction, sample_counts=None,
-                     lit_counts=None) -> RenderOpts:
+                     lit_counts=None, slice_filter=SLICE_NEAREST) -> RenderOpts:
         ptrs = []
         for buf in (sample_counts, lit_counts):
             cp = None
@@ -241,11 +246,11 @@ class Context:
                     raise ValueError("per-pixel counters must be device tensors")
             ptrs.append(cp)
         return RenderOpts(float(ert), (C.c_float * 4)(*map(float, bg)), float(ambient),
-                          int(opacity_correction), *ptrs)
+                          int(opacity_correction), *ptrs, int(slice_filter))
 
     def render(self, cam, W: int, H: int, step_vox: float, out=None, ert: float = 2.0,
                bg=(0.0, 0.0, 0.0, 0.0), ambient: float = 0.0, opacity_correction: int = 0,
-               sample_counts=None, lit_counts=None):
+               sample_counts=None, lit_counts=None, slice_filter: int = SLICE_NEAREST):
         """Render into ``out`` ((H, W, 4) float32; torch CUDA tensor or numpy /
         pinned torch host tensor).  With ``out=None`` a torch CUDA tensor is
         allocated and returned."""
@@ -253,7 +258,8 @@ class Context:
             import torch
             out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
         p, dev = _ptr(out)
-        ro = self._render_opts(ert, bg, ambient, opacity_correction, sample_counts, lit_counts)
+        ro = self._render_opts(ert, bg, ambient, opacity_correction, sample_counts, lit_counts,
+                               slice_filter)
         _check(self.L.vi_render(self.h, C.byref(camera(cam)), int(W), int(H), float(step_vox),
                                 C.c_void_p(p), dev, C.byref(ro)), "vi_render")
         return out
@@ -277,10 +283,10 @@ class Context:
         return out
 
     def trace_pixel(self, cam, W, H, step_vox, x, y, ert=2.0, bg=(0, 0, 0, 0), ambient=0.0,
-                    opacity_correction=0, max_rec=8192) -> np.ndarray:
+                    opacity_correction=0, max_rec=8192, slice_filter=SLICE_NEAREST) -> np.ndarray:
         rec = np.zeros((max_rec, TRACE_WORDS), dtype=np.int32)
         n = C.c_int(0)
-        ro = self._render_opts(ert, bg, ambient, opacity_correction)
+        ro = self._render_opts(ert, bg, ambient, opacity_correction, slice_filter=slice_filter)
         _check(self.L.vi_trace_pixel(self.h, C.byref(camera(cam)), int(W), int(H),
                                      float(step_vox), C.byref(ro), int(x), int(y),
                                      C.c_void_p(rec.ctypes.data), int(max_rec), C.byref(n)),
@@ -368,16 +374,18 @@ class Server:
     def submit(self, volume_id, tf, vmin, vmax, light_dir, n_slices, slice_res, mode, cam, W, H,
                step_vox, out, light_color=(1.0, 1.0, 1.0), format=F32,
                cone_half_angle_deg=15.0, shell_radius_vox=1.0, ert=2.0,
-               bg=(0.0, 0.0, 0.0, 0.0)) -> int:
+               bg=(0.0, 0.0, 0.0, 0.0), quantity=TRANSMITTANCE, shell_count=1,
+               slice_filter=SLICE_NEAREST) -> int:
         tf = np.ascontiguousarray(tf, dtype=np.float32)
         p, dev = _ptr(out)
         q = Request(int(volume_id), C.c_void_p(tf.ctypes.data), tf.shape[0], float(vmin),
                     float(vmax), _f3(light_dir), _f3(light_color), int(n_slices),
                     int(slice_res), int(mode),
                     BuildOpts(int(format), float(cone_half_angle_deg), float(shell_radius_vox),
-                              0, 0.0),
+                              0, 0.0, int(quantity), int(shell_count)),
                     camera(cam), int(W), int(H), float(step_vox),
-                    Context._render_opts(ert, bg, 0.0, 0), C.c_void_p(p), dev)
+                    Context._render_opts(ert, bg, 0.0, 0, slice_filter=slice_filter),
+                    C.c_void_p(p), dev)
         t = C.c_uint64(0)
         _check(self.L.vi_server_submit(self.h, C.byref(q), C.byref(t)), "vi_server_submit")
         self._keep[("out", t.value)] = out

@@ -12,7 +12,8 @@ FORMAT_HALF_ULP = {0: 0.0, 1: 2.0 ** -12, 2: 2.0 ** -9, 3: 0.5 / 65535.0}
 
 
 def gpu_frame(ctx, scene, mode=None, fmt=0, counts=False, ert=None, bg=None,
-              opacity_correction=0, comp_n=0.0, build_oc=0):
+              opacity_correction=0, comp_n=0.0, build_oc=0, quantity=0, shell_count=1,
+              slice_filter=0):
     import torch
     mode = scene.mode if mode is None else mode
     ctx.load_volume(scene.volume)
@@ -21,14 +22,16 @@ def gpu_frame(ctx, scene, mode=None, fmt=0, counts=False, ert=None, bg=None,
     ctx.build_attenuation(scene.n_slices, scene.slice_res, mode, format=fmt,
                           cone_half_angle_deg=scene.cone_half_angle_deg,
                           shell_radius_vox=scene.shell_radius_vox,
-                          opacity_correction=build_oc, comp_n=comp_n)
+                          opacity_correction=build_oc, comp_n=comp_n, quantity=quantity,
+                          shell_count=shell_count)
     cnt = None
     if counts:
         cnt = torch.zeros((scene.height, scene.width), dtype=torch.int32, device="cuda")
     out = ctx.render(scene.camera, scene.width, scene.height, scene.step_vox,
                      ert=scene.ert if ert is None else ert,
                      bg=scene.bg if bg is None else bg,
-                     opacity_correction=opacity_correction, sample_counts=cnt)
+                     opacity_correction=opacity_correction, sample_counts=cnt,
+                     slice_filter=slice_filter)
     torch.cuda.synchronize()
     ctx.sync()
     img = out.cpu().numpy().astype(np.float64)
@@ -36,17 +39,19 @@ def gpu_frame(ctx, scene, mode=None, fmt=0, counts=False, ert=None, bg=None,
 
 
 def oracle_frame(orc, scene, mode=None, xs=None, ys=None, stack=None, ert=None, bg=None,
-                 opacity_correction=0, comp_n=0.0, build_oc=0, ert_band=1e-5):
+                 opacity_correction=0, comp_n=0.0, build_oc=0, ert_band=1e-5, quantity=0,
+                 shell_count=1, slice_filter=0):
     mode = scene.mode if mode is None else mode
     light = orc.light_setup(scene.light_dir, scene.n_slices, scene.slice_res)
     if stack is None and mode != orc.NONE:
         stack = orc.build_stack(scene.volume, scene.tf, scene.vmin, scene.vmax, light,
-                                opacity_correction=build_oc, comp_n=comp_n)
+                                opacity_correction=build_oc, comp_n=comp_n, quantity=quantity)
     ro = orc.render_opts(mode, scene.step_vox, scene.ert if ert is None else ert,
                          scene.bg if bg is None else bg, scene.light_color,
                          opacity_correction=opacity_correction,
                          cone_half_angle_deg=scene.cone_half_angle_deg,
-                         shell_radius_vox=scene.shell_radius_vox, ert_band=ert_band)
+                         shell_radius_vox=scene.shell_radius_vox, ert_band=ert_band,
+                         quantity=quantity, slice_filter=slice_filter, shell_count=shell_count)
     if xs is None:
         img, alt, amb, ns = orc.render_image(scene.volume, scene.tf, scene.vmin, scene.vmax,
                                              light, stack, scene.camera, scene.width,
