@@ -63,7 +63,8 @@ class Light(C.Structure):
                 ("dL", C.c_float), ("kappa", C.c_float), ("Lc", C.c_float),
                 ("U", C.c_float * 3), ("V", C.c_float * 3), ("h", C.c_float),
                 ("sigma", C.c_float), ("rho0", C.c_float), ("n", C.c_int),
-                ("R", C.c_int), ("axis", C.c_int)]
+                ("R", C.c_int), ("axis", C.c_int), ("point", C.c_int),
+                ("P", C.c_float * 3)]
 
 
 class BuildOpts(C.Structure):
@@ -111,7 +112,10 @@ def lib():
                                                C.c_int, C.c_void_p]
             L.orc_frame_setup.argtypes = [P(Camera), C.c_int, C.c_int, C.c_float, C.c_int, P(Frame)]
             L.orc_ray_setup.argtypes = [P(Light), P(Frame), P(RenderOpts), C.c_int, C.c_int, P(Ray)]
-            L.orc_point_light_coords.argtypes = [P(Light), P(C.c_float), P(C.c_float)]
+            L.orc_light_coords.argtypes = [P(Light), P(C.c_float), P(C.c_float)]
+            L.orc_point_light_setup.argtypes = [P(C.c_float), C.c_int, C.c_int, P(Light)]
+            L.orc_point_neighbours.argtypes = [P(Light), P(RenderOpts), C.c_int, P(C.c_float),
+                                               P(C.c_float), P(C.c_float)]
             L.orc_render_pixels.argtypes = [P(Volume), P(TF), P(Light), C.c_void_p, P(Camera),
                                             C.c_int, C.c_int, P(RenderOpts), C.c_void_p,
                                             C.c_void_p, C.c_long, C.c_void_p, C.c_void_p,
@@ -309,10 +313,29 @@ def ray_setup(light: Light, frame: Frame, ro: RenderOpts, x: int, y: int) -> Ray
     return ray
 
 
-def point_light_coords(light: Light, X) -> np.ndarray:
+def light_coords(light: Light, X) -> np.ndarray:
+    """(lambda, tu, tv) of the world point X (binary32 index path)."""
     out = (C.c_float * 3)()
-    lib().orc_point_light_coords(C.byref(light), _f3(X), out)
+    lib().orc_light_coords(C.byref(light), _f3(X), out)
     return np.array(out[:], dtype=np.float32)
+
+
+def point_light_setup(position, n: int, R: int) -> Light:
+    """Frame of a point light at ``position`` (at least 1 from the cube centre)."""
+    out = Light()
+    rc = lib().orc_point_light_setup(_f3(position), int(n), int(R), C.byref(out))
+    if rc:
+        raise ValueError(f"orc_point_light_setup rejected the input ({rc})")
+    return out
+
+
+def point_neighbours(light: Light, ro: RenderOpts, nmax: int, S, d) -> np.ndarray:
+    """World positions of a sample's shell / cone points under a point light."""
+    out = (C.c_float * (3 * MAX_NB))()
+    k = lib().orc_point_neighbours(C.byref(light), C.byref(ro), int(nmax), _f3(S), _f3(d), out)
+    if k < 0:
+        raise ValueError("orc_point_neighbours rejected the input")
+    return np.array(out[: 3 * k], dtype=np.float32).reshape(k, 3)
 
 
 def texel_world(light: Light, i: int, j: int, k: int) -> np.ndarray:

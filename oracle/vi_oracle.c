@@ -32,6 +32,11 @@
  *                   bracketing a sample instead of the nearest slice.
  *   shell_count  -- several shells (Section 3.2.3: the number and size of
  *                   the shells can vary) at radii r, 2r, ..., equal weights.
+ *   point light  -- a light at a position P (the paper speaks of a light
+ *                   position, Fig. 7): light travels along rays from P; the
+ *                   slices are planes perpendicular to the axis from P to the
+ *                   cube centre, and each texel column is one ray from P
+ *                   through a perspective texel grid (orc_point_light_setup).
  *
  * Precision.  Everything whose rounding decides an integer -- the light and
  * camera set-up, sample positions t_i and the count of samples on a ray, the
@@ -97,6 +102,8 @@ typedef struct {
     float rho0;     /* (R - 1) / 2 */
     int n, R;
     int axis;       /* world axis U was built from */
+    int point;      /* 0: directional light L; 1: point light at P, L its axis */
+    float P[3];     /* point light position */
 } orc_light;
 
 typedef struct {
@@ -292,17 +299,87 @@ int orc_light_setup(const float dir[3], int n, int R, orc_light* o) {
     return ORC_OK;
 }
 
+/* Point light at P (f4): L is the axis from P to the centre c, the slices are
+   planes perpendicular to L at depths min + k (max - min) / n from P, where
+   min / max are the extreme depths (V - P).L of the cube's vertices, and the
+   texel grid is perspective: texel (i, j) is the ray from P through
+   L + u U + v V with u, v in [-g, g], g the tangent of the half angle of the
+   cone from P that holds the cube's circumscribed sphere.  P must be at least
+   1 from c (outside that sphere).  U, V as for a directional light along L. */
+int orc_point_light_setup(const float pos[3], int n, int R, orc_light* o) {
+    if (!pos || !o || n < 1 || R < 1) return ORC_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (!isfinite(pos[a])) return ORC_EINVAL;
+    float q[3] = {0.5f - pos[0], 0.5f - pos[1], 0.5f - pos[2]};
+    float dc2 = dot3f(q, q);
+    float dc = sqrtf(dc2);
+    if (!(dc >= 1.0f) || !isfinite(dc)) return ORC_EINVAL;
+    /* The frame of a directional light along the axis; then the depths. */
+    int rc = orc_light_setup(q, n, R, o);
+    if (rc) return rc;
+    o->point = 1;
+    for (int a = 0; a < 3; ++a) o->P[a] = pos[a];
+    float pa = dot3f(o->L, pos);
+    float mn = 0.0f, mx = 0.0f;
+    for (int c = 0; c < 8; ++c) {
+        float V[3] = {(float)(c & 1), (float)((c >> 1) & 1), (float)((c >> 2) & 1)};
+        float d = dot3f(o->L, V) - pa;
+        if (c == 0 || d < mn) mn = d;
+        if (c == 0 || d > mx) mx = d;
+    }
+    o->min = mn;
+    o->max = mx;
+    float span = mx - mn;
+    o->dL = span / (float)n;
+    o->kappa = (float)n / span;
+    o->Lc = 0.0f;
+    /* Half extent of the texel grid at unit depth: tan of the half angle of
+       the cone tangent to the sphere of radius sqrt(3)/2 about c. */
+    float hs = 0x1.bb67aep-1f;
+    float hs2 = hs * hs;
+    o->h = hs / sqrtf(dc2 - hs2);
+    float two_h = 2.0f * o->h;
+    o->sigma = (float)R / two_h;
+    return ORC_OK;
+}
+
 /* World position of texel (i, j) of slice plane k (index path). */
 static void texel_world(const orc_light* lt, int i, int j, float sk, float P[3]) {
     float qi = (float)(2 * i + 1) / (float)lt->R;
     float qj = (float)(2 * j + 1) / (float)lt->R;
     float u = (qi - 1.0f) * lt->h;
     float v = (qj - 1.0f) * lt->h;
+    if (lt->point) {
+        /* The column is the ray from the light through (u, v) on the plane at
+           unit depth: w = L + u U + v V; plane k lies at depth sk along L. */
+        for (int a = 0; a < 3; ++a) {
+            float w0 = fmaf(u, lt->U[a], lt->L[a]);
+            float w = fmaf(v, lt->V[a], w0);
+            P[a] = fmaf(sk, w, lt->P[a]);
+        }
+        return;
+    }
     for (int a = 0; a < 3; ++a) {
         float b0 = fmaf(u, lt->U[a], 0.5f);
         float b1 = fmaf(v, lt->V[a], b0);
         P[a] = fmaf(sk, lt->L[a], b1);
     }
+}
+
+/* Length of a point light's texel column direction w (for opacity
+   correction along the column). */
+static double column_stretch(const orc_light* lt, int i, int j) {
+    if (!lt->point) return 1.0;
+    float qi = (float)(2 * i + 1) / (float)lt->R;
+    float qj = (float)(2 * j + 1) / (float)lt->R;
+    float u = (qi - 1.0f) * lt->h;
+    float v = (qj - 1.0f) * lt->h;
+    double s = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double w = (double)fmaf(v, lt->V[a], fmaf(u, lt->U[a], lt->L[a]));
+        s += w * w;
+    }
+    return sqrt(s);
 }
 
 /* Signed distance of slice plane k from the centre along L (index path). */
@@ -431,7 +508,7 @@ static void sweep_rows(void* p, long lo, long hi) {
                 tf_lookup(s->tf, sample_volume(s->vol, P, cell), rgba);
                 alpha = rgba[3];
                 if (s->opt && s->opt->opacity_correction)
-                    alpha = 1.0 - pow(1.0 - alpha, s->spacing_vox);
+                    alpha = 1.0 - pow(1.0 - alpha, s->spacing_vox * column_stretch(s->lt, i, (int)j));
             }
             const int depth = s->opt && s->opt->quantity == ORC_OPTICAL_DEPTH;
             double stored = s->T[t];
@@ -534,17 +611,98 @@ int orc_frame_setup(const orc_camera* cam, int W, int H, float step_vox, int Nma
     return ORC_OK;
 }
 
-/* Light-space coordinates (lambda, tu, tv) of a world point (Eq. 9, Eq. 10):
-   lambda = kappa (L.X - min), tu = sigma (X - c).U + rho0, tv likewise. */
-int orc_point_light_coords(const orc_light* lt, const float X[3], float out[3]) {
-    if (!lt || !X || !out) return ORC_EINVAL;
+/* Light-space coordinates (lambda, tu, tv) of a world point (Eq. 9, Eq. 10).
+   Directional: lambda = kappa (L.X - min), tu = sigma (X - c).U + rho0, tv
+   likewise.  Point light: with e = X - P and depth d = e.L, lambda =
+   kappa (d - min), tu = sigma (e.U / d) + rho0, tv likewise (the perspective
+   divide; a depth below 1e-6 -- at or behind the light -- counts as 1e-6). */
+static void light_coords(const orc_light* lt, const float X[3], float out[3]) {
+    if (lt->point) {
+        float e[3] = {X[0] - lt->P[0], X[1] - lt->P[1], X[2] - lt->P[2]};
+        float d = dot3f(e, lt->L);
+        out[0] = (d - lt->min) * lt->kappa;
+        float ds = d > 1e-6f ? d : 1e-6f;
+        float su = dot3f(e, lt->U) / ds;
+        float sv = dot3f(e, lt->V) / ds;
+        out[1] = fmaf(su, lt->sigma, lt->rho0);
+        out[2] = fmaf(sv, lt->sigma, lt->rho0);
+        return;
+    }
     float LX = dot3f(lt->L, X);
     float dl = LX - lt->min;
     out[0] = dl * lt->kappa;
     float xc[3] = {X[0] - 0.5f, X[1] - 0.5f, X[2] - 0.5f};
     out[1] = fmaf(dot3f(xc, lt->U), lt->sigma, lt->rho0);
     out[2] = fmaf(dot3f(xc, lt->V), lt->sigma, lt->rho0);
+}
+
+int orc_light_coords(const orc_light* lt, const float X[3], float out[3]) {
+    if (!lt || !X || !out) return ORC_EINVAL;
+    light_coords(lt, X, out);
     return ORC_OK;
+}
+
+/* World positions of a sample's scattering points under a point light
+   (Section 3.2.3 with the light direction taken at the sample):
+   shell q: S +- q r e_a; cone: w = (S - P)/|S - P| the direction the light
+   travels at S, ring n (1, 2) centred at S - n dL w with radius n dL tan(phi),
+   its four points B_proj turned by m pi/2 about w (Eq. 11: w x B for a
+   quarter turn), B_proj the unit part of -d (towards the eye) orthogonal to w
+   (U's part if that is below 1e-6).  Returns the number of points. */
+static int point_neighbours(const orc_light* lt, const orc_render_opts* ro, int Nmax,
+                            const float S[3], const float d[3], float X[ORC_MAX_NB][3]) {
+    if (ro->mode == ORC_SHELL) {
+        const int Q = ro->shell_count > 0 ? ro->shell_count : 1;
+        for (int q = 1; q <= Q; ++q) {
+            float r = ((float)q * ro->shell_radius_vox) / (float)Nmax;
+            for (int a = 0; a < 3; ++a)
+                for (int sgn = 0; sgn < 2; ++sgn) {
+                    float* o = X[6 * (q - 1) + 2 * a + sgn];
+                    o[0] = S[0];
+                    o[1] = S[1];
+                    o[2] = S[2];
+                    o[a] = sgn ? S[a] - r : S[a] + r;
+                }
+        }
+        return 6 * Q;
+    }
+    if (ro->mode != ORC_CONE) return 0;
+    float e[3] = {S[0] - lt->P[0], S[1] - lt->P[1], S[2] - lt->P[2]};
+    float le = sqrtf(dot3f(e, e));
+    float w[3] = {e[0] / le, e[1] / le, e[2] / le};
+    float md[3] = {-d[0], -d[1], -d[2]};
+    float pr = dot3f(md, w);
+    float b[3];
+    for (int a = 0; a < 3; ++a) b[a] = fmaf(-pr, w[a], md[a]);
+    float nb = sqrtf(dot3f(b, b));
+    if (!(nb >= 1e-6f)) {
+        pr = dot3f(lt->U, w);
+        for (int a = 0; a < 3; ++a) b[a] = fmaf(-pr, w[a], lt->U[a]);
+        nb = sqrtf(dot3f(b, b));
+    }
+    float B[4][3];
+    for (int a = 0; a < 3; ++a) B[0][a] = b[a] / nb;
+    cross3f(w, B[0], B[1]);
+    for (int a = 0; a < 3; ++a) {
+        B[2][a] = -B[0][a];
+        B[3][a] = -B[1][a];
+    }
+    float tanphi = (float)tan((double)ro->cone_half_angle_deg * (M_PI / 180.0));
+    for (int ring = 1; ring <= 2; ++ring) {
+        float dist = (float)ring * lt->dL;
+        float rad = dist * tanphi;
+        float c[3];
+        for (int a = 0; a < 3; ++a) c[a] = fmaf(-dist, w[a], S[a]);
+        for (int m = 0; m < 4; ++m)
+            for (int a = 0; a < 3; ++a) X[(ring - 1) * 4 + m][a] = fmaf(rad, B[m][a], c[a]);
+    }
+    return 8;
+}
+
+int orc_point_neighbours(const orc_light* lt, const orc_render_opts* ro, int Nmax,
+                         const float S[3], const float d[3], float* X) {
+    if (!lt || !ro || !S || !d || !X || !lt->point) return -1;
+    return point_neighbours(lt, ro, Nmax, S, d, (float(*)[3])X);
 }
 
 /* Rotation by theta_m = m pi/2 about L of a unit vector in the light plane,
@@ -767,7 +925,10 @@ static void march_one(const march_ctx* s, long p) {
             float S[3];
             for (int a = 0; a < 3; ++a) S[a] = fmaf(t, ray.d[a], ray.o[a]);
             float l[3];
-            for (int c = 0; c < 3; ++c) l[c] = fmaf(t, ray.ld[c], ray.lo[c]);
+            if (s->lt->point)
+                light_coords(s->lt, S, l); /* perspective: per sample */
+            else
+                for (int c = 0; c < 3; ++c) l[c] = fmaf(t, ray.ld[c], ray.lo[c]);
             int cell[3];
             double rgba[4];
             tf_lookup(s->tf, sample_volume(s->vol, S, cell), rgba);
@@ -798,15 +959,23 @@ static void march_one(const march_ctx* s, long p) {
                 if (rec) light_lookup(NULL, s->lt, ro, l[0], l[1], l[2], rec + 8);
                 if (ro->mode == ORC_SHELL || ro->mode == ORC_CONE) {
                     double sum = 0.0;
-                    for (int j = 0; j < ray.nnb; ++j) {
-                        float q0 = l[0] + ray.nb[j][0];
-                        float q1 = l[1] + ray.nb[j][1];
-                        float q2 = l[2] + ray.nb[j][2];
+                    float X[ORC_MAX_NB][3];
+                    int nnb = ray.nnb;
+                    if (s->lt->point) nnb = point_neighbours(s->lt, ro, s->fr->Nmax, S, ray.d, X);
+                    for (int j = 0; j < nnb; ++j) {
+                        float q[3];
+                        if (s->lt->point) {
+                            light_coords(s->lt, X[j], q);
+                        } else {
+                            q[0] = l[0] + ray.nb[j][0];
+                            q[1] = l[1] + ray.nb[j][1];
+                            q[2] = l[2] + ray.nb[j][2];
+                        }
                         /* The record has room for the first 8 neighbours. */
                         int* nrec = (rec && j < 8) ? rec + 11 + 3 * j : NULL;
-                        sum += light_lookup(s->B, s->lt, ro, q0, q1, q2, nrec);
+                        sum += light_lookup(s->B, s->lt, ro, q[0], q[1], q[2], nrec);
                     }
-                    coef = sum / (double)ray.nnb;
+                    coef = sum / (double)nnb;
                 }
             }
             double lf = (double)ro->ambient + (1.0 - (double)ro->ambient) * coef;

@@ -40,26 +40,38 @@ MUTATIONS = {
     "depth-comp-n-sign": ("stored = stored - (double)s->opt->comp_n * log1p(alpha);",
                           "stored = stored + (double)s->opt->comp_n * log1p(alpha);"),
     "slice-lerp-weights-swapped": ("v = (1.0 - w) * b0 + w * b1;", "v = w * b0 + (1.0 - w) * b1;"),
+    "point-axis-away-from-centre": ("float q[3] = {0.5f - pos[0], 0.5f - pos[1], 0.5f - pos[2]};",
+                                    "float q[3] = {pos[0] - 0.5f, pos[1] - 0.5f, pos[2] - 0.5f};"),
+    "point-half-angle-sine": ("o->h = hs / sqrtf(dc2 - hs2);", "o->h = hs / sqrtf(dc2);"),
+    "point-depth-not-from-light": ("float d = dot3f(o->L, V) - pa;", "float d = dot3f(o->L, V);"),
+    "point-no-perspective-divide": ("float su = dot3f(e, lt->U) / ds;", "float su = dot3f(e, lt->U);"),
+    "point-parallel-columns": ("P[a] = fmaf(sk, w, lt->P[a]);",
+                               "P[a] = fmaf(sk, lt->L[a], fmaf(v, lt->V[a], fmaf(u, lt->U[a], lt->P[a]))) + 0.0f * w;"),
+    "point-cone-away-from-light": ("for (int a = 0; a < 3; ++a) c[a] = fmaf(-dist, w[a], S[a]);",
+                                   "for (int a = 0; a < 3; ++a) c[a] = fmaf(dist, w[a], S[a]);"),
+    "point-cone-turn-sign": ("cross3f(w, B[0], B[1]);", "cross3f(B[0], w, B[1]);"),
+    "point-shell-radius": ("o[a] = sgn ? S[a] - r : S[a] + r;", "o[a] = sgn ? S[a] - r : S[a] + 2.0f * r;"),
     "slice-lerp-nearest-base": ("int k0 = floor_clamp(lam, 0, lt->n - 1);",
                                 "int k0 = floor_clamp(lam + 0.5f, 0, lt->n - 1);"),
     "sample-count-le": ("if (!(t < ray.t1)) break;", "if (!(t <= ray.t1)) break;"),
-    "opacity-correction-exponent": ("alpha = 1.0 - pow(1.0 - alpha, s->spacing_vox);",
-                                    "alpha = 1.0 - pow(1.0 - alpha, 1.0 / s->spacing_vox);"),
+    "opacity-correction-exponent": ("alpha = 1.0 - pow(1.0 - alpha, s->spacing_vox * column_stretch(s->lt, i, (int)j));",
+                                    "alpha = 1.0 - pow(1.0 - alpha, 1.0 / (s->spacing_vox * column_stretch(s->lt, i, (int)j)));"),
     "background-not-weighted": ("o[ch] = outC[ch] + (1.0 - outA) * (double)ro->bg[ch];",
                                 "o[ch] = outC[ch] + (double)ro->bg[ch];"),
     "emission-not-opacity-weighted": ("double csrc = lf * (double)ro->color[ch] * alpha * rgba[ch];",
                                       "double csrc = lf * (double)ro->color[ch] * rgba[ch];"),
     "light-colour-dropped": ("double csrc = lf * (double)ro->color[ch] * alpha * rgba[ch];",
                              "double csrc = lf * alpha * rgba[ch];"),
-    "eq8-max-as-min": ("if (c == 0 || d > mx) mx = d;", "if (c == 0 || d < mx) mx = d;"),
+    "eq8-max-as-min": ("float d = dot3f(o->L, V);\n        if (c == 0 || d < mn) mn = d;\n        if (c == 0 || d > mx) mx = d;",
+                       "float d = dot3f(o->L, V);\n        if (c == 0 || d < mn) mn = d;\n        if (c == 0 || d < mx) mx = d;"),
     "basis-axis-most-aligned": ("if (fabsf(o->L[1]) < fabsf(o->L[ax])) ax = 1;",
                                 "if (fabsf(o->L[1]) > fabsf(o->L[ax])) ax = 1;"),
     "ert-threshold-shifted": ("const double ert = (double)ro->ert, band = ro->ert_band;",
                               "const double ert = (double)ro->ert + 0.03, band = ro->ert_band;"),
     "comp-n-inverted": ("stored = stored * pow(1.0 + alpha, (double)s->opt->comp_n);",
                         "stored = stored / pow(1.0 + alpha, (double)s->opt->comp_n);"),
-    "texel-centre-offset": ("float qi = (float)(2 * i + 1) / (float)lt->R;",
-                            "float qi = (float)(2 * i) / (float)lt->R;"),
+    "texel-centre-offset": ("float sk, float P[3]) {\n    float qi = (float)(2 * i + 1) / (float)lt->R;",
+                            "float sk, float P[3]) {\n    float qi = (float)(2 * i) / (float)lt->R;"),
     "shadow-at-sample-light-coords-dropped-kappa": ("ray->ld[0] = dot3f(lt->L, ray->d) * lt->kappa;",
                                                     "ray->ld[0] = dot3f(lt->L, ray->d);"),
 }

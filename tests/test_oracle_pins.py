@@ -94,7 +94,7 @@ def test_texel_world_and_light_coords_are_inverse(orc, seed):
         assert (X - c) @ U == pytest.approx(u_i, abs=2e-6)
         assert (X - c) @ V == pytest.approx(v_j, abs=2e-6)
         assert X @ L == pytest.approx(lt.min + k * (lt.max - lt.min) / n, abs=2e-6)
-        lam, tu, tv = orc.point_light_coords(lt, X)
+        lam, tu, tv = orc.light_coords(lt, X)
         assert lam == pytest.approx(k, abs=1e-3 * max(1, n / 64))
         assert tu == pytest.approx(i, abs=1e-3 * max(1, R / 64))
         assert tv == pytest.approx(j, abs=1e-3 * max(1, R / 64))
@@ -790,3 +790,211 @@ def test_variant_options_are_validated(orc):
     for kw in (dict(quantity=2), dict(slice_filter=2), dict(shell_count=5), dict(shell_count=-1)):
         with pytest.raises(ValueError):
             orc.render_image(vol, tf, 0, 255, lt, B, c, 2, 2, orc.render_opts(orc.SHELL, 0.5, **kw))
+
+
+# --------------------------------------------------------------------------
+# Point light (f4): rays from a light position, perspective texel grid.
+
+def random_light_pos(rng, lo=1.2, hi=4.0):
+    d = unit(rng.normal(size=3))
+    return 0.5 + rng.uniform(lo, hi) * d
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_point_light_frame(orc, seed):
+    rng = np.random.default_rng(80 + seed)
+    P = random_light_pos(rng)
+    n, R = 33, 48
+    lt = orc.point_light_setup(P, n, R)
+    P32 = np.array(lt.P[:], float)
+    a = unit(0.5 - P32)
+    L, U, V = (np.array(x[:], float) for x in (lt.L, lt.U, lt.V))
+    assert np.allclose(L, a, atol=1e-6)
+    assert abs(U @ L) < 1e-6 and abs(V @ L) < 1e-6 and abs(U @ V) < 1e-6
+    assert np.allclose(np.cross(L, U), V, atol=1e-6)
+    verts = np.array([[(c >> b) & 1 for b in range(3)] for c in range(8)], float)
+    depth = (verts - P32) @ a
+    assert lt.min == pytest.approx(depth.min(), abs=1e-5)
+    assert lt.max == pytest.approx(depth.max(), abs=1e-5)
+    assert lt.min > 0.0
+    dc = np.linalg.norm(0.5 - P32)
+    g = (math.sqrt(3) / 2) / math.sqrt(dc * dc - 0.75)
+    assert lt.h == pytest.approx(g, rel=1e-5)
+    assert lt.sigma == pytest.approx(R / (2 * g), rel=1e-5)
+    assert lt.point == 1
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_point_light_frustum_holds_the_cube(orc, seed):
+    """Every point of the cube falls inside the texel grid and the slice range."""
+    rng = np.random.default_rng(90 + seed)
+    lt = orc.point_light_setup(random_light_pos(rng, 1.0, 1.5), 20, 32)
+    pts = np.vstack([np.array([[(c >> b) & 1 for b in range(3)] for c in range(8)], float),
+                     rng.uniform(0, 1, size=(500, 3))])
+    for X in pts:
+        lam, tu, tv = orc.light_coords(lt, X)
+        assert -1e-3 <= lam <= 20 + 1e-3
+        assert -0.5 - 1e-3 <= tu <= 31.5 + 1e-3 and -0.5 - 1e-3 <= tv <= 31.5 + 1e-3
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_point_light_texel_round_trip(orc, seed):
+    """The point of texel (i, j) on slice k maps back to (k, i, j)."""
+    rng = np.random.default_rng(100 + seed)
+    n, R = 25, 40
+    lt = orc.point_light_setup(random_light_pos(rng), n, R)
+    for _ in range(200):
+        i, j, k = (int(x) for x in (rng.integers(R), rng.integers(R), rng.integers(n)))
+        X = orc.texel_world(lt, i, j, k)
+        lam, tu, tv = orc.light_coords(lt, X)
+        assert abs(lam - k) < 1e-3 and abs(tu - i) < 1e-3 and abs(tv - j) < 1e-3
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_point_light_homogeneous_cube_counts_planes_on_each_ray(orc, seed):
+    """Homogeneous cube: B_k of a column is (1 - a)^m, m the planes j < k whose
+    depth lies between where the column's ray enters and leaves the cube
+    (ray-box intersection in FP64)."""
+    a = f32(0.2)
+    N = 8
+    vol = np.full((N, N, N), 200, np.uint8)
+    tf = step_tf(256, [(100, 256, (1, 1, 1, a))])
+    rng = np.random.default_rng(110 + seed)
+    n, R = 37, 16
+    lt = orc.point_light_setup(random_light_pos(rng, 1.1, 2.0), n, R)
+    B = orc.build_stack(vol, tf, 0, 255, lt)
+    P = np.array(lt.P[:], float)
+    L, U, V = (np.array(x[:], float) for x in (lt.L, lt.U, lt.V))
+    g = lt.h
+    d = lt.min + np.arange(n) * (lt.max - lt.min) / n
+    checked = 0
+    for j in range(R):
+        for i in range(R):
+            u = (2 * (i + 0.5) / R - 1) * g
+            v = (2 * (j + 0.5) / R - 1) * g
+            w = L + u * U + v * V
+            with np.errstate(divide="ignore"):
+                t0 = (0.0 - P) / w
+                t1 = (1.0 - P) / w
+            lo, hi = np.minimum(t0, t1).max(), np.maximum(t0, t1).min()
+            if lo > hi:
+                inside = np.zeros(n, bool)
+            else:
+                if np.any(np.abs(d - lo) < 1e-5) or np.any(np.abs(d - hi) < 1e-5):
+                    continue
+                inside = (d >= lo) & (d <= hi)
+            m = np.concatenate([[0], np.cumsum(inside)[:-1]])
+            assert np.abs(B[:, j, i] - (1 - a) ** m).max() < 1e-12
+            checked += 1
+    assert checked > R * R // 2
+
+
+def test_point_light_plate_shadow_grows_by_similar_triangles(orc):
+    """Light at height 2.5 above an opaque plate (half width 0.1, z in
+    [0.5625, 0.625]) over a receiver slab (z in [0.125, 0.25]); camera below.
+    The plate's umbra on the receiver's top face is the plate scaled by
+    (2.5 - 0.25) / (2.5 - 0.5625) (from its lower face): receiver pixels well
+    inside get no light, pixels well outside get the unshadowed closed form.
+    A directional light would give half width 0.1 instead of 0.116."""
+    N, a = 64, f32(0.25)
+    vol = np.zeros((N, N, N), np.uint8)
+    vol[36:40, 26:38, 26:38] = 255            # plate: x, y in [0.40625, 0.59375]
+    vol[8:16] = 100                            # receiver: z in [0.125, 0.25]
+    tf = step_tf(256, [(50, 151, (1, 1, 1, a)), (200, 256, (0, 0, 0, 1.0))])
+    ramp = np.linspace(0, 1, 51)[1:-1]
+    tf[151:200, :3] = (1 - ramp)[:, None]
+    tf[151:200, 3] = a + (1 - a) * ramp
+    n, R = 128, 256
+    lt = orc.point_light_setup((0.5, 0.5, 2.5), n, R)
+    B = orc.build_stack(vol, tf, 0, 255, lt)
+    W = 128
+    c = cam((0.5, 0.5, -1.0), (0.5, 0.5, 0.5), (0, 1, 0), False, 40, 0.5 / W)  # 1 x 1 frame
+    img, *_ = orc.render_image(vol, tf, 0, 255, lt, B, c, W, 1,
+                               orc.render_opts(orc.SHADOW, 0.5))
+    xs = (np.arange(W) + 0.5) / W
+    # The camera looks along +z with up +y: image x runs along -x of the world.
+    half_plate = (38 - 26) / 2 / N              # 0.09375
+    umbra = half_plate * (2.5 - 0.25) / (2.5 - 40 / N)
+    penumbra = half_plate * (2.5 - 0.125) / (2.5 - 36 / N)
+    dist = np.abs(xs - 0.5)
+    dark = dist < umbra - 0.02
+    lit = (dist > penumbra + 0.02) & (dist < 0.45)
+    assert dark.sum() > 10 and lit.sum() > 10
+    assert np.all(img[0, dark, :3] < 1e-3 * img[0, lit, :3].max())
+    # Lit receiver: 17 samples z = i/128, i = 16..32 (first seen: i = 16); the
+    # planes are z = 1 - j/128, so sample i sits on plane 128 - i and receives
+    # the light through the 32 - i receiver planes above it:
+    # C = sum_s a (1 - a)^s (1 - a)^(16 - s) = 17 a (1 - a)^16.
+    assert np.allclose(img[0, lit, :3], 17 * a * (1 - a) ** 16, atol=1e-12)
+    # Between 0.1 and the umbra edge a directional light would already be lit.
+    between = (dist > half_plate + 0.005) & (dist < umbra - 0.005)
+    assert between.sum() >= 2 and np.all(img[0, between, :3] < 1e-3 * img[0, lit, :3].max())
+
+
+@pytest.mark.parametrize("mode", ["shadow", "shell", "cone"])
+def test_point_light_far_away_approaches_directional(orc, mode):
+    """A light 2000 units away along -L gives nearly the directional frame."""
+    vol, tf, vmin, vmax = blob_scene(N=24)
+    tf[:, 3] *= 4.0
+    L = unit((0.3, -0.4, 0.87))
+    n, R = 24, 48
+    md = {"shadow": orc.SHADOW, "shell": orc.SHELL, "cone": orc.CONE}[mode]
+    ro = orc.render_opts(md, 0.5)
+    c = cam((2.2, 1.9, 1.4), (0.5, 0.5, 0.5), (0, 0, 1), True, 40, 0.5)
+    ltd = orc.light_setup(L, n, R)
+    ltp = orc.point_light_setup(0.5 - 2000.0 * L, n, R)
+    Bd = orc.build_stack(vol, tf, vmin, vmax, ltd)
+    Bp = orc.build_stack(vol, tf, vmin, vmax, ltp)
+    imd, *_ = orc.render_image(vol, tf, vmin, vmax, ltd, Bd, c, 24, 20, ro)
+    imp, *_ = orc.render_image(vol, tf, vmin, vmax, ltp, Bp, c, 24, 20, ro)
+    # The columns of the far light still tilt by up to g = 4e-4: about 0.02
+    # voxel of drift across the cube, so steep edges differ by up to ~0.015.
+    assert np.abs(Bd - Bp).mean() < 2e-4 and np.abs(Bd - Bp).max() < 0.03
+    assert np.abs(imd - imp).mean() < 2e-4 and np.abs(imd - imp).max() < 0.01
+    assert imd[..., 3].max() > 0.2
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_point_light_scattering_points(orc, seed):
+    """Shell points are S +- q r e_a; cone ring n is centred n dL from S
+    towards the light, its four points lie at radius n dL tan(phi) in the plane
+    orthogonal to the light direction at S, a quarter turn apart, the first
+    one towards the eye."""
+    rng = np.random.default_rng(120 + seed)
+    lt = orc.point_light_setup(random_light_pos(rng), 40, 64)
+    S = rng.uniform(0.1, 0.9, size=3)
+    d = unit(rng.normal(size=3))
+    Nmax = 48
+    sh = orc.point_neighbours(lt, orc.render_opts(orc.SHELL, 0.5, shell_radius_vox=1.5,
+                                                  shell_count=2), Nmax, S, d)
+    assert sh.shape == (12, 3)
+    for q in (1, 2):
+        for a in range(3):
+            for sgn, s in enumerate((1.0, -1.0)):
+                want = np.array(S, np.float32).astype(float)
+                want[a] += s * q * 1.5 / Nmax
+                assert np.allclose(sh[6 * (q - 1) + 2 * a + sgn], want, atol=1e-6)
+    phi = 20.0
+    co = orc.point_neighbours(lt, orc.render_opts(orc.CONE, 0.5, cone_half_angle_deg=phi),
+                              Nmax, S, d)
+    assert co.shape == (8, 3)
+    P = np.array(lt.P[:], float)
+    w = unit(S - P)
+    toward_eye = -d - (-d @ w) * w
+    for ring in (1, 2):
+        dist = ring * lt.dL
+        centre = S - dist * w
+        pts = co[4 * (ring - 1):4 * ring].astype(float) - centre
+        assert np.allclose(np.linalg.norm(pts, axis=1), dist * math.tan(math.radians(phi)),
+                           rtol=1e-4)
+        assert np.allclose(pts @ w, 0.0, atol=1e-6)
+        assert abs(pts[0] @ pts[1]) < 1e-8 and np.allclose(pts[2], -pts[0], atol=1e-6)
+        assert np.allclose(np.cross(w, pts[0]), pts[1], atol=1e-6)   # quarter turn about w
+        assert pts[0] @ toward_eye > 0
+
+
+def test_point_light_rejects_positions_inside_its_sphere(orc):
+    for P in ((0.5, 0.5, 0.5), (0.5, 0.5, 1.4), (1.2, 0.9, 0.5), (np.nan, 0, 2)):
+        with pytest.raises(ValueError):
+            orc.point_light_setup(P, 8, 8)
+    orc.point_light_setup((0.5, 0.5, 1.5), 8, 8)
