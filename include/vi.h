@@ -139,6 +139,18 @@ int vi_set_transfer_function(vi_ctx* ctx, const float* rgba, int M, float vmin, 
    white).  Marks the stack stale. */
 int vi_set_light(vi_ctx* ctx, const float dir[3], const float color[3]);
 
+/* Point light (not in the paper's experiments, which use a directional light;
+   Fig. 7 speaks of a light position): light travels along rays from
+   `position` (cube coordinates; at least 1 from the cube centre (1/2, 1/2,
+   1/2), outside the cube's circumscribed sphere, else VI_EINVAL).  The
+   slices are planes perpendicular to the axis from the light to the centre;
+   each stack column is one ray from the light through a perspective texel grid
+   that holds the cube; a lookup divides by the depth along the axis.  Shell
+   points are S +- q r e_a; cone rings are centred n dL from S towards the
+   light, turned about the light direction at S.  color as in vi_set_light.
+   Replaces any directional light.  Marks the stack stale. */
+int vi_set_point_light(vi_ctx* ctx, const float position[3], const float color[3]);
+
 /* Algorithm 1: build n_slices attenuation buffers of slice_res x slice_res
    texels, slice 0 nearest the light at min of Eq. 8, spacing (max - min)/n.
    Buffer k holds the light arriving at plane k: B_0 = 1,

@@ -94,6 +94,46 @@ int light_frame(const float dir[3], int n, int R, LightFrame* o) {
     return VI_OK;
 }
 
+// Point light at pos (f4): the frame of a directional light along the axis
+// a = (c - pos) / |c - pos|, then depths from pos (min / max over the cube's
+// vertices of V.a - pos.a), Lc = 0, and a perspective texel grid of tangent
+// half extent h = sqrt(3)/2 / sqrt(|c - pos|^2 - 3/4).  |c - pos| >= 1.
+int point_light_frame(const float pos[3], int n, int R, LightFrame* o) {
+    if (!finite3(pos)) return VI_EINVAL;
+    float q[3] = {0.5f - pos[0], 0.5f - pos[1], 0.5f - pos[2]};
+    float dc2 = dot3(q, q);
+    float dc = std::sqrt(dc2);
+    if (!(dc >= 1.0f) || !std::isfinite(dc)) return VI_EINVAL;
+    int rc = light_frame(q, n, R, o);
+    if (rc) return rc;
+    o->point = 1;
+    for (int a = 0; a < 3; ++a) o->P[a] = pos[a];
+    float pa = dot3(o->L, pos);
+    // min / max over the vertices of V.a - pos.a: the extreme vertices take the
+    // negative (positive) components of a, summed in axis order.
+    float m[3], M[3];
+    for (int a = 0; a < 3; ++a) {
+        m[a] = o->L[a] < 0.0f ? o->L[a] : 0.0f;
+        M[a] = o->L[a] > 0.0f ? o->L[a] : 0.0f;
+    }
+    float mn = m[0] + m[1];
+    mn = mn + m[2];
+    float mx = M[0] + M[1];
+    mx = mx + M[2];
+    o->min = mn - pa;
+    o->max = mx - pa;
+    float span = o->max - o->min;
+    o->dL = span / (float)n;
+    o->kappa = (float)n / span;
+    o->Lc = 0.0f;
+    const float hs = 0x1.bb67aep-1f;
+    float hs2 = hs * hs;
+    o->h = hs / std::sqrt(dc2 - hs2);
+    float two_h = 2.0f * o->h;
+    o->sigma = (float)R / two_h;
+    return VI_OK;
+}
+
 int camera_frame(const vi_camera* cam, int W, int H, float step_vox, int nmax, CameraFrame* c) {
     if (!finite3(cam->eye) || !finite3(cam->target) || !finite3(cam->up)) return VI_EINVAL;
     std::memset(c, 0, sizeof(*c));
@@ -320,6 +360,9 @@ int fill_march_params(vi_ctx* c, const vi_camera* cam, int W, int H, float step_
             }
         }
     }
+    for (int q = 1; q <= p->shells; ++q)
+        p->shell_r[q - 1] = ((float)q * c->bopts.shell_radius_vox) / (float)nmax(c);
+    p->tanphi = (float)std::tan((double)c->bopts.cone_half_angle_deg * (M_PI / 180.0));
     p->depth = c->bopts.quantity == VI_OPTICAL_DEPTH ? 1 : 0;
     p->slice_linear = ro->slice_filter == VI_SLICE_LINEAR ? 1 : 0;
     if (c->mode == VI_CONE && c->lt_valid) {
@@ -625,6 +668,24 @@ int vi_set_light(vi_ctx* c, const float dir[3], const float color[3]) {
         c->color[a] = color ? color[a] : 1.0f;
     }
     c->has_light = true;
+    c->light_point = false;
+    mark_stale(c);
+    return VI_OK;
+}
+
+int vi_set_point_light(vi_ctx* c, const float position[3], const float color[3]) {
+    int rc = enter(c);
+    if (rc) return rc;
+    if (!position || !finite3(position)) return VI_EINVAL;
+    LightFrame probe;
+    if (point_light_frame(position, 1, 1, &probe)) return VI_EINVAL;  // |c - pos| >= 1
+    if (color && !finite3(color)) return VI_EINVAL;
+    for (int a = 0; a < 3; ++a) {
+        c->pos[a] = position[a];
+        c->color[a] = color ? color[a] : 1.0f;
+    }
+    c->has_light = true;
+    c->light_point = true;
     mark_stale(c);
     return VI_OK;
 }
@@ -648,7 +709,7 @@ int vi_build_attenuation(vi_ctx* c, int n, int R, int mode, const vi_build_opts*
     LightFrame lt{};
     bool lt_ok = false;
     if (c->has_light) {
-        rc = light_frame(c->dir, n, R, &lt);
+        rc = c->light_point ? point_light_frame(c->pos, n, R, &lt) : light_frame(c->dir, n, R, &lt);
         if (rc) return rc;
         lt_ok = true;
     }

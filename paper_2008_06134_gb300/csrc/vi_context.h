@@ -50,6 +50,8 @@ struct vi_ctx {
     bool flags_ok = false;  // bflags match the current volume and TF
 
     bool has_light = false;
+    bool light_point = false;             // point light at pos, else directional dir
+    float pos[3] = {0.5f, 0.5f, 2.0f};
     float dir[3] = {0.0f, 0.0f, 1.0f};
     float color[3] = {1.0f, 1.0f, 1.0f};
 

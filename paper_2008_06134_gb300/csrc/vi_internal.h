@@ -18,17 +18,26 @@ namespace vi {
 // Light set-up: Eq. 8 (min/max over the cube's vertices), the slice spacing and
 // the Eq. 9 ratio, and the light-space frame of Eq. 10 (orthographic light
 // view: basis U, V with V = L x U, a square of half extent h about the centre).
+// Directional light: L the direction light travels, slices at L.X = min +
+// k dL, an orthographic texel grid of half extent h about the centre.
+// Point light (point = 1): light travels along rays from P; L is the axis from
+// P to the centre, slices are planes at depths (X - P).L = min + k dL, Lc = 0,
+// and the texel grid is perspective: texel (i, j) is the ray from P along
+// L + u U + v V, with u, v in [-h, h] (h the tangent of the half angle of the
+// cone from P holding the cube's circumscribed sphere).
 struct LightFrame {
     float L[3];
     float min, max;
     float dL;     // (max - min) / n
     float kappa;  // n / (max - min)
-    float Lc;     // L . (1/2, 1/2, 1/2)
+    float Lc;     // L . (1/2, 1/2, 1/2); 0 for a point light
     float U[3], V[3];
-    float h;      // sqrt(3)/2 as binary32
-    float sigma;  // R / (2 h): texels per world unit
+    float h;      // sqrt(3)/2 as binary32; point light: tangent half extent
+    float sigma;  // R / (2 h): texels per world unit (per unit tangent)
     float rho0;   // (R - 1) / 2
     int n, R;
+    int point;    // 1: point light at P
+    float P[3];
 };
 
 // The volume as footprint octets: element (x, y, z) of [nz][ny][nx] holds the
@@ -106,6 +115,8 @@ struct MarchParams {
     CameraFrame cam;
     float shell_off[kMaxShells][6][3];  // light-space offsets of the shell points, per shell
     int shells;             // shells in use (1 .. kMaxShells)
+    float shell_r[kMaxShells];  // point light: world radius of shell q + 1
+    float tanphi;           // point light: tan of the cone half angle
     int depth;              // 1: the stack holds optical depth; light factor exp(-value)
     int slice_linear;       // 1: linear filtering between slices
     float cone_rad[2];      // ring radii in texels, rings 1 and 2

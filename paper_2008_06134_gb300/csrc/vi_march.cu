@@ -187,9 +187,36 @@ __device__ __forceinline__ int last_transparent(const MarchParams& p, const Ray&
 // done), kStopped if early ray termination fired, kEmpty if the sample lies in
 // a brick that cannot yield alpha > 0 (counted, nothing composited), else
 // kContinue.
+// Light-space coordinates of a world point under a point light: with
+// e = X - P and depth d = e.L, lambda = (d - min) kappa, tu = (e.U / d) sigma +
+// rho0, tv likewise (a depth below 1e-6 counts as 1e-6).
+__device__ __forceinline__ void point_coords(const LightFrame& lt, float X0, float X1, float X2,
+                                             float& l0, float& l1, float& l2) {
+    const float e0 = __fsub_rn(X0, lt.P[0]), e1 = __fsub_rn(X1, lt.P[1]),
+                e2 = __fsub_rn(X2, lt.P[2]);
+    const float d = dot3_rn(e0, e1, e2, lt.L[0], lt.L[1], lt.L[2]);
+    l0 = __fmul_rn(__fsub_rn(d, lt.min), lt.kappa);
+    const float ds = d > 1e-6f ? d : 1e-6f;
+    const float su = __fdiv_rn(dot3_rn(e0, e1, e2, lt.U[0], lt.U[1], lt.U[2]), ds);
+    const float sv = __fdiv_rn(dot3_rn(e0, e1, e2, lt.V[0], lt.V[1], lt.V[2]), ds);
+    l1 = __fmaf_rn(su, lt.sigma, lt.rho0);
+    l2 = __fmaf_rn(sv, lt.sigma, lt.rho0);
+}
+
+// Light factor of the world point X under a point light.
+template <typename Fmt>
+__device__ __forceinline__ float point_light_factor(const MarchParams& p, float X0, float X1,
+                                                    float X2, int* rec) {
+    float q0, q1, q2;
+    point_coords(p.lt, X0, X1, X2, q0, q1, q2);
+    return light_factor<Fmt>(p, p.lt.n, p.lt.R, q0, q1, q2, rec);
+}
+
 // EXT enables the variant options (optical-depth stack, linear slice
 // filtering, several shells); the default kernels compile without them.
-template <typename VoxT, typename Fmt, int MODE, bool TRACE, bool EXT>
+// POINT: a point light (coordinates per sample, scattering points built in
+// world space); it always takes the EXT lookups.
+template <typename VoxT, typename Fmt, int MODE, bool TRACE, bool EXT, bool POINT>
 __device__ __forceinline__ int march_sample(const MarchParams& p, const float* s_alpha,
                                             const Ray& r, int i, float& C0, float& C1, float& C2,
                                             float& A, int& count, int& lit, int32_t* rec) {
@@ -222,9 +249,17 @@ __device__ __forceinline__ int march_sample(const MarchParams& p, const float* s
     float coef = 1.0f;
     lit += alpha > 0.0f ? 1 : 0;
     if ((MODE != 0 && alpha > 0.0f) || TRACE) {
-        const float l0 = __fmaf_rn(t, r.ld[0], r.lo[0]);
-        const float l1 = __fmaf_rn(t, r.ld[1], r.lo[1]);
-        const float l2 = __fmaf_rn(t, r.ld[2], r.lo[2]);
+        float l0, l1, l2, S0 = 0.0f, S1 = 0.0f, S2 = 0.0f;
+        if (POINT) {
+            S0 = __fmaf_rn(t, r.d[0], r.o[0]);
+            S1 = __fmaf_rn(t, r.d[1], r.o[1]);
+            S2 = __fmaf_rn(t, r.d[2], r.o[2]);
+            point_coords(p.lt, S0, S1, S2, l0, l1, l2);
+        } else {
+            l0 = __fmaf_rn(t, r.ld[0], r.lo[0]);
+            l1 = __fmaf_rn(t, r.ld[1], r.lo[1]);
+            l2 = __fmaf_rn(t, r.ld[2], r.lo[2]);
+        }
         const int n = p.lt.n, R = p.lt.R;
         if (TRACE) {
             rec[2] = __float_as_int(l0);
@@ -238,7 +273,22 @@ __device__ __forceinline__ int march_sample(const MarchParams& p, const float* s
         } else if (MODE == 2) {
             float sum = 0.0f;
             const int shells = EXT ? p.shells : 1;
-            if (EXT) {
+            if (POINT) {
+                // Shell q + 1: S +- r_q e_a in world space, then the perspective map.
+#pragma unroll 1
+                for (int j = 0; j < 6 * shells; ++j) {
+                    const int sh = j / 6, q = j - 6 * sh, a = q >> 1;
+                    const float rq = p.shell_r[sh];
+                    float X[3] = {S0, S1, S2};
+                    const float Sa = a == 0 ? S0 : (a == 1 ? S1 : S2);
+                    const float Xa = (q & 1) ? __fsub_rn(Sa, rq) : __fadd_rn(Sa, rq);
+                    X[0] = a == 0 ? Xa : X[0];
+                    X[1] = a == 1 ? Xa : X[1];
+                    X[2] = a == 2 ? Xa : X[2];
+                    int* rr = (TRACE && j < 8) ? rec + 11 + 3 * j : nullptr;
+                    sum += point_light_factor<Fmt>(p, X[0], X[1], X[2], rr);
+                }
+            } else if (EXT) {
                 // One point at a time: the variants' lookups are heavier, and
                 // keeping all of them in flight would spill.
 #pragma unroll 1
@@ -264,7 +314,49 @@ __device__ __forceinline__ int march_sample(const MarchParams& p, const float* s
             coef = EXT ? sum * (1.0f / (float)(6 * shells)) : sum * (1.0f / 6.0f);
         } else if (MODE == 3) {
             float sum = 0.0f;
-            if (EXT) {
+            if (POINT) {
+                // w: the direction the light travels at S; B_proj: the unit part
+                // of -d (towards the eye) orthogonal to w (U's, if that vanishes).
+                const float e0 = __fsub_rn(S0, p.lt.P[0]), e1 = __fsub_rn(S1, p.lt.P[1]),
+                            e2 = __fsub_rn(S2, p.lt.P[2]);
+                const float le = __fsqrt_rn(dot3_rn(e0, e1, e2, e0, e1, e2));
+                const float w0 = __fdiv_rn(e0, le), w1 = __fdiv_rn(e1, le), w2 = __fdiv_rn(e2, le);
+                const float md0 = -r.d[0], md1 = -r.d[1], md2 = -r.d[2];
+                float pr = dot3_rn(md0, md1, md2, w0, w1, w2);
+                float b0 = __fmaf_rn(-pr, w0, md0), b1 = __fmaf_rn(-pr, w1, md1),
+                      b2 = __fmaf_rn(-pr, w2, md2);
+                float nb = __fsqrt_rn(dot3_rn(b0, b1, b2, b0, b1, b2));
+                if (!(nb >= 1e-6f)) {
+                    pr = dot3_rn(p.lt.U[0], p.lt.U[1], p.lt.U[2], w0, w1, w2);
+                    b0 = __fmaf_rn(-pr, w0, p.lt.U[0]);
+                    b1 = __fmaf_rn(-pr, w1, p.lt.U[1]);
+                    b2 = __fmaf_rn(-pr, w2, p.lt.U[2]);
+                    nb = __fsqrt_rn(dot3_rn(b0, b1, b2, b0, b1, b2));
+                }
+                const float B00 = __fdiv_rn(b0, nb), B01 = __fdiv_rn(b1, nb), B02 = __fdiv_rn(b2, nb);
+                // A quarter turn about w (Eq. 11): w x B_proj.
+                const float B10 = __fsub_rn(__fmul_rn(w1, B02), __fmul_rn(w2, B01));
+                const float B11 = __fsub_rn(__fmul_rn(w2, B00), __fmul_rn(w0, B02));
+                const float B12 = __fsub_rn(__fmul_rn(w0, B01), __fmul_rn(w1, B00));
+#pragma unroll 1
+                for (int j = 0; j < 8; ++j) {
+                    const int ring = j >> 2, m = j & 3;
+                    const float dist = __fmul_rn((float)(ring + 1), p.lt.dL);
+                    const float rad = __fmul_rn(dist, p.tanphi);
+                    const float c0 = __fmaf_rn(-dist, w0, S0), c1 = __fmaf_rn(-dist, w1, S1),
+                                c2 = __fmaf_rn(-dist, w2, S2);
+                    float Bm0 = (m & 1) ? B10 : B00, Bm1 = (m & 1) ? B11 : B01,
+                          Bm2 = (m & 1) ? B12 : B02;
+                    if (m & 2) {
+                        Bm0 = -Bm0;
+                        Bm1 = -Bm1;
+                        Bm2 = -Bm2;
+                    }
+                    int* rr = TRACE ? rec + 11 + 3 * j : nullptr;
+                    sum += point_light_factor<Fmt>(p, __fmaf_rn(rad, Bm0, c0), __fmaf_rn(rad, Bm1, c1),
+                                                   __fmaf_rn(rad, Bm2, c2), rr);
+                }
+            } else if (EXT) {
                 // One point at a time (see the shell case).  Point j is ring
                 // j / 4, quarter turn m = j % 4 of B_proj about L.
 #pragma unroll 1
@@ -332,7 +424,7 @@ __device__ __forceinline__ void load_alpha(const MarchParams& p, float* s_alpha)
 #define VI_MARCH_MIN_BLOCKS 4
 #endif
 
-template <typename VoxT, typename Fmt, int MODE, bool EXT>
+template <typename VoxT, typename Fmt, int MODE, bool EXT, bool POINT>
 __global__ void __launch_bounds__(kMarchThreads, VI_MARCH_MIN_BLOCKS)
     march_kernel(const MarchParams p) {
     extern __shared__ float s_alpha[];
@@ -351,7 +443,7 @@ __global__ void __launch_bounds__(kMarchThreads, VI_MARCH_MIN_BLOCKS)
         const bool valid = x < p.cam.W && y < p.cam.H;
         Ray r;
         r.hit = false;
-        if (valid) ray_setup<MODE>(p, x, y, r);
+        if (valid) ray_setup<POINT ? 1 : MODE>(p, x, y, r);
 
         float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, A = 0.0f;
         int count = 0, lit = 0;
@@ -364,8 +456,8 @@ __global__ void __launch_bounds__(kMarchThreads, VI_MARCH_MIN_BLOCKS)
         for (int i = 0; __any_sync(0xffffffffu, active);) {
             int st = kEnded;
             if (active)
-                st = march_sample<VoxT, Fmt, MODE, false, EXT>(p, s_alpha, r, i, C0, C1, C2, A,
-                                                               count, lit, nullptr);
+                st = march_sample<VoxT, Fmt, MODE, false, EXT, POINT>(p, s_alpha, r, i, C0, C1,
+                                                                      C2, A, count, lit, nullptr);
             active = active && (st == kContinue || st == kEmpty);
             const unsigned act = __ballot_sync(0xffffffffu, active);
             const unsigned emp = __ballot_sync(0xffffffffu, active && st == kEmpty);
@@ -393,22 +485,22 @@ __global__ void __launch_bounds__(kMarchThreads, VI_MARCH_MIN_BLOCKS)
     }
 }
 
-template <typename VoxT, typename Fmt, int MODE>
+template <typename VoxT, typename Fmt, int MODE, bool POINT>
 __global__ void trace_kernel(const MarchParams p, int x, int y, int32_t* rec, int max_rec,
                              int* n_rec) {
     extern __shared__ float s_alpha[];
     load_alpha(p, s_alpha);
     if (threadIdx.x != 0) return;
     Ray r;
-    ray_setup<MODE>(p, x, y, r);
+    ray_setup<POINT ? 1 : MODE>(p, x, y, r);
     float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, A = 0.0f;
     int count = 0, lit = 0, nrec = 0;
     // Records the first max_rec samples of the ray.
     if (r.hit) {
         for (int i = 0; nrec < max_rec; ++i) {
             int32_t* out = rec + (size_t)nrec * kTraceWords;
-            int st = march_sample<VoxT, Fmt, MODE, true, true>(p, s_alpha, r, i, C0, C1, C2, A,
-                                                               count, lit, out);
+            int st = march_sample<VoxT, Fmt, MODE, true, true, POINT>(p, s_alpha, r, i, C0, C1,
+                                                                      C2, A, count, lit, out);
             if (st == kEnded) break;
             ++nrec;
             if (st == kStopped) break;
@@ -417,10 +509,10 @@ __global__ void trace_kernel(const MarchParams p, int x, int y, int32_t* rec, in
     *n_rec = nrec;
 }
 
-template <typename VoxT, typename Fmt, int MODE, bool EXT>
+template <typename VoxT, typename Fmt, int MODE, bool EXT, bool POINT>
 cudaError_t launch_march_typed(const MarchParams& p, cudaStream_t s) {
     const size_t smem = (size_t)p.M * sizeof(float);
-    auto kern = march_kernel<VoxT, Fmt, MODE, EXT>;
+    auto kern = march_kernel<VoxT, Fmt, MODE, EXT, POINT>;
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -441,7 +533,7 @@ template <typename VoxT, typename Fmt, int MODE>
 cudaError_t launch_trace_typed(const MarchParams& p, int x, int y, int32_t* rec, int max_rec,
                                int* n_rec, cudaStream_t s) {
     const size_t smem = (size_t)p.M * sizeof(float);
-    auto kern = trace_kernel<VoxT, Fmt, MODE>;
+    auto kern = p.lt.point ? trace_kernel<VoxT, Fmt, MODE, true> : trace_kernel<VoxT, Fmt, MODE, false>;
     kern<<<1, 32, smem, s>>>(p, x, y, rec, max_rec, n_rec);
     return cudaGetLastError();
 }
@@ -450,9 +542,10 @@ template <typename VoxT, typename Fmt, int MODE>
 cudaError_t dispatch_ext(const MarchParams& p, bool trace, int x, int y, int32_t* rec,
                          int max_rec, int* n_rec, cudaStream_t s) {
     if (trace) return launch_trace_typed<VoxT, Fmt, MODE>(p, x, y, rec, max_rec, n_rec, s);
+    if (p.lt.point) return launch_march_typed<VoxT, Fmt, MODE, true, true>(p, s);
     const bool ext = p.depth || p.slice_linear || p.shells > 1;
-    return ext ? launch_march_typed<VoxT, Fmt, MODE, true>(p, s)
-               : launch_march_typed<VoxT, Fmt, MODE, false>(p, s);
+    return ext ? launch_march_typed<VoxT, Fmt, MODE, true, false>(p, s)
+               : launch_march_typed<VoxT, Fmt, MODE, false, false>(p, s);
 }
 
 template <typename VoxT, typename Fmt>
@@ -461,7 +554,7 @@ cudaError_t dispatch_mode(const MarchParams& p, int mode, bool trace, int x, int
     switch (mode) {
         case 0:  // no lookups: the options that change lookups do not apply
             return trace ? launch_trace_typed<VoxT, Fmt, 0>(p, x, y, rec, max_rec, n_rec, s)
-                         : launch_march_typed<VoxT, Fmt, 0, false>(p, s);
+                         : launch_march_typed<VoxT, Fmt, 0, false, false>(p, s);
         case 1: return dispatch_ext<VoxT, Fmt, 1>(p, trace, x, y, rec, max_rec, n_rec, s);
         case 2: return dispatch_ext<VoxT, Fmt, 2>(p, trace, x, y, rec, max_rec, n_rec, s);
         case 3: return dispatch_ext<VoxT, Fmt, 3>(p, trace, x, y, rec, max_rec, n_rec, s);

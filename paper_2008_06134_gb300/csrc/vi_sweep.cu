@@ -26,14 +26,18 @@ namespace {
 constexpr int kSweepBX = 32, kSweepBY = 8;
 constexpr int kBatch = 4;  // slices whose loads are issued together
 
-// Whether the point of slice k on the column through (base) lies in [0,1]^3,
-// evaluated exactly as the sweep evaluates it.
-__device__ __forceinline__ bool texel_inside(const LightFrame& lt, int k, float base0,
-                                             float base1, float base2) {
+// A texel column is the line o + s w: for a directional light o is the
+// texel's point on the plane through the centre and w = L; for a point light
+// o = P and w the texel's ray direction.  Slice k is at s_k = min + k dL - Lc.
+
+// Whether the point of slice k on the column lies in [0,1]^3, evaluated
+// exactly as the sweep evaluates it.
+__device__ __forceinline__ bool texel_inside(const LightFrame& lt, int k, const float o[3],
+                                             const float w[3]) {
     const float sk = __fsub_rn(__fmaf_rn((float)k, lt.dL, lt.min), lt.Lc);
-    const float P0 = __fmaf_rn(sk, lt.L[0], base0);
-    const float P1 = __fmaf_rn(sk, lt.L[1], base1);
-    const float P2 = __fmaf_rn(sk, lt.L[2], base2);
+    const float P0 = __fmaf_rn(sk, w[0], o[0]);
+    const float P1 = __fmaf_rn(sk, w[1], o[1]);
+    const float P2 = __fmaf_rn(sk, w[2], o[2]);
     return P0 >= 0.0f && P0 <= 1.0f && P1 >= 0.0f && P1 <= 1.0f && P2 >= 0.0f && P2 <= 1.0f;
 }
 
@@ -61,9 +65,20 @@ __global__ void __launch_bounds__(kSweepBX* kSweepBY)
     float qj = __fdiv_rn((float)(2 * j + 1), (float)lt.R);
     float u = __fmul_rn(__fsub_rn(qi, 1.0f), lt.h);
     float v = __fmul_rn(__fsub_rn(qj, 1.0f), lt.h);
-    float base0 = __fmaf_rn(v, lt.V[0], __fmaf_rn(u, lt.U[0], 0.5f));
-    float base1 = __fmaf_rn(v, lt.V[1], __fmaf_rn(u, lt.U[1], 0.5f));
-    float base2 = __fmaf_rn(v, lt.V[2], __fmaf_rn(u, lt.U[2], 0.5f));
+    float o[3], w[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (lt.point) {
+            o[a] = lt.P[a];
+            w[a] = __fmaf_rn(v, lt.V[a], __fmaf_rn(u, lt.U[a], lt.L[a]));
+        } else {
+            o[a] = __fmaf_rn(v, lt.V[a], __fmaf_rn(u, lt.U[a], 0.5f));
+            w[a] = lt.L[a];
+        }
+    }
+    // Opacity correction: the slice spacing along this column, in voxels.
+    const float spacing = lt.point ? p.spacing_vox * sqrtf(w[0] * w[0] + w[1] * w[1] + w[2] * w[2])
+                                   : p.spacing_vox;
 
     // Pitched stack: slice k, row j at byte (k (R + 1) + j) row_pitch.  The last
     // row (j = R - 1) is written twice, its copy being row R.
@@ -79,16 +94,15 @@ __global__ void __launch_bounds__(kSweepBX* kSweepBY)
     int kin, kout;
     {
         float slo = -3.0e38f, shi = 3.0e38f;
-        const float b[3] = {base0, base1, base2};
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const float La = lt.L[a];
-            if (La != 0.0f) {
-                const float inv = 1.0f / La;
-                const float s0 = -b[a] * inv, s1 = (1.0f - b[a]) * inv;
+            const float wa = w[a];
+            if (wa != 0.0f) {
+                const float inv = 1.0f / wa;
+                const float s0 = -o[a] * inv, s1 = (1.0f - o[a]) * inv;
                 slo = fmaxf(slo, fminf(s0, s1));
                 shi = fminf(shi, fmaxf(s0, s1));
-            } else if (b[a] < 0.0f || b[a] > 1.0f) {
+            } else if (o[a] < 0.0f || o[a] > 1.0f) {
                 slo = 3.0e38f;
             }
         }
@@ -104,16 +118,16 @@ __global__ void __launch_bounds__(kSweepBX* kSweepBY)
             kin = lt.n;
             kout = -1;
             for (int k = max(kc - 2, 0); k <= min(kc + 2, lt.n - 1); ++k)
-                if (texel_inside(lt, k, base0, base1, base2)) {
+                if (texel_inside(lt, k, o, w)) {
                     kin = min(kin, k);
                     kout = max(kout, k);
                 }
         }
         if (kin <= kout) {
-            while (kin > 0 && texel_inside(lt, kin - 1, base0, base1, base2)) --kin;
-            while (kin <= kout && !texel_inside(lt, kin, base0, base1, base2)) ++kin;
-            while (kout < lt.n - 1 && texel_inside(lt, kout + 1, base0, base1, base2)) ++kout;
-            while (kout >= kin && !texel_inside(lt, kout, base0, base1, base2)) --kout;
+            while (kin > 0 && texel_inside(lt, kin - 1, o, w)) --kin;
+            while (kin <= kout && !texel_inside(lt, kin, o, w)) ++kin;
+            while (kout < lt.n - 1 && texel_inside(lt, kout + 1, o, w)) ++kout;
+            while (kout >= kin && !texel_inside(lt, kout, o, w)) --kout;
         }
     }
 
@@ -134,9 +148,9 @@ __global__ void __launch_bounds__(kSweepBX* kSweepBY)
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
             const float sk = __fsub_rn(__fmaf_rn((float)(k + u), lt.dL, lt.min), lt.Lc);
-            const VoxelCoord vc = voxel_coord(p.vol, __fmaf_rn(sk, lt.L[0], base0),
-                                              __fmaf_rn(sk, lt.L[1], base1),
-                                              __fmaf_rn(sk, lt.L[2], base2));
+            const VoxelCoord vc = voxel_coord(p.vol, __fmaf_rn(sk, w[0], o[0]),
+                                              __fmaf_rn(sk, w[1], o[1]),
+                                              __fmaf_rn(sk, w[2], o[2]));
             ref[u] = octet_ref(p.vol, vc);
             lit[u] = k + u <= kout && brick_may_be_lit(p.grid, vc);
         }
@@ -156,7 +170,7 @@ __global__ void __launch_bounds__(kSweepBX* kSweepBY)
                 const float a0 = s_alpha[e];
                 alpha = fmaf(f, s_alpha[e + 1] - a0, a0);
                 if (p.opacity_correction)
-                    alpha = 1.0f - exp2f(p.spacing_vox * log2f(fmaxf(1.0f - alpha, 0.0f)));
+                    alpha = 1.0f - exp2f(spacing * log2f(fmaxf(1.0f - alpha, 0.0f)));
             }
             float stored = T;
             if (p.comp_n != 0.0f)

@@ -31,11 +31,12 @@ TRACE_NONE = 0x7FFFFFFF
 
 # Every symbol include/vi.h declares, in order.
 EXPORTS = ("vi_create", "vi_destroy", "vi_set_memory_budget", "vi_load_volume",
-           "vi_set_transfer_function", "vi_set_light", "vi_build_attenuation", "vi_render",
-           "vi_sync", "vi_error_string", "vi_attenuation_info", "vi_get_attenuation",
-           "vi_trace_pixel", "vi_launch_count", "vi_render_host_noalloc", "vi_server_create",
-           "vi_server_destroy", "vi_server_add_volume", "vi_server_submit", "vi_server_wait",
-           "vi_server_cancel", "vi_server_timing", "vi_server_release", "vi_server_get_stats")
+           "vi_set_transfer_function", "vi_set_light", "vi_set_point_light",
+           "vi_build_attenuation", "vi_render", "vi_sync", "vi_error_string",
+           "vi_attenuation_info", "vi_get_attenuation", "vi_trace_pixel", "vi_launch_count",
+           "vi_render_host_noalloc", "vi_server_create", "vi_server_destroy",
+           "vi_server_add_volume", "vi_server_submit", "vi_server_wait", "vi_server_cancel",
+           "vi_server_timing", "vi_server_release", "vi_server_get_stats")
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = 0, 1, 2, 3, 4
 
 
@@ -99,6 +100,7 @@ def library() -> C.CDLL:
     L.vi_load_volume.argtypes = [vp, vp, i, i, i, i, i]
     L.vi_set_transfer_function.argtypes = [vp, vp, i, f, f]
     L.vi_set_light.argtypes = [vp, vp, vp]
+    L.vi_set_point_light.argtypes = [vp, vp, vp]
     L.vi_build_attenuation.argtypes = [vp, i, i, i, P(BuildOpts)]
     L.vi_render.argtypes = [vp, P(Camera), i, i, f, vp, i, P(RenderOpts)]
     L.vi_sync.argtypes = [vp]
@@ -224,6 +226,11 @@ class Context:
 
     def set_light(self, direction, color=(1.0, 1.0, 1.0)) -> None:
         _check(self.L.vi_set_light(self.h, _f3(direction), _f3(color)), "vi_set_light")
+
+    def set_point_light(self, position, color=(1.0, 1.0, 1.0)) -> None:
+        """A point light at ``position`` (at least 1 from the cube centre)."""
+        _check(self.L.vi_set_point_light(self.h, _f3(position), _f3(color)),
+               "vi_set_point_light")
 
     def build_attenuation(self, n_slices: int, slice_res: int, mode: int, format: int = F32,
                           cone_half_angle_deg: float = 15.0, shell_radius_vox: float = 1.0,

@@ -13,12 +13,15 @@ FORMAT_HALF_ULP = {0: 0.0, 1: 2.0 ** -12, 2: 2.0 ** -9, 3: 0.5 / 65535.0}
 
 def gpu_frame(ctx, scene, mode=None, fmt=0, counts=False, ert=None, bg=None,
               opacity_correction=0, comp_n=0.0, build_oc=0, quantity=0, shell_count=1,
-              slice_filter=0):
+              slice_filter=0, light_pos=None):
     import torch
     mode = scene.mode if mode is None else mode
     ctx.load_volume(scene.volume)
     ctx.set_transfer_function(scene.tf, scene.vmin, scene.vmax)
-    ctx.set_light(scene.light_dir, scene.light_color)
+    if light_pos is None:
+        ctx.set_light(scene.light_dir, scene.light_color)
+    else:
+        ctx.set_point_light(light_pos, scene.light_color)
     ctx.build_attenuation(scene.n_slices, scene.slice_res, mode, format=fmt,
                           cone_half_angle_deg=scene.cone_half_angle_deg,
                           shell_radius_vox=scene.shell_radius_vox,
@@ -40,9 +43,12 @@ def gpu_frame(ctx, scene, mode=None, fmt=0, counts=False, ert=None, bg=None,
 
 def oracle_frame(orc, scene, mode=None, xs=None, ys=None, stack=None, ert=None, bg=None,
                  opacity_correction=0, comp_n=0.0, build_oc=0, ert_band=1e-5, quantity=0,
-                 shell_count=1, slice_filter=0):
+                 shell_count=1, slice_filter=0, light_pos=None):
     mode = scene.mode if mode is None else mode
-    light = orc.light_setup(scene.light_dir, scene.n_slices, scene.slice_res)
+    if light_pos is None:
+        light = orc.light_setup(scene.light_dir, scene.n_slices, scene.slice_res)
+    else:
+        light = orc.point_light_setup(light_pos, scene.n_slices, scene.slice_res)
     if stack is None and mode != orc.NONE:
         stack = orc.build_stack(scene.volume, scene.tf, scene.vmin, scene.vmax, light,
                                 opacity_correction=build_oc, comp_n=comp_n, quantity=quantity)
