@@ -45,10 +45,10 @@ FLOPS_LIT = {0: 0, 1: 6 + 2 + 12, 2: 6 + 2 + 6 * 12 + 7, 3: 6 + 2 + 8 * 12 + 9}
 # entry holds for the kernel sources it was taken from (hash of the files that
 # define the kernel); once they change the figure is stale and reported as null.
 NCU_TRAFFIC = {
-    "march_kernel": (("vi_march.cu", "vi_device.cuh", "vi_internal.h"), "7539b5dd9069b74f",
-                     83_350_528),
-    "sweep_kernel": (("vi_sweep.cu", "vi_device.cuh", "vi_internal.h"), "aaf51e2d5456c23a",
-                     306_188_800),
+    "march_kernel": (("vi_march.cu", "vi_device.cuh", "vi_internal.h"), "a1b835938c90a0a6",
+                     83_276_544),
+    "sweep_kernel": (("vi_sweep.cu", "vi_device.cuh", "vi_internal.h"), "6ceacb8e078d58e7",
+                     306_307_584),
 }
 
 
@@ -71,11 +71,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="ct256-cone",
-                    choices=["ct256-cone", "precision", "scalability", "serving"],
+                    choices=["ct256-cone", "precision", "scalability", "serving", "variants"],
                     help="ct256-cone: the headline frame; precision: storage formats on the "
                          "512^3 blob scene vs the FP64 oracle; scalability: slice count x "
                          "slice resolution grid; serving: the render server on a stream of "
-                         "mixed requests")
+                         "mixed requests; variants: the method variants and the point light "
+                         "on the headline scene")
     ap.add_argument("--requests", type=int, default=512, help="serving: request count")
     ap.add_argument("--rate", default="300,800",
                     help="serving: Poisson arrival rates per second (comma-separated)")
@@ -589,6 +590,61 @@ def scalability_workload(args):
     ctx.close()
 
 
+def variants_workload(args):
+    """Frame cost of each option on the headline scene (256^3 CT phantom, 256
+    slices of 512^2, 1024^2 perspective, step 0.5, ERT 0.99): the directional
+    cone as benchmarked, the optical-depth stack (Eq. 5-6), linear filtering
+    between slices, one to four shells, and a point light 1.5 and 3 units from
+    the centre along the benchmark's light direction."""
+    import numpy as np
+    import torch
+
+    from paper_2008_06134_gb300 import build, phantoms as ph, vi
+    build.build()
+    sc = ph.ct256_cone()
+    ctx = vi.Context(0)
+    ctx.load_volume(torch.from_numpy(sc.volume.view(np.int16)).cuda(), dtype=vi.U16)
+    ctx.set_transfer_function(sc.tf, sc.vmin, sc.vmax)
+    W, H = sc.width, sc.height
+    out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    L = np.asarray(sc.light_dir, np.float64)
+    L = L / np.linalg.norm(L)
+    cases = [("cone (benchmark)", vi.CONE, {}, {}, None),
+             ("cone optical-depth", vi.CONE, {"quantity": vi.OPTICAL_DEPTH}, {}, None),
+             ("cone linear-slices", vi.CONE, {}, {"slice_filter": vi.SLICE_LINEAR}, None),
+             ("shadow", vi.SHADOW, {}, {}, None),
+             ("shell 1", vi.SHELL, {}, {}, None),
+             ("shell 2", vi.SHELL, {"shell_count": 2}, {}, None),
+             ("shell 4", vi.SHELL, {"shell_count": 4}, {}, None),
+             ("cone point-light 1.5", vi.CONE, {}, {}, 0.5 - 1.5 * L),
+             ("cone point-light 3", vi.CONE, {}, {}, 0.5 - 3.0 * L),
+             ("shadow point-light 1.5", vi.SHADOW, {}, {}, 0.5 - 1.5 * L)]
+    rows = []
+    for name, mode, bopts, ropts, pos in cases:
+        if pos is None:
+            ctx.set_light(sc.light_dir, sc.light_color)
+        else:
+            ctx.set_point_light(pos, sc.light_color)
+
+        def bld():
+            ctx.build_attenuation(sc.n_slices, sc.slice_res, mode,
+                                  cone_half_angle_deg=sc.cone_half_angle_deg, **bopts)
+
+        def rnd():
+            ctx.render(sc.camera, W, H, sc.step_vox, out=out, ert=sc.ert, bg=sc.bg, **ropts)
+        for _ in range(args.warmup):
+            bld()
+            rnd()
+        sweep_ms, march_ms = timed_frames(ctx, bld, rnd, flush, args.steps)
+        rows.append({"case": name, "sweep_ms": round(sweep_ms, 4), "march_ms": round(march_ms, 4),
+                     "frames_per_s": round(1000.0 / (sweep_ms + march_ms), 1)})
+    print(json.dumps({"workload": "variants", "scene": "ct256-u16, 256x512^2 FP32, 1024^2 "
+                      "perspective, step 0.5, ERT 0.99", "steps": args.steps, "rows": rows}),
+          flush=True)
+    ctx.close()
+
+
 def serving_workload(args):
     """The render server on the serving mix: 8 registered volumes ({128, 256,
     512}^3, uint8 blobs and uint16 CT ellipsoids) with at most 6 resident under
@@ -701,6 +757,8 @@ def main():
         scalability_workload(args)
     elif args.workload == "serving":
         serving_workload(args)
+    elif args.workload == "variants":
+        variants_workload(args)
     else:
         gb300_arm(args)
 
