@@ -741,6 +741,9 @@ int vi_build_attenuation(vi_ctx* c, int n, int R, int mode, const vi_build_opts*
     p.spacing_vox = lt.dL * (float)nmax(c);
     p.comp_n = o.comp_n;
     p.depth = o.quantity == VI_OPTICAL_DEPTH ? 1 : 0;
+    rc = ensure(c, reinterpret_cast<void**>(&c->counter), &c->counter_cap, 256);
+    if (rc) return rc;
+    p.tile_counter = c->counter;
     cudaError_t e = vi::launch_sweep(p, c->vr->vtype, o.format, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e);
     ++c->launches;

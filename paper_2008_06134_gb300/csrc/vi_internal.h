@@ -88,6 +88,7 @@ struct SweepParams {
     float spacing_vox;        // slice spacing in voxels (opacity correction exponent)
     float comp_n;             // darkening compensation exponent, 0 = off
     int depth;                // 1: store optical depth (Eq. 5-6), else transmittance
+    unsigned* tile_counter;   // work counter of the persistent sweep (zeroed per launch)
 };
 
 // Cap of a stored optical depth (exp(-64) < 2e-28) and the most shells.

@@ -23,8 +23,20 @@ namespace vi {
 
 namespace {
 
-constexpr int kSweepBX = 32, kSweepBY = 8;
-constexpr int kBatch = 4;  // slices whose loads are issued together
+constexpr int kSweepThreads = 256;
+
+// Resident blocks per SM the register allocation is fitted to.  Two (up to
+// 128 registers a thread) measured fastest: 0.119 ms on the 256 x 512^2
+// config-2 sweep, against 0.143 / 0.169 ms for three / four blocks; eight- or
+// sixteen-slice batches were slower than four.
+#ifndef VI_SWEEP_MIN_BLOCKS
+#define VI_SWEEP_MIN_BLOCKS 2
+#endif
+// Slices whose loads are issued together.
+#ifndef VI_SWEEP_BATCH
+#define VI_SWEEP_BATCH 4
+#endif
+constexpr int kBatch = VI_SWEEP_BATCH;
 
 // A texel column is the line o + s w: for a directional light o is the
 // texel's point on the plane through the centre and w = L; for a point light
@@ -41,24 +53,11 @@ __device__ __forceinline__ bool texel_inside(const LightFrame& lt, int k, const 
     return P0 >= 0.0f && P0 <= 1.0f && P1 >= 0.0f && P1 <= 1.0f && P2 >= 0.0f && P2 <= 1.0f;
 }
 
+// One texel column (i, j): every slice's value, nearest the light first.
 template <typename VoxT, typename Fmt, bool DEPTH>
-__global__ void __launch_bounds__(kSweepBX* kSweepBY)
-    sweep_kernel(const SweepParams p) {
-    extern __shared__ float s_alpha[];
-    const int tid = threadIdx.x;
-    for (int e = tid; e < p.M; e += kSweepBX * kSweepBY) s_alpha[e] = p.tf[e].w;
-    __syncthreads();
-
-    // Block tile 32 x 8 texels.  A warp covers TW x (32 / TW) texels, TW chosen
-    // so one row of its store is a whole 32-byte sector: 8 x 4 for FP32, 16 x 2
-    // for the 16-bit formats.
-    constexpr int TW = sizeof(typename Fmt::T) == 2 ? 16 : 8;
-    constexpr int TH = 32 / TW;
+__device__ __forceinline__ void sweep_column(const SweepParams& p, const float* s_alpha, int i,
+                                             int j) {
     const LightFrame& lt = p.lt;
-    const int lane = tid & 31, warp = tid >> 5;
-    const int i = blockIdx.x * kSweepBX + (warp % (kSweepBX / TW)) * TW + (lane % TW);
-    const int j = blockIdx.y * kSweepBY + (warp / (kSweepBX / TW)) * TH + (lane / TW);
-    if (i >= lt.R || j >= lt.R) return;
 
     // World position of texel (i, j) on the plane through the centre.
     float qi = __fdiv_rn((float)(2 * i + 1), (float)lt.R);
@@ -194,12 +193,56 @@ __global__ void __launch_bounds__(kSweepBX* kSweepBY)
     }
 }
 
+
+// Persistent warps: each warp takes TW x TH texel tiles, in raster order, from
+// a global counter until none are left.  Columns through the middle of the
+// cube are long and those near the corners short; taking tiles as warps free
+// up keeps the SMs busy to the end instead of waiting for the last long
+// blocks of a fixed grid.  A warp covers TW x TH texels, TW chosen so one row
+// of its store is a whole 32-byte sector: 8 x 4 for FP32, 16 x 2 for the
+// 16-bit formats.
+template <typename VoxT, typename Fmt, bool DEPTH>
+__global__ void __launch_bounds__(kSweepThreads, VI_SWEEP_MIN_BLOCKS)
+    sweep_kernel(const SweepParams p) {
+    extern __shared__ float s_alpha[];
+    for (int e = threadIdx.x; e < p.M; e += kSweepThreads) s_alpha[e] = p.tf[e].w;
+    __syncthreads();
+    constexpr int TW = sizeof(typename Fmt::T) == 2 ? 16 : 8;
+    constexpr int TH = 32 / TW;
+    const int lane = threadIdx.x & 31;
+    const int R = p.lt.R;
+    const unsigned tiles_x = (unsigned)(R + TW - 1) / TW;
+    const unsigned ntiles = tiles_x * ((unsigned)(R + TH - 1) / TH);
+    for (;;) {
+        unsigned tile = 0;
+        if (lane == 0) tile = atomicAdd(p.tile_counter, 1u);
+        tile = __shfl_sync(0xffffffffu, tile, 0);
+        if (tile >= ntiles) break;
+        const int i = (int)(tile % tiles_x) * TW + (lane % TW);
+        const int j = (int)(tile / tiles_x) * TH + (lane / TW);
+        if (i < R && j < R) sweep_column<VoxT, Fmt, DEPTH>(p, s_alpha, i, j);
+    }
+}
+
 template <typename VoxT, typename Fmt, bool DEPTH>
 cudaError_t launch_typed(const SweepParams& p, cudaStream_t s) {
-    dim3 block(kSweepBX * kSweepBY);
-    dim3 grid((p.lt.R + kSweepBX - 1) / kSweepBX, (p.lt.R + kSweepBY - 1) / kSweepBY);
-    size_t smem = (size_t)p.M * sizeof(float);
-    sweep_kernel<VoxT, Fmt, DEPTH><<<grid, block, smem, s>>>(p);
+    const size_t smem = (size_t)p.M * sizeof(float);
+    auto kern = sweep_kernel<VoxT, Fmt, DEPTH>;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSweepThreads, smem);
+    if (e != cudaSuccess) return e;
+    // Every SM filled once, never more warps than tiles.
+    constexpr int TW = sizeof(typename Fmt::T) == 2 ? 16 : 8;
+    const long long tiles = (long long)((p.lt.R + TW - 1) / TW) * ((p.lt.R + 32 / TW - 1) / (32 / TW));
+    long long blocks = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    const long long need = (tiles + kSweepThreads / 32 - 1) / (kSweepThreads / 32);
+    blocks = blocks < need ? blocks : need;
+    e = cudaMemsetAsync(p.tile_counter, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)blocks, kSweepThreads, smem, s>>>(p);
     return cudaGetLastError();
 }
 
