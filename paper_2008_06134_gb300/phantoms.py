@@ -121,6 +121,56 @@ def ct_phantom(n: int = 256, seed: int = 2, noise_sigma: float = 30.0,
     return out
 
 
+def ct_phantom_device(n: int = 1024, seed: int = 5, noise_sigma: float = 30.0,
+                      device: str = "cuda"):
+    """The CT ellipsoid phantom of ``ct_phantom`` for large n, built on a CUDA
+    device with torch (2 GiB at n = 1024 is minutes of numpy).
+
+    Geometry (rotation, soft-tissue mean, bones) is drawn exactly as in
+    ``ct_phantom``; the ellipsoid tests run in float32, and the noise of z-slab
+    s (64 slices) comes from a torch CUDA generator seeded with
+    1000 * seed + s.  Values are rounded and clamped to [0, 65535].  Returns an
+    int16 torch tensor on ``device`` holding the uint16 bits (the values
+    therefore differ from ``ct_phantom(n, seed)``; the distribution does not).
+    """
+    import torch
+    rng = _child(seed, 0)
+    rot = _quaternion_matrix(rng.normal(size=4))
+    soft = rng.uniform(950.0, 1050.0)
+    outer = np.array([0.45, 0.38, 0.30]) * n
+    bones = []
+    for _ in range(3):
+        off = rng.uniform(-0.4, 0.4, size=3) * outer
+        ax = outer * rng.uniform(0.15, 0.30, size=3)
+        bones.append((off, ax, rng.uniform(2900.0, 3100.0)))
+    out = torch.empty((n, n, n), dtype=torch.int16, device=device)
+    c = torch.arange(n, dtype=torch.float32, device=device) + (0.5 - 0.5 * n)
+    X = c.view(1, 1, n)
+    Y = c.view(1, n, 1)
+    R = [[float(rot[i, j]) for j in range(3)] for i in range(3)]
+    slab = 64
+    for s in range((n + slab - 1) // slab):
+        z0, z1 = s * slab, min(n, (s + 1) * slab)
+        Z = c[z0:z1].view(-1, 1, 1)
+        # Coordinates in the phantom's own frame: q = rot^T p.
+        qx = R[0][0] * X + R[1][0] * Y + R[2][0] * Z
+        qy = R[0][1] * X + R[1][1] * Y + R[2][1] * Z
+        qz = R[0][2] * X + R[1][2] * Y + R[2][2] * Z
+        val = torch.zeros_like(qx)
+        inside = (qx / outer[0]) ** 2 + (qy / outer[1]) ** 2 + (qz / outer[2]) ** 2 <= 1.0
+        val[inside] = soft
+        for off, ax, bone in bones:
+            m = (((qx - off[0]) / ax[0]) ** 2 + ((qy - off[1]) / ax[1]) ** 2
+                 + ((qz - off[2]) / ax[2]) ** 2) <= 1.0
+            val[m] = bone
+        gen = torch.Generator(device=device)
+        gen.manual_seed(1000 * seed + s)
+        val += noise_sigma * torch.randn(val.shape, generator=gen, device=device)
+        u = torch.clamp(torch.round(val), 0.0, 65535.0).to(torch.int32)
+        out[z0:z1] = (u - 65536 * (u >= 32768).to(torch.int32)).to(torch.int16)
+    return out
+
+
 def tf_random_pl(M: int = 256, seed: int = 1, npoints: int = 4,
                  alpha_max: float = 0.1) -> np.ndarray:
     """Random piecewise-linear RGBA transfer function with ``M`` entries.
@@ -267,6 +317,22 @@ def blob512_precision(seed: int = 3, n: int = 512, mode: int = MODE_CONE) -> Sce
     cam = orbit_camera(view, perspective=True, distance=2.6, fovy_deg=40.0)
     return Scene(f"blob{n}-u16 512x1024^2 1920x1080-persp", vol, tf, 0.0, 65535.0, light,
                  (1.0, 1.0, 1.0), 512, 1024, mode, cam, 1920, 1080, 0.5, 2.0)
+
+
+def ct1024_large(seed: int = 5, n: int = 1024) -> Scene:
+    """1024^3 uint16 CT ellipsoid phantom (2 GiB, built on the CUDA device),
+    the 4096-entry CT TF, 1024 light slices of 2048 x 2048 stored FP16 (8 GiB),
+    cone scattering (15 deg), 3840 x 2160 perspective (eye 2.6 from the centre,
+    fovy 40 deg), step 0.5 voxel, early ray termination at 0.99."""
+    vol = ct_phantom_device(n, seed).cpu().numpy().view(np.uint16)
+    tf = tf_ct(4096, seed)
+    drng = _child(seed, 2)
+    light = random_direction(drng)
+    view = random_direction(drng)
+    cam = orbit_camera(view, perspective=True, distance=2.6, fovy_deg=40.0)
+    return Scene(f"ct{n}-u16 cone15 1024x2048^2-f16 3840x2160-persp", vol, tf, 0.0, 4095.0,
+                 light, (1.0, 1.0, 1.0), 1024, 2048, MODE_CONE, cam, 3840, 2160, 0.5, 0.99,
+                 fmt=FMT_F16)
 
 
 def unit(v) -> np.ndarray:
