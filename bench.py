@@ -71,12 +71,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="ct256-cone",
-                    choices=["ct256-cone", "precision", "scalability", "serving", "variants"],
+                    choices=["ct256-cone", "precision", "scalability", "serving", "variants",
+                             "large"],
                     help="ct256-cone: the headline frame; precision: storage formats on the "
                          "512^3 blob scene vs the FP64 oracle; scalability: slice count x "
                          "slice resolution grid; serving: the render server on a stream of "
                          "mixed requests; variants: the method variants and the point light "
-                         "on the headline scene")
+                         "on the headline scene; large: 1024^3 volume, 1024 x 2048^2 FP16 "
+                         "stack, 3840x2160")
     ap.add_argument("--requests", type=int, default=512, help="serving: request count")
     ap.add_argument("--rate", default="300,800",
                     help="serving: Poisson arrival rates per second (comma-separated)")
@@ -645,6 +647,65 @@ def variants_workload(args):
     ctx.close()
 
 
+def large_workload(args):
+    """The large-volume workload: 1024^3 uint16 CT phantom (2 GiB, generated on
+    the device), 1024 slices of 2048^2 stored FP16 (8 GiB), cone, 3840 x 2160
+    perspective, step 0.5, ERT 0.99.  Frames/s, samples/s and the sweep's
+    achieved bandwidth over its algorithmic bytes (volume read once + stack
+    written once = 10.74 GB)."""
+    import torch
+
+    from paper_2008_06134_gb300 import build, phantoms as ph, vi
+    build.build()
+    t0 = time.perf_counter()
+    vol = ph.ct_phantom_device(1024, 5)
+    gen_s = time.perf_counter() - t0
+    drng = ph._child(5, 2)
+    light, view = ph.random_direction(drng), ph.random_direction(drng)
+    cam = ph.orbit_camera(view, perspective=True, distance=2.6, fovy_deg=40.0)
+    tf = ph.tf_ct(4096, 5)
+    n, R, W, H = 1024, 2048, 3840, 2160
+    ctx = vi.Context(0)
+    ctx.load_volume(vol, dtype=vi.U16)
+    ctx.set_transfer_function(tf, 0.0, 4095.0)
+    ctx.set_light(light)
+    out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def bld():
+        ctx.build_attenuation(n, R, vi.CONE, format=vi.F16)
+
+    def rnd(**kw):
+        ctx.render(cam, W, H, 0.5, out=out, ert=0.99, **kw)
+    counts = torch.zeros((H, W), dtype=torch.int32, device="cuda")
+    bld()
+    rnd(sample_counts=counts)
+    torch.cuda.synchronize()
+    samples = int(counts.sum().item())
+    del counts
+    for _ in range(args.warmup):
+        bld()
+        rnd()
+    sweep_ms, march_ms = timed_frames(ctx, bld, rnd, flush, args.steps)
+    sweep_bytes = vol.numel() * 2 + n * R * R * 2
+    peaks, _ = measured_peaks()
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    print(json.dumps({"workload": "large", "metric": "frames/s", "unit": "frames/s",
+                      "scene": "ct1024-u16 (device-generated, seed 5), 1024x2048^2 FP16, cone 15, "
+                               "3840x2160 perspective, step 0.5, ERT 0.99",
+                      "steps": args.steps, "warmup": args.warmup,
+                      "frames_per_s": round(1000.0 / (sweep_ms + march_ms), 2),
+                      "sweep_ms": round(sweep_ms, 4), "march_ms": round(march_ms, 4),
+                      "samples_per_frame": samples,
+                      "gsamples_per_s": round(samples / ((sweep_ms + march_ms) * 1e6), 2),
+                      "march_gsamples_per_s": round(samples / (march_ms * 1e6), 2),
+                      "sweep_algorithmic_bytes": sweep_bytes,
+                      "sweep_gbs": round(sweep_bytes / (sweep_ms * 1e6), 1),
+                      "sweep_frac_of_measured_hbm": round(sweep_bytes / (sweep_ms * 1e6) / hbm, 3),
+                      "volume_generation_s": round(gen_s, 2)}), flush=True)
+    ctx.close()
+
+
 def serving_workload(args):
     """The render server on the serving mix: 8 registered volumes ({128, 256,
     512}^3, uint8 blobs and uint16 CT ellipsoids) with at most 6 resident under
@@ -759,6 +820,8 @@ def main():
         serving_workload(args)
     elif args.workload == "variants":
         variants_workload(args)
+    elif args.workload == "large":
+        large_workload(args)
     else:
         gb300_arm(args)
 
