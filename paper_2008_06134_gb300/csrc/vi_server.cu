@@ -147,12 +147,10 @@ size_t slot_growth(const Slot* sl, const Request* r, const ServerVolume* v) {
 
 // Frees an idle volume's buffers, ordered on `stream`: no device-wide
 // synchronisation, and the pool hands the blocks to the next allocations.
-// Past the byte budget the pool returns its unused blocks to the device.
 void evict(vi_server* s, ServerVolume* v, cudaStream_t stream) {
     vi_detail::volume_release(&v->res, &v->used, stream);
     v->resident = false;
     ++s->stats.volume_evictions;
-    if (s->budget) cudaMemPoolTrimTo(s->pool, s->budget);
 }
 
 // Makes room for `extra` bytes: first frees the stacks of idle slots other
@@ -360,7 +358,7 @@ int vi_server_create(vi_server** out, int device, int slots, size_t memory_budge
     props.allocType = cudaMemAllocationTypePinned;
     props.location.type = cudaMemLocationTypeDevice;
     props.location.id = device;
-    uint64_t keep = UINT64_MAX;  // freed blocks stay in the pool (trimmed to the budget)
+    uint64_t keep = UINT64_MAX;  // freed blocks stay in the pool
     if (cudaMemPoolCreate(&s->pool, &props) != cudaSuccess ||
         cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
         cudaGetLastError();
@@ -386,6 +384,18 @@ int vi_server_create(vi_server** out, int device, int slots, size_t memory_budge
         }
         sl->ctx->pool = s->pool;
         s->slots.push_back(sl);
+    }
+    // With a budget, reserve it in the pool up front (allocated once, freed at
+    // once, kept by the pool): later allocations carve from memory the pool
+    // already holds instead of mapping more while requests are served.
+    if (s->budget) {
+        void* block = nullptr;
+        cudaStream_t st = s->slots[0]->stream;
+        if (cudaMallocFromPoolAsync(&block, s->budget, s->pool, st) == cudaSuccess) {
+            cudaFreeAsync(block, st);
+            cudaStreamSynchronize(st);
+        }
+        cudaGetLastError();  // a budget the device cannot hold is reserved on demand instead
     }
     s->worker = std::thread(worker_main, s);
     *out = s;

@@ -25,6 +25,11 @@ namespace {
 
 constexpr int kSweepThreads = 256;
 
+// 1: persistent warps take tiles from a counter; 0: one tile per warp.
+#ifndef VI_SWEEP_PERSISTENT
+#define VI_SWEEP_PERSISTENT 1
+#endif
+
 // Resident blocks per SM the register allocation is fitted to.  Two (up to
 // 128 registers a thread) measured fastest: 0.119 ms on the 256 x 512^2
 // config-2 sweep, against 0.143 / 0.169 ms for three / four blocks; eight- or
@@ -213,10 +218,15 @@ __global__ void __launch_bounds__(kSweepThreads, VI_SWEEP_MIN_BLOCKS)
     const int R = p.lt.R;
     const unsigned tiles_x = (unsigned)(R + TW - 1) / TW;
     const unsigned ntiles = tiles_x * ((unsigned)(R + TH - 1) / TH);
-    for (;;) {
+    for (int once = 0;; ++once) {
         unsigned tile = 0;
-        if (lane == 0) tile = atomicAdd(p.tile_counter, 1u);
-        tile = __shfl_sync(0xffffffffu, tile, 0);
+        if (VI_SWEEP_PERSISTENT) {
+            if (lane == 0) tile = atomicAdd(p.tile_counter, 1u);
+            tile = __shfl_sync(0xffffffffu, tile, 0);
+        } else {  // one tile per warp, in launch order
+            if (once) break;
+            tile = blockIdx.x * (kSweepThreads / 32) + (threadIdx.x >> 5);
+        }
         if (tile >= ntiles) break;
         const int i = (int)(tile % tiles_x) * TW + (lane % TW);
         const int j = (int)(tile / tiles_x) * TH + (lane / TW);
@@ -239,7 +249,7 @@ cudaError_t launch_typed(const SweepParams& p, cudaStream_t s) {
     const long long tiles = (long long)((p.lt.R + TW - 1) / TW) * ((p.lt.R + 32 / TW - 1) / (32 / TW));
     long long blocks = (long long)sms * (per_sm > 0 ? per_sm : 1);
     const long long need = (tiles + kSweepThreads / 32 - 1) / (kSweepThreads / 32);
-    blocks = blocks < need ? blocks : need;
+    blocks = (blocks < need && VI_SWEEP_PERSISTENT) ? blocks : need;
     e = cudaMemsetAsync(p.tile_counter, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)blocks, kSweepThreads, smem, s>>>(p);
