@@ -52,6 +52,32 @@ NCU_TRAFFIC = {
 }
 
 
+# Other counters of the same march capture, for its candidate bounds: warp-level
+# instructions executed and L2 sectors (32 B) per launch, with the capture's
+# L2 throughput as a fraction of peak.
+NCU_MARCH_COUNTERS = {"inst_executed": 725_232_800, "lts_sectors": 87_832_250,
+                      "lts_throughput_frac": 0.1187}
+
+
+def march_bounds(march_s: float, sms: int, clock_mhz: float, peaks: dict):
+    """The march's three candidate bounds (HBM, L2, instruction issue) with the
+    binding one named; counters from the capture, time from this run."""
+    if ncu_traffic("march_kernel") is None:
+        return None
+    traffic = ncu_traffic("march_kernel")
+    c = NCU_MARCH_COUNTERS
+    issue_slots = march_s * sms * 4 * clock_mhz * 1e6     # one warp instruction / cycle / SMSP
+    out = {"hbm": {"bytes": traffic, "gbs": round(traffic / march_s / 1e9, 1),
+                   "frac": round(traffic / march_s / 1e9 / peaks["hbm_gbs"], 4)},
+           "l2": {"bytes": c["lts_sectors"] * 32, "frac": c["lts_throughput_frac"]},
+           "issue": {"warp_instructions": c["inst_executed"],
+                     "frac": round(c["inst_executed"] / issue_slots, 4)},
+           "source": "counters from the ncu capture of this kernel (profiles/); time and "
+                     "clock from this run"}
+    out["binding"] = max(("hbm", "l2", "issue"), key=lambda k: out[k]["frac"])
+    return out
+
+
 def ncu_traffic(kernel: str):
     import hashlib
     files, digest, nbytes = NCU_TRAFFIC[kernel]
@@ -201,6 +227,26 @@ def oracle_setup(scene):
     return light, stack
 
 
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                low = line.lower()
+                if low.startswith("model name") or low.startswith("cpu part"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
 def cpu_baseline(scene):
     """The oracle, as it stands, on a bounded sample: 1/8 of the sweep's texel
     rows and 1/8 of the image rows (rows spread over the frame), scaled x8."""
@@ -210,7 +256,7 @@ def cpu_baseline(scene):
     secs = oracle_sample(scene, bands, 3, stack, light)
     fps = 1.0 / (secs * bands)
     return {"value": round(fps, 4), "unit": "frames/s", "cores": oracle.threads(),
-            "kind": "oracle",
+            "cpu": cpu_model(), "kind": "oracle",
             "sample": f"texel rows {3 * scene.slice_res // bands}-"
                       f"{4 * scene.slice_res // bands} of every slice + image rows "
                       f"{3 * scene.height // bands}-{4 * scene.height // bands}, FP64, "
@@ -432,6 +478,7 @@ def gb300_arm(args):
                                  f"{FP32_LANES_PER_SM} lanes x 2 x {peaks['sm_max_mhz']} MHz "
                                  f"({peak_kind} max clock)"}
     dominant, other = (march_roof, sweep_roof) if march_s >= sweep_s else (sweep_roof, march_roof)
+    clock_mhz = clock.get("sm_mhz") or peaks["sm_max_mhz"]
     frames = world * K
     line = {
         "metric": "frames/s", "value": round(job_throughput(K, world, max_total_ms / 1e3), 3),
@@ -446,6 +493,8 @@ def gb300_arm(args):
         "march_gsamples_per_s": round(samples / march_s / 1e9, 3),
         "samples_per_frame": samples, "lit_samples_per_frame": lit_samples,
         "sweep_ms": round(sweep_s * 1e3, 4), "march_ms": round(march_s * 1e3, 4),
+        "warm_frames_per_s": round(1.0 / march_s, 2),      # march only, stack cached
+        "march_bounds": march_bounds(march_s, props.multi_processor_count, clock_mhz, peaks),
         "wall_s": round(wall, 3),
         "roofline": dominant, "roofline_other": other,
         "gpu_launches": int(launches),
