@@ -744,6 +744,7 @@ int vi_build_attenuation(vi_ctx* c, int n, int R, int mode, const vi_build_opts*
     rc = ensure(c, reinterpret_cast<void**>(&c->counter), &c->counter_cap, 256);
     if (rc) return rc;
     p.tile_counter = c->counter;
+    p.lockstep = (double)n * (double)R * (double)R >= (double)VI_SWEEP_LOCKSTEP_MIN ? 1 : 0;
     cudaError_t e = vi::launch_sweep(p, c->vr->vtype, o.format, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e);
     ++c->launches;

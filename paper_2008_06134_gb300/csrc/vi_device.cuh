@@ -126,6 +126,33 @@ __device__ __forceinline__ VoxelCoord voxel_coord(const VolumeView& v, float P0,
     return c;
 }
 
+// voxel_coord for a point known to lie in [0,1]^3 (the sweep's exact inside
+// test): x = P N - 1/2 lies in [-1/2, N - 1/2], so floor(x) is already in
+// [-1, N - 1] and each corner needs one bound of its clamp.  Same cells and
+// weights as voxel_coord for such points.  Points outside give indices out of
+// range: the caller must not load through them.
+__device__ __forceinline__ VoxelCoord voxel_coord_inside(const VolumeView& v, float P0, float P1,
+                                                         float P2) {
+    VoxelCoord c;
+    float x = __fmaf_rn(P0, v.fnx, -0.5f);
+    float y = __fmaf_rn(P1, v.fny, -0.5f);
+    float z = __fmaf_rn(P2, v.fnz, -0.5f);
+    float flx = floorf(x), fly = floorf(y), flz = floorf(z);
+    c.cx = (int)flx;
+    c.cy = (int)fly;
+    c.cz = (int)flz;
+    c.wx = x - flx;
+    c.wy = y - fly;
+    c.wz = z - flz;
+    c.x0 = max(c.cx, 0);
+    c.x1 = min(c.cx + 1, v.nx - 1);
+    c.y0 = max(c.cy, 0);
+    c.y1 = min(c.cy + 1, v.ny - 1);
+    c.z0 = max(c.cz, 0);
+    c.z1 = min(c.cz + 1, v.nz - 1);
+    return c;
+}
+
 // Brick coordinates of the footprint's lower corner.  Each is monotone in the
 // position along a ray or a light column, so two samples in one brick have
 // every sample between them in that brick too.

@@ -89,7 +89,16 @@ struct SweepParams {
     float comp_n;             // darkening compensation exponent, 0 = off
     int depth;                // 1: store optical depth (Eq. 5-6), else transmittance
     unsigned* tile_counter;   // work counter of the persistent sweep (zeroed per launch)
+    int lockstep;             // 1: a warp's lanes step through the slices together
 };
+
+// Stacks of at least this many texel-slices are swept in lockstep: each
+// slice's stores of a warp are then coalesced, which pays once the stores
+// dominate (1024 x 2048^2: 5.3 vs 7.1 ms), while smaller stacks sweep faster
+// with each lane walking its own column (256 x 512^2: 0.119 vs 0.123 ms).
+#ifndef VI_SWEEP_LOCKSTEP_MIN
+#define VI_SWEEP_LOCKSTEP_MIN (1ull << 30)
+#endif
 
 // Cap of a stored optical depth (exp(-64) < 2e-28) and the most shells.
 constexpr float kDepthMax = 64.0f;

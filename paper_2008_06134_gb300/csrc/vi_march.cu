@@ -183,10 +183,6 @@ __device__ __forceinline__ int last_transparent(const MarchParams& p, const Ray&
     return s;
 }
 
-// One sample i of a ray.  Returns kEnded if t_i is past the exit (nothing
-// done), kStopped if early ray termination fired, kEmpty if the sample lies in
-// a brick that cannot yield alpha > 0 (counted, nothing composited), else
-// kContinue.
 // Light-space coordinates of a world point under a point light: with
 // e = X - P and depth d = e.L, lambda = (d - min) kappa, tu = (e.U / d) sigma +
 // rho0, tv likewise (a depth below 1e-6 counts as 1e-6).
@@ -212,8 +208,11 @@ __device__ __forceinline__ float point_light_factor(const MarchParams& p, float 
     return light_factor<Fmt>(p, p.lt.n, p.lt.R, q0, q1, q2, rec);
 }
 
-// EXT enables the variant options (optical-depth stack, linear slice
-// filtering, several shells); the default kernels compile without them.
+// One sample i of a ray.  Returns kEnded if t_i is past the exit (nothing
+// done), kStopped if early ray termination fired, kEmpty if the sample lies in
+// a brick that cannot yield alpha > 0 (counted, nothing composited), else
+// kContinue.  EXT enables the variant options (optical-depth stack, linear
+// slice filtering, several shells); the default kernels compile without them.
 // POINT: a point light (coordinates per sample, scattering points built in
 // world space); it always takes the EXT lookups.
 template <typename VoxT, typename Fmt, int MODE, bool TRACE, bool EXT, bool POINT>

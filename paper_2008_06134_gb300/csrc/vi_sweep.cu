@@ -58,11 +58,97 @@ __device__ __forceinline__ bool texel_inside(const LightFrame& lt, int k, const 
     return P0 >= 0.0f && P0 <= 1.0f && P1 >= 0.0f && P1 <= 1.0f && P2 >= 0.0f && P2 <= 1.0f;
 }
 
-// One texel column (i, j): every slice's value, nearest the light first.
+// The slices of a warp's 32 columns, in lockstep: every lane stores slice k at
+// the same step, so each slice's stores of the warp are coalesced.  A lane
+// applies alpha only inside its own interval [kin, kout]; elsewhere it stores
+// its current value, which is the full light before the interval and the light
+// that left the cube after it.  Loads of four slices are issued together.
 template <typename VoxT, typename Fmt, bool DEPTH>
-__device__ __forceinline__ void sweep_column(const SweepParams& p, const float* s_alpha, int i,
-                                             int j) {
+__device__ __forceinline__ void sweep_lockstep(const SweepParams& p, const float* s_alpha,
+                                               const float o[3], const float w[3], float spacing,
+                                               int kin, int kout, bool valid,
+                                               typename Fmt::T* out, size_t slice, size_t dup) {
     const LightFrame& lt = p.lt;
+    const bool has = kin <= kout;
+    const int klo = __reduce_min_sync(0xffffffffu, has ? kin : lt.n);
+    const int khi = __reduce_max_sync(0xffffffffu, has ? kout : -1);
+    float T = DEPTH ? 0.0f : 1.0f;  // transmittance, or optical depth
+    const typename Fmt::T one = Fmt::pack(T);
+    int k = 0;
+    for (; k < klo; ++k) {
+        if (valid) {
+            out[(size_t)k * slice] = one;
+            if (dup) out[(size_t)k * slice + dup] = one;
+        }
+    }
+    for (; k <= khi; k += kBatch) {
+        OctetRef ref[kBatch];
+        bool lit[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            lit[u] = false;
+            if (k + u >= kin && k + u <= kout) {
+                const float sk = __fsub_rn(__fmaf_rn((float)(k + u), lt.dL, lt.min), lt.Lc);
+                const VoxelCoord vc = voxel_coord_inside(p.vol, __fmaf_rn(sk, w[0], o[0]),
+                                                         __fmaf_rn(sk, w[1], o[1]),
+                                                         __fmaf_rn(sk, w[2], o[2]));
+                ref[u] = octet_ref(p.vol, vc);
+                lit[u] = brick_may_be_lit(p.grid, vc);
+            }
+        }
+        typename Octet<VoxT>::V oct[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u)
+            if (lit[u]) oct[u] = octet_load<VoxT>(p.vol, ref[u].idx);
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            if (k + u > khi) break;
+            float alpha = 0.0f;
+            if (lit[u]) {
+                int e;
+                float f;
+                tf_coord(trilinear_octet<VoxT>(oct[u], ref[u]), p.tf_vmin, p.tf_scale, p.M, &e,
+                         &f);
+                const float a0 = s_alpha[e];
+                alpha = fmaf(f, s_alpha[e + 1] - a0, a0);
+                if (p.opacity_correction)
+                    alpha = 1.0f - exp2f(spacing * log2f(fmaxf(1.0f - alpha, 0.0f)));
+            }
+            float stored = T;
+            if (p.comp_n != 0.0f)
+                stored = DEPTH ? fmaxf(0.0f, T - p.comp_n * log1pf(alpha))
+                               : fminf(1.0f, T * powf(1.0f + alpha, p.comp_n));
+            if (valid) {
+                const typename Fmt::T q = Fmt::pack(stored);
+                out[(size_t)(k + u) * slice] = q;
+                if (dup) out[(size_t)(k + u) * slice + dup] = q;
+            }
+            if (DEPTH)
+                T = fminf(T - log1pf(-alpha), kDepthMax);  // alpha = 1: tau = inf, capped
+            else
+                T *= (1.0f - alpha);
+        }
+    }
+    if (klo <= khi) k = khi + 1;  // the last batch may have run past khi
+    const typename Fmt::T last = Fmt::pack(T);
+    for (; k < lt.n; ++k) {
+        if (valid) {
+            out[(size_t)k * slice] = last;
+            if (dup) out[(size_t)k * slice + dup] = last;
+        }
+    }
+}
+
+// One texel column (i, j): every slice's value, nearest the light first.
+template <typename VoxT, typename Fmt, bool DEPTH, bool LOCKSTEP>
+__device__ __forceinline__ void sweep_column(const SweepParams& p, const float* s_alpha, int i,
+                                             int j, bool valid) {
+    const LightFrame& lt = p.lt;
+    if (!LOCKSTEP && !valid) return;
+    if (!valid) {  // a lane past the stack's edge: it joins the warp's steps, stores nothing
+        i = min(i, lt.R - 1);
+        j = min(j, lt.R - 1);
+    }
 
     // World position of texel (i, j) on the plane through the centre.
     float qi = __fdiv_rn((float)(2 * i + 1), (float)lt.R);
@@ -135,6 +221,15 @@ __device__ __forceinline__ void sweep_column(const SweepParams& p, const float* 
         }
     }
 
+    if (LOCKSTEP) {
+        if (!valid) {
+            kin = lt.n;
+            kout = -1;
+        }
+        sweep_lockstep<VoxT, Fmt, DEPTH>(p, s_alpha, o, w, spacing, kin, kout, valid, out, slice,
+                                         dup);
+        return;
+    }
     // Before the cube: full light (transmittance 1, optical depth 0).
     const typename Fmt::T one = Fmt::pack(DEPTH ? 0.0f : 1.0f);
     int k = 0;
@@ -152,9 +247,10 @@ __device__ __forceinline__ void sweep_column(const SweepParams& p, const float* 
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
             const float sk = __fsub_rn(__fmaf_rn((float)(k + u), lt.dL, lt.min), lt.Lc);
-            const VoxelCoord vc = voxel_coord(p.vol, __fmaf_rn(sk, w[0], o[0]),
-                                              __fmaf_rn(sk, w[1], o[1]),
-                                              __fmaf_rn(sk, w[2], o[2]));
+            // Slices past kout (the batch's tail) compute an address but never load.
+            const VoxelCoord vc = voxel_coord_inside(p.vol, __fmaf_rn(sk, w[0], o[0]),
+                                                     __fmaf_rn(sk, w[1], o[1]),
+                                                     __fmaf_rn(sk, w[2], o[2]));
             ref[u] = octet_ref(p.vol, vc);
             lit[u] = k + u <= kout && brick_may_be_lit(p.grid, vc);
         }
@@ -206,7 +302,7 @@ __device__ __forceinline__ void sweep_column(const SweepParams& p, const float* 
 // blocks of a fixed grid.  A warp covers TW x TH texels, TW chosen so one row
 // of its store is a whole 32-byte sector: 8 x 4 for FP32, 16 x 2 for the
 // 16-bit formats.
-template <typename VoxT, typename Fmt, bool DEPTH>
+template <typename VoxT, typename Fmt, bool DEPTH, bool LOCKSTEP>
 __global__ void __launch_bounds__(kSweepThreads, VI_SWEEP_MIN_BLOCKS)
     sweep_kernel(const SweepParams p) {
     extern __shared__ float s_alpha[];
@@ -230,14 +326,15 @@ __global__ void __launch_bounds__(kSweepThreads, VI_SWEEP_MIN_BLOCKS)
         if (tile >= ntiles) break;
         const int i = (int)(tile % tiles_x) * TW + (lane % TW);
         const int j = (int)(tile / tiles_x) * TH + (lane / TW);
-        if (i < R && j < R) sweep_column<VoxT, Fmt, DEPTH>(p, s_alpha, i, j);
+        sweep_column<VoxT, Fmt, DEPTH, LOCKSTEP>(p, s_alpha, i, j, i < R && j < R);
     }
 }
 
 template <typename VoxT, typename Fmt, bool DEPTH>
 cudaError_t launch_typed(const SweepParams& p, cudaStream_t s) {
     const size_t smem = (size_t)p.M * sizeof(float);
-    auto kern = sweep_kernel<VoxT, Fmt, DEPTH>;
+    auto kern = p.lockstep ? sweep_kernel<VoxT, Fmt, DEPTH, true>
+                           : sweep_kernel<VoxT, Fmt, DEPTH, false>;
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
