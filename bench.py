@@ -45,18 +45,18 @@ FLOPS_LIT = {0: 0, 1: 6 + 2 + 12, 2: 6 + 2 + 6 * 12 + 7, 3: 6 + 2 + 8 * 12 + 9}
 # entry holds for the kernel sources it was taken from (hash of the files that
 # define the kernel); once they change the figure is stale and reported as null.
 NCU_TRAFFIC = {
-    "march_kernel": (("vi_march.cu", "vi_device.cuh", "vi_internal.h"), "44fcef73734a385e",
-                     83_479_552),
-    "sweep_kernel": (("vi_sweep.cu", "vi_device.cuh", "vi_internal.h"), "bed0b2c5d6cb3c2b",
-                     295_036_416),
+    "march_kernel": (("vi_march.cu", "vi_device.cuh", "vi_internal.h"), "59e68b3f354818eb",
+                     83_385_344),
+    "sweep_kernel": (("vi_sweep.cu", "vi_device.cuh", "vi_internal.h"), "89c85d375e53dc39",
+                     296_356_864),
 }
 
 
 # Other counters of the same march capture, for its candidate bounds: warp-level
 # instructions executed and L2 sectors (32 B) per launch, with the capture's
 # L2 throughput as a fraction of peak.
-NCU_MARCH_COUNTERS = {"inst_executed": 725_232_800, "lts_sectors": 87_832_250,
-                      "lts_throughput_frac": 0.1187}
+NCU_MARCH_COUNTERS = {"inst_executed": 725_232_800, "lts_sectors": 88_108_800,
+                      "lts_throughput_frac": 0.1189}
 
 
 def march_bounds(march_s: float, sms: int, clock_mhz: float, peaks: dict):
@@ -110,6 +110,10 @@ def parse():
                     help="serving: Poisson arrival rates per second (comma-separated)")
     ap.add_argument("--slots", type=int, default=8, help="serving: concurrent render slots")
     ap.add_argument("--budget-gib", type=float, default=8.0, help="serving: HBM budget")
+    ap.add_argument("--large-n", type=int, default=1024, help="large: volume edge")
+    ap.add_argument("--large-slices", type=int, default=1024, help="large: slice count")
+    ap.add_argument("--large-res", type=int, default=2048, help="large: slice resolution")
+    ap.add_argument("--large-image", default="3840x2160", help="large: image W x H")
     return ap.parse_args()
 
 
@@ -707,13 +711,14 @@ def large_workload(args):
     from paper_2008_06134_gb300 import build, phantoms as ph, vi
     build.build()
     t0 = time.perf_counter()
-    vol = ph.ct_phantom_device(1024, 5)
+    vol = ph.ct_phantom_device(args.large_n, 5)
     gen_s = time.perf_counter() - t0
     drng = ph._child(5, 2)
     light, view = ph.random_direction(drng), ph.random_direction(drng)
     cam = ph.orbit_camera(view, perspective=True, distance=2.6, fovy_deg=40.0)
     tf = ph.tf_ct(4096, 5)
-    n, R, W, H = 1024, 2048, 3840, 2160
+    n, R = args.large_slices, args.large_res
+    W, H = (int(x) for x in args.large_image.split("x"))
     ctx = vi.Context(0)
     ctx.load_volume(vol, dtype=vi.U16)
     ctx.set_transfer_function(tf, 0.0, 4095.0)
@@ -740,8 +745,8 @@ def large_workload(args):
     peaks, _ = measured_peaks()
     hbm = peaks.get("hbm_gbs") or 6800.0
     print(json.dumps({"workload": "large", "metric": "frames/s", "unit": "frames/s",
-                      "scene": "ct1024-u16 (device-generated, seed 5), 1024x2048^2 FP16, cone 15, "
-                               "3840x2160 perspective, step 0.5, ERT 0.99",
+                      "scene": f"ct{args.large_n}-u16 (device-generated, seed 5), {n}x{R}^2 FP16, "
+                               f"cone 15, {W}x{H} perspective, step 0.5, ERT 0.99",
                       "steps": args.steps, "warmup": args.warmup,
                       "frames_per_s": round(1000.0 / (sweep_ms + march_ms), 2),
                       "sweep_ms": round(sweep_ms, 4), "march_ms": round(march_ms, 4),
