@@ -20,9 +20,26 @@
 
 #include "vi_device.cuh"
 
+// Unrolling of the default kernels' lookup loops: the cone's two rings and the
+// shell's six points.  Fully unrolled, every gather of a sample is in flight at
+// once, which costs registers the 64-register budget does not have: the cone
+// kernel spilled 112 bytes a thread and reloaded them every sample (31 M local
+// loads per 1024^2 frame).  Ring by ring it spills 8 bytes and the config-2
+// march drops from 1.148 to 1.042 ms; the shell, three points at a time, from
+// 0.974 to 0.947 ms.
+#ifndef VI_CONE_RING_UNROLL
+#define VI_CONE_RING_UNROLL 1
+#endif
+#ifndef VI_SHELL_UNROLL
+#define VI_SHELL_UNROLL 3
+#endif
+
 namespace vi {
 
 namespace {
+
+constexpr int kConeRingUnroll = VI_CONE_RING_UNROLL;
+constexpr int kShellUnroll = VI_SHELL_UNROLL;
 
 constexpr int kMarchThreads = 256;  // 8 warps per block
 
@@ -301,7 +318,7 @@ __device__ __forceinline__ int march_sample(const MarchParams& p, const float* s
                     sum += light_factor<Fmt>(p, n, R, q0, q1, q2, rr);
                 }
             } else {
-#pragma unroll
+#pragma unroll kShellUnroll
                 for (int q = 0; q < 6; ++q) {
                     float q0 = __fadd_rn(l0, p.shell_off[0][q][0]);
                     float q1 = __fadd_rn(l1, p.shell_off[0][q][1]);
@@ -373,11 +390,11 @@ __device__ __forceinline__ int march_sample(const MarchParams& p, const float* s
                     sum += light_factor<Fmt>(p, n, R, lr, __fadd_rn(l1, cu), __fadd_rn(l2, cv), rr);
                 }
             } else {
-#pragma unroll
+#pragma unroll kConeRingUnroll
                 for (int ring = 0; ring < 2; ++ring) {
                     // The ring's four points share lambda + offset, hence one slice.
                     const int k = slice_index(__fadd_rn(l0, -(float)(ring + 1)), n);
-                    const float bu = r.nbu[ring], bv = r.nbv[ring];
+                    const float bu = ring ? r.nbu[1] : r.nbu[0], bv = ring ? r.nbv[1] : r.nbv[0];
                     // B_proj turned by m pi/2 about L: (bu, bv), (-bv, bu), (-bu, -bv), (bv, -bu).
                     const float du[4] = {bu, -bv, -bu, bv};
                     const float dv[4] = {bv, bu, -bv, -bu};
