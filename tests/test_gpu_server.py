@@ -189,3 +189,54 @@ def test_kept_stack_serves_a_new_view_of_the_same_scene(env):
             c.build_attenuation(24, 40, vi.CONE, format=vi.F16)
             ref = c.render(cam, 48, 40, 0.5, ert=0.95).cpu().numpy()
             assert np.array_equal(got, ref)
+
+
+def test_threads_submitting_waiting_and_cancelling_concurrently(env):
+    """Four host threads submit, wait and sometimes cancel at once: every
+    request ends (done or cancelled), no call deadlocks, and every finished
+    frame equals the one-at-a-time frame."""
+    import threading
+    torch, ph, vi, vols, tfs = env
+    reqs = make_requests(ph, vi, 24, seed=11)
+    alone, _ = run(env, reqs, slots=1, together=False)
+    outs = [None] * len(reqs)
+    status = [None] * len(reqs)
+    errors = []
+    with vi.Server(0, slots=3, memory_budget=1 << 30, max_resident_volumes=2) as s:
+        vids = [s.add_volume(v) for v in vols]
+
+        def worker(w):
+            try:
+                rng = np.random.default_rng(100 + w)
+                for q_i in range(w, len(reqs), 4):
+                    q = reqs[q_i]
+                    out = torch.full((q["H"], q["W"], 4), float("nan"), device="cuda")
+                    tf, vmin, vmax = tfs[q["vol"]]
+                    t = s.submit(vids[q["vol"]], tf, vmin, vmax, q["light"], q["n"], q["R"],
+                                 q["mode"], q["cam"], q["W"], q["H"], 0.5, out, format=q["fmt"],
+                                 ert=q["ert"])
+                    if rng.random() < 0.25:
+                        s.cancel(t)           # may already be running: then it completes
+                    status[q_i] = s.wait(t, timeout_ms=120000.0)
+                    outs[q_i] = out
+            except Exception as e:            # surfaced below
+                errors.append(repr(e))
+
+        threads = [threading.Thread(target=worker, args=(w,)) for w in range(4)]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join(timeout=300)
+        assert not any(th.is_alive() for th in threads)
+        st = s.stats()
+    assert not errors, errors
+    torch.cuda.synchronize()
+    done = 0
+    for q_i, (stt, res) in enumerate(status):
+        assert (stt, res) in ((vi.REQ_DONE, vi.OK), (vi.REQ_CANCELLED, vi.OK))
+        if stt == vi.REQ_DONE:
+            assert np.array_equal(outs[q_i].cpu().numpy(), alone[q_i])
+            done += 1
+    assert done >= 12
+    assert st["completed"] == done and st["cancelled"] == len(reqs) - done
+    assert st["peak_bytes"] <= 1 << 30
