@@ -171,7 +171,8 @@ __device__ __forceinline__ float brick_exit(const VolumeView& v, const VoxelCoor
     float s_exit = 3.0e38f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        // Cells [8 b, 8 b + 7] <=> P in [(8 b + 0.5) / N, (8 b + 8.5) / N).
+        // Cells [B b, B b + B - 1] <=> P in [(B b + 0.5) / N, (B b + B + 0.5) / N),
+        // B = 2^kBrickShift.
         const float lo_p = __fdividef((float)(lo[a] << kBrickShift) + 0.5f, N[a]);
         const float hi_p = __fdividef((float)((lo[a] + 1) << kBrickShift) + 0.5f, N[a]);
         if (dir[a] > 0.0f) s_exit = fminf(s_exit, __fdividef(hi_p - base[a], dir[a]));

@@ -1,6 +1,6 @@
 // vi_grid.cu -- brick occupancy for exact empty-space skipping.
 //
-// The volume is cut into bricks of 8^3 voxels.  For each brick the value range
+// The volume is cut into bricks of 2^kBrickShift voxels per axis (16^3).  For each brick the value range
 // over its voxels plus a one-voxel apron on the high side (the voxels a
 // trilinear footprint whose lower corner lies in the brick can touch) is kept;
 // it changes only with the volume.  From it and the transfer function, a flag
