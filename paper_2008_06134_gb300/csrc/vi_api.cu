@@ -383,6 +383,7 @@ int fill_march_params(vi_ctx* c, const vi_camera* cam, int W, int H, float step_
     p->step_vox = step_vox;
     p->counts = ro->sample_counts;
     p->lit = ro->lit_counts;
+    p->block_threads = c->march_block;
     return VI_OK;
 }
 

@@ -75,6 +75,7 @@ struct vi_ctx {
     size_t trace_cap = 0;
     unsigned* counter = nullptr;  // tile counter of the persistent march kernel
     size_t counter_cap = 0;
+    int march_block = 0;          // march block size cap (0: one 1024-thread block per SM)
 };
 
 namespace vi_detail {

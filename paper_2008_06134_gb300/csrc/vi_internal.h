@@ -144,6 +144,7 @@ struct MarchParams {
     int32_t* counts;        // optional [H][W]: samples composited
     int32_t* lit;           // optional [H][W]: samples with alpha > 0
     unsigned* tile_counter; // work counter of the persistent march (zeroed per launch)
+    int block_threads;      // threads per block at most (0: the kernel's maximum)
 };
 
 enum { kTraceWords = 40, kTraceNone = 0x7fffffff };

@@ -50,7 +50,15 @@ constexpr int kTileW = VI_MARCH_TILE_W;
 constexpr int kTileH = 32 / kTileW;
 constexpr int kShellUnroll = VI_SHELL_UNROLL;
 
-constexpr int kMarchThreads = 256;  // 8 warps per block
+// One block of 1024 threads per SM (32 warps, 64 registers each): the same
+// occupancy as four blocks of 256, but one shared copy of the TF's alpha
+// column per SM instead of four, which leaves more of the unified L1 / shared
+// storage to L1 (config-2 march 0.870 ms, against 0.885 / 0.899 / 0.918 ms
+// for blocks of 512 / 256 / 128).
+#ifndef VI_MARCH_THREADS
+#define VI_MARCH_THREADS 1024
+#endif
+constexpr int kMarchThreads = VI_MARCH_THREADS;  // threads per block
 
 struct Ray {
     float o[3], d[3];
@@ -448,10 +456,10 @@ __device__ __forceinline__ void load_alpha(const MarchParams& p, float* s_alpha)
 // Persistent warps: each warp takes 4 x 8 pixel tiles, in raster order, from a
 // global counter until none are left, so warps whose rays end early pick up
 // more work instead of idling while others march through dense regions.
-// Resident blocks per SM the register allocation is fitted to (4 x 256
-// threads = 32 warps by default).
+// Resident blocks per SM the register allocation is fitted to (1 x 1024
+// threads = 32 warps, 64 registers a thread).
 #ifndef VI_MARCH_MIN_BLOCKS
-#define VI_MARCH_MIN_BLOCKS 4
+#define VI_MARCH_MIN_BLOCKS 1
 #endif
 
 template <typename VoxT, typename Fmt, int MODE, bool EXT, bool POINT>
@@ -546,17 +554,26 @@ cudaError_t launch_march_typed(const MarchParams& p, cudaStream_t s) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // Blocks of at most `cap` threads: kMarchThreads, or fewer where kernels of
+    // several streams share the GPU (smaller blocks let them share SMs).
+    const int cap = p.block_threads > 0 && p.block_threads < kMarchThreads ? p.block_threads
+                                                                              : kMarchThreads;
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kMarchThreads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, cap, smem);
     if (e != cudaSuccess) return e;
-    // Enough warps to fill every SM once, never more than there are tiles.
+    // Enough warps for the frame's tiles spread over every SM (a small frame
+    // takes smaller blocks on all SMs rather than full blocks on a few), at
+    // most `cap` threads a block, never more warps than tiles.
     const long long tiles =
         (long long)((p.cam.W + kTileW - 1) / kTileW) * ((p.cam.H + kTileH - 1) / kTileH);
-    long long blocks = (long long)sms * (per_sm > 0 ? per_sm : 1);
-    blocks = blocks < (tiles + 7) / 8 ? blocks : (tiles + 7) / 8;
+    const long long slots = (long long)sms * (per_sm > 0 ? per_sm : 1);
+    long long warps = (tiles + slots - 1) / (slots > 0 ? slots : 1);
+    warps = warps < 1 ? 1 : (warps > cap / 32 ? cap / 32 : warps);
+    const int threads = (int)warps * 32;
+    long long blocks = slots < (tiles + warps - 1) / warps ? slots : (tiles + warps - 1) / warps;
     e = cudaMemsetAsync(p.tile_counter, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)blocks, kMarchThreads, smem, s>>>(p);
+    kern<<<(unsigned)blocks, threads, smem, s>>>(p);
     return cudaGetLastError();
 }
 

@@ -383,6 +383,10 @@ int vi_server_create(vi_server** out, int device, int slots, size_t memory_budge
             return VI_ECUDA;
         }
         sl->ctx->pool = s->pool;
+        // Slots render concurrently: blocks of 256 threads let the marches of
+        // several slots share SMs (one 1024-thread block needs a whole SM's
+        // registers; with them the 8-slot capacity fell by about 15 %).
+        sl->ctx->march_block = 256;
         s->slots.push_back(sl);
     }
     // With a budget, reserve it in the pool up front (allocated once, freed at
