@@ -21,24 +21,27 @@ namespace {
 template <typename VoxT>
 __global__ void brick_range_kernel(const VoxT* __restrict__ vol, int nx, int ny, int nz, int nbx,
                                    int nby, int nbz, uint32_t* __restrict__ range) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nbx * nby * nbz) return;
+    // One warp per brick: the lanes stride over the brick's voxels (x fastest,
+    // so a row's loads are coalesced) and combine their extremes at the end.
+    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= nbx * nby * nbz) return;  // the whole warp leaves together
     const int bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
     const int x0 = bx << kBrickShift, y0 = by << kBrickShift, z0 = bz << kBrickShift;
-    const int x1 = min(x0 + (1 << kBrickShift), nx - 1);
-    const int y1 = min(y0 + (1 << kBrickShift), ny - 1);
-    const int z1 = min(z0 + (1 << kBrickShift), nz - 1);
+    // The brick plus a one-voxel apron on the high side, clamped to the volume.
+    const int wx = min(x0 + (1 << kBrickShift), nx - 1) - x0 + 1;
+    const int wy = min(y0 + (1 << kBrickShift), ny - 1) - y0 + 1;
+    const int wz = min(z0 + (1 << kBrickShift), nz - 1) - z0 + 1;
     uint32_t lo = 0xffffu, hi = 0u;
-    for (int z = z0; z <= z1; ++z)
-        for (int y = y0; y <= y1; ++y) {
-            const VoxT* row = vol + ((size_t)z * ny + y) * nx;
-            for (int x = x0; x <= x1; ++x) {
-                uint32_t v = row[x];
-                lo = min(lo, v);
-                hi = max(hi, v);
-            }
-        }
-    range[b] = (lo << 16) | hi;
+    for (int t = lane; t < wx * wy * wz; t += 32) {
+        const int x = t % wx, yz = t / wx, y = yz % wy, z = yz / wy;
+        const uint32_t v = vol[((size_t)(z0 + z) * ny + (y0 + y)) * nx + (x0 + x)];
+        lo = min(lo, v);
+        hi = max(hi, v);
+    }
+    lo = __reduce_min_sync(0xffffffffu, lo);
+    hi = __reduce_max_sync(0xffffffffu, hi);
+    if (lane == 0) range[b] = (lo << 16) | hi;
 }
 
 __global__ void brick_flag_kernel(const uint32_t* __restrict__ range, int nbricks,
@@ -64,7 +67,7 @@ cudaError_t launch_brick_range(const void* raw, int nx, int ny, int nz, int voxe
     const int nby = (ny + (1 << kBrickShift) - 1) >> kBrickShift;
     const int nbz = (nz + (1 << kBrickShift) - 1) >> kBrickShift;
     const int n = nbx * nby * nbz;
-    const int threads = 128, blocks = (n + threads - 1) / threads;
+    const int threads = 256, blocks = (n + threads / 32 - 1) / (threads / 32);  // a warp per brick
     if (voxel_type == 0)
         brick_range_kernel<uint8_t><<<blocks, threads, 0, s>>>(
             static_cast<const uint8_t*>(raw), nx, ny, nz, nbx, nby, nbz, range);
