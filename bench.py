@@ -767,7 +767,9 @@ def serving_workload(args):
     64-512 slices of 256^2 or 512^2, shadow / shell / cone, light and view
     uniform on the sphere).  Runs: one slot with FP32 stacks (one frame at a
     time: the plain path), and `--slots` concurrent slots with FP32 and with
-    FP16 stacks, each under Poisson arrivals at `--rate` and as one burst.
+    FP16 stacks, each under Poisson arrivals at `--rate` and as one burst, and
+    the FP32 served runs again with each request's device work launched as one
+    CUDA graph.
     Reports per run frames/s and request latency (submission to completion)
     percentiles; the FP32 served frames are compared with the plain ones."""
     import numpy as np
@@ -794,9 +796,10 @@ def serving_workload(args):
                         q["slice_res"], q["mode"], q["camera"], q["width"], q["height"],
                         q["step_vox"], out, format=fmt, ert=q["ert"])
 
-    def run(slots, fmt, burst, reqs):
+    def run(slots, fmt, burst, reqs, graphs=False):
         outs = [torch.empty((q["height"], q["width"], 4), device="cuda") for q in reqs]
-        with vi.Server(0, slots=slots, memory_budget=budget, max_resident_volumes=6) as s:
+        with vi.Server(0, slots=slots, memory_budget=budget, max_resident_volumes=6,
+                       graphs=graphs) as s:
             vids = [s.add_volume(h, c) for h, c in zip(host, codes)]
             warm = torch.empty((64, 64, 4), device="cuda")
             for i in range(len(specs)):           # untimed: load every volume once
@@ -831,6 +834,9 @@ def serving_workload(args):
                "volume_evictions": st["volume_evictions"] - base["volume_evictions"],
                "stack_reuses": st["stack_reuses"] - base["stack_reuses"],
                "peak_bytes": st["peak_bytes"]}
+        if graphs:
+            row["graph_launches"] = st["graph_launches"] - base["graph_launches"]
+            row["graph_instantiations"] = st["graph_instantiations"]
         return row, outs
 
     runs = {}
@@ -848,11 +854,18 @@ def serving_workload(args):
                 row["max_abs_err_vs_plain_f32"] = float(f"{err:.3g}")
             runs[f"served-{fname}-{args.slots}slots-poisson{rate:g}"] = row
             del outs
+        # The same FP32 runs with each request's device work as one CUDA graph.
+        row, outs = run(args.slots, vi.F32, False, reqs, graphs=True)
+        row["frames_identical_to_plain"] = sum(bool(torch.equal(a, b))
+                                               for a, b in zip(outs, plain_outs))
+        runs[f"served-f32-graphs-{args.slots}slots-poisson{rate:g}"] = row
+        del outs
         del plain_outs
     # Capacity: every request of the first mix submitted at once.
-    for slots, name in ((1, "plain-f32-1slot-burst"),
-                        (args.slots, f"served-f32-{args.slots}slots-burst")):
-        runs[name] = run(slots, vi.F32, True, mixes[rates[0]])[0]
+    for slots, name, graphs in ((1, "plain-f32-1slot-burst", False),
+                                (args.slots, f"served-f32-{args.slots}slots-burst", False),
+                                (args.slots, f"served-f32-graphs-{args.slots}slots-burst", True)):
+        runs[name] = run(slots, vi.F32, True, mixes[rates[0]], graphs=graphs)[0]
     print(json.dumps({"workload": "serving", "metric": "frames/s", "unit": "frames/s",
                       "requests": args.requests, "rates_per_s": rates, "slots": args.slots,
                       "budget_bytes": budget, "max_resident_volumes": 6,

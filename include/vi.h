@@ -252,7 +252,9 @@ int vi_render_host_noalloc(vi_ctx* ctx, const vi_camera* camera, int W, int H, f
    Each slot keeps the attenuation stack of its last request.  A request with
    the same volume, TF (entries and range), light, stack shape, mode and build
    options as a free slot's last one is placed on that slot and renders from
-   its stack without a new sweep (a new view of an unchanged scene). */
+   its stack without a new sweep (a new view of an unchanged scene); other
+   requests go to a free slot without a stack, else to the free slot whose
+   stack was used longest ago. */
 typedef struct vi_server vi_server;
 
 enum { VI_REQ_QUEUED = 0, VI_REQ_RUNNING = 1, VI_REQ_DONE = 2, VI_REQ_FAILED = 3,
@@ -285,6 +287,8 @@ typedef struct {
     int queued, running, resident_volumes;
     size_t bytes_in_use, peak_bytes;
     uint64_t stack_reuses;  /* requests that rendered from a slot's kept stack */
+    uint64_t graph_launches;        /* requests whose device work ran as one CUDA graph */
+    uint64_t graph_instantiations;  /* executable graphs created (the rest were updated) */
 } vi_server_stats;
 
 /* Create / destroy a server (destroy cancels queued requests, lets running
@@ -321,6 +325,21 @@ int vi_server_timing(vi_server* server, uint64_t ticket, double* submit_ms, doub
 int vi_server_release(vi_server* server, uint64_t ticket);
 
 int vi_server_get_stats(vi_server* server, vi_server_stats* stats);
+
+/* Launch each request's device work as one CUDA graph (enabled != 0) or as
+   separate launches (0, the default); applies to requests started after the
+   call.  With graphs, the work a request queues after its uploads (the TF
+   copy and the brick flags stay ordinary stream operations) -- the sweep,
+   the march, the copy of a host output and the completion callback -- is
+   captured from the slot's stream and launched as one graph.  Each slot
+   keeps one executable graph per shape of that work (with or without a
+   sweep, device or host output) and updates its parameters in place for the
+   next request of the same shape, so a graph is instantiated only the first
+   time a shape appears on a slot.  The frames are bit-identical to those of
+   separate launches (the same kernels with the same parameters).  A request
+   whose host output is pageable memory (not capturable) runs with separate
+   launches.  Returns VI_EINVAL for a null server. */
+int vi_server_set_graphs(vi_server* server, int enabled);
 
 #ifdef __cplusplus
 }

@@ -202,6 +202,7 @@ int cuda_fail(vi_ctx* c, cudaError_t e) {
 
 // Grow a device buffer to `bytes` under the context's budget.
 int ensure(vi_ctx* c, void** p, size_t* cap, size_t bytes) {
+    if (c->capturing && !(bytes <= *cap && *p)) return VI_ESTATE;  // see ctx_reserve
     return vi_detail::ensure_mem(&c->used, c->budget, p, cap, bytes, c->stream, c->pool);
 }
 
@@ -253,8 +254,9 @@ int setup_stack(vi_ctx* c, int n, int R, int fmt) {
     void* base = reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(c->stack_mem) + 511) &
                                          ~(uintptr_t)511);
     const bool same = before == c->stack_mem && c->stack == base && c->row_pitch == pitch &&
-                      c->ntex == ntex && c->sview.spt_log2 == spt_log2 && c->lt.R == R &&
-                      c->bopts.format == fmt && c->stack_valid_shape_n == n;
+                      c->ntex == ntex && c->sview.spt_log2 == spt_log2 &&
+                      c->stack_valid_shape_n == n && c->stack_valid_shape_R == R &&
+                      c->stack_valid_shape_fmt == fmt;
     c->stack = base;
     c->row_pitch = pitch;
     if (same) return VI_OK;
@@ -289,6 +291,8 @@ int setup_stack(vi_ctx* c, int n, int R, int fmt) {
     }
     c->sview.spt_log2 = spt_log2;
     c->stack_valid_shape_n = n;
+    c->stack_valid_shape_R = R;
+    c->stack_valid_shape_fmt = fmt;
     return VI_OK;
 }
 
@@ -544,6 +548,21 @@ int ctx_render_async(vi_ctx* c, const vi_camera* cam, int W, int H, float step_v
         if (e != cudaSuccess) return cuda_fail(c, e);
     }
     return VI_OK;
+}
+
+int ctx_reserve(vi_ctx* c, int build_stack, int n, int R, int fmt, int W, int H,
+                int out_on_device) {
+    int rc = enter(c);
+    if (rc) return rc;
+    if (build_stack) {
+        if (n < 1 || R < 1 || fmt < VI_F32 || fmt > VI_UNORM16) return VI_EINVAL;
+        rc = setup_stack(c, n, R, fmt);
+        if (rc) return rc;
+    }
+    rc = ensure(c, reinterpret_cast<void**>(&c->counter), &c->counter_cap, 256);
+    if (rc || out_on_device || W <= 0 || H <= 0) return rc;
+    return ensure(c, reinterpret_cast<void**>(&c->out), &c->out_cap,
+                  (size_t)W * (size_t)H * sizeof(float4));
 }
 
 }  // namespace vi_detail

@@ -62,7 +62,9 @@ struct vi_ctx {
     size_t row_pitch = 0;        // bytes per stack row (pitched layout, R + 1 rows per slice)
     vi::StackView sview{};       // texture views of the stack
     int ntex = 0;
-    int stack_valid_shape_n = 0; // slice count the texture views were made for
+    int stack_valid_shape_n = 0; // slice count, resolution and format the texture views
+    int stack_valid_shape_R = 0; // were made for
+    int stack_valid_shape_fmt = -1;
     int mode = -1;          // mode of the last build; -1 = none yet
     bool stack_valid = false;
     vi_build_opts bopts{};
@@ -76,6 +78,10 @@ struct vi_ctx {
     unsigned* counter = nullptr;  // tile counter of the persistent march kernel
     size_t counter_cap = 0;
     int march_block = 0;          // march block size cap (0: one 1024-thread block per SM)
+    // Set while the context's stream is being captured into a graph: no buffer
+    // may grow then (an allocation would become part of the graph), so a call
+    // that needs more memory fails instead (ctx_reserve sizes them first).
+    bool capturing = false;
 };
 
 namespace vi_detail {
@@ -109,5 +115,11 @@ void ctx_trim(vi_ctx* c);
 // buffer overlaps; a pageable one makes the copy synchronous).
 int ctx_render_async(vi_ctx* c, const vi_camera* cam, int W, int H, float step_vox, float* out,
                      int out_on_device, const vi_render_opts* opts);
+// Grows, ahead of a capture, every buffer a build of an n x R x R stack of
+// format fmt (build_stack != 0) and a W x H render (host output staging when
+// out_on_device is 0) will use, so that the calls inside the capture allocate
+// nothing.  Also makes the stack's texture views.
+int ctx_reserve(vi_ctx* c, int build_stack, int n, int R, int fmt, int W, int H,
+                int out_on_device);
 
 }  // namespace vi_detail

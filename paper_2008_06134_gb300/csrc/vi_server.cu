@@ -8,8 +8,10 @@
 // Volumes are registered once and kept resident (octets and brick ranges) up
 // to a count and a byte budget; the least recently used idle volume is
 // evicted when room is needed and reloaded from the caller's host copy on its
-// next request.  Completion is signalled by a stream host callback; every wait
-// on the host side is bounded (VI_ETIMEOUT).
+// next request.  Each slot keeps its last attenuation stack for a later view of
+// the same scene.  Optionally a request's device work after its uploads is
+// captured and launched as one CUDA graph.  Completion is signalled by a stream
+// host callback; every wait on the host side is bounded (VI_ETIMEOUT).
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -56,8 +58,12 @@ struct Slot {
     // The request whose attenuation stack the context holds (its build
     // succeeded and nothing has freed it since); null if none.
     bool has_stack = false;
+    uint64_t stack_use = 0;  // admission counter when the kept stack last served a request
     vi_request stack_req{};
     std::vector<float> stack_tf;
+    // Executable graphs of a request's device work, one per shape of it:
+    // index 1 with a sweep, + 2 with a copy to host output.
+    cudaGraphExec_t exec[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 bool same_bits(float a, float b) { return std::memcmp(&a, &b, sizeof(float)) == 0; }
@@ -102,6 +108,7 @@ struct vi_server {
     // Stream-ordered pool for every device buffer of the server (volumes and
     // slots): evictions and reloads reuse blocks without cudaMalloc / cudaFree.
     cudaMemPool_t pool = nullptr;
+    bool graphs = false;  // launch each request's device work as one CUDA graph
 };
 
 namespace {
@@ -188,8 +195,55 @@ void finish(vi_server* s, Request* r, int status, int result) {
     s->done.notify_all();
 }
 
+// True if the request's output can be the target of a captured copy: device
+// memory, or page-locked host memory (a copy to pageable memory is not).
+bool output_capturable(const vi_request& q) {
+    if (q.out_on_device) return true;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, q.out_rgba) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+// Ends the capture begun on the slot's stream and, if the captured calls
+// succeeded (rc), launches the graph: through the slot's executable graph
+// for this shape of work, updated in place, or a new one when there is none
+// or the update is refused.  Returns a vi_status.
+int launch_captured(vi_server* s, Slot* sl, int rc, int shape) {
+    sl->ctx->capturing = false;
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(sl->stream, &g);
+    if (!rc && (e != cudaSuccess || !g)) rc = VI_ECUDA;
+    cudaGraphExec_t& x = sl->exec[shape];
+    if (!rc && x) {
+        cudaGraphExecUpdateResultInfo info;
+        if (cudaGraphExecUpdate(x, g, &info) != cudaSuccess) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(x);
+            x = nullptr;
+        }
+    }
+    if (!rc && !x) {
+        if (cudaGraphInstantiate(&x, g, 0) == cudaSuccess) {
+            ++s->stats.graph_instantiations;
+        } else {
+            x = nullptr;
+            rc = VI_ECUDA;
+        }
+    }
+    if (!rc) rc = cudaGraphLaunch(x, sl->stream) == cudaSuccess ? VI_OK : VI_ECUDA;
+    if (!rc) ++s->stats.graph_launches;
+    if (g) cudaGraphDestroy(g);
+    if (rc) cudaGetLastError();
+    return rc;
+}
+
 // Enqueues a request's work on a slot; returns a vi_status.  With `reuse` the
 // slot's kept stack (and TF and light) serve the request and no sweep runs.
+// With graphs on, the sweep, the march, the output copy and the completion
+// callback are captured and launched as one graph after the uploads.
 int start(vi_server* s, Slot* sl, Request* r, bool reuse) {
     const vi_request& q = r->req;
     ServerVolume* v = s->vols[q.volume_id];
@@ -201,7 +255,21 @@ int start(vi_server* s, Slot* sl, Request* r, bool reuse) {
         if (!rc)
             rc = vi_set_transfer_function(c, r->tf.data(), q.tf_entries, q.tf_vmin, q.tf_vmax);
         if (!rc) rc = vi_set_light(c, q.light_dir, q.light_color);
-        if (!rc) rc = vi_build_attenuation(c, q.n_slices, q.slice_res, q.mode, &q.build);
+    }
+    const bool sweep = !reuse && q.mode != VI_NONE;
+    const bool graph = !rc && s->graphs && output_capturable(q);
+    if (graph) {
+        rc = vi_detail::ctx_reserve(c, sweep, q.n_slices, q.slice_res, q.build.format, q.width,
+                                    q.height, q.out_on_device);
+        if (rc) return rc;
+        if (cudaStreamBeginCapture(sl->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            return VI_ECUDA;
+        }
+        c->capturing = true;
+    }
+    if (!rc && !reuse) {
+        rc = vi_build_attenuation(c, q.n_slices, q.slice_res, q.mode, &q.build);
         if (!rc) {
             sl->has_stack = true;
             sl->stack_req = q;
@@ -212,6 +280,7 @@ int start(vi_server* s, Slot* sl, Request* r, bool reuse) {
         rc = vi_detail::ctx_render_async(c, &q.camera, q.width, q.height, q.step_vox, q.out_rgba,
                                          q.out_on_device, &q.render);
     if (!rc && cudaLaunchHostFunc(sl->stream, on_slot_done, sl) != cudaSuccess) rc = VI_ECUDA;
+    if (graph) rc = launch_captured(s, sl, rc, (sweep ? 1 : 0) + (q.out_on_device ? 0 : 2));
     return rc;
 }
 
@@ -230,7 +299,8 @@ void schedule(vi_server* s) {
     while (!s->queue.empty()) {
         Request* r = s->queue.front();
         // A free slot that holds the stack this request needs; else a free one
-        // that holds no stack; else the first free one.
+        // that holds no stack; else the free one whose stack was used longest
+        // ago (the kept stacks are a least-recently-used cache).
         Slot* sl = nullptr;
         bool reuse = false;
         for (Slot* cand : s->slots) {
@@ -240,7 +310,9 @@ void schedule(vi_server* s) {
                 reuse = true;
                 break;
             }
-            if (!sl || (sl->has_stack && !cand->has_stack)) sl = cand;
+            if (!sl || (sl->has_stack && !cand->has_stack) ||
+                (sl->has_stack == cand->has_stack && cand->stack_use < sl->stack_use))
+                sl = cand;
         }
         if (!sl) return;
         const int vid = r->req.volume_id;
@@ -293,6 +365,7 @@ void schedule(vi_server* s) {
             ++s->stats.volume_loads;
         }
         v->last_use = ++s->admissions;
+        sl->stack_use = s->admissions;
         ++v->pins;
         sl->req = r;
         sl->vol = vid;
@@ -420,6 +493,8 @@ int vi_server_destroy(vi_server* s) {
     // The completion callbacks touch the server: let every one of them return.
     for (Slot* sl : s->slots) cudaStreamSynchronize(sl->stream);
     for (Slot* sl : s->slots) {
+        for (cudaGraphExec_t x : sl->exec)
+            if (x) cudaGraphExecDestroy(x);
         vi_destroy(sl->ctx);
         cudaStreamDestroy(sl->stream);
         delete sl;
@@ -556,6 +631,13 @@ int vi_server_release(vi_server* s, uint64_t ticket) {
     if (it->second->status < VI_REQ_DONE) return VI_ESTATE;
     delete it->second;
     s->reqs.erase(it);
+    return VI_OK;
+}
+
+int vi_server_set_graphs(vi_server* s, int enabled) {
+    if (!s) return VI_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->graphs = enabled != 0;
     return VI_OK;
 }
 

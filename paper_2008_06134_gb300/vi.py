@@ -36,7 +36,8 @@ EXPORTS = ("vi_create", "vi_destroy", "vi_set_memory_budget", "vi_load_volume",
            "vi_attenuation_info", "vi_get_attenuation", "vi_trace_pixel", "vi_launch_count",
            "vi_render_host_noalloc", "vi_server_create", "vi_server_destroy",
            "vi_server_add_volume", "vi_server_submit", "vi_server_wait", "vi_server_cancel",
-           "vi_server_timing", "vi_server_release", "vi_server_get_stats")
+           "vi_server_timing", "vi_server_release", "vi_server_get_stats",
+           "vi_server_set_graphs")
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = 0, 1, 2, 3, 4
 
 
@@ -77,7 +78,8 @@ class ServerStats(C.Structure):
                 ("cancelled", C.c_uint64), ("volume_loads", C.c_uint64),
                 ("volume_evictions", C.c_uint64), ("queued", C.c_int), ("running", C.c_int),
                 ("resident_volumes", C.c_int), ("bytes_in_use", C.c_size_t),
-                ("peak_bytes", C.c_size_t), ("stack_reuses", C.c_uint64)]
+                ("peak_bytes", C.c_size_t), ("stack_reuses", C.c_uint64),
+                ("graph_launches", C.c_uint64), ("graph_instantiations", C.c_uint64)]
 
 
 _lib = None
@@ -121,6 +123,7 @@ def library() -> C.CDLL:
     L.vi_server_timing.argtypes = [vp, u64, P(d), P(d), P(d)]
     L.vi_server_release.argtypes = [vp, u64]
     L.vi_server_get_stats.argtypes = [vp, P(ServerStats)]
+    L.vi_server_set_graphs.argtypes = [vp, i]
     _lib = L
     return L
 
@@ -332,13 +335,20 @@ class Server:
     """A vi_server: continuous batching of render requests over resident volumes."""
 
     def __init__(self, device: int = 0, slots: int = 4, memory_budget: int = 0,
-                 max_resident_volumes: int = 0):
+                 max_resident_volumes: int = 0, graphs: bool = False):
         L = library()
         h = C.c_void_p()
         _check(L.vi_server_create(C.byref(h), int(device), int(slots), int(memory_budget),
                                   int(max_resident_volumes)), "vi_server_create")
         self.h, self.L = h, L
         self._keep = {}   # host volumes and outputs the server reads or writes later
+        if graphs:
+            self.set_graphs(True)
+
+    def set_graphs(self, enabled: bool) -> None:
+        """Launch each later request's sweep, march and output copy as one
+        CUDA graph (vi_server_set_graphs)."""
+        _check(self.L.vi_server_set_graphs(self.h, int(bool(enabled))), "vi_server_set_graphs")
 
     def close(self) -> None:
         if getattr(self, "h", None):

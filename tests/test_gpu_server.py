@@ -240,3 +240,90 @@ def test_threads_submitting_waiting_and_cancelling_concurrently(env):
     assert done >= 12
     assert st["completed"] == done and st["cancelled"] == len(reqs) - done
     assert st["peak_bytes"] <= 1 << 30
+
+
+def test_graph_launches_give_the_same_frames(env):
+    """With graphs on, each request's sweep, march and output copy run as one
+    captured CUDA graph, updated in place for the next request of the same
+    shape of work: every frame equals the frame separate launches give, for
+    device, page-locked host and pageable host outputs (the last not
+    captured), new scenes, a kept-stack view and an unlit frame; one at a
+    time and all at once; and a graph is instantiated only when a shape of
+    work first appears on a slot."""
+    torch, ph, vi, vols, tfs = env
+    reqs = make_requests(ph, vi, 20, seed=7)
+    again = dict(reqs[3], cam=ph.orbit_camera(np.array((0.2, -0.7, 0.4)), True, 2.4))
+    unlit = dict(reqs[5], mode=vi.NONE)
+    reqs = reqs[:4] + [again] + reqs[4:] + [unlit]
+    kinds = ("device", "pinned", "pageable")
+    slots = 3
+
+    def serve(graphs, together):
+        with vi.Server(0, slots=slots, graphs=graphs) as s:
+            vids = [s.add_volume(v) for v in vols]
+            outs, tickets = [], []
+            for k, q in enumerate(reqs):
+                shape = (q["H"], q["W"], 4)
+                kind = kinds[k % 3]
+                if kind == "device":
+                    out = torch.full(shape, float("nan"), device="cuda")
+                elif kind == "pinned":
+                    out = torch.full(shape, float("nan")).pin_memory()
+                else:
+                    out = np.full(shape, np.nan, dtype=np.float32)
+                tf, vmin, vmax = tfs[q["vol"]]
+                t = s.submit(vids[q["vol"]], tf, vmin, vmax, q["light"], q["n"], q["R"],
+                             q["mode"], q["cam"], q["W"], q["H"], 0.5, out, format=q["fmt"],
+                             ert=q["ert"])
+                outs.append(out)
+                tickets.append(t)
+                if not together:
+                    assert s.wait(t) == (vi.REQ_DONE, vi.OK)
+            for t in tickets:
+                assert s.wait(t) == (vi.REQ_DONE, vi.OK)
+            stats = s.stats()
+        torch.cuda.synchronize()
+        return [o.cpu().numpy() if hasattr(o, "cpu") else o for o in outs], stats
+
+    captured = sum(kinds[k % 3] != "pageable" for k in range(len(reqs)))
+    for together in (False, True):
+        ref, st0 = serve(False, together)
+        got, st1 = serve(True, together)
+        for a, b in zip(ref, got):
+            assert np.isfinite(a).all()
+            assert np.array_equal(a, b)
+        assert st0["graph_launches"] == 0 and st0["graph_instantiations"] == 0
+        assert st1["graph_launches"] == captured
+        assert 1 <= st1["graph_instantiations"] <= 4 * slots
+        if not together:
+            assert st0["stack_reuses"] >= 1 and st1["stack_reuses"] == st0["stack_reuses"]
+
+
+def test_kept_stacks_are_evicted_least_recently_used(env):
+    """Two slots, one request at a time: scenes A, B, A (new view), C, A (new
+    view).  C replaces the stack used longest ago (B's), so the last view of A
+    still renders from A's kept stack: two reuses, and every frame equals the
+    frame of a fresh context."""
+    torch, ph, vi, vols, tfs = env
+    tf, vmin, vmax = tfs[1]
+    views = [ph.orbit_camera(np.array(d), True, 2.4)
+             for d in ((0.3, 0.4, -0.8), (-0.6, 0.1, 0.5), (0.1, -0.9, 0.2))]
+    lights = {"A": (0.3, -0.2, 0.9), "B": (-0.5, 0.4, 0.3), "C": (0.2, 0.8, -0.4)}
+    seq = [("A", views[0]), ("B", views[0]), ("A", views[1]), ("C", views[0]), ("A", views[2])]
+    got = []
+    with vi.Server(0, slots=2) as s:
+        vid = s.add_volume(vols[1])
+        for scene, cam in seq:
+            out = torch.empty((40, 48, 4), device="cuda")
+            t = s.submit(vid, tf, vmin, vmax, lights[scene], 24, 40, vi.SHELL, cam, 48, 40,
+                         0.5, out)
+            assert s.wait(t) == (vi.REQ_DONE, vi.OK)
+            got.append(out.cpu().numpy())
+        assert s.stats()["stack_reuses"] == 2
+    with vi.Context(0) as c:
+        c.load_volume(vols[1])
+        c.set_transfer_function(tf, vmin, vmax)
+        for (scene, cam), frame in zip(seq, got):
+            c.set_light(lights[scene])
+            c.build_attenuation(24, 40, vi.SHELL)
+            assert np.array_equal(frame, c.render(cam, 48, 40, 0.5).cpu().numpy())
