@@ -251,20 +251,23 @@ def cpu_model() -> str:
     return platform.machine()
 
 
-def cpu_baseline(scene):
-    """The oracle, as it stands, on a bounded sample: 1/8 of the sweep's texel
-    rows and 1/8 of the image rows (rows spread over the frame), scaled x8."""
+def cpu_baseline(scene, min_seconds: float = 10.0, max_frames: int = 4):
+    """The oracle, as it stands, on a bounded sample: bands of 1/8 of the
+    sweep's texel rows and 1/8 of the image rows, taken in turn over the frame
+    until at least `min_seconds` have been timed (at most `max_frames` whole
+    frames); frames/s = bands / 8 / seconds."""
     import oracle
     light, stack = oracle_setup(scene)
-    bands = 8
-    secs = oracle_sample(scene, bands, 3, stack, light)
-    fps = 1.0 / (secs * bands)
+    bands, done, secs = 8, 0, 0.0
+    while secs < min_seconds and done < max_frames * bands:
+        secs += oracle_sample(scene, bands, done % bands, stack, light)
+        done += 1
+    fps = done / bands / secs
     return {"value": round(fps, 4), "unit": "frames/s", "cores": oracle.threads(),
             "cpu": cpu_model(), "kind": "oracle",
-            "sample": f"texel rows {3 * scene.slice_res // bands}-"
-                      f"{4 * scene.slice_res // bands} of every slice + image rows "
-                      f"{3 * scene.height // bands}-{4 * scene.height // bands}, FP64, "
-                      f"{secs:.2f} s, scaled x{bands} to one frame"}
+            "sample": f"{done} bands of 1/{bands} frame (1/{bands} of the sweep's texel rows "
+                      f"+ 1/{bands} of the image rows, in turn over the frame) = "
+                      f"{done / bands:.3g} frames, FP64, {secs:.1f} s"}
 
 
 def reference_arm(args):
