@@ -236,6 +236,20 @@ int vi_launch_count(vi_ctx* ctx, uint64_t* count);
 int vi_render_host_noalloc(vi_ctx* ctx, const vi_camera* camera, int W, int H, float step_vox,
                            float* out_rgba, const vi_render_opts* opts);
 
+/* Bounds-check record of a checked build of this library (libvi_checked.so,
+   compiled with VI_DEBUG_BOUNDS=1).  In that build every kernel tests each
+   voxel, brick, TF, stack, output and grid index before the access; a bad
+   index is counted and the access skipped, so a kernel neither traps nor
+   faults.  The call waits for the device, stores the number of violations
+   since the last call for that device, the site of a first one (1 volume
+   octet, 2 brick flag, 3 TF alpha, 4 TF colour, 5 stack slice or row of a
+   lookup, 6 stack store, 7 output pixel, 8 raw voxel, 9 grid build; 0 if
+   none) and its index, and clears the record.  The record covers every
+   context of the process on the device.  VI_ESTATE from a library built
+   without the checks (the outputs are set to 0); VI_EINVAL for a bad device
+   or a null pointer. */
+int vi_debug_bounds(int device, uint64_t* violations, int* first_site, int64_t* first_index);
+
 /* ---- Serving: continuous batching of render requests ---------------------- */
 
 /* A render server on one device.  It is not in the paper (which renders one

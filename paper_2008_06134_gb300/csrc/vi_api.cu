@@ -316,6 +316,9 @@ vi::GridView grid_view(const vi_ctx* c) {
     g.flags = c->bflags;
     g.nbx = c->vr->nbx;
     g.nby = c->vr->nby;
+#if VI_DEBUG_BOUNDS
+    g.nbz = c->vr->nbz;
+#endif
     return g;
 }
 
@@ -629,6 +632,7 @@ int vi_set_memory_budget(vi_ctx* c, size_t bytes) {
 
 int vi_load_volume(vi_ctx* c, const void* data, int dtype, int nx, int ny, int nz,
                    int data_on_device) {
+    vi_detail::NvtxRange nvtx_range("vi_load_volume");
     int rc = enter(c);
     if (rc) return rc;
     if (!data || (dtype != VI_U8 && dtype != VI_U16)) return VI_EINVAL;
@@ -644,6 +648,7 @@ int vi_load_volume(vi_ctx* c, const void* data, int dtype, int nx, int ny, int n
 }
 
 int vi_set_transfer_function(vi_ctx* c, const float* rgba, int M, float vmin, float vmax) {
+    vi_detail::NvtxRange nvtx_range("vi_set_transfer_function");
     int rc = enter(c);
     if (rc) return rc;
     if (!rgba || M < 2 || M > 8192) return VI_EINVAL;
@@ -677,6 +682,7 @@ int vi_set_transfer_function(vi_ctx* c, const float* rgba, int M, float vmin, fl
 }
 
 int vi_set_light(vi_ctx* c, const float dir[3], const float color[3]) {
+    vi_detail::NvtxRange nvtx_range("vi_set_light");
     int rc = enter(c);
     if (rc) return rc;
     if (!dir || !finite3(dir)) return VI_EINVAL;
@@ -694,6 +700,7 @@ int vi_set_light(vi_ctx* c, const float dir[3], const float color[3]) {
 }
 
 int vi_set_point_light(vi_ctx* c, const float position[3], const float color[3]) {
+    vi_detail::NvtxRange nvtx_range("vi_set_point_light");
     int rc = enter(c);
     if (rc) return rc;
     if (!position || !finite3(position)) return VI_EINVAL;
@@ -711,6 +718,7 @@ int vi_set_point_light(vi_ctx* c, const float position[3], const float color[3])
 }
 
 int vi_build_attenuation(vi_ctx* c, int n, int R, int mode, const vi_build_opts* opts) {
+    vi_detail::NvtxRange nvtx_range("vi_build_attenuation");
     int rc = enter(c);
     if (rc) return rc;
     vi_build_opts o = opts ? *opts : default_build_opts();
@@ -779,12 +787,14 @@ int vi_build_attenuation(vi_ctx* c, int n, int R, int mode, const vi_build_opts*
 
 int vi_render(vi_ctx* c, const vi_camera* cam, int W, int H, float step_vox, float* out,
               int out_on_device, const vi_render_opts* opts) {
+    vi_detail::NvtxRange nvtx_range("vi_render");
     int rc = vi_detail::ctx_render_async(c, cam, W, H, step_vox, out, out_on_device, opts);
     if (rc || out_on_device || W == 0 || H == 0) return rc;
     return cuda_fail(c, cudaStreamSynchronize(c->stream));
 }
 
 int vi_sync(vi_ctx* c) {
+    vi_detail::NvtxRange nvtx_range("vi_sync");
     if (!c) return VI_EINVAL;
     if (cudaSetDevice(c->device) != cudaSuccess) {
         cudaGetLastError();
@@ -811,6 +821,7 @@ int vi_attenuation_info(vi_ctx* c, int* n, int* R, int* format, size_t* bytes) {
 }
 
 int vi_get_attenuation(vi_ctx* c, void* out, size_t out_bytes, int out_on_device) {
+    vi_detail::NvtxRange nvtx_range("vi_get_attenuation");
     int rc = enter(c);
     if (rc) return rc;
     if (!c->stack_valid) return VI_ESTATE;
@@ -832,6 +843,7 @@ int vi_get_attenuation(vi_ctx* c, void* out, size_t out_bytes, int out_on_device
 int vi_trace_pixel(vi_ctx* c, const vi_camera* cam, int W, int H, float step_vox,
                    const vi_render_opts* opts, int x, int y, int32_t* rec, int max_rec,
                    int* n_rec) {
+    vi_detail::NvtxRange nvtx_range("vi_trace_pixel");
     int rc = enter(c);
     if (rc) return rc;
     vi_render_opts ro = opts ? *opts : default_render_opts();
@@ -869,6 +881,7 @@ int vi_trace_pixel(vi_ctx* c, const vi_camera* cam, int W, int H, float step_vox
 
 int vi_render_host_noalloc(vi_ctx* c, const vi_camera* cam, int W, int H, float step_vox,
                            float* out, const vi_render_opts* opts) {
+    vi_detail::NvtxRange nvtx_range("vi_render_host_noalloc");
     int rc = enter(c);
     if (rc) return rc;
     vi_render_opts ro = opts ? *opts : default_render_opts();
@@ -894,6 +907,40 @@ int vi_render_host_noalloc(vi_ctx* c, const vi_camera* cam, int W, int H, float 
     if (e != cudaSuccess) return cuda_fail(c, e);
     e = cudaStreamSynchronize(c->stream);
     return cuda_fail(c, e);
+}
+
+int vi_debug_bounds(int device, uint64_t* violations, int* first_site, int64_t* first_index) {
+    if (!violations || !first_site || !first_index) return VI_EINVAL;
+    *violations = 0;
+    *first_site = 0;
+    *first_index = 0;
+#if VI_DEBUG_BOUNDS
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess) {
+        cudaGetLastError();
+        return VI_ECUDA;
+    }
+    if (device < 0 || device >= count) return VI_EINVAL;
+    if (cudaSetDevice(device) != cudaSuccess) return VI_ECUDA;
+    cudaError_t (*const records[3])(unsigned*) = {vi::debug_record_sweep, vi::debug_record_march,
+                                                  vi::debug_record_grid};
+    for (auto read : records) {
+        unsigned r[4] = {0u, 0u, 0u, 0u};
+        if (read(r) != cudaSuccess) {
+            cudaGetLastError();
+            return VI_ECUDA;
+        }
+        if (r[0] && !*violations) {
+            *first_site = (int)r[1];
+            *first_index = (int64_t)(((uint64_t)r[3] << 32) | r[2]);
+        }
+        *violations += r[0];
+    }
+    return VI_OK;
+#else
+    (void)device;
+    return VI_ESTATE;
+#endif
 }
 
 int vi_launch_count(vi_ctx* c, uint64_t* count) {

@@ -5,6 +5,8 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/vi.h"
 #include "vi_internal.h"
 
@@ -85,6 +87,14 @@ struct vi_ctx {
 };
 
 namespace vi_detail {
+// An NVTX range over one API call (header-only NVTX: without a profiler
+// attached, a push or pop is a check of a function pointer).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Device allocation under a byte budget (0 = none) with a usage counter; keeps
 // the old buffer on failure.  Without a pool: cudaMalloc, and the old buffer is

@@ -9,6 +9,38 @@
 namespace vi {
 
 // ---------------------------------------------------------------------------
+// Bounds checks of checked builds (VI_DEBUG_BOUNDS, see vi_internal.h).
+// VI_BOUNDS_OK(site, i, n) is true when 0 <= i < n; otherwise it counts the
+// violation in this translation unit's record (the first one's site and index
+// kept) and is false, and the caller skips the access.  In release builds it
+// is the constant true and its arguments are not evaluated.
+#if VI_DEBUG_BOUNDS
+static __device__ unsigned g_debug_record[4];  // count, first site, first index (low, high)
+
+__device__ __forceinline__ bool bounds_ok(int site, long long i, long long n) {
+    if (i >= 0 && i < n) return true;
+    if (atomicAdd(&g_debug_record[0], 1u) == 0u) {
+        g_debug_record[1] = (unsigned)site;
+        g_debug_record[2] = (unsigned)((unsigned long long)i & 0xffffffffull);
+        g_debug_record[3] = (unsigned)((unsigned long long)i >> 32);
+    }
+    return false;
+}
+#define VI_BOUNDS_OK(site, i, n) ::vi::bounds_ok((site), (long long)(i), (long long)(n))
+// Defines the host accessor of this translation unit's record.
+#define VI_DEBUG_RECORD_ACCESSOR(name)                                                 \
+    cudaError_t name(unsigned out[4]) {                                                \
+        cudaError_t e = cudaDeviceSynchronize();                                       \
+        if (e == cudaSuccess) e = cudaMemcpyFromSymbol(out, g_debug_record, 16);       \
+        const unsigned zero[4] = {0u, 0u, 0u, 0u};                                     \
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_debug_record, zero, 16);        \
+        return e;                                                                      \
+    }
+#else
+#define VI_BOUNDS_OK(site, i, n) true
+#endif
+
+// ---------------------------------------------------------------------------
 // Stack storage formats.  Accumulation is FP32; these only round at store.
 
 // gather() fetches the 2 x 2 footprint whose lower-left texel is (i0, j0) from
@@ -183,6 +215,10 @@ __device__ __forceinline__ float brick_exit(const VolumeView& v, const VoxelCoor
 
 // Whether the brick holding the footprint's lower corner may yield alpha > 0.
 __device__ __forceinline__ bool brick_may_be_lit(const GridView& g, const VoxelCoord& c) {
+    if (!(VI_BOUNDS_OK(kSiteBrick, c.x0 >> kBrickShift, g.nbx) &&
+          VI_BOUNDS_OK(kSiteBrick, c.y0 >> kBrickShift, g.nby) &&
+          VI_BOUNDS_OK(kSiteBrick, c.z0 >> kBrickShift, g.nbz)))
+        return false;
     const int b = ((c.z0 >> kBrickShift) * g.nby + (c.y0 >> kBrickShift)) * g.nbx +
                   (c.x0 >> kBrickShift);
     return __ldg(g.flags + b) != 0;
@@ -237,6 +273,8 @@ __device__ __forceinline__ OctetRef octet_ref(const VolumeView& v, const VoxelCo
 
 template <typename VoxT>
 __device__ __forceinline__ typename Octet<VoxT>::V octet_load(const VolumeView& v, size_t idx) {
+    if (!VI_BOUNDS_OK(kSiteOctet, idx, (long long)v.nx * v.ny * v.nz))
+        return typename Octet<VoxT>::V{};
     return __ldg(static_cast<const typename Octet<VoxT>::V*>(v.data) + idx);
 }
 
@@ -287,8 +325,8 @@ __device__ __forceinline__ int slice_index(float lam, int n) {
 // footprint of the last row stays inside the slice, and the texture's clamp
 // addressing covers the last column.
 template <typename Fmt>
-__device__ __forceinline__ float bilinear(const StackView& sv, int k, int R, float tu, float tv,
-                                          int* rec = nullptr) {
+__device__ __forceinline__ float bilinear(const StackView& sv, int k, int n, int R, float tu,
+                                          float tv, int* rec = nullptr) {
     if (rec) {
         rec[1] = clampi(__float2int_rd(tu), -1, R);
         rec[2] = clampi(__float2int_rd(tv), -1, R);
@@ -303,6 +341,8 @@ __device__ __forceinline__ float bilinear(const StackView& sv, int k, int R, flo
     const float cv = fminf(fmaxf(tv, 0.0f), (float)(R - 1));
     const float fv = floorf(cv);
     const float wv = cv - fv;
+    if (!(VI_BOUNDS_OK(kSiteStackTex, k, n) && VI_BOUNDS_OK(kSiteStackTex, (int)fv, R)))
+        return 1.0f;
     // Gather takes the footprint's lower-left texel plus one (exact integers).
     const float row0 = (float)((k & ((1 << sv.spt_log2) - 1)) * (R + 1) + 1);
     float b00, b01, b10, b11;
@@ -317,7 +357,7 @@ __device__ __forceinline__ float stack_lookup(const StackView& sv, int n, int R,
                                               float tv, int* rec = nullptr) {
     const int k = slice_index(lam, n);
     if (rec) rec[0] = k;
-    return bilinear<Fmt>(sv, k, R, tu, tv, rec);
+    return bilinear<Fmt>(sv, k, n, R, tu, tv, rec);
 }
 
 }  // namespace vi

@@ -35,7 +35,9 @@ __global__ void brick_range_kernel(const VoxT* __restrict__ vol, int nx, int ny,
     uint32_t lo = 0xffffu, hi = 0u;
     for (int t = lane; t < wx * wy * wz; t += 32) {
         const int x = t % wx, yz = t / wx, y = yz % wy, z = yz / wy;
-        const uint32_t v = vol[((size_t)(z0 + z) * ny + (y0 + y)) * nx + (x0 + x)];
+        const size_t at = ((size_t)(z0 + z) * ny + (y0 + y)) * nx + (x0 + x);
+        if (!VI_BOUNDS_OK(kSiteRaw, at, (long long)nx * ny * nz)) continue;
+        const uint32_t v = vol[at];
         lo = min(lo, v);
         hi = max(hi, v);
     }
@@ -56,6 +58,8 @@ __global__ void brick_flag_kernel(const uint32_t* __restrict__ range, int nbrick
     long e_hi = (long)floor((hi - vmin) * scale) + 2;
     e_lo = e_lo < 0 ? 0 : (e_lo > M - 2 ? M - 2 : e_lo);
     e_hi = e_hi < 1 ? 1 : (e_hi > M - 1 ? M - 1 : e_hi);
+    if (!(VI_BOUNDS_OK(kSiteGrid, e_lo, M + 1) && VI_BOUNDS_OK(kSiteGrid, e_hi + 1, M + 1)))
+        return;
     flags[b] = (lit_prefix[e_hi + 1] - lit_prefix[e_lo]) > 0 ? 1 : 0;
 }
 
@@ -89,7 +93,9 @@ __global__ void build_octets_kernel(const VoxT* __restrict__ raw, int nx, int ny
     const int x = (int)(id % nx), y = (int)((id / nx) % ny), z = (int)(id / ((size_t)nx * ny));
     const int x1 = min(x + 1, nx - 1), y1 = min(y + 1, ny - 1), z1 = min(z + 1, nz - 1);
     auto at = [&](int xx, int yy, int zz) -> unsigned {
-        return raw[((size_t)zz * ny + yy) * nx + xx];
+        const size_t i = ((size_t)zz * ny + yy) * nx + xx;
+        if (!VI_BOUNDS_OK(kSiteRaw, i, (long long)total)) return 0u;
+        return raw[i];
     };
     const unsigned c000 = at(x, y, z), c001 = at(x1, y, z), c010 = at(x, y1, z), c011 = at(x1, y1, z);
     const unsigned c100 = at(x, y, z1), c101 = at(x1, y, z1), c110 = at(x, y1, z1), c111 = at(x1, y1, z1);
@@ -126,5 +132,9 @@ cudaError_t launch_brick_flags(const uint32_t* range, int nbricks, const int* li
                                                  scale, flags);
     return cudaGetLastError();
 }
+
+#if VI_DEBUG_BOUNDS
+VI_DEBUG_RECORD_ACCESSOR(debug_record_grid)
+#endif
 
 }  // namespace vi

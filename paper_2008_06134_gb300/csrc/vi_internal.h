@@ -45,6 +45,27 @@ struct LightFrame {
 // the volume), in the order c000 c001 c010 c011 c100 c101 c110 c111 (c{z}{y}{x});
 // 16 bytes for uint16 voxels, 8 for uint8.  One aligned vector load brings a
 // whole trilinear footprint.
+// Checked builds (-DVI_DEBUG_BOUNDS=1, the library libvi_checked.so): every
+// voxel-octet, brick-flag, TF, stack-texture, stack-store, output, raw-voxel
+// and grid index is tested against its array before the access.  A bad one is
+// counted in a device-wide record of the kernel's translation unit (count,
+// first site, first index) and the access is skipped: no trap, no fault, the
+// kernel runs to its end.  The release build compiles the tests out.
+#ifndef VI_DEBUG_BOUNDS
+#define VI_DEBUG_BOUNDS 0
+#endif
+enum DebugSite {
+    kSiteOctet = 1,       // volume octet load (sweep, march)
+    kSiteBrick = 2,       // brick flag load (sweep, march)
+    kSiteTfAlpha = 3,     // TF alpha entry (sweep, march)
+    kSiteTfColour = 4,    // TF RGBA entry (march)
+    kSiteStackTex = 5,    // stack texture / slice of a lookup (march)
+    kSiteStackStore = 6,  // stack element a sweep store writes
+    kSitePixel = 7,       // output pixel (march)
+    kSiteRaw = 8,         // raw voxel read (octet and brick-range builds)
+    kSiteGrid = 9,        // octet, brick range or brick flag written by a grid build
+};
+
 struct VolumeView {
     const void* data;  // octets
     int nx, ny, nz;
@@ -64,6 +85,9 @@ constexpr int kBrickShift = VI_BRICK_SHIFT;
 struct GridView {
     const uint8_t* flags;
     int nbx, nby;
+#if VI_DEBUG_BOUNDS
+    int nbz;
+#endif
 };
 
 // The attenuation stack in device memory.  Slice k, row j (0 <= j <= R) starts
@@ -165,5 +189,12 @@ cudaError_t launch_build_octets(const void* raw, int nx, int ny, int nz, int vox
                                 void* octets, cudaStream_t s);
 cudaError_t launch_brick_flags(const uint32_t* range, int nbricks, const int* lit_prefix, int M,
                                float vmin, float vmax, uint8_t* flags, cudaStream_t s);
+#if VI_DEBUG_BOUNDS
+// Copies the violation record of the sweep, march or grid kernels on the
+// current device to out[4] and clears it (waits for the device first).
+cudaError_t debug_record_sweep(unsigned out[4]);
+cudaError_t debug_record_march(unsigned out[4]);
+cudaError_t debug_record_grid(unsigned out[4]);
+#endif
 
 }  // namespace vi

@@ -160,8 +160,8 @@ __device__ __forceinline__ float slice_value(const MarchParams& p, int n, int R,
         const int k1 = min(k0 + 1, n - 1);
         const float w = fminf(fmaxf(__fsub_rn(lam, (float)k0), 0.0f), 1.0f);
         if (rec) rec[0] = k0;
-        const float b0 = bilinear<Fmt>(p.stack, k0, R, tu, tv, rec);
-        const float b1 = bilinear<Fmt>(p.stack, k1, R, tu, tv);
+        const float b0 = bilinear<Fmt>(p.stack, k0, n, R, tu, tv, rec);
+        const float b1 = bilinear<Fmt>(p.stack, k1, n, R, tu, tv);
         return fmaf(w, b1 - b0, b0);
     }
     return stack_lookup<Fmt>(p.stack, n, R, lam, tu, tv, rec);
@@ -269,6 +269,7 @@ __device__ __forceinline__ int march_sample(const MarchParams& p, const float* s
     int e;
     float f;
     tf_coord(val, p.tf_vmin, p.tf_scale, p.M, &e, &f);
+    if (!VI_BOUNDS_OK(kSiteTfAlpha, e, p.M - 1)) e = 0;
     const float a0 = s_alpha[e], a1 = s_alpha[e + 1];
     float alpha = fmaf(f, a1 - a0, a0);
     if (p.opacity_correction)
@@ -424,7 +425,7 @@ __device__ __forceinline__ int march_sample(const MarchParams& p, const float* s
                     for (int m = 0; m < 4; ++m) {
                         int* rr = TRACE ? rec + 11 + 3 * (ring * 4 + m) : nullptr;
                         if (TRACE) rr[0] = k;
-                        sum += bilinear<Fmt>(p.stack, k, R, __fadd_rn(l1, du[m]),
+                        sum += bilinear<Fmt>(p.stack, k, n, R, __fadd_rn(l1, du[m]),
                                              __fadd_rn(l2, dv[m]), rr);
                     }
                 }
@@ -437,6 +438,7 @@ __device__ __forceinline__ int march_sample(const MarchParams& p, const float* s
     // A sample with alpha = 0 leaves C and A unchanged, so it is skipped.
     ++count;
     if (alpha > 0.0f) {
+        if (!VI_BOUNDS_OK(kSiteTfColour, e, p.M - 1)) e = 0;
         const float4 ta = __ldg(p.tf + e), tb = __ldg(p.tf + e + 1);
         const float lf = fmaf(1.0f - p.ambient, coef, p.ambient);
         const float w = (1.0f - A) * lf * alpha;
@@ -512,7 +514,8 @@ __global__ void __launch_bounds__(kMarchThreads, VI_MARCH_MIN_BLOCKS)
             }
             i = to;
         }
-        if (valid) {
+        if (valid && VI_BOUNDS_OK(kSitePixel, (long long)y * p.cam.W + x,
+                                  (long long)p.cam.W * p.cam.H)) {
             const size_t idx = (size_t)y * p.cam.W + x;
             const float rem = 1.0f - A;
             p.out[idx] = make_float4(fmaf(rem, p.bg[0], C0), fmaf(rem, p.bg[1], C1),
@@ -675,5 +678,9 @@ cudaError_t noalloc_scratch(unsigned** counter, float4** image) {
     *image = reinterpret_cast<float4*>(base + kNoallocCounterBytes);
     return cudaSuccess;
 }
+
+#if VI_DEBUG_BOUNDS
+VI_DEBUG_RECORD_ACCESSOR(debug_record_march)
+#endif
 
 }  // namespace vi

@@ -245,6 +245,7 @@ int launch_captured(vi_server* s, Slot* sl, int rc, int shape) {
 // With graphs on, the sweep, the march, the output copy and the completion
 // callback are captured and launched as one graph after the uploads.
 int start(vi_server* s, Slot* sl, Request* r, bool reuse) {
+    vi_detail::NvtxRange nvtx_range("vi_server request");
     const vi_request& q = r->req;
     ServerVolume* v = s->vols[q.volume_id];
     vi_ctx* c = sl->ctx;
@@ -351,6 +352,7 @@ void schedule(vi_server* s) {
         }
         s->queue.pop_front();
         if (!v->resident) {
+            vi_detail::NvtxRange nvtx_range("vi_server volume load");
             int rc = vi_detail::volume_load(&v->res, &v->used, 0, v->host, v->dtype, v->nx,
                                                   v->ny, v->nz, 0, sl->stream, nullptr);
             // Slots on other streams may read this volume next: they wait on

@@ -65,6 +65,15 @@ __device__ __forceinline__ bool texel_inside(const LightFrame& lt, int k, const 
     return P0 >= 0.0f && P0 <= 1.0f && P1 >= 0.0f && P1 <= 1.0f && P2 >= 0.0f && P2 <= 1.0f;
 }
 
+// One stack store; a checked build first tests the element against the stack.
+template <typename T>
+__device__ __forceinline__ void put(const SweepParams& p, T* out, size_t at, T v) {
+    if (!VI_BOUNDS_OK(kSiteStackStore, (out + at) - static_cast<T*>(p.stack),
+                      (long long)p.lt.n * (p.lt.R + 1) * (long long)(p.row_pitch / sizeof(T))))
+        return;
+    out[at] = v;
+}
+
 // The slices of a warp's 32 columns, in lockstep: every lane stores slice k at
 // the same step, so each slice's stores of the warp are coalesced.  A lane
 // applies alpha only inside its own interval [kin, kout]; elsewhere it stores
@@ -84,8 +93,8 @@ __device__ __forceinline__ void sweep_lockstep(const SweepParams& p, const float
     int k = 0;
     for (; k < klo; ++k) {
         if (valid) {
-            out[(size_t)k * slice] = one;
-            if (dup) out[(size_t)k * slice + dup] = one;
+            put(p, out, (size_t)k * slice, one);
+            if (dup) put(p, out, (size_t)k * slice + dup, one);
         }
     }
     for (; k <= khi; k += kBatch) {
@@ -116,6 +125,7 @@ __device__ __forceinline__ void sweep_lockstep(const SweepParams& p, const float
                 float f;
                 tf_coord(trilinear_octet<VoxT>(oct[u], ref[u]), p.tf_vmin, p.tf_scale, p.M, &e,
                          &f);
+                if (!VI_BOUNDS_OK(kSiteTfAlpha, e, p.M - 1)) e = 0;
                 const float a0 = s_alpha[e];
                 alpha = fmaf(f, s_alpha[e + 1] - a0, a0);
                 if (p.opacity_correction)
@@ -127,8 +137,8 @@ __device__ __forceinline__ void sweep_lockstep(const SweepParams& p, const float
                                : fminf(1.0f, T * powf(1.0f + alpha, p.comp_n));
             if (valid) {
                 const typename Fmt::T q = Fmt::pack(stored);
-                out[(size_t)(k + u) * slice] = q;
-                if (dup) out[(size_t)(k + u) * slice + dup] = q;
+                put(p, out, (size_t)(k + u) * slice, q);
+                if (dup) put(p, out, (size_t)(k + u) * slice + dup, q);
             }
             if (DEPTH)
                 T = fminf(T - log1pf(-alpha), kDepthMax);  // alpha = 1: tau = inf, capped
@@ -140,8 +150,8 @@ __device__ __forceinline__ void sweep_lockstep(const SweepParams& p, const float
     const typename Fmt::T last = Fmt::pack(T);
     for (; k < lt.n; ++k) {
         if (valid) {
-            out[(size_t)k * slice] = last;
-            if (dup) out[(size_t)k * slice + dup] = last;
+            put(p, out, (size_t)k * slice, last);
+            if (dup) put(p, out, (size_t)k * slice + dup, last);
         }
     }
 }
@@ -241,8 +251,8 @@ __device__ __forceinline__ void sweep_column(const SweepParams& p, const float* 
     const typename Fmt::T one = Fmt::pack(DEPTH ? 0.0f : 1.0f);
     int k = 0;
     for (; k < min(kin, lt.n); ++k) {
-        out[(size_t)k * slice] = one;
-        if (dup) out[(size_t)k * slice + dup] = one;
+        put(p, out, (size_t)k * slice, one);
+        if (dup) put(p, out, (size_t)k * slice + dup, one);
     }
     // Inside the cube, four slices at a time: their positions, brick flags and
     // octets do not depend on T, so the loads of a batch are issued together
@@ -274,6 +284,7 @@ __device__ __forceinline__ void sweep_column(const SweepParams& p, const float* 
                 float f;
                 tf_coord(trilinear_octet<VoxT>(oct[u], ref[u]), p.tf_vmin, p.tf_scale, p.M, &e,
                          &f);
+                if (!VI_BOUNDS_OK(kSiteTfAlpha, e, p.M - 1)) e = 0;
                 const float a0 = s_alpha[e];
                 alpha = fmaf(f, s_alpha[e + 1] - a0, a0);
                 if (p.opacity_correction)
@@ -284,8 +295,8 @@ __device__ __forceinline__ void sweep_column(const SweepParams& p, const float* 
                 stored = DEPTH ? fmaxf(0.0f, T - p.comp_n * log1pf(alpha))
                                : fminf(1.0f, T * powf(1.0f + alpha, p.comp_n));
             const typename Fmt::T q = Fmt::pack(stored);
-            out[(size_t)(k + u) * slice] = q;
-            if (dup) out[(size_t)(k + u) * slice + dup] = q;
+            put(p, out, (size_t)(k + u) * slice, q);
+            if (dup) put(p, out, (size_t)(k + u) * slice + dup, q);
             if (DEPTH)
                 T = fminf(T - log1pf(-alpha), kDepthMax);  // alpha = 1: tau = inf, capped
             else
@@ -296,8 +307,8 @@ __device__ __forceinline__ void sweep_column(const SweepParams& p, const float* 
     // Past the cube: the light that left it.
     const typename Fmt::T last = Fmt::pack(T);
     for (; k < lt.n; ++k) {
-        out[(size_t)k * slice] = last;
-        if (dup) out[(size_t)k * slice + dup] = last;
+        put(p, out, (size_t)k * slice, last);
+        if (dup) put(p, out, (size_t)k * slice + dup, last);
     }
 }
 
@@ -384,5 +395,9 @@ cudaError_t launch_sweep(const SweepParams& p, int voxel_type, int format, cudaS
     if (voxel_type == 0) return launch_fmt<uint8_t>(p, format, s);
     return launch_fmt<uint16_t>(p, format, s);
 }
+
+#if VI_DEBUG_BOUNDS
+VI_DEBUG_RECORD_ACCESSOR(debug_record_sweep)
+#endif
 
 }  // namespace vi

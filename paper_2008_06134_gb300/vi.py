@@ -16,6 +16,9 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libvi.so")
+# The same library built with every kernel's memory indices checked
+# (VI_DEBUG_BOUNDS=1; violations read with debug_bounds()).
+LIB_CHECKED_PATH = os.path.join(HERE, "libvi_checked.so")
 
 OK, EINVAL, ENOMEM, ESTATE, ECUDA, ETIMEOUT = 0, -1, -2, -3, -4, -5
 U8, U16 = 0, 1
@@ -34,7 +37,7 @@ EXPORTS = ("vi_create", "vi_destroy", "vi_set_memory_budget", "vi_load_volume",
            "vi_set_transfer_function", "vi_set_light", "vi_set_point_light",
            "vi_build_attenuation", "vi_render", "vi_sync", "vi_error_string",
            "vi_attenuation_info", "vi_get_attenuation", "vi_trace_pixel", "vi_launch_count",
-           "vi_render_host_noalloc", "vi_server_create", "vi_server_destroy",
+           "vi_render_host_noalloc", "vi_debug_bounds", "vi_server_create", "vi_server_destroy",
            "vi_server_add_volume", "vi_server_submit", "vi_server_wait", "vi_server_cancel",
            "vi_server_timing", "vi_server_release", "vi_server_get_stats",
            "vi_server_set_graphs")
@@ -82,19 +85,20 @@ class ServerStats(C.Structure):
                 ("graph_launches", C.c_uint64), ("graph_instantiations", C.c_uint64)]
 
 
-_lib = None
+_libs = {}
 
 
-def library() -> C.CDLL:
-    """Load ``libvi.so`` (built by ``python -m paper_2008_06134_gb300.build``)."""
-    global _lib
-    if _lib is not None:
-        return _lib
-    if not os.path.exists(LIB_PATH):
+def library(checked: bool = False) -> C.CDLL:
+    """Load ``libvi.so``, or with ``checked`` ``libvi_checked.so`` (both built
+    by ``python -m paper_2008_06134_gb300.build``)."""
+    path = LIB_CHECKED_PATH if checked else LIB_PATH
+    if path in _libs:
+        return _libs[path]
+    if not os.path.exists(path):
         raise RuntimeError(
-            f"{LIB_PATH} is not built; run `python -m paper_2008_06134_gb300.build` "
+            f"{path} is not built; run `python -m paper_2008_06134_gb300.build` "
             "(needs nvcc) -- there is no CPU fallback")
-    L = C.CDLL(LIB_PATH)
+    L = C.CDLL(path)
     P, vp, i, f, sz = C.POINTER, C.c_void_p, C.c_int, C.c_float, C.c_size_t
     L.vi_create.argtypes = [P(vp), i, vp]
     L.vi_destroy.argtypes = [vp]
@@ -124,8 +128,19 @@ def library() -> C.CDLL:
     L.vi_server_release.argtypes = [vp, u64]
     L.vi_server_get_stats.argtypes = [vp, P(ServerStats)]
     L.vi_server_set_graphs.argtypes = [vp, i]
-    _lib = L
+    L.vi_debug_bounds.argtypes = [i, P(C.c_uint64), P(i), P(C.c_int64)]
+    _libs[path] = L
     return L
+
+
+def debug_bounds(device: int = 0):
+    """(violations, first site, first index) of the checked library's kernels
+    on ``device`` since the last call (vi_debug_bounds), which clears them."""
+    L = library(checked=True)
+    n, site, idx = C.c_uint64(), C.c_int(), C.c_int64()
+    _check(L.vi_debug_bounds(int(device), C.byref(n), C.byref(site), C.byref(idx)),
+           "vi_debug_bounds")
+    return n.value, site.value, idx.value
 
 
 def error_string(code: int) -> str:
@@ -158,8 +173,8 @@ def _ptr(buf):
 class Context:
     """One ``vi_ctx``: a device, a stream and the resident volume / TF / stack."""
 
-    def __init__(self, device: int = 0, stream=None):
-        L = library()
+    def __init__(self, device: int = 0, stream=None, checked: bool = False):
+        L = library(checked)
         if stream is None:
             try:
                 import torch
@@ -335,8 +350,8 @@ class Server:
     """A vi_server: continuous batching of render requests over resident volumes."""
 
     def __init__(self, device: int = 0, slots: int = 4, memory_budget: int = 0,
-                 max_resident_volumes: int = 0, graphs: bool = False):
-        L = library()
+                 max_resident_volumes: int = 0, graphs: bool = False, checked: bool = False):
+        L = library(checked)
         h = C.c_void_p()
         _check(L.vi_server_create(C.byref(h), int(device), int(slots), int(memory_budget),
                                   int(max_resident_volumes)), "vi_server_create")

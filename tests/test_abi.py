@@ -90,3 +90,17 @@ def test_server_calls_reject_bad_arguments_without_cuda(lib):
         assert lib.vi_server_destroy(h) == vi.OK
     else:                    # no GPU here: a clean error, no crash
         assert rc in (vi.ECUDA, vi.EINVAL)
+
+
+def test_checked_library_exports_every_symbol_and_reports_its_kind(lib):
+    """libvi_checked.so (VI_DEBUG_BOUNDS=1) exports the same ABI; the release
+    library answers vi_debug_bounds with VI_ESTATE without touching CUDA."""
+    from paper_2008_06134_gb300 import vi
+    checked = vi.library(checked=True)
+    for name in declared_functions():
+        assert hasattr(checked, name), name
+    n, site, idx = C.c_uint64(7), C.c_int(7), C.c_int64(7)
+    for L in (lib, checked):
+        assert L.vi_debug_bounds(0, None, None, None) == vi.EINVAL
+    assert lib.vi_debug_bounds(0, C.byref(n), C.byref(site), C.byref(idx)) == vi.ESTATE
+    assert (n.value, site.value, idx.value) == (0, 0, 0)
