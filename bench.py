@@ -498,6 +498,8 @@ def gb300_arm(args):
                    "parallelism": f"replicas x{world} (independent frames)"},
         "gsamples_per_s": round(samples * frames / (max_total_ms / 1e3) / 1e9, 3),
         "march_gsamples_per_s": round(samples / march_s / 1e9, 3),
+        # The sweep's own unit: texel-slices (n R^2 per frame), apart from eye-ray samples.
+        "sweep_gtexel_steps_per_s": round(n * R * R / sweep_s / 1e9, 3),
         "samples_per_frame": samples, "lit_samples_per_frame": lit_samples,
         "sweep_ms": round(sweep_s * 1e3, 4), "march_ms": round(march_s * 1e3, 4),
         "warm_frames_per_s": round(1.0 / march_s, 2),      # march only, stack cached
