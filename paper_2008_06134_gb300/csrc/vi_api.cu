@@ -480,10 +480,10 @@ int volume_load(VolumeRes* v, size_t* used, size_t budget, const void* data, int
                                     data_on_device ? cudaMemcpyDeviceToDevice
                                                    : cudaMemcpyHostToDevice,
                                     s);
-    if (e == cudaSuccess) e = vi::launch_build_octets(v->raw, nx, ny, nz, dtype, v->oct, s);
-    if (e == cudaSuccess) e = vi::launch_brick_range(v->raw, nx, ny, nz, dtype, v->brange, s);
+    if (e == cudaSuccess)
+        e = vi::launch_volume_grid(v->raw, nx, ny, nz, dtype, v->oct, v->brange, s);
     if (e != cudaSuccess) return VI_ECUDA;
-    if (launches) *launches += 2;
+    if (launches) *launches += 1;
     v->vtype = dtype;
     v->nx = nx;
     v->ny = ny;

@@ -18,32 +18,80 @@ namespace vi {
 
 namespace {
 
+// One block per brick builds the brick's footprint octets and its value range
+// in one pass over the raw voxels.  The brick and its one-voxel apron on the
+// high side (17^3 voxels, each coordinate clamped to the volume) are staged in
+// shared memory; a thread then writes the octets of a column of 16 voxels
+// along z (a warp's stores cover two contiguous rows) from the tile.  The
+// octet of voxel (x, y, z) holds its footprint with the upper corners clamped,
+// min(x + 1, nx - 1) and so on -- the staged tile's clamp -- and the union of
+// the brick's octets is exactly the brick plus its clamped apron, so the
+// brick's range is the min / max over the values of its octets.
+constexpr int kBrick = 1 << kBrickShift;
+constexpr int kApron = kBrick + 1;
+constexpr int kGridThreads = kBrick * kBrick;  // one thread per (x, y) of the brick
+
 template <typename VoxT>
-__global__ void brick_range_kernel(const VoxT* __restrict__ vol, int nx, int ny, int nz, int nbx,
-                                   int nby, int nbz, uint32_t* __restrict__ range) {
-    // One warp per brick: the lanes stride over the brick's voxels (x fastest,
-    // so a row's loads are coalesced) and combine their extremes at the end.
-    const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (b >= nbx * nby * nbz) return;  // the whole warp leaves together
+__device__ __forceinline__ typename Octet<VoxT>::V pack_octet(const unsigned c[8]) {
+    if constexpr (sizeof(VoxT) == 2) {
+        return make_uint4(c[0] | (c[1] << 16), c[2] | (c[3] << 16), c[4] | (c[5] << 16),
+                          c[6] | (c[7] << 16));
+    } else {
+        return make_uint2(c[0] | (c[1] << 8) | (c[2] << 16) | (c[3] << 24),
+                          c[4] | (c[5] << 8) | (c[6] << 16) | (c[7] << 24));
+    }
+}
+
+template <typename VoxT>
+__global__ void __launch_bounds__(kGridThreads)
+    volume_grid_kernel(const VoxT* __restrict__ raw, int nx, int ny, int nz, int nbx, int nby,
+                       typename Octet<VoxT>::V* __restrict__ oct, uint32_t* __restrict__ range) {
+    __shared__ VoxT tile[kApron][kApron][kApron];  // [z][y][x]
+    __shared__ uint32_t part_lo[kGridThreads / 32], part_hi[kGridThreads / 32];
+    const int b = blockIdx.x;
     const int bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
-    const int x0 = bx << kBrickShift, y0 = by << kBrickShift, z0 = bz << kBrickShift;
-    // The brick plus a one-voxel apron on the high side, clamped to the volume.
-    const int wx = min(x0 + (1 << kBrickShift), nx - 1) - x0 + 1;
-    const int wy = min(y0 + (1 << kBrickShift), ny - 1) - y0 + 1;
-    const int wz = min(z0 + (1 << kBrickShift), nz - 1) - z0 + 1;
+    const int x0 = bx * kBrick, y0 = by * kBrick, z0 = bz * kBrick;
+    const size_t total = (size_t)nx * ny * nz;
+    for (int t = threadIdx.x; t < kApron * kApron * kApron; t += kGridThreads) {
+        const int x = t % kApron, y = (t / kApron) % kApron, z = t / (kApron * kApron);
+        const size_t at = ((size_t)min(z0 + z, nz - 1) * ny + min(y0 + y, ny - 1)) * nx +
+                          min(x0 + x, nx - 1);
+        tile[z][y][x] = VI_BOUNDS_OK(kSiteRaw, at, (long long)total) ? raw[at] : VoxT(0);
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % kBrick, ty = threadIdx.x / kBrick;
+    const int gx = x0 + tx, gy = y0 + ty;
     uint32_t lo = 0xffffu, hi = 0u;
-    for (int t = lane; t < wx * wy * wz; t += 32) {
-        const int x = t % wx, yz = t / wx, y = yz % wy, z = yz / wy;
-        const size_t at = ((size_t)(z0 + z) * ny + (y0 + y)) * nx + (x0 + x);
-        if (!VI_BOUNDS_OK(kSiteRaw, at, (long long)nx * ny * nz)) continue;
-        const uint32_t v = vol[at];
-        lo = min(lo, v);
-        hi = max(hi, v);
+    if (gx < nx && gy < ny) {
+        const int zn = min(kBrick, nz - z0);
+        for (int z = 0; z < zn; ++z) {
+            const unsigned c[8] = {tile[z][ty][tx],         tile[z][ty][tx + 1],
+                                   tile[z][ty + 1][tx],     tile[z][ty + 1][tx + 1],
+                                   tile[z + 1][ty][tx],     tile[z + 1][ty][tx + 1],
+                                   tile[z + 1][ty + 1][tx], tile[z + 1][ty + 1][tx + 1]};
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                lo = min(lo, (uint32_t)c[k]);
+                hi = max(hi, (uint32_t)c[k]);
+            }
+            const size_t id = ((size_t)(z0 + z) * ny + gy) * nx + gx;
+            if (VI_BOUNDS_OK(kSiteGrid, id, (long long)total)) oct[id] = pack_octet<VoxT>(c);
+        }
     }
     lo = __reduce_min_sync(0xffffffffu, lo);
     hi = __reduce_max_sync(0xffffffffu, hi);
-    if (lane == 0) range[b] = (lo << 16) | hi;
+    if ((threadIdx.x & 31) == 0) {
+        part_lo[threadIdx.x >> 5] = lo;
+        part_hi[threadIdx.x >> 5] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        lo = threadIdx.x < kGridThreads / 32 ? part_lo[threadIdx.x] : 0xffffu;
+        hi = threadIdx.x < kGridThreads / 32 ? part_hi[threadIdx.x] : 0u;
+        lo = __reduce_min_sync(0xffffffffu, lo);
+        hi = __reduce_max_sync(0xffffffffu, hi);
+        if (threadIdx.x == 0) range[b] = (lo << 16) | hi;
+    }
 }
 
 __global__ void brick_flag_kernel(const uint32_t* __restrict__ range, int nbricks,
@@ -65,62 +113,20 @@ __global__ void brick_flag_kernel(const uint32_t* __restrict__ range, int nbrick
 
 }  // namespace
 
-cudaError_t launch_brick_range(const void* raw, int nx, int ny, int nz, int voxel_type,
-                               uint32_t* range, cudaStream_t s) {
-    const int nbx = (nx + (1 << kBrickShift) - 1) >> kBrickShift;
-    const int nby = (ny + (1 << kBrickShift) - 1) >> kBrickShift;
-    const int nbz = (nz + (1 << kBrickShift) - 1) >> kBrickShift;
-    const int n = nbx * nby * nbz;
-    const int threads = 256, blocks = (n + threads / 32 - 1) / (threads / 32);  // a warp per brick
+cudaError_t launch_volume_grid(const void* raw, int nx, int ny, int nz, int voxel_type,
+                               void* octets, uint32_t* range, cudaStream_t s) {
+    const int nbx = (nx + kBrick - 1) >> kBrickShift;
+    const int nby = (ny + kBrick - 1) >> kBrickShift;
+    const int nbz = (nz + kBrick - 1) >> kBrickShift;
+    const unsigned blocks = (unsigned)nbx * nby * nbz;
     if (voxel_type == 0)
-        brick_range_kernel<uint8_t><<<blocks, threads, 0, s>>>(
-            static_cast<const uint8_t*>(raw), nx, ny, nz, nbx, nby, nbz, range);
+        volume_grid_kernel<uint8_t><<<blocks, kGridThreads, 0, s>>>(
+            static_cast<const uint8_t*>(raw), nx, ny, nz, nbx, nby, static_cast<uint2*>(octets),
+            range);
     else
-        brick_range_kernel<uint16_t><<<blocks, threads, 0, s>>>(
-            static_cast<const uint16_t*>(raw), nx, ny, nz, nbx, nby, nbz, range);
-    return cudaGetLastError();
-}
-
-namespace {
-
-// One thread per voxel: gather its 2 x 2 x 2 footprint (clamped) into an octet.
-template <typename VoxT>
-__global__ void build_octets_kernel(const VoxT* __restrict__ raw, int nx, int ny, int nz,
-                                    typename Octet<VoxT>::V* __restrict__ oct) {
-    const size_t id = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const size_t total = (size_t)nx * ny * nz;
-    if (id >= total) return;
-    const int x = (int)(id % nx), y = (int)((id / nx) % ny), z = (int)(id / ((size_t)nx * ny));
-    const int x1 = min(x + 1, nx - 1), y1 = min(y + 1, ny - 1), z1 = min(z + 1, nz - 1);
-    auto at = [&](int xx, int yy, int zz) -> unsigned {
-        const size_t i = ((size_t)zz * ny + yy) * nx + xx;
-        if (!VI_BOUNDS_OK(kSiteRaw, i, (long long)total)) return 0u;
-        return raw[i];
-    };
-    const unsigned c000 = at(x, y, z), c001 = at(x1, y, z), c010 = at(x, y1, z), c011 = at(x1, y1, z);
-    const unsigned c100 = at(x, y, z1), c101 = at(x1, y, z1), c110 = at(x, y1, z1), c111 = at(x1, y1, z1);
-    if constexpr (sizeof(VoxT) == 2) {
-        oct[id] = make_uint4(c000 | (c001 << 16), c010 | (c011 << 16), c100 | (c101 << 16),
-                             c110 | (c111 << 16));
-    } else {
-        oct[id] = make_uint2(c000 | (c001 << 8) | (c010 << 16) | (c011 << 24),
-                             c100 | (c101 << 8) | (c110 << 16) | (c111 << 24));
-    }
-}
-
-}  // namespace
-
-cudaError_t launch_build_octets(const void* raw, int nx, int ny, int nz, int voxel_type,
-                                void* octets, cudaStream_t s) {
-    const size_t total = (size_t)nx * ny * nz;
-    const unsigned threads = 256;
-    const size_t blocks = (total + threads - 1) / threads;
-    if (voxel_type == 0)
-        build_octets_kernel<uint8_t><<<(unsigned)blocks, threads, 0, s>>>(
-            static_cast<const uint8_t*>(raw), nx, ny, nz, static_cast<uint2*>(octets));
-    else
-        build_octets_kernel<uint16_t><<<(unsigned)blocks, threads, 0, s>>>(
-            static_cast<const uint16_t*>(raw), nx, ny, nz, static_cast<uint4*>(octets));
+        volume_grid_kernel<uint16_t><<<blocks, kGridThreads, 0, s>>>(
+            static_cast<const uint16_t*>(raw), nx, ny, nz, nbx, nby,
+            static_cast<uint4*>(octets), range);
     return cudaGetLastError();
 }
 

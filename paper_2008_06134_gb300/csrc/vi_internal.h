@@ -179,14 +179,14 @@ cudaError_t launch_march(const MarchParams& p, int voxel_type, int format, int m
                          cudaStream_t s);
 cudaError_t launch_trace(const MarchParams& p, int voxel_type, int format, int mode, int x,
                          int y, int32_t* rec, int max_rec, int* n_rec, cudaStream_t s);
-cudaError_t launch_brick_range(const void* raw, int nx, int ny, int nz, int voxel_type,
-                               uint32_t* range, cudaStream_t s);
+// Footprint octets of every voxel and the value range of every brick (with its
+// one-voxel apron), in one pass over the raw voxels.
+cudaError_t launch_volume_grid(const void* raw, int nx, int ny, int nz, int voxel_type,
+                               void* octets, uint32_t* range, cudaStream_t s);
 // Device addresses of the fixed scratch behind vi_render_host_noalloc on the
 // current device (looked up once per device; no allocation).
 constexpr size_t kNoallocMaxPixels = 512 * 512;
 cudaError_t noalloc_scratch(unsigned** counter, float4** image);
-cudaError_t launch_build_octets(const void* raw, int nx, int ny, int nz, int voxel_type,
-                                void* octets, cudaStream_t s);
 cudaError_t launch_brick_flags(const uint32_t* range, int nbricks, const int* lit_prefix, int M,
                                float vmin, float vmax, uint8_t* flags, cudaStream_t s);
 #if VI_DEBUG_BOUNDS
