@@ -98,13 +98,14 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="ct256-cone",
                     choices=["ct256-cone", "precision", "scalability", "serving", "variants",
-                             "large"],
+                             "large", "oracle"],
                     help="ct256-cone: the headline frame; precision: storage formats on the "
                          "512^3 blob scene vs the FP64 oracle; scalability: slice count x "
                          "slice resolution grid; serving: the render server on a stream of "
                          "mixed requests; variants: the method variants and the point light "
                          "on the headline scene; large: 1024^3 volume, 1024 x 2048^2 FP16 "
-                         "stack, 3840x2160")
+                         "stack, 3840x2160; oracle: the FP64 oracle timed beside the GPU on "
+                         "every scene")
     ap.add_argument("--requests", type=int, default=512, help="serving: request count")
     ap.add_argument("--rate", default="300,800",
                     help="serving: Poisson arrival rates per second (comma-separated)")
@@ -765,6 +766,95 @@ def large_workload(args):
     ctx.close()
 
 
+def oracle_workload(args):
+    """The FP64 oracle timed on this host's cores beside the GPU, scene by scene:
+    the 64^3 blob scene (shell) and the 256^3 CT scene (shadow and cone) on
+    whole frames, the 512^3 precision scene (shell and cone) and the 1024^3
+    large scene (cone) on their centred 256 x 144 crops.  The oracle's sweep
+    always builds the whole FP64 stack (a crop's rays can look up any of it).
+    Per scene and mode: the oracle's sweep and render seconds, its samples and
+    Gsamples/s; the GPU's sweep and march ms and Gsamples/s on the whole frame
+    (5 timed frames, L2 flushed); and the ratio of the two sample rates."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2008_06134_gb300 import build, phantoms as ph, vi
+    build.build()
+    oracle.build()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    scenes = [(ph.blob64_shell, (vi.SHELL,), None), (ph.ct256_cone, (vi.SHADOW, vi.CONE), None),
+              (ph.blob512_precision, (vi.SHELL, vi.CONE), (256, 144)),
+              (ph.ct1024_large, (vi.CONE,), (256, 144))]
+    rows = []
+    for make, modes, crop in scenes:
+        sc = make()
+        W, H = sc.width, sc.height
+        gpu = {}
+        with vi.Context(0) as ctx:
+            ctx.load_volume(sc.volume)
+            ctx.set_transfer_function(sc.tf, sc.vmin, sc.vmax)
+            ctx.set_light(sc.light_dir, sc.light_color)
+            out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
+            for mode in modes:
+                def bld():
+                    ctx.build_attenuation(sc.n_slices, sc.slice_res, mode, format=sc.fmt,
+                                          cone_half_angle_deg=sc.cone_half_angle_deg,
+                                          shell_radius_vox=sc.shell_radius_vox)
+
+                def rnd(**kw):
+                    ctx.render(sc.camera, W, H, sc.step_vox, out=out, ert=sc.ert, bg=sc.bg, **kw)
+                counts = torch.zeros((H, W), dtype=torch.int32, device="cuda")
+                bld()
+                rnd(sample_counts=counts)
+                torch.cuda.synchronize()
+                samples = int(counts.sum().item())
+                del counts
+                for _ in range(3):
+                    bld()
+                    rnd()
+                sweep_ms, march_ms = timed_frames(ctx, bld, rnd, flush, 5)
+                gpu[mode] = (sweep_ms, march_ms, samples)
+        del out
+        torch.cuda.empty_cache()
+        if crop:
+            cw, ch = crop
+            ys, xs = np.mgrid[(H - ch) // 2:(H + ch) // 2, (W - cw) // 2:(W + cw) // 2]
+        else:
+            ys, xs = np.mgrid[0:H, 0:W]
+        xs, ys = xs.ravel(), ys.ravel()
+        t0 = time.perf_counter()
+        light = oracle.light_setup(sc.light_dir, sc.n_slices, sc.slice_res)
+        stack = oracle.build_stack(sc.volume, sc.tf, sc.vmin, sc.vmax, light)
+        sweep_s = time.perf_counter() - t0
+        for mode in modes:
+            ro = oracle.render_opts(mode, sc.step_vox, sc.ert, sc.bg, sc.light_color,
+                                    cone_half_angle_deg=sc.cone_half_angle_deg,
+                                    shell_radius_vox=sc.shell_radius_vox)
+            t0 = time.perf_counter()
+            ns = oracle.render_pixels(sc.volume, sc.tf, sc.vmin, sc.vmax, light, stack,
+                                      sc.camera, W, H, ro, xs, ys)[3]
+            render_s = time.perf_counter() - t0
+            o_samples = int(ns.sum())
+            sweep_ms, march_ms, samples = gpu[mode]
+            o_rate = o_samples / render_s / 1e9
+            g_rate = samples / (march_ms * 1e6)
+            rows.append({"scene": sc.name, "mode": ["none", "shadow", "shell", "cone"][mode],
+                         "oracle": {"pixels": int(xs.size), "sweep_s": round(sweep_s, 2),
+                                    "render_s": round(render_s, 3), "samples": o_samples,
+                                    "gsamples_per_s": round(o_rate, 5)},
+                         "gpu": {"pixels": W * H, "stack": ["f32", "f16", "bf16", "unorm16"][sc.fmt],
+                                 "sweep_ms": round(sweep_ms, 4), "march_ms": round(march_ms, 4),
+                                 "samples": samples, "gsamples_per_s": round(g_rate, 2)},
+                         "march_sample_rate_ratio": round(g_rate / o_rate, 1),
+                         "sweep_time_ratio": round(sweep_s * 1e3 / sweep_ms, 1)})
+        del stack, sc
+    print(json.dumps({"workload": "oracle", "cores": oracle.threads(), "cpu": cpu_model(),
+                      "note": "oracle FP64 on whole frames (64^3, 256^3) or the centred "
+                              "256x144 crop (512^3, 1024^3); GPU on whole frames",
+                      "rows": rows}), flush=True)
+
+
 def serving_workload(args):
     """The render server on the serving mix: 8 registered volumes ({128, 256,
     512}^3, uint8 blobs and uint16 CT ellipsoids) with at most 6 resident under
@@ -894,6 +984,8 @@ def main():
         variants_workload(args)
     elif args.workload == "large":
         large_workload(args)
+    elif args.workload == "oracle":
+        oracle_workload(args)
     else:
         gb300_arm(args)
 
