@@ -27,6 +27,13 @@ namespace {
 // min(x + 1, nx - 1) and so on -- the staged tile's clamp -- and the union of
 // the brick's octets is exactly the brick plus its clamped apron, so the
 // brick's range is the min / max over the values of its octets.
+// Staging loads a thread keeps in flight (the loop over the tile is unrolled by
+// it).  8 measured fastest: 256^3 u16 in 57.6 us (71.5 us not unrolled, 58.3
+// us at 4), 512^3 in 427 us (519, 434).
+#ifndef VI_GRID_STAGE_UNROLL
+#define VI_GRID_STAGE_UNROLL 8
+#endif
+constexpr int kStageUnroll = VI_GRID_STAGE_UNROLL;
 constexpr int kBrick = 1 << kBrickShift;
 constexpr int kApron = kBrick + 1;
 constexpr int kGridThreads = kBrick * kBrick;  // one thread per (x, y) of the brick
@@ -52,6 +59,7 @@ __global__ void __launch_bounds__(kGridThreads)
     const int bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
     const int x0 = bx * kBrick, y0 = by * kBrick, z0 = bz * kBrick;
     const size_t total = (size_t)nx * ny * nz;
+#pragma unroll kStageUnroll
     for (int t = threadIdx.x; t < kApron * kApron * kApron; t += kGridThreads) {
         const int x = t % kApron, y = (t / kApron) % kApron, z = t / (kApron * kApron);
         const size_t at = ((size_t)min(z0 + z, nz - 1) * ny + min(y0 + y, ny - 1)) * nx +
