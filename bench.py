@@ -47,8 +47,8 @@ FLOPS_LIT = {0: 0, 1: 6 + 2 + 12, 2: 6 + 2 + 6 * 12 + 7, 3: 6 + 2 + 8 * 12 + 9}
 NCU_TRAFFIC = {
     "march_kernel": (("vi_march.cu", "vi_device.cuh", "vi_internal.h"), "c851711f39f26480",
                      92_271_616),
-    "sweep_kernel": (("vi_sweep.cu", "vi_device.cuh", "vi_internal.h"), "49bc6be819f5ea2c",
-                     307_687_936),
+    "sweep_kernel": (("vi_sweep.cu", "vi_device.cuh", "vi_internal.h"), "72d918a53c609721",
+                     307_985_920),
 }
 
 

@@ -49,6 +49,19 @@ constexpr int kSweepThreads = 256;
 #define VI_SWEEP_BATCH 4
 #endif
 constexpr int kBatch = VI_SWEEP_BATCH;
+// The lockstep sweep (stacks of 2^30 texel-slices and more) keeps fewer loads
+// per lane in flight and more warps per SM: two-slice batches at three blocks
+// per SM (80 registers) measured 4.42 ms on the 1024 x 2048^2 FP16 sweep of the
+// 1024^3 workload, against 5.06 ms at four-slice batches and two blocks (4.60
+// and 4.68 ms at 2 x 4 and 3 x 3; 4.91 ms at 1 x 5).  The per-lane sweep is
+// fastest at 4 x 2 (0.111 ms on config 2; 0.121-0.179 ms for the others).
+#ifndef VI_SWEEP_LOCKSTEP_MIN_BLOCKS
+#define VI_SWEEP_LOCKSTEP_MIN_BLOCKS 3
+#endif
+#ifndef VI_SWEEP_LOCKSTEP_BATCH
+#define VI_SWEEP_LOCKSTEP_BATCH 2
+#endif
+constexpr int kLockBatch = VI_SWEEP_LOCKSTEP_BATCH;
 
 // A texel column is the line o + s w: for a directional light o is the
 // texel's point on the plane through the centre and w = L; for a point light
@@ -97,11 +110,11 @@ __device__ __forceinline__ void sweep_lockstep(const SweepParams& p, const float
             if (dup) put(p, out, (size_t)k * slice + dup, one);
         }
     }
-    for (; k <= khi; k += kBatch) {
-        OctetRef ref[kBatch];
-        bool lit[kBatch];
+    for (; k <= khi; k += kLockBatch) {
+        OctetRef ref[kLockBatch];
+        bool lit[kLockBatch];
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
+        for (int u = 0; u < kLockBatch; ++u) {
             lit[u] = false;
             if (k + u >= kin && k + u <= kout) {
                 const float sk = __fsub_rn(__fmaf_rn((float)(k + u), lt.dL, lt.min), lt.Lc);
@@ -112,12 +125,12 @@ __device__ __forceinline__ void sweep_lockstep(const SweepParams& p, const float
                 lit[u] = brick_may_be_lit(p.grid, vc);
             }
         }
-        typename Octet<VoxT>::V oct[kBatch];
+        typename Octet<VoxT>::V oct[kLockBatch];
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u)
+        for (int u = 0; u < kLockBatch; ++u)
             if (lit[u]) oct[u] = octet_load<VoxT>(p.vol, ref[u].idx);
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
+        for (int u = 0; u < kLockBatch; ++u) {
             if (k + u > khi) break;
             float alpha = 0.0f;
             if (lit[u]) {
@@ -320,7 +333,8 @@ __device__ __forceinline__ void sweep_column(const SweepParams& p, const float* 
 // blocks of a fixed grid.  A warp covers TW x TH texels (16 x 2), so each row
 // of its store fills whole 32-byte sectors.
 template <typename VoxT, typename Fmt, bool DEPTH, bool LOCKSTEP>
-__global__ void __launch_bounds__(kSweepThreads, VI_SWEEP_MIN_BLOCKS)
+__global__ void __launch_bounds__(kSweepThreads, LOCKSTEP ? VI_SWEEP_LOCKSTEP_MIN_BLOCKS
+                                                       : VI_SWEEP_MIN_BLOCKS)
     sweep_kernel(const SweepParams p) {
     extern __shared__ float s_alpha[];
     for (int e = threadIdx.x; e < p.M; e += kSweepThreads) s_alpha[e] = p.tf[e].w;
