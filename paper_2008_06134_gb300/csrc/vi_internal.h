@@ -121,10 +121,11 @@ struct SweepParams {
 
 // Stacks of at least this many texel-slices are swept in lockstep: each
 // slice's stores of a warp are then coalesced, which pays once the stores
-// dominate (1024 x 2048^2: 5.3 vs 7.1 ms), while smaller stacks sweep faster
-// with each lane walking its own column (256 x 512^2: 0.119 vs 0.123 ms).
+// dominate (1024 x 2048^2: 4.43 vs 7.1 ms; 512 x 1024^2 FP32: 0.664 vs 0.695
+// ms), while smaller stacks sweep faster with each lane walking its own column
+// (256 x 512^2 and every smaller scalability stack: 0.111 vs 0.140 ms).
 #ifndef VI_SWEEP_LOCKSTEP_MIN
-#define VI_SWEEP_LOCKSTEP_MIN (1ull << 30)
+#define VI_SWEEP_LOCKSTEP_MIN (1ull << 29)
 #endif
 
 // Cap of a stored optical depth (exp(-64) < 2e-28) and the most shells.
