@@ -37,6 +37,9 @@ constexpr int kStageUnroll = VI_GRID_STAGE_UNROLL;
 constexpr int kBrick = 1 << kBrickShift;
 constexpr int kApron = kBrick + 1;
 constexpr int kGridThreads = kBrick * kBrick;  // one thread per (x, y) of the brick
+static_assert(kApron * kApron * kApron * sizeof(uint16_t) <= 48 * 1024 && kGridThreads <= 1024,
+              "volume_grid_kernel stages a brick and its apron in static shared memory and "
+              "runs a thread per (x, y): bricks of at most 16^3 voxels");
 
 template <typename VoxT>
 __device__ __forceinline__ typename Octet<VoxT>::V pack_octet(const unsigned c[8]) {
@@ -58,7 +61,7 @@ __global__ void __launch_bounds__(kGridThreads)
     const int b = blockIdx.x;
     const int bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
     const int x0 = bx * kBrick, y0 = by * kBrick, z0 = bz * kBrick;
-    const size_t total = (size_t)nx * ny * nz;
+    [[maybe_unused]] const size_t total = (size_t)nx * ny * nz;  // the checked build's bound
 #pragma unroll kStageUnroll
     for (int t = threadIdx.x; t < kApron * kApron * kApron; t += kGridThreads) {
         const int x = t % kApron, y = (t / kApron) % kApron, z = t / (kApron * kApron);
