@@ -464,6 +464,32 @@ __device__ __forceinline__ void load_alpha(const MarchParams& p, float* s_alpha)
 #define VI_MARCH_MIN_BLOCKS 1
 #endif
 
+// Order in which the tiles are taken.  Raster order, except for frames of at
+// most kCentreOutTiles tiles per launched warp (VI_MARCH_TILE_ORDER 1, the
+// default): there the rows are taken from the middle outwards (columns in
+// order), so the rows where rays cross the volume (costly) come first and the
+// cheap border rows last, where they fill the time the last costly tiles take
+// instead of leaving warps idle.  Config 2 (1024^2, 6.7 tiles per warp): march
+// 0.870 -> 0.796 ms, every variant 3-10 % faster.  With many tiles per warp
+// there is little idle time to fill, and two bands of rows in flight (above
+// and below the middle) lose cache locality: 3840 x 2160 (53 per warp) 4.77 ->
+// 5.27 ms, so such frames keep raster order.  Centre-out columns as well gave
+// no more.
+#ifndef VI_MARCH_TILE_ORDER
+#define VI_MARCH_TILE_ORDER 1
+#endif
+#ifndef VI_MARCH_CENTRE_OUT_TILES
+#define VI_MARCH_CENTRE_OUT_TILES 8
+#endif
+constexpr bool kTileOrderAdaptive = VI_MARCH_TILE_ORDER == 1;
+constexpr unsigned kCentreOutTiles = VI_MARCH_CENTRE_OUT_TILES;
+
+// Offsets 0, -1, +1, -2, +2, ... of index r from the middle: m + offset(r) for
+// r in [0, n) with m = n / 2 visits 0 .. n - 1 once each, for n odd or even.
+__device__ __forceinline__ int centre_offset(int r) {
+    return (r & 1) ? -((r + 1) >> 1) : (r >> 1);
+}
+
 template <typename VoxT, typename Fmt, int MODE, bool EXT, bool POINT>
 __global__ void __launch_bounds__(kMarchThreads, VI_MARCH_MIN_BLOCKS)
     march_kernel(const MarchParams p) {
@@ -472,14 +498,19 @@ __global__ void __launch_bounds__(kMarchThreads, VI_MARCH_MIN_BLOCKS)
 
     const int lane = threadIdx.x & 31;
     const unsigned tiles_x = (unsigned)(p.cam.W + kTileW - 1) / kTileW;
-    const unsigned ntiles = tiles_x * ((unsigned)(p.cam.H + kTileH - 1) / kTileH);
+    const unsigned tiles_y = (unsigned)(p.cam.H + kTileH - 1) / kTileH;
+    const unsigned ntiles = tiles_x * tiles_y;
+    const bool rows_out =
+        kTileOrderAdaptive && ntiles <= kCentreOutTiles * gridDim.x * (blockDim.x / 32);
     for (;;) {
         unsigned tile = 0;
         if (lane == 0) tile = atomicAdd(p.tile_counter, 1u);
         tile = __shfl_sync(0xffffffffu, tile, 0);
         if (tile >= ntiles) break;
-        const int x = (int)(tile % tiles_x) * kTileW + (lane % kTileW);
-        const int y = (int)(tile / tiles_x) * kTileH + (lane / kTileW);
+        int tcol = (int)(tile % tiles_x), trow = (int)(tile / tiles_x);
+        if (rows_out) trow = (int)(tiles_y / 2) + centre_offset(trow);
+        const int x = tcol * kTileW + (lane % kTileW);
+        const int y = trow * kTileH + (lane / kTileW);
         const bool valid = x < p.cam.W && y < p.cam.H;
         Ray r;
         r.hit = false;
