@@ -119,7 +119,8 @@ def lib():
             L.orc_render_pixels.argtypes = [P(Volume), P(TF), P(Light), C.c_void_p, P(Camera),
                                             C.c_int, C.c_int, P(RenderOpts), C.c_void_p,
                                             C.c_void_p, C.c_long, C.c_void_p, C.c_void_p,
-                                            C.c_void_p, C.c_void_p]
+                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                            C.c_void_p]
             L.orc_trace_pixel.argtypes = [P(Volume), P(TF), P(Light), C.c_void_p, P(Camera),
                                           C.c_int, C.c_int, P(RenderOpts), C.c_int, C.c_int,
                                           C.c_void_p, C.c_int, P(C.c_int)]
@@ -236,15 +237,20 @@ def render_opts(mode: int, step_vox: float, ert: float = 2.0, bg=(0, 0, 0, 0),
                       int(quantity), int(slice_filter), int(shell_count))
 
 
-def render_pixels(vol, tf, vmin, vmax, light: Light, stack, cam, W: int, H: int,
+def render_window(vol, tf, vmin, vmax, light: Light, stack, cam, W: int, H: int,
                   ro: RenderOpts, xs, ys):
-    """Render the pixels (xs[i], ys[i]) of a W x H frame.
+    """Render the pixels (xs[i], ys[i]) of a W x H frame, with the early ray
+    termination window of each (reading R12 of Eq. 3).
 
-    Returns (rgba, alt, ambiguous, nsamples): rgba and alt are (count, 4)
-    float64, ambiguous (count,) bool, nsamples (count,) int64.  ``ambiguous``
-    marks pixels whose accumulated opacity came within ``ro.ert_band`` of the
-    early-termination threshold; there ``alt`` holds the other valid outcome
-    (stopping inside that band vs. at the first sample past it).
+    Returns (rgba, alt, window, nsamples, nsamples_alt, end, nsamples_end):
+    rgba, alt and end are (count, 4) float64, window (count,) uint8, the sample
+    counts (count,) int64.  Where the accumulated opacity passes within
+    ``ro.ert_band`` of the threshold a binary32 renderer may stop anywhere
+    from the first sample with A > ert - band to the first with A > ert + band
+    (or the ray's end).  window = 0: one outcome (alt = end = rgba); 1: two,
+    rgba (the binary64 decision) and alt; 2: three or more, every stop from
+    the window's start to ``end``, with rgba the binary64 decision and alt the
+    window's start (or its end, if the decision is at the start).
     """
     V = volume(vol)
     T = transfer_function(tf, vmin, vmax)
@@ -255,6 +261,9 @@ def render_pixels(vol, tf, vmin, vmax, light: Light, stack, cam, W: int, H: int,
     alt = np.empty((n, 4), dtype=np.float64)
     amb = np.zeros(n, dtype=np.uint8)
     ns = np.zeros(n, dtype=np.int64)
+    ns_alt = np.zeros(n, dtype=np.int64)
+    end = np.empty((n, 4), dtype=np.float64)
+    ns_end = np.zeros(n, dtype=np.int64)
     Bp = None
     if stack is not None:
         stack = np.ascontiguousarray(stack, dtype=np.float64)
@@ -263,10 +272,25 @@ def render_pixels(vol, tf, vmin, vmax, light: Light, stack, cam, W: int, H: int,
     rc = lib().orc_render_pixels(C.byref(V.struct), C.byref(T.struct), C.byref(light), Bp,
                                  C.byref(cam_s), int(W), int(H), C.byref(ro), xs.ctypes.data,
                                  ys.ctypes.data, n, out.ctypes.data, alt.ctypes.data,
-                                 amb.ctypes.data, ns.ctypes.data)
+                                 amb.ctypes.data, ns.ctypes.data, ns_alt.ctypes.data,
+                                 end.ctypes.data, ns_end.ctypes.data)
     if rc:
         raise ValueError(f"orc_render_pixels failed ({rc})")
-    return out, alt, amb.astype(bool), ns
+    return out, alt, amb, ns, ns_alt, end, ns_end
+
+
+def render_pixels(vol, tf, vmin, vmax, light: Light, stack, cam, W: int, H: int,
+                  ro: RenderOpts, xs, ys):
+    """Render the pixels (xs[i], ys[i]) of a W x H frame.
+
+    Returns (rgba, alt, ambiguous, nsamples): rgba and alt are (count, 4)
+    float64, ambiguous (count,) bool, nsamples (count,) int64.  ``ambiguous``
+    marks pixels where early ray termination has more than one valid outcome
+    (see ``render_window``); there ``alt`` holds the other end of the window.
+    """
+    out, alt, win, ns, *_ = render_window(vol, tf, vmin, vmax, light, stack, cam, W, H, ro,
+                                          xs, ys)
+    return out, alt, win.astype(bool), ns
 
 
 def render_image(vol, tf, vmin, vmax, light, stack, cam, W, H, ro):

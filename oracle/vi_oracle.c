@@ -894,6 +894,9 @@ typedef struct {
     double* alt;
     uint8_t* ambiguous;
     long long* nsamples;
+    long long* nsamples_alt;
+    double* end;
+    long long* nsamples_end;
     int32_t* trace;
     int trace_max;
     int* trace_count;
@@ -907,16 +910,20 @@ static void march_one(const march_ctx* s, long p) {
     double C[3] = {0.0, 0.0, 0.0}, A = 0.0;
     long long count = 0;
     int ntrace = 0;
-    /* Early ray termination stops at the first sample with A > ert.  Where A
-       comes within ert_band of ert, a binary32 renderer may legitimately stop
-       anywhere in that run of samples or at the first sample past it, so both
-       outcomes are kept: the state at the first in-band sample (S) and the
-       state at the first sample with A > ert + band (X).  "out" is the binary64
-       decision, "alt" the other outcome. */
+    /* Early ray termination (Eq. 3; the test A > ert after each composited
+       sample, reading R12).  A binary32 renderer carries A with an error far
+       below ert_band, so where the binary64 A passes within ert_band of ert
+       it may stop at any sample of a window: from lo, the first sample with
+       A > ert - band, to hi, the first with A > ert + band (or the ray's last
+       sample if none).  "out" is the binary64 decision: the first sample with
+       A > ert, else the ray's end.  "alt" is the state at the window's other
+       end (lo, unless out is at lo; then hi).  ambiguous = 0 for a window of
+       one sample (one outcome), 1 for two samples (out and alt are both
+       outcomes), 2 for three or more (out and alt are its two ends and the
+       binary64 decision; the samples between them are outcomes too). */
     const double ert = (double)ro->ert, band = ro->ert_band;
-    int amb = 0, have_main = 0;
-    double SC[3] = {0, 0, 0}, SA = 0.0, MC[3] = {0, 0, 0}, MA = 0.0;
-    long long Mcount = 0, main_at = -1, last = -1;
+    double LC[3] = {0, 0, 0}, LA = 0.0, MC[3] = {0, 0, 0}, MA = 0.0;
+    long long lo_at = -1, main_at = -1, last = -1, Lcount = 0, Mcount = 0;
     if (ray.hit) {
         for (long i = 0;; ++i) {
             /* Sample i at t_i = t0 + i dt while t_i < t1. */
@@ -989,31 +996,37 @@ static void march_one(const march_ctx* s, long p) {
             ++count;
             last = (long long)i;
 
-            /* Early ray termination. */
-            if (!have_main && A > ert) {
-                have_main = 1;
+            /* Early ray termination: the window's start, the binary64
+               decision, and its end (where the loop stops). */
+            if (lo_at < 0 && A > ert - band) {
+                lo_at = (long long)i;
+                LC[0] = C[0]; LC[1] = C[1]; LC[2] = C[2]; LA = A; Lcount = count;
+            }
+            if (main_at < 0 && A > ert) {
                 main_at = (long long)i;
                 MC[0] = C[0]; MC[1] = C[1]; MC[2] = C[2]; MA = A; Mcount = count;
             }
-            if (!amb && fabs(A - ert) <= band) {
-                amb = 1;
-                SC[0] = C[0]; SC[1] = C[1]; SC[2] = C[2]; SA = A;
-            }
             if (A > ert + band) break;
-            if (have_main && !amb) break;
         }
     }
+    /* Here C, A, count hold the state at the window's end (hi) or the ray's end. */
     double outC[3], outA, altC[3], altA;
-    long long outcount = count;
-    if (!amb) {
-        for (int ch = 0; ch < 3; ++ch) outC[ch] = altC[ch] = C[ch];
-        outA = altA = A;
-    } else if (have_main && main_at != last) {
-        for (int ch = 0; ch < 3; ++ch) { outC[ch] = MC[ch]; altC[ch] = C[ch]; }
-        outA = MA; altA = A; outcount = Mcount;
-    } else {
-        for (int ch = 0; ch < 3; ++ch) { outC[ch] = C[ch]; altC[ch] = SC[ch]; }
-        outA = A; altA = SA;
+    long long outcount = count, altcount = count;
+    int amb = 0;
+    for (int ch = 0; ch < 3; ++ch) outC[ch] = altC[ch] = C[ch];
+    outA = altA = A;
+    if (main_at >= 0) {
+        for (int ch = 0; ch < 3; ++ch) outC[ch] = MC[ch];
+        outA = MA;
+        outcount = Mcount;
+    }
+    if (lo_at >= 0 && lo_at < last) {
+        amb = last - lo_at >= 2 ? 2 : 1;
+        if (main_at != lo_at) {
+            for (int ch = 0; ch < 3; ++ch) altC[ch] = LC[ch];
+            altA = LA;
+            altcount = Lcount;
+        }
     }
     /* Background behind the remaining transparency. */
     double* o = s->out + 4 * (size_t)p;
@@ -1026,6 +1039,13 @@ static void march_one(const march_ctx* s, long p) {
     }
     if (s->ambiguous) s->ambiguous[p] = (uint8_t)amb;
     if (s->nsamples) s->nsamples[p] = outcount;
+    if (s->nsamples_alt) s->nsamples_alt[p] = altcount;
+    if (s->end) {
+        double* q = s->end + 4 * (size_t)p;
+        for (int ch = 0; ch < 3; ++ch) q[ch] = C[ch] + (1.0 - A) * (double)ro->bg[ch];
+        q[3] = A + (1.0 - A) * (double)ro->bg[3];
+    }
+    if (s->nsamples_end) s->nsamples_end[p] = count;
     if (s->trace_count) *s->trace_count = ntrace;
 }
 
@@ -1038,6 +1058,7 @@ static int render_common(const orc_volume* vol, const orc_tf* tf, const orc_ligh
                          const double* B, const orc_camera* cam, int W, int H,
                          const orc_render_opts* ro, const int* xs, const int* ys, long count,
                          double* out, double* alt, uint8_t* ambiguous, long long* nsamples,
+                         long long* nsamples_alt, double* end, long long* nsamples_end,
                          int32_t* trace, int trace_max, int* trace_count) {
     if (!valid_inputs(vol, tf) || !lt || !cam || !ro || !out || !xs || !ys) return ORC_EINVAL;
     if (ro->mode < ORC_NONE || ro->mode > ORC_CONE) return ORC_EINVAL;
@@ -1064,6 +1085,9 @@ static int render_common(const orc_volume* vol, const orc_tf* tf, const orc_ligh
     s.alt = alt;
     s.ambiguous = ambiguous;
     s.nsamples = nsamples;
+    s.nsamples_alt = nsamples_alt;
+    s.end = end;
+    s.nsamples_end = nsamples_end;
     s.trace = trace;
     s.trace_max = trace_max;
     s.trace_count = trace_count;
@@ -1075,14 +1099,18 @@ static int render_common(const orc_volume* vol, const orc_tf* tf, const orc_ligh
     return ORC_OK;
 }
 
-/* Render the listed pixels of a W x H image.  out, alt: count x RGBA
-   (binary64); alt differs from out only on ERT-ambiguous pixels. */
+/* Render the listed pixels of a W x H image.  out, alt, end: count x RGBA
+   (binary64); alt differs from out only on ERT-ambiguous pixels (ambiguous
+   1 or 2, see march_one); end is the state at the end of the ERT window (out
+   where there is no window).  nsamples, nsamples_alt, nsamples_end: the
+   samples composited for each.  alt, end and their counts may be NULL. */
 int orc_render_pixels(const orc_volume* vol, const orc_tf* tf, const orc_light* lt,
                       const double* B, const orc_camera* cam, int W, int H,
                       const orc_render_opts* ro, const int* xs, const int* ys, long count,
-                      double* out, double* alt, uint8_t* ambiguous, long long* nsamples) {
+                      double* out, double* alt, uint8_t* ambiguous, long long* nsamples,
+                      long long* nsamples_alt, double* end, long long* nsamples_end) {
     return render_common(vol, tf, lt, B, cam, W, H, ro, xs, ys, count, out, alt, ambiguous,
-                         nsamples, NULL, 0, NULL);
+                         nsamples, nsamples_alt, end, nsamples_end, NULL, 0, NULL);
 }
 
 /* Per-sample index-path record of one pixel's ray (ORC_TRACE_WORDS int32 per
@@ -1095,8 +1123,8 @@ int orc_trace_pixel(const orc_volume* vol, const orc_tf* tf, const orc_light* lt
     if (!rec || max_rec < 0 || !n_rec) return ORC_EINVAL;
     double out[4];
     *n_rec = 0;
-    return render_common(vol, tf, lt, B, cam, W, H, ro, &x, &y, 1, out, NULL, NULL, NULL, rec,
-                         max_rec, n_rec);
+    return render_common(vol, tf, lt, B, cam, W, H, ro, &x, &y, 1, out, NULL, NULL, NULL, NULL,
+                         NULL, NULL, rec, max_rec, n_rec);
 }
 
 /* ------------------------------------------------------------------ */

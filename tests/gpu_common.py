@@ -59,14 +59,19 @@ def oracle_frame(orc, scene, mode=None, xs=None, ys=None, stack=None, ert=None, 
                          shell_radius_vox=scene.shell_radius_vox, ert_band=ert_band,
                          quantity=quantity, slice_filter=slice_filter, shell_count=shell_count)
     if xs is None:
-        img, alt, amb, ns = orc.render_image(scene.volume, scene.tf, scene.vmin, scene.vmax,
-                                             light, stack, scene.camera, scene.width,
-                                             scene.height, ro)
+        ys_, xs_ = np.mgrid[0:scene.height, 0:scene.width]
+        xs_, ys_ = xs_.ravel(), ys_.ravel()
     else:
-        img, alt, amb, ns = orc.render_pixels(scene.volume, scene.tf, scene.vmin, scene.vmax,
-                                              light, stack, scene.camera, scene.width,
-                                              scene.height, ro, xs, ys)
-    return img, alt, amb, ns, stack, light, ro
+        xs_, ys_ = xs, ys
+    img, alt, win, ns, ns_alt, end, ns_end = orc.render_window(
+        scene.volume, scene.tf, scene.vmin, scene.vmax, light, stack, scene.camera,
+        scene.width, scene.height, ro, xs_, ys_)
+    if xs is None:
+        shape = (scene.height, scene.width)
+        img, alt, end = (a.reshape(*shape, 4) for a in (img, alt, end))
+        win, ns, ns_alt, ns_end = (a.reshape(shape) for a in (win, ns, ns_alt, ns_end))
+    window = {"win": win, "ns_alt": ns_alt, "end": end, "ns_end": ns_end}
+    return img, alt, win > 0, ns, stack, light, ro, window
 
 
 def image_errors(gpu, ref, alt, amb):
@@ -74,3 +79,45 @@ def image_errors(gpu, ref, alt, amb):
     e_main = np.abs(gpu - ref).max(axis=-1)
     e_alt = np.abs(gpu - alt).max(axis=-1)
     return np.where(amb, np.minimum(e_main, e_alt), e_main)
+
+
+# Early ray termination (Eq. 3, reading R12): where the binary64 opacity passes
+# within the oracle's band (1e-5) of the threshold, a binary32 renderer may stop
+# at any sample of a short window.  Frames that terminate at 0.99 have such a
+# window on 0.2-0.5 % of their pixels (opacity steps near the threshold are
+# about 1e-4 to 1e-3 against a band 2e-5 wide); a larger share means the band
+# or the window logic has widened.
+MAX_AMBIGUOUS_FRACTION = 1e-2
+
+
+def check_frame(gpu, counts, ora, tol=IMAGE_TOL):
+    """Compare a GPU frame (and its per-pixel sample counts, if given) with the
+    oracle's (the tuple oracle_frame returns).  Every pixel must match a valid
+    early-termination outcome within tol: without an ERT window the binary64
+    one, with its exact sample count; with a window of two samples the outcome
+    whose sample count the GPU reports; with a longer window any stop inside
+    it (the composited colour and opacity grow monotonically along it, so they
+    lie between the window's two ends).  Returns the per-pixel errors."""
+    ref, alt, amb, ns, *_, w = ora
+    win, ns_alt, end, ns_end = w["win"], w["ns_alt"], w["end"], w["ns_end"]
+    gpu = np.asarray(gpu, dtype=np.float64).reshape(ref.shape)
+    assert amb.mean() <= MAX_AMBIGUOUS_FRACTION, amb.mean()
+    e_main = np.abs(gpu - ref).max(axis=-1)
+    e_alt = np.abs(gpu - alt).max(axis=-1)
+    # The window's two ends: its start is alt unless the decision is there.
+    first = np.where((ns_alt < ns)[..., None], alt, ref)
+    lo, hi = np.minimum(first, end), np.maximum(first, end)
+    e_hull = np.maximum(np.maximum(lo - gpu, gpu - hi), 0.0).max(axis=-1)
+    if counts is None:
+        err = np.where(win == 0, e_main, np.where(win == 1, np.minimum(e_main, e_alt), e_hull))
+    else:
+        counts = np.asarray(counts).reshape(ns.shape)
+        n_first = np.minimum(ns, ns_alt)
+        err = np.full(ns.shape, np.inf)
+        err = np.where(counts == ns, e_main, err)
+        err = np.where((win > 0) & (counts == ns_alt), np.minimum(err, e_alt), err)
+        inside = (win == 2) & (counts >= n_first) & (counts <= ns_end)
+        err = np.where(inside, np.minimum(err, e_hull), err)
+    worst = np.unravel_index(int(np.argmax(err)), err.shape)
+    assert err.max() <= tol, (float(err.max()), worst, int(win[worst]))
+    return err

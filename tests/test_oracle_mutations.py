@@ -68,6 +68,19 @@ MUTATIONS = {
                                 "if (fabsf(o->L[1]) > fabsf(o->L[ax])) ax = 1;"),
     "ert-threshold-shifted": ("const double ert = (double)ro->ert, band = ro->ert_band;",
                               "const double ert = (double)ro->ert + 0.03, band = ro->ert_band;"),
+    "ert-window-start-at-threshold": ("if (lo_at < 0 && A > ert - band) {",
+                                      "if (lo_at < 0 && A > ert) {"),
+    "ert-band-on-wrong-side": ("if (A > ert + band) break;", "if (A > ert - band) break;"),
+    "ert-outcount-from-window-end": ("        outcount = Mcount;\n", "        outcount = count;\n"),
+    "ert-alt-one-sample-late": ("""            if (lo_at < 0 && A > ert - band) {
+                lo_at = (long long)i;
+                LC[0] = C[0]; LC[1] = C[1]; LC[2] = C[2]; LA = A; Lcount = count;
+            }""", """            if (lo_at >= 0 && Lcount == 0) {
+                LC[0] = C[0]; LC[1] = C[1]; LC[2] = C[2]; LA = A; Lcount = count;
+            }
+            if (lo_at < 0 && A > ert - band) lo_at = (long long)i;"""),
+    "ert-alt-always-window-end": ("if (main_at != lo_at) {", "if (0) {"),
+    "ert-wide-window-off-by-one": ("amb = last - lo_at >= 2 ? 2 : 1;", "amb = last - lo_at >= 1 ? 2 : 1;"),
     "comp-n-inverted": ("stored = stored * pow(1.0 + alpha, (double)s->opt->comp_n);",
                         "stored = stored / pow(1.0 + alpha, (double)s->opt->comp_n);"),
     "texel-centre-offset": ("float sk, float P[3]) {\n    float qi = (float)(2 * i + 1) / (float)lt->R;",

@@ -470,6 +470,66 @@ def test_early_ray_termination_threshold(orc):
     assert np.all(img == alt)
 
 
+# Early ray termination window (Eq. 3 with the test A > ert after each
+# sample, reading R12).  Homogeneous cube, alpha a = 0.25, vertical orthographic
+# rays with 32 samples: after q samples A_q = 1 - 0.75^q (A_7 = 0.86652,
+# A_8 = 0.89989, A_9 = 0.92492, A_11 = 0.95776, A_12 = 0.96832, A_30 = 0.99982,
+# A_31 = 0.99987, A_32 = 0.99990) and C = rgb A_q.  The window runs from the
+# first sample with A > ert - band to the first with A > ert + band (or the
+# ray's last sample); each case below is worked out by hand from those values:
+# (ert, band, window kind, samples of the binary64 decision, of alt, of the
+# window's end).
+def _a_after(q, a=f32(0.25)):
+    return 1 - (1 - a) ** q
+
+
+ERT_WINDOW_CASES = [
+    # A_8 just above ert, inside the band: stop at 8 (binary64) or 9 (A_9 > ert + band).
+    (lambda: _a_after(8) - 4e-6, 1e-5, 1, 8, 9, 9),
+    # A_8 just below ert, inside the band: stop at 9 (binary64) or already at 8.
+    (lambda: _a_after(8) + 4e-6, 1e-5, 1, 9, 8, 9),
+    # ert between A_8 + band and A_9 - band: one outcome.
+    (lambda: 0.91, 1e-5, 0, 9, 9, 9),
+    # The ray ends (32 samples) with A_32 in the band below ert: one outcome, all samples.
+    (lambda: _a_after(32) + 4e-6, 1e-5, 0, 32, 32, 32),
+    # A_32 in the band above ert, A_31 below it: the window is the last sample alone.
+    (lambda: _a_after(32) - 4e-6, 1e-5, 0, 32, 32, 32),
+    # A_31 in the band below ert, A_32 past ert + band: stop at 32 or at 31.
+    (lambda: _a_after(31) + 4e-6, 1e-5, 1, 32, 31, 32),
+    # A wide band: samples 7..12 are in the window, the binary64 decision is 9.
+    (lambda: 0.9, 0.06, 2, 9, 7, 12),
+    # A_30..A_32 in the window and the ray ends inside it: decision 31, window start 30.
+    (lambda: _a_after(31) - 1e-6, 5e-5, 2, 31, 30, 32),
+    # A wide band whose binary64 decision is its first sample (A_8 > 0.8998;
+    # A_10 = 0.94369 is the first past 0.9298): alt is the window's end.
+    (lambda: 0.8998, 0.03, 2, 8, 10, 10),
+]
+
+
+@pytest.mark.parametrize("case", range(len(ERT_WINDOW_CASES)))
+def test_early_ray_termination_window(orc, case):
+    ert_of, band, want_win, want_ns, want_alt, want_end = ERT_WINDOW_CASES[case]
+    a = f32(0.25)
+    rgb = np.array([0.2, 0.5, 0.9], dtype=np.float32).astype(np.float64)
+    vol, tf = homog_cube(a, rgb)
+    lt = orc.light_setup((0, 0, 1), 4, 4)
+    c = cam((0.5, 0.5, 3.0), (0.5, 0.5, 0.5), (0, 1, 0), False, 40, 0.5)
+    ro = orc.render_opts(orc.NONE, 0.5, ert=ert_of(), ert_band=band)
+    xs, ys = np.array([0, 1, 0, 1]), np.array([0, 0, 1, 1])
+    out, alt, win, ns, ns_alt, end, ns_end = orc.render_window(vol, tf, 0, 255, lt, None, c,
+                                                               2, 2, ro, xs, ys)
+    assert np.all(win == want_win)
+    assert np.all(ns == want_ns) and np.all(ns_alt == want_alt)
+    assert np.all(ns_end == want_end)
+    for img, q in ((out, want_ns), (alt, want_alt), (end, want_end)):
+        assert np.allclose(img[:, 3], _a_after(q), atol=1e-14)
+        assert np.allclose(img[:, :3], rgb * _a_after(q), atol=1e-14)
+    # render_pixels reports the same decision with a boolean flag.
+    out2, alt2, amb2, ns2 = orc.render_pixels(vol, tf, 0, 255, lt, None, c, 2, 2, ro, xs, ys)
+    assert np.array_equal(out2, out) and np.array_equal(alt2, alt)
+    assert np.array_equal(amb2, win > 0) and np.array_equal(ns2, ns)
+
+
 def test_opacity_correction_in_eye_pass(orc):
     a, s = f32(0.25), 0.5
     vol, tf = homog_cube(a, (1, 1, 1))
