@@ -224,8 +224,9 @@ int vi_launch_count(vi_ctx* ctx, uint64_t* count);
    (256 B + VI_NOALLOC_MAX_PIXELS * 16 B, about 4 MiB), which every GPU that
    loads the library holds until the process exits.
      - W * H above VI_NOALLOC_MAX_PIXELS returns VI_EINVAL (nothing runs).
-     - The first call on a device looks up that array's device address; make
-       it before any stream capture.
+     - The first call on a device (and the first after a cudaDeviceReset of
+       it) looks up that array's device address in the current CUDA context;
+       make it before any stream capture.
      - Every call on every context of a device shares the array: the counter
        is cleared on the stream at each call, the staged frame is overwritten
        (the array keeps the last call's contents), and calls whose GPU work

@@ -16,6 +16,8 @@
 //
 // The same per-sample body runs in trace_kernel, which records every integer
 // decision of one ray for exact comparison with an independent implementation.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "vi_device.cuh"
@@ -684,9 +686,52 @@ constexpr size_t kNoallocCounterBytes = 256;
 __device__ __align__(256) static unsigned char
     g_noalloc_scratch[kNoallocCounterBytes + kNoallocMaxPixels * sizeof(float4)];
 
+// The array's device address is looked up once per CUDA context (a device's
+// context created after cudaDeviceReset may hold the array elsewhere).  A
+// context is known by the driver's unique context ID, read through the
+// runtime's driver entry points; where they are missing, the address is looked
+// up on every call.
+using CtxGetCurrent = CUresult (*)(CUcontext*);
+using CtxGetId = CUresult (*)(CUcontext, unsigned long long*);
+
+struct NoallocCache {
+    int device = -1;
+    unsigned long long ctx_id = 0;  // 0: none cached
+    void* addr = nullptr;
+};
+
 constexpr int kNoallocMaxDevices = 64;
 std::mutex g_noalloc_mu;
-void* g_noalloc_addr[kNoallocMaxDevices] = {};
+NoallocCache g_noalloc_cache[kNoallocMaxDevices];
+std::once_flag g_entry_once;
+CtxGetCurrent g_ctx_get_current = nullptr;
+CtxGetId g_ctx_get_id = nullptr;
+
+void find_entry_points() {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+        g_ctx_get_current = reinterpret_cast<CtxGetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+        g_ctx_get_id = reinterpret_cast<CtxGetId>(f);
+    cudaGetLastError();
+}
+
+// Unique ID of the calling thread's current context; 0 if it cannot be read.
+unsigned long long current_context_id() {
+    std::call_once(g_entry_once, find_entry_points);
+    if (!g_ctx_get_current || !g_ctx_get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    if (g_ctx_get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 }  // namespace
 
@@ -695,16 +740,20 @@ cudaError_t noalloc_scratch(unsigned** counter, float4** image) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kNoallocMaxDevices) return cudaErrorInvalidDevice;
+    // A host-side reference to the array is a stand-in, not a device address:
+    // the address is looked up with the device current.
+    const unsigned long long id = current_context_id();
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        // A host-side reference to the array is a stand-in, not a device
-        // address: look the address up once per device, with it current.
+    NoallocCache& c = g_noalloc_cache[dev];
+    if (!(id != 0 && c.ctx_id == id && c.addr)) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
-        g_noalloc_addr[dev] = p;
+        c.device = dev;
+        c.ctx_id = id;
+        c.addr = p;
     }
-    unsigned char* base = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+    unsigned char* base = static_cast<unsigned char*>(c.addr);
     *counter = reinterpret_cast<unsigned*>(base);
     *image = reinterpret_cast<float4*>(base + kNoallocCounterBytes);
     return cudaSuccess;

@@ -407,7 +407,9 @@ class Server:
                step_vox, out, light_color=(1.0, 1.0, 1.0), format=F32,
                cone_half_angle_deg=15.0, shell_radius_vox=1.0, ert=2.0,
                bg=(0.0, 0.0, 0.0, 0.0), quantity=TRANSMITTANCE, shell_count=1,
-               slice_filter=SLICE_NEAREST) -> int:
+               slice_filter=SLICE_NEAREST, sample_counts=None) -> int:
+        """Queue a render request; ``sample_counts`` (optional (H, W) int32 CUDA
+        tensor) receives the samples composited per pixel."""
         tf = np.ascontiguousarray(tf, dtype=np.float32)
         p, dev = _ptr(out)
         q = Request(int(volume_id), C.c_void_p(tf.ctypes.data), tf.shape[0], float(vmin),
@@ -416,11 +418,12 @@ class Server:
                     BuildOpts(int(format), float(cone_half_angle_deg), float(shell_radius_vox),
                               0, 0.0, int(quantity), int(shell_count)),
                     camera(cam), int(W), int(H), float(step_vox),
-                    Context._render_opts(ert, bg, 0.0, 0, slice_filter=slice_filter),
+                    Context._render_opts(ert, bg, 0.0, 0, sample_counts=sample_counts,
+                                         slice_filter=slice_filter),
                     C.c_void_p(p), dev)
         t = C.c_uint64(0)
         _check(self.L.vi_server_submit(self.h, C.byref(q), C.byref(t)), "vi_server_submit")
-        self._keep[("out", t.value)] = out
+        self._keep[("out", t.value)] = (out, sample_counts)
         return t.value
 
     def wait(self, ticket: int, timeout_ms: float = 60000.0):

@@ -83,11 +83,13 @@ def image_errors(gpu, ref, alt, amb):
 
 # Early ray termination (Eq. 3, reading R12): where the binary64 opacity passes
 # within the oracle's band (1e-5) of the threshold, a binary32 renderer may stop
-# at any sample of a short window.  Frames that terminate at 0.99 have such a
-# window on 0.2-0.5 % of their pixels (opacity steps near the threshold are
-# about 1e-4 to 1e-3 against a band 2e-5 wide); a larger share means the band
-# or the window logic has widened.
-MAX_AMBIGUOUS_FRACTION = 1e-2
+# at any sample of a short window.  A ray that reaches the threshold has one
+# with a chance of about 2 band / (alpha (1 - ert)), the band against the
+# opacity step there: near 10 % for soft tissue (alpha 0.02) at ert = 0.99,
+# under 1 % for bone.  Whole frames that terminate at 0.99 have 0.2-0.5 % of
+# their pixels in a window, the sampled rows through the 1024^3 volume 1.6 %.
+# A larger share means the band or the window logic has widened.
+MAX_AMBIGUOUS_FRACTION = 0.05
 
 
 def check_frame(gpu, counts, ora, tol=IMAGE_TOL):

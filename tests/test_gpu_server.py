@@ -83,6 +83,49 @@ def test_server_frame_equals_context_frame(env):
     assert np.array_equal(served, ref)
 
 
+def test_served_frames_match_the_oracle(env):
+    """Every served frame matches the FP64 oracle, not only the server's own
+    one-slot frames: 4 slots, all requests submitted at once, graphs on, mixed
+    volumes (uint8 blobs, uint16 ellipsoids, a non-cubic one), TFs, shadow /
+    shell / cone and the four storage formats.  Tolerance: the image tolerance
+    plus half an ulp of the stack's format; sample counts exact (inside an
+    early-termination window, one of its outcomes)."""
+    import oracle
+    from gpu_common import FORMAT_HALF_ULP, IMAGE_TOL, check_frame, oracle_frame
+    torch, ph, vi, vols, tfs = env
+    oracle.build()
+    reqs = make_requests(ph, vi, 12, seed=21)
+    fmts = [vi.F32, vi.F16, vi.BF16, vi.UNORM16]
+    for k, q in enumerate(reqs):
+        q["fmt"] = fmts[k % 4]
+        q["vol"] = k % 3
+        q["mode"] = 1 + (k // 4) % 3
+    outs, counts = [], []
+    with vi.Server(0, slots=4, graphs=True) as s:
+        vids = [s.add_volume(v) for v in vols]
+        tickets = []
+        for q in reqs:
+            out = torch.full((q["H"], q["W"], 4), float("nan"), device="cuda")
+            cnt = torch.full((q["H"], q["W"]), -1, dtype=torch.int32, device="cuda")
+            tf, vmin, vmax = tfs[q["vol"]]
+            tickets.append(s.submit(vids[q["vol"]], tf, vmin, vmax, q["light"], q["n"], q["R"],
+                                    q["mode"], q["cam"], q["W"], q["H"], 0.5, out,
+                                    format=q["fmt"], ert=q["ert"], sample_counts=cnt))
+            outs.append(out)
+            counts.append(cnt)
+        for t in tickets:
+            assert s.wait(t) == (vi.REQ_DONE, vi.OK)
+        assert s.stats()["graph_launches"] == len(reqs)
+    torch.cuda.synchronize()
+    for q, out, cnt in zip(reqs, outs, counts):
+        tf, vmin, vmax = tfs[q["vol"]]
+        sc = ph.Scene("served", vols[q["vol"]], tf, vmin, vmax, np.asarray(q["light"]),
+                      (1.0, 1.0, 1.0), q["n"], q["R"], q["mode"], q["cam"], q["W"], q["H"],
+                      0.5, q["ert"])
+        check_frame(out.cpu().numpy(), cnt.cpu().numpy(), oracle_frame(oracle, sc),
+                    IMAGE_TOL + FORMAT_HALF_ULP[q["fmt"]])
+
+
 def test_residency_limit_evicts_and_reloads(env):
     torch, ph, vi, vols, tfs = env
     reqs = make_requests(ph, vi, 12, seed=3)

@@ -7,17 +7,19 @@ context's resident data into a host buffer, using only a fixed device array
 inside the library for the march's work counter and the frame's staging.
 
 These tests call it through the C ABI and check its frames against vi_render's
-(the existing entry point) within the image tolerance of the other GPU tests,
-on two calls in a row: the shared array keeps the previous call's contents,
-which must not leak into the next frame.  The file is named to be collected
-last, and passes both alone in a fresh process and after the other tests.
+(the existing entry point): the same kernel with the same parameters on the
+same data, so the frames must be equal bit for bit, on two calls in a row (the
+shared array keeps the previous call's contents, which must not leak into the
+next frame).  They also check that a call allocates nothing: on a fresh
+context, before any vi_render, a byte budget that refuses every new buffer
+still lets it run, and the device's free memory does not move across a call.
+The file is named to be collected last, and passes both alone in a fresh
+process and after the other tests.
 """
 import ctypes as C
 
 import numpy as np
 import pytest
-
-from gpu_common import IMAGE_TOL
 
 pytestmark = pytest.mark.gpu
 
@@ -52,6 +54,36 @@ def _noalloc(vi, ctx, sc, W, H, ert):
     return rc, out
 
 
+def test_noalloc_allocates_nothing(setup):
+    """On a fresh context, before any vi_render: with a budget of one byte
+    the context can grow no buffer, yet the call succeeds (vi_render, which
+    stages host output in a context buffer, is refused); and once the
+    library's device code is loaded, the device's free memory is the same
+    before and after a call."""
+    import torch
+    ctx, vi, ph = setup
+    sc = ph.blob64_shell(ert=0.95)
+    sc.mode = vi.CONE
+    _load(ctx, sc)
+    ctx.set_memory_budget(1)
+    for _ in range(2):                      # the first call may load the module's code
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        rc, out = _noalloc(vi, ctx, sc, 256, 256, sc.ert)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert rc == vi.OK, vi.error_string(rc)
+        assert np.isfinite(out).all()
+    assert free1 == free0
+    with pytest.raises(vi.ViError) as e:     # host output needs a staging buffer
+        ctx.render(sc.camera, 256, 256, sc.step_vox, out=np.empty((256, 256, 4), np.float32),
+                   ert=sc.ert)
+    assert e.value.code == vi.ENOMEM
+    ctx.set_memory_budget(0)
+    ref = ctx.render(sc.camera, 256, 256, sc.step_vox, ert=sc.ert, bg=sc.bg).cpu().numpy()
+    assert np.array_equal(out, ref)
+
+
 def test_noalloc_frames_match_vi_render_on_two_calls_in_a_row(setup):
     ctx, vi, ph = setup
     sc = ph.blob64_shell(ert=0.95)
@@ -62,8 +94,7 @@ def test_noalloc_frames_match_vi_render_on_two_calls_in_a_row(setup):
         ref = ctx.render(sc.camera, W, H, sc.step_vox, ert=sc.ert, bg=sc.bg).cpu().numpy()
         rc, out = _noalloc(vi, ctx, sc, W, H, sc.ert)
         assert rc == vi.OK, vi.error_string(rc)
-        assert np.isfinite(out).all()
-        assert np.abs(out.astype(np.float64) - ref).max() <= IMAGE_TOL
+        assert np.array_equal(out, ref)
     # Same frame twice more: identical results, call after call.
     rc1, a = _noalloc(vi, ctx, sc, 256, 256, sc.ert)
     rc2, b = _noalloc(vi, ctx, sc, 256, 256, sc.ert)
