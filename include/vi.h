@@ -206,6 +206,56 @@ int vi_trace_pixel(vi_ctx* ctx, const vi_camera* camera, int W, int H, float ste
 /* Number of kernels this context has launched so far. */
 int vi_launch_count(vi_ctx* ctx, uint64_t* count);
 
+/* ---- Batched frames: one persistent launch over several contexts ---------- */
+
+/* Most frames one vi_render_batch call takes. */
+#define VI_BATCH_MAX_FRAMES 64
+
+/* One frame of a batch.  The paper renders one frame at a time (Section 4);
+   batching is a serving feature.  ctx supplies the volume, TF, light and
+   stack (built with VI_F32 or VI_F16 storage, transmittance, one shell, a
+   directional light; the options' slice_filter must be VI_SLICE_NEAREST).
+   camera, width, height, step_vox and opts as for vi_render; out_rgba is a
+   device pointer of width*height*4 float32 (caller-owned).  status is
+   written by the call: VI_OK, or VI_ETIMEOUT if the frame's stack was not
+   published in time (its output is then incomplete). */
+typedef struct {
+    vi_ctx* ctx;
+    vi_camera camera;
+    int width, height;
+    float step_vox;
+    float* out_rgba;
+    vi_render_opts opts;
+    int status;
+} vi_batch_frame;
+
+/* Publishes the context's stack to batched frames: enqueues on the context's
+   stream, after its work so far (normally its vi_build_attenuation), a device
+   write of a new epoch to the context's ready word, released to the whole
+   device.  A batch frame of this context waits for the latest epoch published
+   before the vi_render_batch call. */
+int vi_post_ready(vi_ctx* ctx);
+
+/* Renders `count` frames (1..VI_BATCH_MAX_FRAMES) in persistent launches on
+   `cuda_stream` (a cudaStream_t of the frames' device; NULL = the legacy
+   default stream), for callers that serve many small frames at once.  The
+   frames are grouped by kind (voxel type, storage format, mode); each group
+   is one launch whose frames are consecutive ranges of a queue of 4 x 8 pixel
+   tiles in device memory, and whose warps take (frame, tile) items from it in
+   order, so the warps that finish one frame go on with the next.
+   Before a frame's tiles a warp waits, on the device, until the frame's
+   context has published its stack with vi_post_ready (a context that never
+   published waits for its first epoch): at most wait_ms, measured on the
+   GPU's nanosecond timer.  A wait that runs out sets the frame's status to
+   VI_ETIMEOUT and the frame's remaining tiles are skipped; the kernel always
+   returns.  Each published frame equals the one vi_render gives from the
+   same context.  Synchronous: returns when the launch has finished, with every
+   status filled in; VI_OK if all frames rendered, VI_ETIMEOUT if any wait ran
+   out, VI_EINVAL for a frame outside the restrictions above, contexts of
+   different devices or wait_ms outside [0, 1e7], VI_ESTATE as vi_render for a
+   context without its inputs.  The stream must not be captured. */
+int vi_render_batch(vi_batch_frame* frames, int count, void* cuda_stream, double wait_ms);
+
 /* ---- Rendering without allocation ----------------------------------------- */
 
 /* Largest frame vi_render_host_noalloc takes: 512 x 512 pixels. */

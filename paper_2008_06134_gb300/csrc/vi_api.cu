@@ -16,6 +16,7 @@ using vi::CameraFrame;
 using vi::LightFrame;
 using vi::MarchParams;
 using vi::SweepParams;
+using vi::BatchFrame;
 
 namespace {
 
@@ -602,6 +603,25 @@ int vi_create(vi_ctx** out, int device, void* cuda_stream) {
     c->device = device;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     c->bopts = default_build_opts();
+    // The ready word of batched frames: zeroed on the context's stream, and an
+    // event after the zeroing that every batch waits for, so no batch reads the
+    // freshly allocated word before it is zero.
+    // It is a plain cudaMalloc of 256 bytes, outside the memory budget (a
+    // context made for a server gets the server's pool only after this).
+    if (cudaMalloc(reinterpret_cast<void**>(&c->ready), 256) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return VI_ENOMEM;
+    }
+    if (cudaEventCreateWithFlags(&c->ready_event, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMemsetAsync(c->ready, 0, 256, c->stream) != cudaSuccess ||
+        cudaEventRecord(c->ready_event, c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        if (c->ready_event) cudaEventDestroy(c->ready_event);
+        cudaFree(c->ready);
+        delete c;
+        return VI_ECUDA;
+    }
     *out = c;
     return VI_OK;
 }
@@ -620,6 +640,8 @@ int vi_destroy(vi_ctx* c) {
     release(c, reinterpret_cast<void**>(&c->tfcnt), &c->tfcnt_cap);
     release(c, reinterpret_cast<void**>(&c->bflags), &c->bflags_cap);
     release(c, reinterpret_cast<void**>(&c->counter), &c->counter_cap);
+    cudaFree(c->ready);
+    if (c->ready_event) cudaEventDestroy(c->ready_event);
     delete c;
     return VI_OK;
 }
@@ -907,6 +929,84 @@ int vi_render_host_noalloc(vi_ctx* c, const vi_camera* cam, int W, int H, float 
     if (e != cudaSuccess) return cuda_fail(c, e);
     e = cudaStreamSynchronize(c->stream);
     return cuda_fail(c, e);
+}
+
+int vi_post_ready(vi_ctx* c) {
+    vi_detail::NvtxRange nvtx_range("vi_post_ready");
+    int rc = enter(c);
+    if (rc) return rc;
+    cudaError_t e = vi::launch_post_ready(c->ready, c->post_epoch + 1u, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    ++c->post_epoch;
+    ++c->launches;
+    return VI_OK;
+}
+
+int vi_render_batch(vi_batch_frame* frames, int count, void* cuda_stream, double wait_ms) {
+    vi_detail::NvtxRange nvtx_range("vi_render_batch");
+    if (!frames || count < 1 || count > VI_BATCH_MAX_FRAMES) return VI_EINVAL;
+    if (!(wait_ms >= 0.0 && wait_ms <= 1e7)) return VI_EINVAL;
+    static_assert(VI_BATCH_MAX_FRAMES == vi::kBatchMaxFrames, "batch limit differs");
+    std::vector<BatchFrame> tab((size_t)count);
+    unsigned total = 0;
+    int device = -1;
+    for (int f = 0; f < count; ++f) {
+        vi_batch_frame& fr = frames[f];
+        fr.status = VI_OK;
+        vi_ctx* c = fr.ctx;
+        int rc = enter(c);
+        if (rc) return rc;
+        if (device < 0) device = c->device;
+        if (c->device != device) return VI_EINVAL;
+        rc = check_render_inputs(c, &fr.camera, fr.width, fr.height, fr.step_vox, &fr.opts);
+        if (rc) return rc;
+        if (!fr.out_rgba || fr.width < 1 || fr.height < 1) return VI_EINVAL;
+        const int fmt = c->mode == VI_NONE ? VI_F32 : c->bopts.format;
+        if ((fmt != VI_F32 && fmt != VI_F16) || c->bopts.quantity != VI_TRANSMITTANCE ||
+            c->bopts.shell_count > 1 || c->light_point ||
+            fr.opts.slice_filter != VI_SLICE_NEAREST)
+            return VI_EINVAL;
+        BatchFrame& b = tab[(size_t)f];
+        std::memset(&b, 0, sizeof(b));
+        rc = fill_march_params(c, &fr.camera, fr.width, fr.height, fr.step_vox, &fr.opts, &b.p);
+        if (rc) return rc;
+        b.p.out = reinterpret_cast<float4*>(fr.out_rgba);
+        b.ready = c->ready;
+        b.epoch = c->post_epoch ? c->post_epoch : 1u;  // never published: its first epoch
+        b.tiles_x = (unsigned)(fr.width + 3) / 4;
+        const unsigned tiles = b.tiles_x * ((unsigned)(fr.height + 7) / 8);
+        if (total + (unsigned long long)tiles > 0xffffffffull) return VI_EINVAL;
+        total += tiles;
+        b.kind = c->vr->vtype * 8 + fmt * 4 + c->mode;
+        b.index = f;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return VI_ECUDA;
+    }
+    // Every frame's ready word is zero before the batch reads it.
+    for (int f = 0; f < count; ++f)
+        if (cudaStreamWaitEvent(static_cast<cudaStream_t>(cuda_stream), frames[f].ctx->ready_event,
+                                0) != cudaSuccess) {
+            cudaGetLastError();
+            return VI_ECUDA;
+        }
+    std::vector<int> status((size_t)count, VI_OK);
+    const cudaError_t e = vi::launch_march_batch(tab.data(), count,
+                                                 (unsigned long long)(wait_ms * 1e6),
+                                                 status.data(),
+                                                 static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return VI_ECUDA;
+    }
+    int rc = VI_OK;
+    for (int f = 0; f < count; ++f) {
+        frames[f].status = status[(size_t)f];
+        if (status[(size_t)f] != VI_OK) rc = VI_ETIMEOUT;
+        ++frames[f].ctx->launches;
+    }
+    return rc;
 }
 
 int vi_debug_bounds(int device, uint64_t* violations, int* first_site, int64_t* first_index) {

@@ -80,6 +80,9 @@ struct vi_ctx {
     unsigned* counter = nullptr;  // tile counter of the persistent march kernel
     size_t counter_cap = 0;
     int march_block = 0;          // march block size cap (0: one 1024-thread block per SM)
+    unsigned* ready = nullptr;    // ready word batched frames wait on (vi_post_ready)
+    cudaEvent_t ready_event = nullptr;  // recorded after the ready word was zeroed
+    unsigned post_epoch = 0;      // the last epoch vi_post_ready enqueued
     // Set while the context's stream is being captured into a graph: no buffer
     // may grow then (an allocation would become part of the graph), so a call
     // that needs more memory fails instead (ctx_reserve sizes them first).

@@ -298,6 +298,85 @@ __device__ __forceinline__ float trilinear_fetch(const VolumeView& v, const Voxe
     return trilinear_octet<VoxT>(octet_load<VoxT>(v, o.idx), o);
 }
 
+// The footprint of a sample known to lie in the cube, as the march needs it:
+// the octet's voxel (the lower corners, clamped to the volume) and the weights
+// of the upper corners.  For such a sample x = P N - 1/2 lies in [-1/2, N - 1/2],
+// so floor(x) is -1 .. N - 1: at -1 the lower corner clamps to 0 and the
+// weight max(x - 0, 0) is 0 (the footprint collapses onto voxel 0), elsewhere
+// the weight is x - floor(x).  Same cells and weights as voxel_coord /
+// octet_ref, with fewer integer steps.
+struct FootprintCell {
+    int x0, y0, z0;
+    float wx, wy, wz;
+};
+
+__device__ __forceinline__ void footprint_axis(float P, float fn, int& i0, float& w) {
+    const float x = __fmaf_rn(P, fn, -0.5f);
+    const float f0 = fminf(fmaxf(floorf(x), 0.0f), fn - 1.0f);
+    i0 = (int)f0;
+    w = fmaxf(x - f0, 0.0f);
+}
+
+__device__ __forceinline__ FootprintCell footprint_cell(const VolumeView& v, float P0, float P1,
+                                                        float P2) {
+    FootprintCell c;
+    footprint_axis(P0, v.fnx, c.x0, c.wx);
+    footprint_axis(P1, v.fny, c.y0, c.wy);
+    footprint_axis(P2, v.fnz, c.z0, c.wz);
+    return c;
+}
+
+__device__ __forceinline__ size_t footprint_index(const VolumeView& v, const FootprintCell& c) {
+    return ((size_t)c.z0 * (size_t)v.ny + (size_t)c.y0) * (size_t)v.nx + (size_t)c.x0;
+}
+
+__device__ __forceinline__ bool footprint_may_be_lit(const GridView& g, const FootprintCell& c) {
+    if (!(VI_BOUNDS_OK(kSiteBrick, c.x0 >> kBrickShift, g.nbx) &&
+          VI_BOUNDS_OK(kSiteBrick, c.y0 >> kBrickShift, g.nby) &&
+          VI_BOUNDS_OK(kSiteBrick, c.z0 >> kBrickShift, g.nbz)))
+        return false;
+    const int b = ((c.z0 >> kBrickShift) * g.nby + (c.y0 >> kBrickShift)) * g.nbx +
+                  (c.x0 >> kBrickShift);
+    return __ldg(g.flags + b) != 0;
+}
+
+// Trilinear value of an octet at a footprint's weights.  uint16 voxels are
+// unpacked as 2^23 + v (one OR each) and the 2^23 taken off only the four
+// lower corners: differences of two such floats are exact, so the result is
+// the one trilinear_octet gives, bit for bit.
+template <typename VoxT>
+__device__ __forceinline__ float trilinear_cell(const typename Octet<VoxT>::V q,
+                                                const FootprintCell& c) {
+    float m[8];
+    if constexpr (sizeof(VoxT) == 2) {
+        m[0] = __uint_as_float(0x4b000000u | (q.x & 0xffffu));
+        m[1] = __uint_as_float(0x4b000000u | (q.x >> 16));
+        m[2] = __uint_as_float(0x4b000000u | (q.y & 0xffffu));
+        m[3] = __uint_as_float(0x4b000000u | (q.y >> 16));
+        m[4] = __uint_as_float(0x4b000000u | (q.z & 0xffffu));
+        m[5] = __uint_as_float(0x4b000000u | (q.z >> 16));
+        m[6] = __uint_as_float(0x4b000000u | (q.w & 0xffffu));
+        m[7] = __uint_as_float(0x4b000000u | (q.w >> 16));
+        constexpr float B = 8388608.0f;
+        const float c00 = fmaf(c.wx, m[1] - m[0], m[0] - B);
+        const float c01 = fmaf(c.wx, m[3] - m[2], m[2] - B);
+        const float c10 = fmaf(c.wx, m[5] - m[4], m[4] - B);
+        const float c11 = fmaf(c.wx, m[7] - m[6], m[6] - B);
+        const float c0 = fmaf(c.wy, c01 - c00, c00);
+        const float c1 = fmaf(c.wy, c11 - c10, c10);
+        return fmaf(c.wz, c1 - c0, c0);
+    } else {
+        Octet<VoxT>::unpack(q, m);
+        const float c00 = fmaf(c.wx, m[1] - m[0], m[0]);
+        const float c01 = fmaf(c.wx, m[3] - m[2], m[2]);
+        const float c10 = fmaf(c.wx, m[5] - m[4], m[4]);
+        const float c11 = fmaf(c.wx, m[7] - m[6], m[6]);
+        const float c0 = fmaf(c.wy, c01 - c00, c00);
+        const float c1 = fmaf(c.wy, c11 - c10, c10);
+        return fmaf(c.wz, c1 - c0, c0);
+    }
+}
+
 // Transfer function position of a value: x in [0, M - 1], entry i = floor(x)
 // (at most M - 2) and weight f = x - i.
 __device__ __forceinline__ void tf_coord(float v, float vmin, float scale, int M, int* i,

@@ -188,6 +188,27 @@ cudaError_t launch_volume_grid(const void* raw, int nx, int ny, int nz, int voxe
 // current device (looked up once per device; no allocation).
 constexpr size_t kNoallocMaxPixels = 512 * 512;
 cudaError_t noalloc_scratch(unsigned** counter, float4** image);
+// One frame of a batched launch (vi_render_batch): its march parameters, the
+// ready word its context publishes (vi_post_ready) and the epoch it must
+// reach, and its place in the batch's queue of tiles.
+struct BatchFrame {
+    MarchParams p;
+    const unsigned* ready;
+    unsigned epoch;
+    unsigned first_tile;  // the frame's first item in its launch's queue
+    unsigned tiles_x;     // tiles per row
+    int kind;             // voxel type * 8 + format * 4 + mode (formats F32 = 0, F16 = 1)
+    int index;            // the frame's place in the caller's list (its status word)
+};
+constexpr int kBatchMaxFrames = 64;
+// Renders a batch (see vi_render_batch): one persistent launch per kind of
+// frame present, and copies the frames' status words (VI_OK / VI_ETIMEOUT) to
+// status[count]; synchronous.
+cudaError_t launch_march_batch(const BatchFrame* frames, int count, unsigned long long wait_ns,
+                               int* status, cudaStream_t s);
+// Writes `epoch` to *ready on stream s, ordered after the stream's earlier work
+// and released to the whole device.
+cudaError_t launch_post_ready(unsigned* ready, unsigned epoch, cudaStream_t s);
 cudaError_t launch_brick_flags(const uint32_t* range, int nbricks, const int* lit_prefix, int M,
                                float vmin, float vmax, uint8_t* flags, cudaStream_t s);
 #if VI_DEBUG_BOUNDS

@@ -19,7 +19,9 @@
 #include <cuda.h>
 
 #include <mutex>
+#include <vector>
 
+#include "vi.h"
 #include "vi_device.cuh"
 
 // Unrolling of the default kernels' lookup loops: the cone's two rings and the
@@ -180,6 +182,18 @@ __device__ __forceinline__ float light_factor(const MarchParams& p, int n, int R
 
 enum { kEnded = 0, kContinue = 1, kStopped = 2, kEmpty = 3 };
 
+// The TF's alpha column, as the sample loop reads it: staged in shared memory
+// by a kernel that renders one frame, read through L1 from the TF itself by
+// the batched kernel (whose warps render several frames with their own TFs).
+struct SharedAlpha {
+    const float* a;
+    __device__ __forceinline__ float operator[](int e) const { return a[e]; }
+};
+struct GlobalAlpha {
+    const float4* tf;
+    __device__ __forceinline__ float operator[](int e) const { return __ldg(&tf[e].w); }
+};
+
 // Footprint cell of sample i (index path).
 __device__ __forceinline__ VoxelCoord sample_cell(const MarchParams& p, const Ray& r, int i,
                                                   float* t_out) {
@@ -256,18 +270,32 @@ __device__ __forceinline__ float point_light_factor(const MarchParams& p, float 
 // slice filtering, several shells); the default kernels compile without them.
 // POINT: a point light (coordinates per sample, scattering points built in
 // world space); it always takes the EXT lookups.
-template <typename VoxT, typename Fmt, int MODE, bool TRACE, bool EXT, bool POINT>
-__device__ __forceinline__ int march_sample(const MarchParams& p, const float* s_alpha,
+template <typename VoxT, typename Fmt, int MODE, bool TRACE, bool EXT, bool POINT, typename AlphaT>
+__device__ __forceinline__ int march_sample(const MarchParams& p, const AlphaT& s_alpha,
                                             const Ray& r, int i, float& C0, float& C1, float& C2,
                                             float& A, int& count, int& lit, int32_t* rec) {
-    float t;
-    const VoxelCoord vc = sample_cell(p, r, i, &t);
-    if (!(t < r.t1)) return kEnded;
-    if (!TRACE && !brick_may_be_lit(p.grid, vc)) {
-        ++count;
-        return A > p.ert ? kStopped : kEmpty;
+    float t, val;
+    VoxelCoord vc;  // the trace's record of the cell
+    if (TRACE) {
+        vc = sample_cell(p, r, i, &t);
+        if (!(t < r.t1)) return kEnded;
+        val = trilinear_fetch<VoxT>(p.vol, vc);
+    } else {
+        t = __fmaf_rn((float)i, p.cam.dt, r.t0);
+        if (!(t < r.t1)) return kEnded;
+        const FootprintCell fc = footprint_cell(p.vol, __fmaf_rn(t, r.d[0], r.o[0]),
+                                                __fmaf_rn(t, r.d[1], r.o[1]),
+                                                __fmaf_rn(t, r.d[2], r.o[2]));
+        // The octet load is issued before the brick flag is known: the two loads
+        // overlap, and a sample in a transparent brick drops its octet unused.
+        const size_t idx = footprint_index(p.vol, fc);
+        const typename Octet<VoxT>::V q = octet_load<VoxT>(p.vol, idx);
+        if (!footprint_may_be_lit(p.grid, fc)) {
+            ++count;
+            return A > p.ert ? kStopped : kEmpty;
+        }
+        val = trilinear_cell<VoxT>(q, fc);
     }
-    const float val = trilinear_fetch<VoxT>(p.vol, vc);
     int e;
     float f;
     tf_coord(val, p.tf_vmin, p.tf_scale, p.M, &e, &f);
@@ -492,6 +520,58 @@ __device__ __forceinline__ int centre_offset(int r) {
     return (r & 1) ? -((r + 1) >> 1) : (r >> 1);
 }
 
+// One warp's pixel tile (column tcol, row trow of the frame's kTileW x kTileH
+// tiles): ray set-up, the sample loop and the output.
+template <typename VoxT, typename Fmt, int MODE, bool EXT, bool POINT, typename AlphaT>
+__device__ __forceinline__ void march_tile(const MarchParams& p, const AlphaT& alpha, int tcol,
+                                           int trow, int lane) {
+    const int x = tcol * kTileW + (lane % kTileW);
+    const int y = trow * kTileH + (lane / kTileW);
+    const bool valid = x < p.cam.W && y < p.cam.H;
+    Ray r;
+    r.hit = false;
+    if (valid) ray_setup<POINT ? 1 : MODE>(p, x, y, r);
+
+    float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, A = 0.0f;
+    int count = 0, lit = 0;
+    bool active = valid && r.hit;
+    // The warp's rays advance in lockstep (same sample index), which keeps
+    // their gathers coherent.  All 32 lanes stay in the loop; it ends when
+    // the ballot finds none active.  When every active lane sits in a brick
+    // that cannot yield alpha > 0, the warp skips together to the end of
+    // the shortest such run (each lane's run is verified exactly).
+    for (int i = 0; __any_sync(0xffffffffu, active);) {
+        int st = kEnded;
+        if (active)
+            st = march_sample<VoxT, Fmt, MODE, false, EXT, POINT>(p, alpha, r, i, C0, C1, C2, A,
+                                                                  count, lit, nullptr);
+        active = active && (st == kContinue || st == kEmpty);
+        const unsigned act = __ballot_sync(0xffffffffu, active);
+        const unsigned emp = __ballot_sync(0xffffffffu, active && st == kEmpty);
+        int to = i + 1;
+        if (act != 0u && emp == act) {
+            int next = 0x7fffffff;
+            if (active) {
+                float t;
+                const VoxelCoord vc = sample_cell(p, r, i, &t);
+                next = last_transparent(p, r, i, t, vc) + 1;
+            }
+            to = __reduce_min_sync(0xffffffffu, next);
+            if (active) count += to - i - 1;  // the rest of the run: transparent
+        }
+        i = to;
+    }
+    if (valid && VI_BOUNDS_OK(kSitePixel, (long long)y * p.cam.W + x,
+                              (long long)p.cam.W * p.cam.H)) {
+        const size_t idx = (size_t)y * p.cam.W + x;
+        const float rem = 1.0f - A;
+        p.out[idx] = make_float4(fmaf(rem, p.bg[0], C0), fmaf(rem, p.bg[1], C1),
+                                 fmaf(rem, p.bg[2], C2), fmaf(rem, p.bg[3], A));
+        if (p.counts) p.counts[idx] = count;
+        if (p.lit) p.lit[idx] = lit;
+    }
+}
+
 template <typename VoxT, typename Fmt, int MODE, bool EXT, bool POINT>
 __global__ void __launch_bounds__(kMarchThreads, VI_MARCH_MIN_BLOCKS)
     march_kernel(const MarchParams p) {
@@ -504,6 +584,7 @@ __global__ void __launch_bounds__(kMarchThreads, VI_MARCH_MIN_BLOCKS)
     const unsigned ntiles = tiles_x * tiles_y;
     const bool rows_out =
         kTileOrderAdaptive && ntiles <= kCentreOutTiles * gridDim.x * (blockDim.x / 32);
+    const SharedAlpha alpha{s_alpha};
     for (;;) {
         unsigned tile = 0;
         if (lane == 0) tile = atomicAdd(p.tile_counter, 1u);
@@ -511,52 +592,107 @@ __global__ void __launch_bounds__(kMarchThreads, VI_MARCH_MIN_BLOCKS)
         if (tile >= ntiles) break;
         int tcol = (int)(tile % tiles_x), trow = (int)(tile / tiles_x);
         if (rows_out) trow = (int)(tiles_y / 2) + centre_offset(trow);
-        const int x = tcol * kTileW + (lane % kTileW);
-        const int y = trow * kTileH + (lane / kTileW);
-        const bool valid = x < p.cam.W && y < p.cam.H;
-        Ray r;
-        r.hit = false;
-        if (valid) ray_setup<POINT ? 1 : MODE>(p, x, y, r);
-
-        float C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, A = 0.0f;
-        int count = 0, lit = 0;
-        bool active = valid && r.hit;
-        // The warp's rays advance in lockstep (same sample index), which keeps
-        // their gathers coherent.  All 32 lanes stay in the loop; it ends when
-        // the ballot finds none active.  When every active lane sits in a brick
-        // that cannot yield alpha > 0, the warp skips together to the end of
-        // the shortest such run (each lane's run is verified exactly).
-        for (int i = 0; __any_sync(0xffffffffu, active);) {
-            int st = kEnded;
-            if (active)
-                st = march_sample<VoxT, Fmt, MODE, false, EXT, POINT>(p, s_alpha, r, i, C0, C1,
-                                                                      C2, A, count, lit, nullptr);
-            active = active && (st == kContinue || st == kEmpty);
-            const unsigned act = __ballot_sync(0xffffffffu, active);
-            const unsigned emp = __ballot_sync(0xffffffffu, active && st == kEmpty);
-            int to = i + 1;
-            if (act != 0u && emp == act) {
-                int next = 0x7fffffff;
-                if (active) {
-                    float t;
-                    const VoxelCoord vc = sample_cell(p, r, i, &t);
-                    next = last_transparent(p, r, i, t, vc) + 1;
-                }
-                to = __reduce_min_sync(0xffffffffu, next);
-                if (active) count += to - i - 1;  // the rest of the run: transparent
-            }
-            i = to;
-        }
-        if (valid && VI_BOUNDS_OK(kSitePixel, (long long)y * p.cam.W + x,
-                                  (long long)p.cam.W * p.cam.H)) {
-            const size_t idx = (size_t)y * p.cam.W + x;
-            const float rem = 1.0f - A;
-            p.out[idx] = make_float4(fmaf(rem, p.bg[0], C0), fmaf(rem, p.bg[1], C1),
-                                     fmaf(rem, p.bg[2], C2), fmaf(rem, p.bg[3], A));
-            if (p.counts) p.counts[idx] = count;
-            if (p.lit) p.lit[idx] = lit;
-        }
+        march_tile<VoxT, Fmt, MODE, EXT, POINT>(p, alpha, tcol, trow, lane);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Batched frames: persistent launches over several contexts' frames, one per
+// kind of frame (voxel type, storage format, mode).  A launch's frames are
+// consecutive ranges of a queue of pixel tiles in device memory; warps take
+// (frame, tile) items in queue order from an atomic counter.  Before a frame's tiles, a warp waits until the frame's context has
+// published its stack (vi_post_ready: an epoch released to the device after
+// the context's earlier work) -- at most wait_ns on the GPU's nanosecond
+// timer.  A wait that runs out marks the frame VI_ETIMEOUT in its status word
+// and the frame's remaining tiles are skipped: the kernel always returns.
+// Each frame reads its TF's alpha through L1 (the frames have different TFs)
+// and its parameters from the batch's table.
+
+constexpr int kBatchThreads = 256;
+
+__device__ __forceinline__ unsigned load_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// True once *ready has reached epoch (wrap-safe); false if wait_ns passes
+// first.  Two clocks bound the wait: the GPU's nanosecond timer, and the SM's
+// cycle counter at four cycles a nanosecond (twice the part's 2.07 GHz), so the
+// wait ends even if one of them stood still.
+__device__ __noinline__ bool wait_ready(const unsigned* ready, unsigned epoch,
+                                        unsigned long long wait_ns) {
+    if ((int)(load_acquire(ready) - epoch) >= 0) return true;
+    const unsigned long long t0 = global_ns();
+    const long long c0 = clock64();
+    const long long cycles = (long long)(wait_ns > (1ull << 60) ? (1ull << 60) : wait_ns) * 4;
+    for (;;) {
+        __nanosleep(200);
+        if ((int)(load_acquire(ready) - epoch) >= 0) return true;
+        if (global_ns() - t0 > wait_ns || clock64() - c0 > cycles) return false;
+    }
+}
+
+// One kind of frame (voxel type, storage format, mode) per launch: the frames
+// of a batch are grouped by kind and each group gets a persistent launch.
+template <typename VoxT, typename Fmt, int MODE>
+__global__ void __launch_bounds__(kBatchThreads, 4)
+    march_batch_kernel(const BatchFrame* __restrict__ frames, int nframes, unsigned total,
+                       unsigned* counter, int* status, unsigned long long wait_ns) {
+    const int lane = threadIdx.x & 31;
+    int f = 0, ready_f = -1;
+    for (;;) {
+        unsigned item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= total) break;
+        while (f + 1 < nframes && item >= frames[f + 1].first_tile) ++f;  // items in queue order
+        const BatchFrame& bf = frames[f];
+        if (ready_f != f) {
+            int ok = 0;
+            if (lane == 0) {
+                int* st = &status[bf.index];
+                ok = *(volatile int*)st == VI_OK && wait_ready(bf.ready, bf.epoch, wait_ns);
+                if (!ok) atomicExch(st, VI_ETIMEOUT);
+            }
+            if (!__shfl_sync(0xffffffffu, ok, 0)) continue;  // skip the frame's tile
+            ready_f = f;
+        }
+        const unsigned tile = item - bf.first_tile;
+        march_tile<VoxT, Fmt, MODE, false, false>(bf.p, GlobalAlpha{bf.p.tf},
+                                                  (int)(tile % bf.tiles_x),
+                                                  (int)(tile / bf.tiles_x), lane);
+    }
+}
+
+using BatchKernel = void (*)(const BatchFrame*, int, unsigned, unsigned*, int*,
+                             unsigned long long);
+
+BatchKernel batch_kernel_of(int kind) {
+    switch (kind) {
+#define VI_BATCH_CASE(K, V, F, M) \
+    case K: return march_batch_kernel<V, F, M>;
+        VI_BATCH_CASE(0, uint8_t, F32, 0) VI_BATCH_CASE(1, uint8_t, F32, 1)
+        VI_BATCH_CASE(2, uint8_t, F32, 2) VI_BATCH_CASE(3, uint8_t, F32, 3)
+        VI_BATCH_CASE(4, uint8_t, F16, 0) VI_BATCH_CASE(5, uint8_t, F16, 1)
+        VI_BATCH_CASE(6, uint8_t, F16, 2) VI_BATCH_CASE(7, uint8_t, F16, 3)
+        VI_BATCH_CASE(8, uint16_t, F32, 0) VI_BATCH_CASE(9, uint16_t, F32, 1)
+        VI_BATCH_CASE(10, uint16_t, F32, 2) VI_BATCH_CASE(11, uint16_t, F32, 3)
+        VI_BATCH_CASE(12, uint16_t, F16, 0) VI_BATCH_CASE(13, uint16_t, F16, 1)
+        VI_BATCH_CASE(14, uint16_t, F16, 2) VI_BATCH_CASE(15, uint16_t, F16, 3)
+#undef VI_BATCH_CASE
+    }
+    return nullptr;
+}
+
+__global__ void post_ready_kernel(unsigned* ready, unsigned epoch) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(ready), "r"(epoch) : "memory");
 }
 
 template <typename VoxT, typename Fmt, int MODE, bool POINT>
@@ -573,7 +709,7 @@ __global__ void trace_kernel(const MarchParams p, int x, int y, int32_t* rec, in
     if (r.hit) {
         for (int i = 0; nrec < max_rec; ++i) {
             int32_t* out = rec + (size_t)nrec * kTraceWords;
-            int st = march_sample<VoxT, Fmt, MODE, true, true, POINT>(p, s_alpha, r, i, C0, C1,
+            int st = march_sample<VoxT, Fmt, MODE, true, true, POINT>(p, SharedAlpha{s_alpha}, r, i, C0, C1,
                                                                       C2, A, count, lit, out);
             if (st == kEnded) break;
             ++nrec;
@@ -664,6 +800,74 @@ cudaError_t launch_march(const MarchParams& p, int voxel_type, int format, int m
                          cudaStream_t s) {
     if (voxel_type == 0) return dispatch_fmt<uint8_t>(p, format, mode, false, 0, 0, nullptr, 0, nullptr, s);
     return dispatch_fmt<uint16_t>(p, format, mode, false, 0, 0, nullptr, 0, nullptr, s);
+}
+
+cudaError_t launch_march_batch(const BatchFrame* frames, int count, unsigned long long wait_ns,
+                               int* status, cudaStream_t s) {
+    if (count < 1 || count > kBatchMaxFrames) return cudaErrorInvalidValue;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    // The frames grouped by kind (in their order within a kind), each group's
+    // tiles numbered from 0: one queue and one launch per group.
+    std::vector<BatchFrame> tab;
+    std::vector<int> group_first, group_kind;
+    std::vector<unsigned> group_tiles;
+    for (int kind = 0; kind < 16; ++kind) {
+        unsigned tiles = 0;
+        const size_t first = tab.size();
+        for (int f = 0; f < count; ++f) {
+            if (frames[f].kind != kind) continue;
+            BatchFrame b = frames[f];
+            b.first_tile = tiles;
+            tiles += b.tiles_x * ((unsigned)(b.p.cam.H + kTileH - 1) / kTileH);
+            tab.push_back(b);
+        }
+        if (tab.size() == first) continue;
+        if (!batch_kernel_of(kind)) return cudaErrorInvalidValue;
+        group_first.push_back((int)first);
+        group_kind.push_back(kind);
+        group_tiles.push_back(tiles);
+    }
+    if ((int)tab.size() != count) return cudaErrorInvalidValue;  // a frame of no known kind
+    // One allocation, ordered on the stream: the table, the status words, the
+    // groups' counters.
+    const size_t tab_bytes = tab.size() * sizeof(BatchFrame);
+    const size_t bytes = tab_bytes + 256 + 256;
+    char* d = nullptr;
+    e = cudaMallocAsync(reinterpret_cast<void**>(&d), bytes, s);
+    if (e != cudaSuccess) return e;
+    int* d_status = reinterpret_cast<int*>(d + tab_bytes);
+    unsigned* d_counter = reinterpret_cast<unsigned*>(d + tab_bytes + 256);
+    e = cudaMemcpyAsync(d, tab.data(), tab_bytes, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d + tab_bytes, 0, 512, s);  // VI_OK is 0
+    const BatchFrame* d_tab = reinterpret_cast<const BatchFrame*>(d);
+    for (size_t g = 0; e == cudaSuccess && g < group_kind.size(); ++g) {
+        const int first = group_first[g];
+        const int n = (g + 1 < group_first.size() ? group_first[g + 1] : count) - first;
+        // At most two blocks of 256 threads per SM (half its registers): the
+        // rest stays free for the sweeps the frames wait on, which run on the
+        // contexts' streams, so a wait never starves the work it waits for.
+        const unsigned per_block = kBatchThreads / 32;
+        unsigned blocks = (group_tiles[g] + per_block - 1) / per_block;
+        if (blocks > (unsigned)(2 * sms)) blocks = (unsigned)(2 * sms);
+        batch_kernel_of(group_kind[g])<<<blocks, kBatchThreads, 0, s>>>(
+            d_tab + first, n, group_tiles[g], d_counter + g, d_status, wait_ns);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(status, d_status, (size_t)count * sizeof(int), cudaMemcpyDeviceToHost,
+                            s);
+    const cudaError_t ef = cudaFreeAsync(d, s);
+    if (e == cudaSuccess) e = ef;
+    const cudaError_t es = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? es : e;
+}
+
+cudaError_t launch_post_ready(unsigned* ready, unsigned epoch, cudaStream_t s) {
+    post_ready_kernel<<<1, 1, 0, s>>>(ready, epoch);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_trace(const MarchParams& p, int voxel_type, int format, int mode, int x, int y,

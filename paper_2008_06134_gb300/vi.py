@@ -37,7 +37,7 @@ EXPORTS = ("vi_create", "vi_destroy", "vi_set_memory_budget", "vi_load_volume",
            "vi_set_transfer_function", "vi_set_light", "vi_set_point_light",
            "vi_build_attenuation", "vi_render", "vi_sync", "vi_error_string",
            "vi_attenuation_info", "vi_get_attenuation", "vi_trace_pixel", "vi_launch_count",
-           "vi_render_host_noalloc", "vi_debug_bounds", "vi_server_create", "vi_server_destroy",
+           "vi_post_ready", "vi_render_batch", "vi_render_host_noalloc", "vi_debug_bounds", "vi_server_create", "vi_server_destroy",
            "vi_server_add_volume", "vi_server_submit", "vi_server_wait", "vi_server_cancel",
            "vi_server_timing", "vi_server_release", "vi_server_get_stats",
            "vi_server_set_graphs")
@@ -65,6 +65,12 @@ class RenderOpts(C.Structure):
     _fields_ = [("ert", C.c_float), ("bg", C.c_float * 4), ("ambient", C.c_float),
                 ("opacity_correction", C.c_int), ("sample_counts", C.c_void_p),
                 ("lit_counts", C.c_void_p), ("slice_filter", C.c_int)]
+
+
+class BatchFrame(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("camera", Camera), ("width", C.c_int),
+                ("height", C.c_int), ("step_vox", C.c_float), ("out_rgba", C.c_void_p),
+                ("opts", RenderOpts), ("status", C.c_int)]
 
 
 class Request(C.Structure):
@@ -117,6 +123,8 @@ def library(checked: bool = False) -> C.CDLL:
     L.vi_trace_pixel.argtypes = [vp, P(Camera), i, i, f, P(RenderOpts), i, i, vp, i, P(i)]
     L.vi_launch_count.argtypes = [vp, P(C.c_uint64)]
     L.vi_render_host_noalloc.argtypes = [vp, P(Camera), i, i, f, vp, P(RenderOpts)]
+    L.vi_post_ready.argtypes = [vp]
+    L.vi_render_batch.argtypes = [P(BatchFrame), i, vp, C.c_double]
     d, u64 = C.c_double, C.c_uint64
     L.vi_server_create.argtypes = [P(vp), i, i, sz, i]
     L.vi_server_destroy.argtypes = [vp]
@@ -331,10 +339,51 @@ class Context:
                                              C.byref(ro)), "vi_render_host_noalloc")
         return out
 
+    def post_ready(self) -> None:
+        """vi_post_ready: publish this context's stack to batched frames."""
+        _check(self.L.vi_post_ready(self.h), "vi_post_ready")
+
     def launch_count(self) -> int:
         v = C.c_uint64(0)
         _check(self.L.vi_launch_count(self.h, C.byref(v)), "vi_launch_count")
         return int(v.value)
+
+
+BATCH_MAX_FRAMES = 64
+
+
+def render_batch(frames, stream=None, wait_ms: float = 1000.0):
+    """vi_render_batch: render several contexts' frames in persistent launches.
+
+    ``frames`` is a list of dicts with keys ctx, cam, W, H, step_vox, out (an
+    (H, W, 4) float32 CUDA tensor) and optionally ert, bg, sample_counts.
+    Returns (rc, statuses): the call's status and each frame's (VI_OK or
+    VI_ETIMEOUT); argument errors raise ViError."""
+    n = len(frames)
+    arr = (BatchFrame * n)()
+    keep = []
+    for k, fr in enumerate(frames):
+        p, dev = _ptr(fr["out"])
+        if not dev:
+            raise ValueError("batched frames render into device tensors")
+        arr[k].ctx = fr["ctx"].h
+        arr[k].camera = camera(fr["cam"])
+        arr[k].width, arr[k].height = int(fr["W"]), int(fr["H"])
+        arr[k].step_vox = float(fr["step_vox"])
+        arr[k].out_rgba = p
+        arr[k].opts = Context._render_opts(fr.get("ert", 2.0), fr.get("bg", (0, 0, 0, 0)), 0.0, 0,
+                                           sample_counts=fr.get("sample_counts"))
+        keep.append(fr["out"])
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    L = frames[0]["ctx"].L
+    rc = L.vi_render_batch(arr, n, C.c_void_p(int(stream)), float(wait_ms))
+    if rc not in (OK, ETIMEOUT):
+        raise ViError(rc, "vi_render_batch")
+    return rc, [arr[k].status for k in range(n)]
 
 
 def decode_stack(raw: np.ndarray, fmt: int) -> np.ndarray:
