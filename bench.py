@@ -59,17 +59,22 @@ NCU_MARCH_COUNTERS = {"inst_executed": 620_166_423, "lts_sectors": 14_062_604,
                       "lts_throughput_frac": 0.0284}
 
 
-def march_bounds(march_s: float, sms: int, clock_mhz: float, peaks: dict):
+def march_bounds(march_s: float, sms: int, clock_mhz: float, peaks: dict, probe: dict):
     """The march's three candidate bounds (HBM, L2, instruction issue) with the
-    binding one named; counters from the capture, time from this run."""
+    binding one named: DRAM bytes, L2 sectors and warp instructions from the
+    capture of this kernel, time and clock from this run, the L2 peak from the
+    probe kernel."""
     if ncu_traffic("march_kernel") is None:
         return None
     traffic = ncu_traffic("march_kernel")
     c = NCU_MARCH_COUNTERS
     issue_slots = march_s * sms * 4 * clock_mhz * 1e6     # one warp instruction / cycle / SMSP
+    l2_gbs = c["lts_sectors"] * 32 / march_s / 1e9
     out = {"hbm": {"bytes": traffic, "gbs": round(traffic / march_s / 1e9, 1),
                    "frac": round(traffic / march_s / 1e9 / peaks["hbm_gbs"], 4)},
-           "l2": {"bytes": c["lts_sectors"] * 32, "frac": c["lts_throughput_frac"]},
+           "l2": {"bytes": c["lts_sectors"] * 32, "gbs": round(l2_gbs, 1),
+                  "frac": round(l2_gbs / probe["l2_read_gbs"], 4),
+                  "peak_gbs": round(probe["l2_read_gbs"], 1), "peak_source": "probe kernel"},
            "issue": {"warp_instructions": c["inst_executed"],
                      "frac": round(c["inst_executed"] / issue_slots, 4)},
            "source": "counters from the ncu capture of this kernel (profiles/); time and "
@@ -96,6 +101,9 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-baseline-only", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--no-summaries", action="store_true",
+                    help="leave the serving and precision summaries out of the headline line")
     ap.add_argument("--workload", default="ct256-cone",
                     choices=["ct256-cone", "precision", "scalability", "serving", "variants",
                              "large", "oracle"],
@@ -271,7 +279,27 @@ def cpu_baseline(scene, min_seconds: float = 10.0, max_frames: int = 4):
                       f"{done / bands:.3g} frames, FP64, {secs:.1f} s"}
 
 
+def cpu_baseline_fresh(timeout_s: float = 600.0):
+    """cpu_baseline in a fresh process: this one holds a CUDA context and
+    torch's thread pools, which measured up to 1.7x slower oracle bands than a
+    process of its own (the reference arm's conditions)."""
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-only"],
+                       capture_output=True, text=True, timeout=timeout_s, cwd=ROOT)
+    for line in reversed(r.stdout.splitlines()):
+        if line.startswith("{"):
+            out = json.loads(line)
+            out["process"] = "fresh (python bench.py --cpu-baseline-only)"
+            return out
+    return {"unavailable": f"cpu baseline process exited {r.returncode}: {r.stderr[-300:]}"}
+
+
 def reference_arm(args):
+    """The FP64 oracle as it stands, timed on this host's cores.  Each step is
+    one band of the headline frame: 1/8 of the sweep's texel rows and 1/8 of
+    the image rows, the bands taken in turn over the frame (the same sample as
+    cpu_baseline, wide enough for every core); ms_per_step is the measured
+    mean time of a step, and frames/s is one over the sum of the eight bands'
+    mean times."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
@@ -279,23 +307,31 @@ def reference_arm(args):
     from paper_2008_06134_gb300 import phantoms as ph
     scene = ph.ct256_cone()
     light, stack = oracle_setup(scene)
-    bands = 64
+    bands = 8
     for w in range(args.warmup):
         oracle_sample(scene, bands, w % bands, stack, light)
-    secs = [oracle_sample(scene, bands, s % bands, stack, light) for s in range(args.steps)]
+    secs, per_band = [], {}
+    for s in range(args.steps):
+        t = oracle_sample(scene, bands, s % bands, stack, light)
+        secs.append(t)
+        per_band.setdefault(s % bands, []).append(t)
     total = sum(secs)
-    fps = args.steps / (total * bands)
+    # A frame is the sum of its bands' mean times (bands differ in cost: the
+    # middle ones cross the phantom), so any step count gives an unbiased rate.
+    frame_s = sum(statistics.mean(v) for v in per_band.values()) * bands / len(per_band)
+    fps = 1.0 / frame_s
     line = {"metric": "frames/s", "value": round(fps, 5), "unit": "frames/s", "impl": "reference",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(1000 * total * bands / args.steps, 3),
+            "ms_per_step": round(1000 * total / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "impl": "FP64 CPU oracle (oracle/vi_oracle.c)"},
+            "config": {"workload": WORKLOAD, "impl": "FP64 CPU oracle (oracle/vi_oracle.c)",
+                       "step": f"1/{bands} of a frame (a band of texel rows and image rows)"},
             "cpu_baseline": {"value": round(fps, 5), "unit": "frames/s", "kind": "oracle",
-                             "cores": oracle.threads(),
-                             "sample": f"each step: 1/{bands} of the texel rows of the sweep "
-                                       f"+ 1/{bands} of the image rows, bands rotating over "
-                                       f"the frame; frames/s scaled x{bands}"},
+                             "cores": oracle.threads(), "cpu": cpu_model(),
+                             "sample": f"{args.steps} steps, each 1/{bands} of the texel rows "
+                                       f"of the sweep + 1/{bands} of the image rows, bands "
+                                       f"rotating over the frame; {total:.1f} s timed"},
             "e2e": {"value": round(fps, 5), "unit": "frames/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -351,6 +387,8 @@ def gb300_arm(args):
         flush.fill_(0)
         build_stack()
         render()
+    # Roofline denominators of this device, measured by probe kernels.
+    probe = vi.measure_peaks(local)
     K = args.steps
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
     clocks = ClockSampler(local)
@@ -405,15 +443,15 @@ def gb300_arm(args):
         serial = job_throughput(K, world, max_over_ranks(secs, dist, "cuda"))
 
         # Pipelined: two contexts on two streams, so step s + 1's upload and
-        # sweep overlap step s's march and read-back.  Every step still copies
-        # its volume and TF from pinned host memory and reads its frame back;
-        # the host waits for a frame before its buffers are reused.
+        # sweep overlap step s's march and read-back.  Every step copies its
+        # volume and TF from pinned host memory and reads its frame back into
+        # pinned host memory, all through the C ABI (vi_render with
+        # VI_OUT_HOST_ASYNC; vi_sync completes the frame); the host waits for
+        # a frame before its buffers are reused.
         streams = [torch.cuda.Stream(local), torch.cuda.Stream(local)]
         ctxs = [vi.Context(local, stream=st) for st in streams]
-        dev_out = [torch.empty((H, W, 4), dtype=torch.float32, device="cuda") for _ in range(2)]
         host_out = [torch.empty((H, W, 4), dtype=torch.float32, pin_memory=True)
                     for _ in range(2)]
-        done = [torch.cuda.Event() for _ in range(2)]
         flushes = [torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda") for _ in range(2)]
         checksum = 0.0
 
@@ -427,14 +465,12 @@ def gb300_arm(args):
             c.set_light(sc.light_dir, sc.light_color)
             c.build_attenuation(sc.n_slices, sc.slice_res, sc.mode,
                                 cone_half_angle_deg=sc.cone_half_angle_deg)
-            c.render(sc.camera, W, H, sc.step_vox, out=dev_out[b], ert=sc.ert, bg=sc.bg)
-            with torch.cuda.stream(st):
-                host_out[b].copy_(dev_out[b], non_blocking=True)
-            done[b].record(st)
+            c.render(sc.camera, W, H, sc.step_vox, out=host_out[b], ert=sc.ert, bg=sc.bg,
+                     host_async=True)
 
         def collect(s):
             nonlocal checksum
-            done[s & 1].synchronize()
+            ctxs[s & 1].sync()
             checksum += float(host_out[s & 1][H // 2, W // 2, 3])   # the host reads the frame
 
         for s in range(args.warmup):
@@ -458,7 +494,8 @@ def gb300_arm(args):
                "h2d_bytes_per_step": int(sc.volume.nbytes + tf.nbytes),
                "d2h_bytes_per_step": int(H * W * 16),
                "pipeline": "2 contexts on 2 streams; step s+1's upload and sweep overlap "
-                           "step s's march and read-back",
+                           "step s's march and read-back; the frame comes back through "
+                           "vi_render (VI_OUT_HOST_ASYNC) into pinned memory, vi_sync per frame",
                "one_at_a_time_value": round(serial, 3)}
 
     if rank != 0:
@@ -476,15 +513,18 @@ def gb300_arm(args):
                   "kernel": "sweep_kernel",
                   "peak_source": f"{peak_kind} HBM copy bandwidth"}
     flops = samples * FLOPS_BASE + lit_samples * FLOPS_LIT[sc.mode]
-    fp32_peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * peaks["sm_max_mhz"] / 1e6
+    nominal_fp32 = props.multi_processor_count * FP32_LANES_PER_SM * 2 * peaks["sm_max_mhz"] / 1e6
+    fp32_peak = probe["fp32_tflops"]
     march_roof = {"bound": "alu", "achieved": round(flops / march_s / 1e12, 3),
                   "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
                   "frac": round(flops / march_s / 1e12 / fp32_peak, 4),
                   "traffic": ncu_traffic("march_kernel"), "algorithmic_flops": int(flops),
                   "kernel": "march_kernel",
-                  "peak_source": f"FP32 FMA rate: {props.multi_processor_count} SMs x "
-                                 f"{FP32_LANES_PER_SM} lanes x 2 x {peaks['sm_max_mhz']} MHz "
-                                 f"({peak_kind} max clock)"}
+                  "peak_source": "measured by probe: vi_measure_peaks (eight independent FMA "
+                                 "chains per thread on every SM, best of 3 launches) in this "
+                                 f"run; nominal {props.multi_processor_count} SMs x "
+                                 f"{FP32_LANES_PER_SM} lanes x 2 x {peaks['sm_max_mhz']} MHz = "
+                                 f"{nominal_fp32:.1f}"}
     dominant, other = (march_roof, sweep_roof) if march_s >= sweep_s else (sweep_roof, march_roof)
     clock_mhz = clock.get("sm_mhz") or peaks["sm_max_mhz"]
     frames = world * K
@@ -504,7 +544,9 @@ def gb300_arm(args):
         "samples_per_frame": samples, "lit_samples_per_frame": lit_samples,
         "sweep_ms": round(sweep_s * 1e3, 4), "march_ms": round(march_s * 1e3, 4),
         "warm_frames_per_s": round(1.0 / march_s, 2),      # march only, stack cached
-        "march_bounds": march_bounds(march_s, props.multi_processor_count, clock_mhz, peaks),
+        "march_bounds": march_bounds(march_s, props.multi_processor_count, clock_mhz, peaks,
+                                     probe),
+        "peaks_probe": {k: round(v, 1) for k, v in probe.items()},
         "wall_s": round(wall, 3),
         "roofline": dominant, "roofline_other": other,
         "gpu_launches": int(launches),
@@ -512,9 +554,17 @@ def gb300_arm(args):
         "e2e": e2e,
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(sc)
-    print(json.dumps(line), flush=True)
+        line["cpu_baseline"] = cpu_baseline_fresh()
     ctx.close()
+    del out, flush, counts, lit
+    torch.cuda.empty_cache()
+    if world == 1 and not args.no_summaries:
+        # The other configs' headline figures, so that every run records them:
+        # the served reduced-precision path against the plain FP32 path
+        # (config 4), and the storage formats' error against the oracle (config 3).
+        line["serving"] = serving_summary(args)
+        line["precision"] = precision_summary(args)
+    print(json.dumps(line), flush=True)
 
 
 def timed_frames(ctx, build, render, flush, steps):
@@ -535,10 +585,11 @@ def timed_frames(ctx, build, render, flush, steps):
     return statistics.mean(sw), statistics.mean(ma)
 
 
-def precision_workload(args):
-    """Storage formats FP32 / FP16 / BF16 / UNORM16 on the 512^3 blob scene:
-    frames/s of each and its per-channel error against the FP64 oracle on the
-    centred 256x144 crop (the oracle builds its own FP64 stack)."""
+def precision_rows(steps: int, warmup: int, modes=("shell", "cone"), depth: bool = True):
+    """Storage formats FP32 / FP16 / BF16 / UNORM16 on the 512^3 blob scene
+    (config 3): frames/s of each and its per-channel error against the FP64
+    oracle on the centred 256x144 crop (the oracle builds its own FP64 stack).
+    Returns (scene name, oracle seconds, rows)."""
     import numpy as np
     import torch
 
@@ -550,25 +601,29 @@ def precision_workload(args):
     W, H = sc.width, sc.height
     x0, y0 = (W - 256) // 2, (H - 144) // 2
     ys, xs = np.mgrid[y0:y0 + 144, x0:x0 + 256]
+    mode_of = {"shell": vi.SHELL, "cone": vi.CONE}
     t0 = time.perf_counter()
     light = oracle.light_setup(sc.light_dir, sc.n_slices, sc.slice_res)
     ref_stack = oracle.build_stack(sc.volume, sc.tf, sc.vmin, sc.vmax, light)
     refs = {}
-    for mode in (vi.SHELL, vi.CONE):
-        ro = oracle.render_opts(mode, sc.step_vox, sc.ert, sc.bg, sc.light_color,
+    for mname in modes:
+        ro = oracle.render_opts(mode_of[mname], sc.step_vox, sc.ert, sc.bg, sc.light_color,
                                 cone_half_angle_deg=sc.cone_half_angle_deg)
-        refs[mode] = oracle.render_pixels(sc.volume, sc.tf, sc.vmin, sc.vmax, light, ref_stack,
-                                          sc.camera, W, H, ro, xs.ravel(), ys.ravel())[0]
+        refs[mode_of[mname]] = oracle.render_pixels(sc.volume, sc.tf, sc.vmin, sc.vmax, light,
+                                                    ref_stack, sc.camera, W, H, ro, xs.ravel(),
+                                                    ys.ravel())[0]
     del ref_stack
-    # The extinction form (Eq. 5-6) against the oracle's own optical-depth frame.
-    depth_stack = oracle.build_stack(sc.volume, sc.tf, sc.vmin, sc.vmax, light,
-                                     quantity=oracle.OPTICAL_DEPTH)
-    ro = oracle.render_opts(vi.CONE, sc.step_vox, sc.ert, sc.bg, sc.light_color,
-                            cone_half_angle_deg=sc.cone_half_angle_deg,
-                            quantity=oracle.OPTICAL_DEPTH)
-    depth_ref = oracle.render_pixels(sc.volume, sc.tf, sc.vmin, sc.vmax, light, depth_stack,
-                                     sc.camera, W, H, ro, xs.ravel(), ys.ravel())[0]
-    del depth_stack
+    depth_ref = None
+    if depth:
+        # The extinction form (Eq. 5-6) against the oracle's own optical-depth frame.
+        depth_stack = oracle.build_stack(sc.volume, sc.tf, sc.vmin, sc.vmax, light,
+                                         quantity=oracle.OPTICAL_DEPTH)
+        ro = oracle.render_opts(vi.CONE, sc.step_vox, sc.ert, sc.bg, sc.light_color,
+                                cone_half_angle_deg=sc.cone_half_angle_deg,
+                                quantity=oracle.OPTICAL_DEPTH)
+        depth_ref = oracle.render_pixels(sc.volume, sc.tf, sc.vmin, sc.vmax, light, depth_stack,
+                                         sc.camera, W, H, ro, xs.ravel(), ys.ravel())[0]
+        del depth_stack
     oracle_s = time.perf_counter() - t0
     ctx = vi.Context(0)
     ctx.load_volume(torch.from_numpy(sc.volume.view(np.int16)).cuda(), dtype=vi.U16)
@@ -578,10 +633,11 @@ def precision_workload(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     names = {vi.F32: "f32", vi.F16: "f16", vi.BF16: "bf16", vi.UNORM16: "unorm16"}
     rows = {}
-    cases = [(mode, mname, fmt, vi.TRANSMITTANCE) for mode, mname in
-             ((vi.SHELL, "shell"), (vi.CONE, "cone"))
+    cases = [(mode_of[mname], mname, fmt, vi.TRANSMITTANCE) for mname in modes
              for fmt in (vi.F32, vi.F16, vi.BF16, vi.UNORM16)]
-    cases += [(vi.CONE, "cone-depth", fmt, vi.OPTICAL_DEPTH) for fmt in (vi.F32, vi.F16, vi.BF16)]
+    if depth:
+        cases += [(vi.CONE, "cone-depth", fmt, vi.OPTICAL_DEPTH)
+                  for fmt in (vi.F32, vi.F16, vi.BF16)]
     for mode, mname, fmt, quantity in cases:
         def bld():
             ctx.build_attenuation(sc.n_slices, sc.slice_res, mode, format=fmt,
@@ -589,10 +645,10 @@ def precision_workload(args):
 
         def rnd():
             ctx.render(sc.camera, W, H, sc.step_vox, out=out, ert=sc.ert, bg=sc.bg)
-        for _ in range(args.warmup):
+        for _ in range(warmup):
             bld()
             rnd()
-        sweep_ms, march_ms = timed_frames(ctx, bld, rnd, flush, args.steps)
+        sweep_ms, march_ms = timed_frames(ctx, bld, rnd, flush, steps)
         img = out.cpu().numpy().astype(np.float64)[y0:y0 + 144, x0:x0 + 256].reshape(-1, 4)
         err = np.abs(img - (depth_ref if quantity == vi.OPTICAL_DEPTH else refs[mode]))
         rows[f"{mname}-{names[fmt]}"] = {
@@ -600,14 +656,41 @@ def precision_workload(args):
             "sweep_ms": round(sweep_ms, 4), "march_ms": round(march_ms, 4),
             "max_abs_err_rgba": [float(f"{v:.3g}") for v in err.max(axis=0)],
             "mean_abs_err_rgba": [float(f"{v:.3g}") for v in err.mean(axis=0)]}
-    for mname in ("shell", "cone", "cone-depth"):
+    for mname in tuple(modes) + (("cone-depth",) if depth else ()):
         base = rows[f"{mname}-f32"]["frames_per_s"]
         for fmt in names.values():
             if f"{mname}-{fmt}" in rows:
                 rows[f"{mname}-{fmt}"]["gain_vs_f32"] = round(
                     rows[f"{mname}-{fmt}"]["frames_per_s"] / base, 3)
+    ctx.close()
+    del out, flush
+    torch.cuda.empty_cache()
+    return sc.name, oracle_s, rows
+
+
+def precision_summary(args):
+    """The headline line's precision figures: config 3's cone frames in each
+    storage format, their max error per RGBA channel against the FP64 oracle
+    (256x144 crop) and their frame rate against FP32."""
+    import oracle
+    name, oracle_s, rows = precision_rows(max(3, min(args.steps, 10)), 3, modes=("cone",),
+                                          depth=False)
+    return {"scene": name, "error_reference": f"FP64 oracle, centred 256x144 crop "
+                                              f"({oracle_s:.1f} s on {oracle.threads()} cores)",
+            "formats": {k: {"max_abs_err_rgba": v["max_abs_err_rgba"],
+                            "frames_per_s": v["frames_per_s"],
+                            "gain_vs_f32": v["gain_vs_f32"]} for k, v in rows.items()}}
+
+
+def precision_workload(args):
+    """Storage formats FP32 / FP16 / BF16 / UNORM16 on the 512^3 blob scene:
+    frames/s of each and its per-channel error against the FP64 oracle on the
+    centred 256x144 crop (the oracle builds its own FP64 stack)."""
+    import oracle
+    name, oracle_s, rows = precision_rows(args.steps, args.warmup)
+    sc_name = name
     print(json.dumps({"workload": "precision", "metric": "frames/s", "unit": "frames/s",
-                      "scene": sc.name, "steps": args.steps, "warmup": args.warmup,
+                      "scene": sc_name, "steps": args.steps, "warmup": args.warmup,
                       "error_reference": "FP64 oracle, centred 256x144 crop "
                                          f"({oracle_s:.1f} s on {oracle.threads()} cores)",
                       "results": rows}), flush=True)
@@ -855,18 +938,11 @@ def oracle_workload(args):
                       "rows": rows}), flush=True)
 
 
-def serving_workload(args):
-    """The render server on the serving mix: 8 registered volumes ({128, 256,
-    512}^3, uint8 blobs and uint16 CT ellipsoids) with at most 6 resident under
-    a fixed HBM budget, and a seeded stream of requests (256^2 to 1920x1080,
-    64-512 slices of 256^2 or 512^2, shadow / shell / cone, light and view
-    uniform on the sphere).  Runs: one slot with FP32 stacks (one frame at a
-    time: the plain path), and `--slots` concurrent slots with FP32 and with
-    FP16 stacks, each under Poisson arrivals at `--rate` and as one burst, and
-    the FP32 served runs again with each request's device work launched as one
-    CUDA graph.
-    Reports per run frames/s and request latency (submission to completion)
-    percentiles; the FP32 served frames are compared with the plain ones."""
+def serving_setup(args):
+    """The serving mix (config 4): the registered volumes in pinned host memory,
+    the request streams per Poisson rate, and run(slots, fmt, burst, reqs,
+    graphs, batching), which serves one stream on a fresh server and returns
+    (row of frames/s and latency percentiles, frames)."""
     import numpy as np
     import torch
     from concurrent.futures import ThreadPoolExecutor
@@ -891,10 +967,10 @@ def serving_workload(args):
                         q["slice_res"], q["mode"], q["camera"], q["width"], q["height"],
                         q["step_vox"], out, format=fmt, ert=q["ert"])
 
-    def run(slots, fmt, burst, reqs, graphs=False):
+    def run(slots, fmt, burst, reqs, graphs=False, batching=False):
         outs = [torch.empty((q["height"], q["width"], 4), device="cuda") for q in reqs]
         with vi.Server(0, slots=slots, memory_budget=budget, max_resident_volumes=6,
-                       graphs=graphs) as s:
+                       graphs=graphs, batching=batching) as s:
             vids = [s.add_volume(h, c) for h, c in zip(host, codes)]
             warm = torch.empty((64, 64, 4), device="cuda")
             for i in range(len(specs)):           # untimed: load every volume once
@@ -932,7 +1008,63 @@ def serving_workload(args):
         if graphs:
             row["graph_launches"] = st["graph_launches"] - base["graph_launches"]
             row["graph_instantiations"] = st["graph_instantiations"]
+        if batching:
+            row["batches"] = st["batches"] - base["batches"]
+            row["batched_frames"] = st["batched_frames"] - base["batched_frames"]
         return row, outs
+
+    return dict(specs=specs, rates=rates, mixes=mixes, budget=budget, run=run, t_gen=t_gen)
+
+
+def serving_summary(args):
+    """The headline line's serving figures: 512 requests of the serving mix at
+    800/s, the plain path (one slot, one frame at a time, FP32 stacks) against
+    the served reduced-precision path (8 slots, FP16 stacks; per-slot marches
+    and batched marches), with the served frames' max error against the plain
+    FP32 frames."""
+    import torch
+    from paper_2008_06134_gb300 import vi
+    a = argparse.Namespace(**vars(args))
+    a.rate, a.requests, a.slots = "800", 512, 8
+    sv = serving_setup(a)
+    reqs = sv["mixes"][800.0]
+    out = {"requests": 512, "rate_per_s": 800, "slots": 8, "budget_gib": a.budget_gib,
+           "max_resident_volumes": 6}
+    plain, plain_outs = sv["run"](1, vi.F32, False, reqs)
+    out["plain-f32-1slot"] = {k: plain[k] for k in ("frames_per_s", "latency_ms", "failed")}
+    for name, batching in (("served-f16-8slots", False), ("served-f16-8slots-batched", True)):
+        row, outs = sv["run"](8, vi.F16, False, reqs, batching=batching)
+        err = max(float((x - y).abs().max()) for x, y in zip(outs, plain_outs))
+        out[name] = {k: row[k] for k in ("frames_per_s", "latency_ms", "failed")}
+        out[name]["max_abs_err_vs_plain_f32"] = float(f"{err:.3g}")
+        del outs
+    p99 = {k: out[k]["latency_ms"]["p99"] for k in out if isinstance(out[k], dict)}
+    out["served_f16_beats_plain_f32_p99"] = min(p99["served-f16-8slots"],
+                                                p99["served-f16-8slots-batched"]) \
+        <= p99["plain-f32-1slot"]
+    del plain_outs
+    torch.cuda.empty_cache()
+    return out
+
+
+def serving_workload(args):
+    """The render server on the serving mix: 8 registered volumes ({128, 256,
+    512}^3, uint8 blobs and uint16 CT ellipsoids) with at most 6 resident under
+    a fixed HBM budget, and a seeded stream of requests (256^2 to 1920x1080,
+    64-512 slices of 256^2 or 512^2, shadow / shell / cone, light and view
+    uniform on the sphere).  Runs: one slot with FP32 stacks (one frame at a
+    time: the plain path), and `--slots` concurrent slots with FP32 and with
+    FP16 stacks, each under Poisson arrivals at `--rate` and as one burst; the
+    FP32 served runs again with each request's device work launched as one
+    CUDA graph, and the served runs with batched marches.
+    Reports per run frames/s and request latency (submission to completion)
+    percentiles; the FP32 served frames are compared with the plain ones."""
+    import torch
+    from paper_2008_06134_gb300 import vi
+    sv = serving_setup(args)
+    specs, rates, mixes, budget, run = (sv["specs"], sv["rates"], sv["mixes"], sv["budget"],
+                                        sv["run"])
+    t_gen = sv["t_gen"]
 
     runs = {}
     for rate in rates:
@@ -955,12 +1087,27 @@ def serving_workload(args):
                                                for a, b in zip(outs, plain_outs))
         runs[f"served-f32-graphs-{args.slots}slots-poisson{rate:g}"] = row
         del outs
+        # Batched marches: the requests admitted together march as one batch.
+        for fmt, fname in ((vi.F32, "f32"), (vi.F16, "f16")):
+            row, outs = run(args.slots, fmt, False, reqs, batching=True)
+            if fmt == vi.F32:
+                row["frames_identical_to_plain"] = sum(bool(torch.equal(a, b))
+                                                       for a, b in zip(outs, plain_outs))
+            else:
+                err = max(float((a - b).abs().max()) for a, b in zip(outs, plain_outs))
+                row["max_abs_err_vs_plain_f32"] = float(f"{err:.3g}")
+            runs[f"served-{fname}-batched-{args.slots}slots-poisson{rate:g}"] = row
+            del outs
         del plain_outs
     # Capacity: every request of the first mix submitted at once.
-    for slots, name, graphs in ((1, "plain-f32-1slot-burst", False),
-                                (args.slots, f"served-f32-{args.slots}slots-burst", False),
-                                (args.slots, f"served-f32-graphs-{args.slots}slots-burst", True)):
-        runs[name] = run(slots, vi.F32, True, mixes[rates[0]], graphs=graphs)[0]
+    for slots, name, fmt, graphs, batching in (
+            (1, "plain-f32-1slot-burst", vi.F32, False, False),
+            (args.slots, f"served-f32-{args.slots}slots-burst", vi.F32, False, False),
+            (args.slots, f"served-f16-{args.slots}slots-burst", vi.F16, False, False),
+            (args.slots, f"served-f32-graphs-{args.slots}slots-burst", vi.F32, True, False),
+            (args.slots, f"served-f32-batched-{args.slots}slots-burst", vi.F32, False, True),
+            (args.slots, f"served-f16-batched-{args.slots}slots-burst", vi.F16, False, True)):
+        runs[name] = run(slots, fmt, True, mixes[rates[0]], graphs=graphs, batching=batching)[0]
     print(json.dumps({"workload": "serving", "metric": "frames/s", "unit": "frames/s",
                       "requests": args.requests, "rates_per_s": rates, "slots": args.slots,
                       "budget_bytes": budget, "max_resident_volumes": 6,
@@ -972,7 +1119,10 @@ def serving_workload(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.cpu_baseline_only:
+        from paper_2008_06134_gb300 import phantoms as ph
+        print(json.dumps(cpu_baseline(ph.ct256_cone())), flush=True)
+    elif args.impl == "reference":
         reference_arm(args)
     elif args.workload == "precision":
         precision_workload(args)

@@ -165,10 +165,15 @@ int vi_build_attenuation(vi_ctx* ctx, int n_slices, int slice_res, int mode,
    step_vox voxels from where the ray enters the unit cube (a voxel is
    1/max(nx,ny,nz); step_vox in [1e-3, 1e3] and sqrt(3) max(nx,ny,nz) / step_vox
    <= 2^24), front-to-back compositing with the mode's coefficient.
-   out_rgba: W*H*4 float32, row-major RGBA, caller-owned; a device pointer
-   (out_on_device = 1, written asynchronously) or host memory (0, filled when
-   the call returns).  W or H == 0 renders nothing.  VI_ESTATE if the volume
-   or TF is missing or the stack (modes other than VI_NONE) is stale. */
+   out_rgba: W*H*4 float32, row-major RGBA, caller-owned, where out_on_device
+   says: VI_OUT_DEVICE (1): a device pointer, written asynchronously on the
+   context's stream; VI_OUT_HOST (0): host memory, filled when the call
+   returns; VI_OUT_HOST_ASYNC (2): host memory, the frame's copy enqueued on
+   the context's stream and complete at the next vi_sync (page-locked memory
+   lets the copy overlap other work; the buffer must stay valid until then).
+   W or H == 0 renders nothing.  VI_ESTATE if the volume or TF is missing or
+   the stack (modes other than VI_NONE) is stale. */
+enum { VI_OUT_HOST = 0, VI_OUT_DEVICE = 1, VI_OUT_HOST_ASYNC = 2 };
 int vi_render(vi_ctx* ctx, const vi_camera* camera, int W, int H, float step_vox,
               float* out_rgba, int out_on_device, const vi_render_opts* opts);
 
@@ -185,7 +190,8 @@ int vi_attenuation_info(vi_ctx* ctx, int* n_slices, int* slice_res, int* format,
                         size_t* bytes);
 
 /* Copy the stack as stored ([n][R][R] of the storage format) into `out`
-   (out_bytes >= the stack's size); out_on_device as for vi_render.  Waits for
+   (out_bytes >= the stack's size); out_on_device as for vi_render (a host
+   buffer is filled before the call returns in either host mode).  Waits for
    the copy. */
 int vi_get_attenuation(vi_ctx* ctx, void* out, size_t out_bytes, int out_on_device);
 
@@ -205,6 +211,14 @@ int vi_trace_pixel(vi_ctx* ctx, const vi_camera* camera, int W, int H, float ste
 
 /* Number of kernels this context has launched so far. */
 int vi_launch_count(vi_ctx* ctx, uint64_t* count);
+
+/* Roofline denominators measured on `device` by probe kernels (not part of
+   the method): *fp32_tflops, the FP32 FMA rate of eight independent FMA
+   chains per thread on every SM; *l2_read_gbs, the read bandwidth of a buffer
+   of a quarter of L2 read repeatedly through L2 by every SM.  Each is the
+   best of three timed launches (CUDA events) after one warm-up.  Allocates
+   and frees its buffers; synchronous. */
+int vi_measure_peaks(int device, double* fp32_tflops, double* l2_read_gbs);
 
 /* ---- Batched frames: one persistent launch over several contexts ---------- */
 
@@ -232,8 +246,8 @@ typedef struct {
 /* Publishes the context's stack to batched frames: enqueues on the context's
    stream, after its work so far (normally its vi_build_attenuation), a device
    write of a new epoch to the context's ready word, released to the whole
-   device.  A batch frame of this context waits for the latest epoch published
-   before the vi_render_batch call. */
+   device, and records an event after it.  A batch frame of this context
+   renders the state published last before the vi_render_batch call. */
 int vi_post_ready(vi_ctx* ctx);
 
 /* Renders `count` frames (1..VI_BATCH_MAX_FRAMES) in persistent launches on
@@ -243,12 +257,15 @@ int vi_post_ready(vi_ctx* ctx);
    is one launch whose frames are consecutive ranges of a queue of 4 x 8 pixel
    tiles in device memory, and whose warps take (frame, tile) items from it in
    order, so the warps that finish one frame go on with the next.
-   Before a frame's tiles a warp waits, on the device, until the frame's
-   context has published its stack with vi_post_ready (a context that never
-   published waits for its first epoch): at most wait_ms, measured on the
-   GPU's nanosecond timer.  A wait that runs out sets the frame's status to
-   VI_ETIMEOUT and the frame's remaining tiles are skipped; the kernel always
-   returns.  Each published frame equals the one vi_render gives from the
+   The batch is ordered on the stream after each frame's last publication
+   (vi_post_ready's event): a kernel that spun on work of another stream could
+   hold that work up, since streams share the GPU's hardware work queues.
+   Before a frame's tiles a warp still checks, on the device, that the
+   frame's context has published (a context that never published waits for
+   its first epoch): it waits at most wait_ms, measured on the GPU's
+   nanosecond timer and bounded by the SM clock as well.  A wait that runs out
+   sets the frame's status to VI_ETIMEOUT and the frame's remaining tiles are
+   skipped; the kernel always returns.  Each published frame equals the one vi_render gives from the
    same context.  Synchronous: returns when the launch has finished, with every
    status filled in; VI_OK if all frames rendered, VI_ETIMEOUT if any wait ran
    out, VI_EINVAL for a frame outside the restrictions above, contexts of
@@ -343,7 +360,7 @@ typedef struct {
     float step_vox;
     vi_render_opts render;
     float* out_rgba;
-    int out_on_device;
+    int out_on_device;  /* VI_OUT_DEVICE or VI_OUT_HOST (VI_EINVAL otherwise) */
 } vi_request;
 
 typedef struct {
@@ -354,6 +371,8 @@ typedef struct {
     uint64_t stack_reuses;  /* requests that rendered from a slot's kept stack */
     uint64_t graph_launches;        /* requests whose device work ran as one CUDA graph */
     uint64_t graph_instantiations;  /* executable graphs created (the rest were updated) */
+    uint64_t batches;               /* batches of marches enqueued (vi_server_set_batching) */
+    uint64_t batched_frames;        /* frames marched in those batches */
 } vi_server_stats;
 
 /* Create / destroy a server (destroy cancels queued requests, lets running
@@ -405,6 +424,21 @@ int vi_server_get_stats(vi_server* server, vi_server_stats* stats);
    whose host output is pageable memory (not capturable) runs with separate
    launches.  Returns VI_EINVAL for a null server. */
 int vi_server_set_graphs(vi_server* server, int enabled);
+
+/* Batched marches (1) or one march per request on its slot's stream (0, the
+   default); applies to requests admitted after the call.  With batching, the
+   requests admitted in one pass of the scheduler run their uploads and
+   sweeps on their slots' streams as before and publish their stacks
+   (vi_post_ready); their marches are then enqueued together as one batch of
+   persistent launches on the server's batch stream (vi_render_batch's
+   kernels), each frame's tiles waiting on the device for its slot's stack for
+   at most wait_ms (VI_ETIMEOUT fails the request).  Requests outside
+   vi_render_batch's restrictions (BF16 / UNORM16 stacks, optical depth,
+   several shells, linear slices) keep their own march.  Batching takes
+   precedence over graphs for the requests it batches.  Returns VI_EINVAL for
+   a null server or wait_ms outside [0, 1e7], VI_ECUDA if the batch stream
+   or the status words cannot be made. */
+int vi_server_set_batching(vi_server* server, int enabled, double wait_ms);
 
 #ifdef __cplusplus
 }

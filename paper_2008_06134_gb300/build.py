@@ -17,7 +17,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-SOURCES = ["vi_api.cu", "vi_sweep.cu", "vi_march.cu", "vi_grid.cu", "vi_server.cu"]
+SOURCES = ["vi_api.cu", "vi_sweep.cu", "vi_march.cu", "vi_grid.cu", "vi_server.cu", "vi_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # variant -> (library, object folder, extra defines)
 VARIANTS = {

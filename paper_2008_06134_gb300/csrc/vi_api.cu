@@ -554,6 +554,53 @@ int ctx_render_async(vi_ctx* c, const vi_camera* cam, int W, int H, float step_v
     return VI_OK;
 }
 
+int ctx_batch_frame(vi_ctx* c, const vi_camera* cam, int W, int H, float step_vox, float* out,
+                    int out_on_device, const vi_render_opts* opts, BatchFrame* b) {
+    int rc = enter(c);
+    if (rc) return rc;
+    vi_render_opts ro = opts ? *opts : default_render_opts();
+    rc = check_render_inputs(c, cam, W, H, step_vox, &ro);
+    if (rc) return rc;
+    if (W < 1 || H < 1 || !out) return VI_EINVAL;
+    const int fmt = c->mode == VI_NONE ? VI_F32 : c->bopts.format;
+    if ((fmt != VI_F32 && fmt != VI_F16) || c->bopts.quantity != VI_TRANSMITTANCE ||
+        c->bopts.shell_count > 1 || c->light_point || ro.slice_filter != VI_SLICE_NEAREST)
+        return VI_EINVAL;
+    std::memset(b, 0, sizeof(*b));
+    rc = fill_march_params(c, cam, W, H, step_vox, &ro, &b->p);
+    if (rc) return rc;
+    if (out_on_device) {
+        b->p.out = reinterpret_cast<float4*>(out);
+    } else {
+        rc = ensure(c, reinterpret_cast<void**>(&c->out), &c->out_cap,
+                    (size_t)W * (size_t)H * sizeof(float4));
+        if (rc) return rc;
+        b->p.out = c->out;
+    }
+    b->ready = c->ready;
+    b->epoch = c->post_epoch ? c->post_epoch : 1u;  // never published: its first epoch
+    b->tiles_x = (unsigned)(W + 3) / 4;
+    b->kind = c->vr->vtype * 8 + fmt * 4 + c->mode;
+    return VI_OK;
+}
+
+cudaError_t enqueue_batch(vi_ctx* const* ctxs, const BatchFrame* frames, int count,
+                          unsigned long long wait_ns, int* const* status_dst, cudaStream_t s) {
+    // Every frame's ready word is zero before the batch reads it, and the batch
+    // starts after each context's last publication: streams share the GPU's
+    // hardware work queues once there are more streams than queues, so a kernel
+    // spinning on another stream's later work could hold up that very work.
+    // The device-side wait stays as a bounded check (it returns at once here),
+    // and runs out only for a context that never published.
+    for (int f = 0; f < count; ++f) {
+        cudaError_t e = cudaStreamWaitEvent(s, ctxs[f]->ready_event, 0);
+        if (e == cudaSuccess && ctxs[f]->post_epoch)
+            e = cudaStreamWaitEvent(s, ctxs[f]->posted_event, 0);
+        if (e != cudaSuccess) return e;
+    }
+    return vi::enqueue_march_batch(frames, count, wait_ns, status_dst, s);
+}
+
 int ctx_reserve(vi_ctx* c, int build_stack, int n, int R, int fmt, int W, int H,
                 int out_on_device) {
     int rc = enter(c);
@@ -614,10 +661,12 @@ int vi_create(vi_ctx** out, int device, void* cuda_stream) {
         return VI_ENOMEM;
     }
     if (cudaEventCreateWithFlags(&c->ready_event, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->posted_event, cudaEventDisableTiming) != cudaSuccess ||
         cudaMemsetAsync(c->ready, 0, 256, c->stream) != cudaSuccess ||
         cudaEventRecord(c->ready_event, c->stream) != cudaSuccess) {
         cudaGetLastError();
         if (c->ready_event) cudaEventDestroy(c->ready_event);
+        if (c->posted_event) cudaEventDestroy(c->posted_event);
         cudaFree(c->ready);
         delete c;
         return VI_ECUDA;
@@ -642,6 +691,7 @@ int vi_destroy(vi_ctx* c) {
     release(c, reinterpret_cast<void**>(&c->counter), &c->counter_cap);
     cudaFree(c->ready);
     if (c->ready_event) cudaEventDestroy(c->ready_event);
+    if (c->posted_event) cudaEventDestroy(c->posted_event);
     delete c;
     return VI_OK;
 }
@@ -810,8 +860,12 @@ int vi_build_attenuation(vi_ctx* c, int n, int R, int mode, const vi_build_opts*
 int vi_render(vi_ctx* c, const vi_camera* cam, int W, int H, float step_vox, float* out,
               int out_on_device, const vi_render_opts* opts) {
     vi_detail::NvtxRange nvtx_range("vi_render");
-    int rc = vi_detail::ctx_render_async(c, cam, W, H, step_vox, out, out_on_device, opts);
-    if (rc || out_on_device || W == 0 || H == 0) return rc;
+    if (out_on_device != VI_OUT_HOST && out_on_device != VI_OUT_DEVICE &&
+        out_on_device != VI_OUT_HOST_ASYNC)
+        return VI_EINVAL;
+    const bool device = out_on_device == VI_OUT_DEVICE;
+    int rc = vi_detail::ctx_render_async(c, cam, W, H, step_vox, out, device ? 1 : 0, opts);
+    if (rc || out_on_device != VI_OUT_HOST || W == 0 || H == 0) return rc;
     return cuda_fail(c, cudaStreamSynchronize(c->stream));
 }
 
@@ -848,6 +902,10 @@ int vi_get_attenuation(vi_ctx* c, void* out, size_t out_bytes, int out_on_device
     if (rc) return rc;
     if (!c->stack_valid) return VI_ESTATE;
     if (!out || out_bytes < c->stack_bytes) return VI_EINVAL;
+    if (out_on_device != VI_OUT_HOST && out_on_device != VI_OUT_DEVICE &&
+        out_on_device != VI_OUT_HOST_ASYNC)
+        return VI_EINVAL;
+    out_on_device = out_on_device == VI_OUT_DEVICE;  // the copy is waited for either way
     const int n = c->lt.n, R = c->lt.R;
     const size_t row = (size_t)R * format_bytes(c->bopts.format);
     for (int k = 0; k < n; ++k) {
@@ -936,6 +994,7 @@ int vi_post_ready(vi_ctx* c) {
     int rc = enter(c);
     if (rc) return rc;
     cudaError_t e = vi::launch_post_ready(c->ready, c->post_epoch + 1u, c->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(c->posted_event, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e);
     ++c->post_epoch;
     ++c->launches;
@@ -948,54 +1007,33 @@ int vi_render_batch(vi_batch_frame* frames, int count, void* cuda_stream, double
     if (!(wait_ms >= 0.0 && wait_ms <= 1e7)) return VI_EINVAL;
     static_assert(VI_BATCH_MAX_FRAMES == vi::kBatchMaxFrames, "batch limit differs");
     std::vector<BatchFrame> tab((size_t)count);
-    unsigned total = 0;
     int device = -1;
     for (int f = 0; f < count; ++f) {
         vi_batch_frame& fr = frames[f];
         fr.status = VI_OK;
-        vi_ctx* c = fr.ctx;
-        int rc = enter(c);
+        if (!fr.ctx) return VI_EINVAL;
+        if (device < 0) device = fr.ctx->device;
+        if (fr.ctx->device != device) return VI_EINVAL;
+        if (!fr.out_rgba) return VI_EINVAL;
+        const int rc = vi_detail::ctx_batch_frame(fr.ctx, &fr.camera, fr.width, fr.height,
+                                                  fr.step_vox, fr.out_rgba, 1, &fr.opts,
+                                                  &tab[(size_t)f]);
         if (rc) return rc;
-        if (device < 0) device = c->device;
-        if (c->device != device) return VI_EINVAL;
-        rc = check_render_inputs(c, &fr.camera, fr.width, fr.height, fr.step_vox, &fr.opts);
-        if (rc) return rc;
-        if (!fr.out_rgba || fr.width < 1 || fr.height < 1) return VI_EINVAL;
-        const int fmt = c->mode == VI_NONE ? VI_F32 : c->bopts.format;
-        if ((fmt != VI_F32 && fmt != VI_F16) || c->bopts.quantity != VI_TRANSMITTANCE ||
-            c->bopts.shell_count > 1 || c->light_point ||
-            fr.opts.slice_filter != VI_SLICE_NEAREST)
-            return VI_EINVAL;
-        BatchFrame& b = tab[(size_t)f];
-        std::memset(&b, 0, sizeof(b));
-        rc = fill_march_params(c, &fr.camera, fr.width, fr.height, fr.step_vox, &fr.opts, &b.p);
-        if (rc) return rc;
-        b.p.out = reinterpret_cast<float4*>(fr.out_rgba);
-        b.ready = c->ready;
-        b.epoch = c->post_epoch ? c->post_epoch : 1u;  // never published: its first epoch
-        b.tiles_x = (unsigned)(fr.width + 3) / 4;
-        const unsigned tiles = b.tiles_x * ((unsigned)(fr.height + 7) / 8);
-        if (total + (unsigned long long)tiles > 0xffffffffull) return VI_EINVAL;
-        total += tiles;
-        b.kind = c->vr->vtype * 8 + fmt * 4 + c->mode;
-        b.index = f;
+        tab[(size_t)f].index = f;
     }
     if (cudaSetDevice(device) != cudaSuccess) {
         cudaGetLastError();
         return VI_ECUDA;
     }
-    // Every frame's ready word is zero before the batch reads it.
-    for (int f = 0; f < count; ++f)
-        if (cudaStreamWaitEvent(static_cast<cudaStream_t>(cuda_stream), frames[f].ctx->ready_event,
-                                0) != cudaSuccess) {
-            cudaGetLastError();
-            return VI_ECUDA;
-        }
+    const cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     std::vector<int> status((size_t)count, VI_OK);
-    const cudaError_t e = vi::launch_march_batch(tab.data(), count,
-                                                 (unsigned long long)(wait_ms * 1e6),
-                                                 status.data(),
-                                                 static_cast<cudaStream_t>(cuda_stream));
+    std::vector<int*> dst((size_t)count);
+    for (int f = 0; f < count; ++f) dst[(size_t)f] = &status[(size_t)f];
+    std::vector<vi_ctx*> ctxs((size_t)count);
+    for (int f = 0; f < count; ++f) ctxs[(size_t)f] = frames[f].ctx;
+    cudaError_t e = vi_detail::enqueue_batch(ctxs.data(), tab.data(), count,
+                                             (unsigned long long)(wait_ms * 1e6), dst.data(), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return VI_ECUDA;

@@ -82,6 +82,7 @@ struct vi_ctx {
     int march_block = 0;          // march block size cap (0: one 1024-thread block per SM)
     unsigned* ready = nullptr;    // ready word batched frames wait on (vi_post_ready)
     cudaEvent_t ready_event = nullptr;  // recorded after the ready word was zeroed
+    cudaEvent_t posted_event = nullptr; // recorded after the last vi_post_ready
     unsigned post_epoch = 0;      // the last epoch vi_post_ready enqueued
     // Set while the context's stream is being captured into a graph: no buffer
     // may grow then (an allocation would become part of the graph), so a call
@@ -128,6 +129,17 @@ void ctx_trim(vi_ctx* c);
 // buffer overlaps; a pageable one makes the copy synchronous).
 int ctx_render_async(vi_ctx* c, const vi_camera* cam, int W, int H, float step_vox, float* out,
                      int out_on_device, const vi_render_opts* opts);
+// The batched frame of context c (vi_render's checks and parameters; a host
+// output is staged in the context's buffer), or a vi_status.  b->index is
+// left to the caller.
+int ctx_batch_frame(vi_ctx* c, const vi_camera* cam, int W, int H, float step_vox, float* out,
+                    int out_on_device, const vi_render_opts* opts, vi::BatchFrame* b);
+// Enqueues a batch on stream s (after every frame's ready word was zeroed):
+// its persistent launches, then a copy of frame f's status word to
+// status_dst[f] (host memory); returns without waiting.
+cudaError_t enqueue_batch(vi_ctx* const* ctxs, const vi::BatchFrame* frames, int count,
+                          unsigned long long wait_ns, int* const* status_dst, cudaStream_t s);
+
 // Grows, ahead of a capture, every buffer a build of an n x R x R stack of
 // format fmt (build_stack != 0) and a W x H render (host output staging when
 // out_on_device is 0) will use, so that the calls inside the capture allocate

@@ -201,11 +201,12 @@ struct BatchFrame {
     int index;            // the frame's place in the caller's list (its status word)
 };
 constexpr int kBatchMaxFrames = 64;
-// Renders a batch (see vi_render_batch): one persistent launch per kind of
-// frame present, and copies the frames' status words (VI_OK / VI_ETIMEOUT) to
-// status[count]; synchronous.
-cudaError_t launch_march_batch(const BatchFrame* frames, int count, unsigned long long wait_ns,
-                               int* status, cudaStream_t s);
+// Enqueues a batch (see vi_render_batch) on stream s: one persistent launch
+// per kind of frame present, then a copy of frame f's status word (VI_OK /
+// VI_ETIMEOUT) to the host address status_dst[f] (page-locked for the copy to
+// be asynchronous).  Returns without waiting.
+cudaError_t enqueue_march_batch(const BatchFrame* frames, int count, unsigned long long wait_ns,
+                                int* const* status_dst, cudaStream_t s);
 // Writes `epoch` to *ready on stream s, ordered after the stream's earlier work
 // and released to the whole device.
 cudaError_t launch_post_ready(unsigned* ready, unsigned epoch, cudaStream_t s);

@@ -600,13 +600,16 @@ __global__ void __launch_bounds__(kMarchThreads, VI_MARCH_MIN_BLOCKS)
 // Batched frames: persistent launches over several contexts' frames, one per
 // kind of frame (voxel type, storage format, mode).  A launch's frames are
 // consecutive ranges of a queue of pixel tiles in device memory; warps take
-// (frame, tile) items in queue order from an atomic counter.  Before a frame's tiles, a warp waits until the frame's context has
-// published its stack (vi_post_ready: an epoch released to the device after
-// the context's earlier work) -- at most wait_ns on the GPU's nanosecond
-// timer.  A wait that runs out marks the frame VI_ETIMEOUT in its status word
-// and the frame's remaining tiles are skipped: the kernel always returns.
-// Each frame reads its TF's alpha through L1 (the frames have different TFs)
-// and its parameters from the batch's table.
+// (frame, tile) items in queue order from an atomic counter.  Before a frame's
+// tiles, a warp checks that the frame's context has published its stack
+// (vi_post_ready: an epoch released to the device after the context's earlier
+// work), waiting at most wait_ns on the GPU's nanosecond timer.  (The host
+// orders a batch after each context's publication with events, so the wait
+// runs out only for a context that never published.)  A wait that runs out
+// marks the frame VI_ETIMEOUT in its status word and the frame's remaining
+// tiles are skipped: the kernel always returns.  Each frame reads its TF's
+// alpha through L1 (the frames have different TFs) and its parameters from
+// the batch's table.
 
 constexpr int kBatchThreads = 256;
 
@@ -802,8 +805,8 @@ cudaError_t launch_march(const MarchParams& p, int voxel_type, int format, int m
     return dispatch_fmt<uint16_t>(p, format, mode, false, 0, 0, nullptr, 0, nullptr, s);
 }
 
-cudaError_t launch_march_batch(const BatchFrame* frames, int count, unsigned long long wait_ns,
-                               int* status, cudaStream_t s) {
+cudaError_t enqueue_march_batch(const BatchFrame* frames, int count, unsigned long long wait_ns,
+                                int* const* status_dst, cudaStream_t s) {
     if (count < 1 || count > kBatchMaxFrames) return cudaErrorInvalidValue;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -856,13 +859,10 @@ cudaError_t launch_march_batch(const BatchFrame* frames, int count, unsigned lon
             d_tab + first, n, group_tiles[g], d_counter + g, d_status, wait_ns);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(status, d_status, (size_t)count * sizeof(int), cudaMemcpyDeviceToHost,
-                            s);
+    for (int f = 0; e == cudaSuccess && f < count; ++f)
+        e = cudaMemcpyAsync(status_dst[f], d_status + f, sizeof(int), cudaMemcpyDeviceToHost, s);
     const cudaError_t ef = cudaFreeAsync(d, s);
-    if (e == cudaSuccess) e = ef;
-    const cudaError_t es = cudaStreamSynchronize(s);
-    return e == cudaSuccess ? es : e;
+    return e == cudaSuccess ? ef : e;
 }
 
 cudaError_t launch_post_ready(unsigned* ready, unsigned epoch, cudaStream_t s) {

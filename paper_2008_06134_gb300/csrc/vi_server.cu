@@ -64,6 +64,8 @@ struct Slot {
     // Executable graphs of a request's device work, one per shape of it:
     // index 1 with a sweep, + 2 with a copy to host output.
     cudaGraphExec_t exec[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool batched = false;         // the current request's march is in a batch
+    int* batch_status = nullptr;  // page-locked: its frame's status word
 };
 
 bool same_bits(float a, float b) { return std::memcmp(&a, &b, sizeof(float)) == 0; }
@@ -109,6 +111,13 @@ struct vi_server {
     // slots): evictions and reloads reuse blocks without cudaMalloc / cudaFree.
     cudaMemPool_t pool = nullptr;
     bool graphs = false;  // launch each request's device work as one CUDA graph
+    // Batched marches: the requests admitted in one scheduling pass are
+    // marched together in persistent launches on batch_stream, each frame
+    // waiting on the device for its slot's stack.
+    bool batching = false;
+    cudaStream_t batch_stream = nullptr;
+    std::vector<Slot*> pending;  // admitted this pass, march not yet enqueued
+    double batch_wait_ms = 10000.0;
 };
 
 namespace {
@@ -240,6 +249,13 @@ int launch_captured(vi_server* s, Slot* sl, int rc, int shape) {
     return rc;
 }
 
+// Whether a request's march can join a batch (vi_render_batch's restrictions).
+bool batchable(const vi_request& q) {
+    return (q.mode == VI_NONE || q.build.format == VI_F32 || q.build.format == VI_F16) &&
+           q.build.quantity == VI_TRANSMITTANCE && q.build.shell_count <= 1 &&
+           q.render.slice_filter == VI_SLICE_NEAREST && q.width > 0 && q.height > 0;
+}
+
 // Enqueues a request's work on a slot; returns a vi_status.  With `reuse` the
 // slot's kept stack (and TF and light) serve the request and no sweep runs.
 // With graphs on, the sweep, the march, the output copy and the completion
@@ -258,6 +274,26 @@ int start(vi_server* s, Slot* sl, Request* r, bool reuse) {
         if (!rc) rc = vi_set_light(c, q.light_dir, q.light_color);
     }
     const bool sweep = !reuse && q.mode != VI_NONE;
+    sl->batched = false;
+    if (!rc && s->batching && batchable(q)) {
+        // The sweep (or nothing) on the slot's stream, then the publication the
+        // batch's frame waits for on the device; the march joins this pass's
+        // batch (flush_batch).
+        if (!reuse) {
+            rc = vi_build_attenuation(c, q.n_slices, q.slice_res, q.mode, &q.build);
+            if (!rc) {
+                sl->has_stack = true;
+                sl->stack_req = q;
+                sl->stack_tf = r->tf;
+            }
+        }
+        if (!rc) rc = vi_post_ready(c);
+        if (!rc) {
+            sl->batched = true;
+            s->pending.push_back(sl);
+        }
+        return rc;
+    }
     const bool graph = !rc && s->graphs && output_capturable(q);
     if (graph) {
         rc = vi_detail::ctx_reserve(c, sweep, q.n_slices, q.slice_res, q.build.format, q.width,
@@ -285,12 +321,74 @@ int start(vi_server* s, Slot* sl, Request* r, bool reuse) {
     return rc;
 }
 
+// Fails a slot's request that could not be enqueued.
+void fail_slot(vi_server* s, Slot* sl, int rc) {
+    sl->has_stack = false;
+    cudaStreamSynchronize(sl->stream);
+    vi_sync(sl->ctx);
+    --s->vols[sl->vol]->pins;
+    finish(s, sl->req, VI_REQ_FAILED, rc);
+    sl->req = nullptr;
+    sl->vol = -1;
+    sl->batched = false;
+}
+
+// Enqueues the marches of the requests admitted in this pass as one batch on
+// the batch stream, then their host-output copies and completion callbacks.
+void flush_batch(vi_server* s) {
+    if (s->pending.empty()) return;
+    vi_detail::NvtxRange nvtx_range("vi_server batch");
+    std::vector<Slot*> slots;
+    std::vector<vi::BatchFrame> tab;
+    std::vector<vi_ctx*> ctxs;
+    std::vector<int*> dst;
+    for (Slot* sl : s->pending) {
+        const vi_request& q = sl->req->req;
+        vi::BatchFrame b;
+        const int rc = vi_detail::ctx_batch_frame(sl->ctx, &q.camera, q.width, q.height,
+                                                  q.step_vox, q.out_rgba, q.out_on_device,
+                                                  &q.render, &b);
+        if (rc) {
+            fail_slot(s, sl, rc);
+            continue;
+        }
+        b.index = (int)tab.size();
+        *sl->batch_status = VI_OK;
+        tab.push_back(b);
+        slots.push_back(sl);
+        ctxs.push_back(sl->ctx);
+        dst.push_back(sl->batch_status);
+    }
+    s->pending.clear();
+    if (tab.empty()) return;
+    cudaError_t e = vi_detail::enqueue_batch(ctxs.data(), tab.data(), (int)tab.size(),
+                                             (unsigned long long)(s->batch_wait_ms * 1e6),
+                                             dst.data(), s->batch_stream);
+    for (size_t k = 0; k < slots.size(); ++k) {
+        Slot* sl = slots[k];
+        const vi_request& q = sl->req->req;
+        if (e == cudaSuccess && !q.out_on_device)
+            e = cudaMemcpyAsync(q.out_rgba, sl->ctx->out, (size_t)q.width * q.height * 16,
+                                cudaMemcpyDeviceToHost, s->batch_stream);
+        if (e == cudaSuccess) e = cudaLaunchHostFunc(s->batch_stream, on_slot_done, sl);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cudaStreamSynchronize(s->batch_stream);
+            fail_slot(s, sl, VI_ECUDA);
+        }
+    }
+    ++s->stats.batches;
+    s->stats.batched_frames += tab.size();
+}
+
 // One pass of the scheduler under the lock: retire finished slots, then admit
 // queued requests in order while a slot and the memory budget allow.
 void schedule(vi_server* s) {
     for (Slot* sl : s->slots) {
         if (!sl->req || !sl->gpu_done.load(std::memory_order_acquire)) continue;
-        const int rc = vi_sync(sl->ctx);
+        int rc = vi_sync(sl->ctx);
+        if (!rc && sl->batched) rc = *sl->batch_status;  // VI_ETIMEOUT if its wait ran out
+        sl->batched = false;
         finish(s, sl->req, rc ? VI_REQ_FAILED : VI_REQ_DONE, rc);
         --s->vols[sl->vol]->pins;
         sl->req = nullptr;
@@ -315,7 +413,7 @@ void schedule(vi_server* s) {
                 (sl->has_stack == cand->has_stack && cand->stack_use < sl->stack_use))
                 sl = cand;
         }
-        if (!sl) return;
+        if (!sl) break;
         const int vid = r->req.volume_id;
         ServerVolume* v = s->vols[vid];
         const size_t vol_need = v->resident ? 0 : vi_detail::volume_bytes(v->dtype, v->nx, v->ny,
@@ -324,7 +422,7 @@ void schedule(vi_server* s) {
         bool busy = false;
         for (Slot* o : s->slots) busy = busy || o->req;
         if (!make_room(s, need, sl, vid)) {
-            if (busy) return;  // wait for running frames to release memory
+            if (busy) break;  // wait for running frames to release memory
             s->queue.pop_front();
             finish(s, r, VI_REQ_FAILED, VI_ENOMEM);
             continue;
@@ -344,7 +442,7 @@ void schedule(vi_server* s) {
                 --resident;
             }
             if (resident >= s->max_resident) {
-                if (busy) return;
+                if (busy) break;
                 s->queue.pop_front();
                 finish(s, r, VI_REQ_FAILED, VI_ENOMEM);
                 continue;
@@ -376,18 +474,11 @@ void schedule(vi_server* s) {
         r->t_start = now_ms(s);
         const int rc = start(s, sl, r, reuse);
         if (!rc && reuse) ++s->stats.stack_reuses;
-        if (rc) {
-            sl->has_stack = false;
-            cudaStreamSynchronize(sl->stream);
-            vi_sync(sl->ctx);
-            --v->pins;
-            sl->req = nullptr;
-            sl->vol = -1;
-            finish(s, r, VI_REQ_FAILED, rc);
-        }
+        if (rc) fail_slot(s, sl, rc);
         const size_t b = bytes_in_use(s);
         if (b > s->stats.peak_bytes) s->stats.peak_bytes = b;
     }
+    flush_batch(s);
 }
 
 void worker_main(vi_server* s) {
@@ -494,7 +585,12 @@ int vi_server_destroy(vi_server* s) {
     cudaSetDevice(s->device);
     // The completion callbacks touch the server: let every one of them return.
     for (Slot* sl : s->slots) cudaStreamSynchronize(sl->stream);
+    if (s->batch_stream) {
+        cudaStreamSynchronize(s->batch_stream);
+        cudaStreamDestroy(s->batch_stream);
+    }
     for (Slot* sl : s->slots) {
+        if (sl->batch_status) cudaFreeHost(sl->batch_status);
         for (cudaGraphExec_t x : sl->exec)
             if (x) cudaGraphExecDestroy(x);
         vi_destroy(sl->ctx);
@@ -564,6 +660,7 @@ int vi_server_submit(vi_server* s, const vi_request* q, uint64_t* ticket) {
         return VI_EINVAL;
     if (q->width < 0 || q->height < 0 || (q->width * (long long)q->height > 0 && !q->out_rgba))
         return VI_EINVAL;
+    if (q->out_on_device != VI_OUT_HOST && q->out_on_device != VI_OUT_DEVICE) return VI_EINVAL;
     std::lock_guard<std::mutex> lk(s->mu);
     if (q->volume_id < 0 || q->volume_id >= (int)s->vols.size()) return VI_EINVAL;
     if (s->stop) return VI_ESTATE;
@@ -633,6 +730,30 @@ int vi_server_release(vi_server* s, uint64_t ticket) {
     if (it->second->status < VI_REQ_DONE) return VI_ESTATE;
     delete it->second;
     s->reqs.erase(it);
+    return VI_OK;
+}
+
+int vi_server_set_batching(vi_server* s, int enabled, double wait_ms) {
+    if (!s || !(wait_ms >= 0.0 && wait_ms <= 1e7)) return VI_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (enabled && !s->batch_stream) {
+        if (cudaSetDevice(s->device) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&s->batch_stream, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            s->batch_stream = nullptr;
+            return VI_ECUDA;
+        }
+        for (Slot* sl : s->slots)
+            if (!sl->batch_status &&
+                cudaHostAlloc(reinterpret_cast<void**>(&sl->batch_status), sizeof(int),
+                              cudaHostAllocDefault) != cudaSuccess) {
+                cudaGetLastError();
+                sl->batch_status = nullptr;
+                return VI_ECUDA;
+            }
+    }
+    s->batching = enabled != 0;
+    s->batch_wait_ms = wait_ms;
     return VI_OK;
 }
 

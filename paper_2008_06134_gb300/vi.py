@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(HERE, "libvi.so")
 LIB_CHECKED_PATH = os.path.join(HERE, "libvi_checked.so")
 
 OK, EINVAL, ENOMEM, ESTATE, ECUDA, ETIMEOUT = 0, -1, -2, -3, -4, -5
+OUT_HOST, OUT_DEVICE, OUT_HOST_ASYNC = 0, 1, 2   # where vi_render's output lives
 U8, U16 = 0, 1
 NONE, SHADOW, SHELL, CONE = 0, 1, 2, 3
 F32, F16, BF16, UNORM16 = 0, 1, 2, 3
@@ -37,10 +38,10 @@ EXPORTS = ("vi_create", "vi_destroy", "vi_set_memory_budget", "vi_load_volume",
            "vi_set_transfer_function", "vi_set_light", "vi_set_point_light",
            "vi_build_attenuation", "vi_render", "vi_sync", "vi_error_string",
            "vi_attenuation_info", "vi_get_attenuation", "vi_trace_pixel", "vi_launch_count",
-           "vi_post_ready", "vi_render_batch", "vi_render_host_noalloc", "vi_debug_bounds", "vi_server_create", "vi_server_destroy",
+           "vi_measure_peaks", "vi_post_ready", "vi_render_batch", "vi_render_host_noalloc", "vi_debug_bounds", "vi_server_create", "vi_server_destroy",
            "vi_server_add_volume", "vi_server_submit", "vi_server_wait", "vi_server_cancel",
            "vi_server_timing", "vi_server_release", "vi_server_get_stats",
-           "vi_server_set_graphs")
+           "vi_server_set_graphs", "vi_server_set_batching")
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = 0, 1, 2, 3, 4
 
 
@@ -88,7 +89,8 @@ class ServerStats(C.Structure):
                 ("volume_evictions", C.c_uint64), ("queued", C.c_int), ("running", C.c_int),
                 ("resident_volumes", C.c_int), ("bytes_in_use", C.c_size_t),
                 ("peak_bytes", C.c_size_t), ("stack_reuses", C.c_uint64),
-                ("graph_launches", C.c_uint64), ("graph_instantiations", C.c_uint64)]
+                ("graph_launches", C.c_uint64), ("graph_instantiations", C.c_uint64),
+                ("batches", C.c_uint64), ("batched_frames", C.c_uint64)]
 
 
 _libs = {}
@@ -124,6 +126,7 @@ def library(checked: bool = False) -> C.CDLL:
     L.vi_launch_count.argtypes = [vp, P(C.c_uint64)]
     L.vi_render_host_noalloc.argtypes = [vp, P(Camera), i, i, f, vp, P(RenderOpts)]
     L.vi_post_ready.argtypes = [vp]
+    L.vi_measure_peaks.argtypes = [i, P(C.c_double), P(C.c_double)]
     L.vi_render_batch.argtypes = [P(BatchFrame), i, vp, C.c_double]
     d, u64 = C.c_double, C.c_uint64
     L.vi_server_create.argtypes = [P(vp), i, i, sz, i]
@@ -136,6 +139,7 @@ def library(checked: bool = False) -> C.CDLL:
     L.vi_server_release.argtypes = [vp, u64]
     L.vi_server_get_stats.argtypes = [vp, P(ServerStats)]
     L.vi_server_set_graphs.argtypes = [vp, i]
+    L.vi_server_set_batching.argtypes = [vp, i, C.c_double]
     L.vi_debug_bounds.argtypes = [i, P(C.c_uint64), P(i), P(C.c_int64)]
     _libs[path] = L
     return L
@@ -283,14 +287,21 @@ class Context:
 
     def render(self, cam, W: int, H: int, step_vox: float, out=None, ert: float = 2.0,
                bg=(0.0, 0.0, 0.0, 0.0), ambient: float = 0.0, opacity_correction: int = 0,
-               sample_counts=None, lit_counts=None, slice_filter: int = SLICE_NEAREST):
+               sample_counts=None, lit_counts=None, slice_filter: int = SLICE_NEAREST,
+               host_async: bool = False):
         """Render into ``out`` ((H, W, 4) float32; torch CUDA tensor or numpy /
         pinned torch host tensor).  With ``out=None`` a torch CUDA tensor is
-        allocated and returned."""
+        allocated and returned.  ``host_async`` (host ``out`` only): enqueue
+        the frame's copy on the context's stream and return; it is complete
+        after ``sync()`` (VI_OUT_HOST_ASYNC)."""
         if out is None:
             import torch
             out = torch.empty((H, W, 4), dtype=torch.float32, device="cuda")
         p, dev = _ptr(out)
+        if host_async:
+            if dev:
+                raise ValueError("host_async needs a host output")
+            dev = OUT_HOST_ASYNC
         ro = self._render_opts(ert, bg, ambient, opacity_correction, sample_counts, lit_counts,
                                slice_filter)
         _check(self.L.vi_render(self.h, C.byref(camera(cam)), int(W), int(H), float(step_vox),
@@ -349,6 +360,14 @@ class Context:
         return int(v.value)
 
 
+def measure_peaks(device: int = 0) -> dict:
+    """vi_measure_peaks: the FP32 FMA rate and L2 read bandwidth of the device."""
+    L = library()
+    f, l2 = C.c_double(), C.c_double()
+    _check(L.vi_measure_peaks(int(device), C.byref(f), C.byref(l2)), "vi_measure_peaks")
+    return {"fp32_tflops": f.value, "l2_read_gbs": l2.value}
+
+
 BATCH_MAX_FRAMES = 64
 
 
@@ -399,7 +418,8 @@ class Server:
     """A vi_server: continuous batching of render requests over resident volumes."""
 
     def __init__(self, device: int = 0, slots: int = 4, memory_budget: int = 0,
-                 max_resident_volumes: int = 0, graphs: bool = False, checked: bool = False):
+                 max_resident_volumes: int = 0, graphs: bool = False, checked: bool = False,
+                 batching: bool = False, batch_wait_ms: float = 10000.0):
         L = library(checked)
         h = C.c_void_p()
         _check(L.vi_server_create(C.byref(h), int(device), int(slots), int(memory_budget),
@@ -408,6 +428,14 @@ class Server:
         self._keep = {}   # host volumes and outputs the server reads or writes later
         if graphs:
             self.set_graphs(True)
+        if batching:
+            self.set_batching(True, batch_wait_ms)
+
+    def set_batching(self, enabled: bool, wait_ms: float = 10000.0) -> None:
+        """March the requests admitted in one scheduling pass as one batch of
+        persistent launches (vi_server_set_batching)."""
+        _check(self.L.vi_server_set_batching(self.h, int(bool(enabled)), float(wait_ms)),
+               "vi_server_set_batching")
 
     def set_graphs(self, enabled: bool) -> None:
         """Launch each later request's sweep, march and output copy as one

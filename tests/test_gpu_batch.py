@@ -83,10 +83,10 @@ def test_batched_frames_equal_vi_render_and_the_oracle(env):
         c.close()
 
 
-def test_batched_frame_waits_on_the_device_for_a_stack_built_on_another_stream(env):
+def test_batch_on_another_stream_follows_the_publication(env):
     """The batch is enqueued on its own stream right after a large sweep was
-    enqueued on the context's stream: its tiles wait on the device for the
-    context's post, and the frame equals vi_render's."""
+    enqueued on the context's stream: it runs after the context's
+    publication, and the frame equals vi_render's."""
     torch, ph, vi = env
     sc = scenes(ph, vi)[3]
     other = torch.cuda.Stream()

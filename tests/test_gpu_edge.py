@@ -149,6 +149,14 @@ def test_host_and_device_buffers_agree(ctx, vi, orc):
     ctx.build_attenuation(sc.n_slices, sc.slice_res, 3)
     ctx.render(sc.camera, sc.width, sc.height, sc.step_vox)
     assert ctx.launch_count() == before + 2
+    # VI_OUT_HOST_ASYNC: the copy is enqueued on the context's stream and the
+    # frame is complete at vi_sync, into page-locked and pageable memory alike.
+    for pinned in (True, False):
+        buf = torch.full((sc.height, sc.width, 4), float("nan"), pin_memory=pinned)
+        ctx.render(sc.camera, sc.width, sc.height, sc.step_vox, out=buf, host_async=True)
+        ctx.sync()
+        assert np.array_equal(buf.numpy().astype(np.float64), dev)
+    assert vi.library().vi_render(ctx.h, None, 1, 1, 0.5, None, 3, None) == vi.EINVAL
 
 
 @pytest.mark.parametrize("case", ["one-slice", "one-texel", "one-voxel", "two-entry-tf",

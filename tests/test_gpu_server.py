@@ -36,9 +36,10 @@ def make_requests(ph, vi, count, seed=0):
     return reqs
 
 
-def run(env, reqs, slots, together, budget=0, max_resident=0):
+def run(env, reqs, slots, together, budget=0, max_resident=0, batching=False):
     torch, ph, vi, vols, tfs = env
-    with vi.Server(0, slots=slots, memory_budget=budget, max_resident_volumes=max_resident) as s:
+    with vi.Server(0, slots=slots, memory_budget=budget, max_resident_volumes=max_resident,
+                   batching=batching) as s:
         vids = [s.add_volume(v) for v in vols]
         outs, tickets = [], []
         for q in reqs:
@@ -83,7 +84,30 @@ def test_server_frame_equals_context_frame(env):
     assert np.array_equal(served, ref)
 
 
-def test_served_frames_match_the_oracle(env):
+def test_batched_marches_give_the_same_frames(env):
+    """With batching on, the marches of the requests admitted together run as
+    batches of persistent launches whose frames wait on the device for their
+    slots' stacks: every frame equals the one-slot frame, and the BF16 /
+    UNORM16 requests (outside the batches' restrictions) keep their own march."""
+    torch, ph, vi, vols, tfs = env
+    reqs = make_requests(ph, vi, 24, seed=17)
+    for k, q in enumerate(reqs):
+        q["fmt"] = [vi.F32, vi.F16, vi.F32, vi.UNORM16][k % 4]
+    alone, _ = run(env, reqs, slots=1, together=False)
+    for together in (False, True):
+        got, stats = run(env, reqs, slots=4, together=together, batching=True)
+        for a, b in zip(alone, got):
+            assert np.isfinite(a).all()
+            assert np.array_equal(a, b)
+        assert stats["completed"] == 24 and stats["failed"] == 0
+        assert stats["batched_frames"] == sum(q["fmt"] != vi.UNORM16 for q in reqs)
+        assert 1 <= stats["batches"] <= stats["batched_frames"]
+        if together:
+            assert stats["batches"] < stats["batched_frames"]  # several frames per batch
+
+
+@pytest.mark.parametrize("path", ["graphs", "batching"])
+def test_served_frames_match_the_oracle(env, path):
     """Every served frame matches the FP64 oracle, not only the server's own
     one-slot frames: 4 slots, all requests submitted at once, graphs on, mixed
     volumes (uint8 blobs, uint16 ellipsoids, a non-cubic one), TFs, shadow /
@@ -101,7 +125,7 @@ def test_served_frames_match_the_oracle(env):
         q["vol"] = k % 3
         q["mode"] = 1 + (k // 4) % 3
     outs, counts = [], []
-    with vi.Server(0, slots=4, graphs=True) as s:
+    with vi.Server(0, slots=4, graphs=path == "graphs", batching=path == "batching") as s:
         vids = [s.add_volume(v) for v in vols]
         tickets = []
         for q in reqs:
@@ -115,7 +139,11 @@ def test_served_frames_match_the_oracle(env):
             counts.append(cnt)
         for t in tickets:
             assert s.wait(t) == (vi.REQ_DONE, vi.OK)
-        assert s.stats()["graph_launches"] == len(reqs)
+        st = s.stats()
+        if path == "graphs":
+            assert st["graph_launches"] == len(reqs)
+        else:
+            assert st["batched_frames"] == sum(q["fmt"] in (vi.F32, vi.F16) for q in reqs)
     torch.cuda.synchronize()
     for q, out, cnt in zip(reqs, outs, counts):
         tf, vmin, vmax = tfs[q["vol"]]
