@@ -686,13 +686,11 @@ def precision_workload(args):
     centred 256x144 crop (the oracle builds its own FP64 stack)."""
     import oracle
     name, oracle_s, rows = precision_rows(args.steps, args.warmup)
-    sc_name = name
     print(json.dumps({"workload": "precision", "metric": "frames/s", "unit": "frames/s",
-                      "scene": sc_name, "steps": args.steps, "warmup": args.warmup,
+                      "scene": name, "steps": args.steps, "warmup": args.warmup,
                       "error_reference": "FP64 oracle, centred 256x144 crop "
                                          f"({oracle_s:.1f} s on {oracle.threads()} cores)",
                       "results": rows}), flush=True)
-    ctx.close()
 
 
 def scalability_workload(args):
