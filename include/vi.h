@@ -310,7 +310,7 @@ int vi_render_host_noalloc(vi_ctx* ctx, const vi_camera* camera, int W, int H, f
    index is counted and the access skipped, so a kernel neither traps nor
    faults.  The call waits for the device, stores the number of violations
    since the last call for that device, the site of a first one (1 volume
-   octet, 2 brick flag, 3 TF alpha, 4 TF colour, 5 stack slice or row of a
+   footprint, 2 brick flag, 3 TF alpha, 4 TF colour, 5 stack slice or row of a
    lookup, 6 stack store, 7 output pixel, 8 raw voxel, 9 grid build; 0 if
    none) and its index, and clears the record.  The record covers every
    context of the process on the device.  VI_ESTATE from a library built
@@ -325,7 +325,7 @@ int vi_debug_bounds(int device, uint64_t* violations, int* first_site, int64_t* 
    order into `slots` concurrent render slots (each a context on its own CUDA
    stream) whenever a slot is free and the device memory they need fits the
    budget, so frames of different requests run on the GPU together.  Volumes
-   are registered once and kept resident (octets and brick ranges) up to
+   are registered once and kept resident (pair bricks and brick ranges) up to
    max_resident_volumes (0 = no count limit) and memory_budget bytes in total
    with the slots' buffers (0 = no byte limit); the least recently used idle
    volume is evicted when room is needed and reloaded from the caller's host

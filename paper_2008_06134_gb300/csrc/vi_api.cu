@@ -302,10 +302,13 @@ int nbricks(const vi_ctx* c) { return c->vr->nbx * c->vr->nby * c->vr->nbz; }
 vi::VolumeView volume_view(const vi_ctx* c) {
     const VolumeRes* r = c->vr;
     vi::VolumeView v;
-    v.data = r->oct;
+    v.data = r->pairs;
     v.nx = r->nx;
     v.ny = r->ny;
     v.nz = r->nz;
+    v.nbx = r->nbx;
+    v.nby = r->nby;
+    v.nbz = r->nbz;
     v.fnx = (float)r->nx;
     v.fny = (float)r->ny;
     v.fnz = (float)r->nz;
@@ -455,7 +458,7 @@ size_t volume_bytes(int dtype, int nx, int ny, int nz) {
     constexpr int B = 1 << vi::kBrickShift;
     const size_t raw = (size_t)nx * (size_t)ny * (size_t)nz * voxel_bytes(dtype);
     const size_t bricks = (size_t)((nx + B - 1) / B) * ((ny + B - 1) / B) * ((nz + B - 1) / B);
-    return raw + 8 * raw + bricks * sizeof(uint32_t);
+    return raw + vi::pair_brick_bytes(nx, ny, nz, voxel_bytes(dtype)) + bricks * sizeof(uint32_t);
 }
 
 int volume_load(VolumeRes* v, size_t* used, size_t budget, const void* data, int dtype, int nx,
@@ -464,14 +467,15 @@ int volume_load(VolumeRes* v, size_t* used, size_t budget, const void* data, int
     constexpr int B = 1 << vi::kBrickShift;
     const int nbx = (nx + B - 1) / B, nby = (ny + B - 1) / B, nbz = (nz + B - 1) / B;
     // Check the whole footprint first, so a refusal leaves the old volume intact.
+    const size_t pair_bytes = vi::pair_brick_bytes(nx, ny, nz, voxel_bytes(dtype));
     const size_t have = std::max(v->raw_cap, bytes) - v->raw_cap +
-                        std::max(v->oct_cap, 8 * bytes) - v->oct_cap +
+                        std::max(v->pairs_cap, pair_bytes) - v->pairs_cap +
                         std::max(v->brange_cap, (size_t)nbx * nby * nbz * sizeof(uint32_t)) -
                         v->brange_cap;
     if (budget && *used + have > budget) return VI_ENOMEM;
     int rc = ensure_mem(used, budget, &v->raw, &v->raw_cap, bytes, s, v->pool);
     if (rc) return rc;
-    rc = ensure_mem(used, budget, &v->oct, &v->oct_cap, 8 * bytes, s, v->pool);
+    rc = ensure_mem(used, budget, &v->pairs, &v->pairs_cap, pair_bytes, s, v->pool);
     if (rc) return rc;
     rc = ensure_mem(used, budget, reinterpret_cast<void**>(&v->brange), &v->brange_cap,
                     (size_t)nbx * nby * nbz * sizeof(uint32_t), s, v->pool);
@@ -482,7 +486,7 @@ int volume_load(VolumeRes* v, size_t* used, size_t budget, const void* data, int
                                                    : cudaMemcpyHostToDevice,
                                     s);
     if (e == cudaSuccess)
-        e = vi::launch_volume_grid(v->raw, nx, ny, nz, dtype, v->oct, v->brange, s);
+        e = vi::launch_volume_grid(v->raw, nx, ny, nz, dtype, v->pairs, v->brange, s);
     if (e != cudaSuccess) return VI_ECUDA;
     if (launches) *launches += 1;
     v->vtype = dtype;
@@ -497,7 +501,7 @@ int volume_load(VolumeRes* v, size_t* used, size_t budget, const void* data, int
 
 void volume_release(VolumeRes* v, size_t* used, cudaStream_t s) {
     release_mem(used, &v->raw, &v->raw_cap, s, v->pool);
-    release_mem(used, &v->oct, &v->oct_cap, s, v->pool);
+    release_mem(used, &v->pairs, &v->pairs_cap, s, v->pool);
     release_mem(used, reinterpret_cast<void**>(&v->brange), &v->brange_cap, s, v->pool);
     v->vtype = -1;
 }

@@ -10,14 +10,14 @@
 #include "../../include/vi.h"
 #include "vi_internal.h"
 
-// A loaded volume: the voxels as given ([nz][ny][nx]), their footprint octets
-// and the per-brick value ranges.  A context owns one (vi_load_volume); a
+// A loaded volume: the voxels as given ([nz][ny][nx]), their pair bricks and
+// the per-brick value ranges.  A context owns one (vi_load_volume); a
 // server owns several and lends them to its render slots.
 struct VolumeRes {
     void* raw = nullptr;
     size_t raw_cap = 0;
-    void* oct = nullptr;  // footprint octets (8 voxels per element)
-    size_t oct_cap = 0;
+    void* pairs = nullptr;  // pair bricks (vi_internal.h, VolumeView)
+    size_t pairs_cap = 0;
     uint32_t* brange = nullptr;
     size_t brange_cap = 0;
     int vtype = -1, nx = 0, ny = 0, nz = 0;
@@ -109,7 +109,7 @@ int ensure_mem(size_t* used, size_t budget, void** p, size_t* cap, size_t bytes,
 // Frees a buffer: cudaFree, or a free ordered on `s` when it came from `pool`.
 void release_mem(size_t* used, void** p, size_t* cap, cudaStream_t s, cudaMemPool_t pool);
 
-// Loads nx*ny*nz voxels into v (octets and brick ranges built on stream s).
+// Loads nx*ny*nz voxels into v (pair bricks and brick ranges built on stream s).
 int volume_load(VolumeRes* v, size_t* used, size_t budget, const void* data, int dtype, int nx,
                 int ny, int nz, int data_on_device, cudaStream_t s, uint64_t* launches);
 // Frees the volume's buffers (ordered on `s` when they came from a pool).

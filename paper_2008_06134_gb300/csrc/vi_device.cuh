@@ -253,10 +253,19 @@ struct Octet<uint8_t> {
     }
 };
 
-// What a trilinear fetch needs: the octet holding the footprint and the
-// weights of its upper corners.  The octet's upper voxels are clamped copies
-// at the high edges; at the low edges (cell -1) the footprint collapses onto
-// voxel 0, so the upper corner's weight is 0 there.
+// The first pair of the footprint whose lower corner is voxel (x0, y0, z0),
+// in the pair bricks (see VolumeView).
+__device__ __forceinline__ size_t pair_index(const VolumeView& v, int x0, int y0, int z0) {
+    const int b = ((z0 >> kBrickShift) * v.nby + (y0 >> kBrickShift)) * v.nbx + (x0 >> kBrickShift);
+    constexpr int m = kBrick - 1;
+    return (size_t)b * kPairsPerBrick +
+           (size_t)(((z0 & m) * (kBrick + 1) + (y0 & m)) * kPairRow + (x0 & m));
+}
+
+// What a trilinear fetch needs: the first pair of the footprint and the
+// weights of its upper corners.  The footprint's upper voxels are clamped
+// copies at the high edges; at the low edges (cell -1) the footprint collapses
+// onto voxel 0, so the upper corner's weight is 0 there.
 struct OctetRef {
     size_t idx;
     float wx, wy, wz;
@@ -264,18 +273,31 @@ struct OctetRef {
 
 __device__ __forceinline__ OctetRef octet_ref(const VolumeView& v, const VoxelCoord& c) {
     OctetRef o;
-    o.idx = ((size_t)c.z0 * (size_t)v.ny + (size_t)c.y0) * (size_t)v.nx + (size_t)c.x0;
+    o.idx = pair_index(v, c.x0, c.y0, c.z0);
     o.wx = c.cx < 0 ? 0.0f : c.wx;
     o.wy = c.cy < 0 ? 0.0f : c.wy;
     o.wz = c.cz < 0 ? 0.0f : c.wz;
     return o;
 }
 
+// The eight voxels of the footprint whose first pair is idx: four aligned pair
+// loads (rows y, y + 1 of planes z, z + 1), packed as one octet (the eight
+// voxels in the order c000 c001 c010 c011 c100 c101 c110 c111).
 template <typename VoxT>
 __device__ __forceinline__ typename Octet<VoxT>::V octet_load(const VolumeView& v, size_t idx) {
-    if (!VI_BOUNDS_OK(kSiteOctet, idx, (long long)v.nx * v.ny * v.nz))
+    if (!VI_BOUNDS_OK(kSiteOctet, idx + kPairPlane + kPairRow,
+                      (long long)v.nbx * v.nby * v.nbz * kPairsPerBrick))
         return typename Octet<VoxT>::V{};
-    return __ldg(static_cast<const typename Octet<VoxT>::V*>(v.data) + idx);
+    if constexpr (sizeof(VoxT) == 2) {
+        const unsigned* q = static_cast<const unsigned*>(v.data) + idx;
+        return make_uint4(__ldg(q), __ldg(q + kPairRow), __ldg(q + kPairPlane),
+                          __ldg(q + kPairPlane + kPairRow));
+    } else {
+        const unsigned short* q = static_cast<const unsigned short*>(v.data) + idx;
+        return make_uint2((unsigned)__ldg(q) | ((unsigned)__ldg(q + kPairRow) << 16),
+                          (unsigned)__ldg(q + kPairPlane) |
+                              ((unsigned)__ldg(q + kPairPlane + kPairRow) << 16));
+    }
 }
 
 template <typename VoxT>
@@ -299,7 +321,7 @@ __device__ __forceinline__ float trilinear_fetch(const VolumeView& v, const Voxe
 }
 
 // The footprint of a sample known to lie in the cube, as the march needs it:
-// the octet's voxel (the lower corners, clamped to the volume) and the weights
+// the footprint's lower corner (clamped to the volume) and the weights
 // of the upper corners.  For such a sample x = P N - 1/2 lies in [-1/2, N - 1/2],
 // so floor(x) is -1 .. N - 1: at -1 the lower corner clamps to 0 and the
 // weight max(x - 0, 0) is 0 (the footprint collapses onto voxel 0), elsewhere
@@ -327,7 +349,7 @@ __device__ __forceinline__ FootprintCell footprint_cell(const VolumeView& v, flo
 }
 
 __device__ __forceinline__ size_t footprint_index(const VolumeView& v, const FootprintCell& c) {
-    return ((size_t)c.z0 * (size_t)v.ny + (size_t)c.y0) * (size_t)v.nx + (size_t)c.x0;
+    return pair_index(v, c.x0, c.y0, c.z0);
 }
 
 __device__ __forceinline__ bool footprint_may_be_lit(const GridView& g, const FootprintCell& c) {
@@ -340,7 +362,7 @@ __device__ __forceinline__ bool footprint_may_be_lit(const GridView& g, const Fo
     return __ldg(g.flags + b) != 0;
 }
 
-// Trilinear value of an octet at a footprint's weights.  uint16 voxels are
+// Trilinear value of a footprint's eight voxels (an octet) at its weights.  uint16 voxels are
 // unpacked as 2^23 + v (one OR each) and the 2^23 taken off only the four
 // lower corners: differences of two such floats are exact, so the result is
 // the one trilinear_octet gives, bit for bit.

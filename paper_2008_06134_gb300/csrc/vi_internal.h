@@ -40,13 +40,19 @@ struct LightFrame {
     float P[3];
 };
 
-// The volume as footprint octets: element (x, y, z) of [nz][ny][nx] holds the
-// eight voxels v(x + a, y + b, z + c), a, b, c in {0, 1} (indices clamped to
-// the volume), in the order c000 c001 c010 c011 c100 c101 c110 c111 (c{z}{y}{x});
-// 16 bytes for uint16 voxels, 8 for uint8.  One aligned vector load brings a
-// whole trilinear footprint.
+// The volume as pair bricks.  The volume is cut into bricks of B^3 voxels, B =
+// 2^kBrickShift (16), stored one after the other in brick order ([bz][by][bx]).
+// Brick b holds the voxels its trilinear footprints can touch -- the brick and
+// a one-voxel apron on its high sides, (B + 1)^3 voxels with indices clamped
+// to the volume -- as x-pairs: for x in [0, B), y and z in [0, B], the pair
+// v(x, y, z) | v(x + 1, y, z) << (8 * voxel bytes), [z][y][x], B (B + 1)^2
+// pairs from element b B (B + 1)^2.  A footprint is four aligned pair loads
+// (rows y and y + 1 of planes z and z + 1), which together are the eight
+// voxels in the order c000 c001 c010 c011 c100 c101 c110 c111 (c{z}{y}{x}).
+// The layout takes 2 (B + 1)^2 / B^2 = 2.26 times the raw voxels' bytes for
+// whole bricks (the footprint octets this replaced took 8 times).
 // Checked builds (-DVI_DEBUG_BOUNDS=1, the library libvi_checked.so): every
-// voxel-octet, brick-flag, TF, stack-texture, stack-store, output, raw-voxel
+// voxel-pair, brick-flag, TF, stack-texture, stack-store, output, raw-voxel
 // and grid index is tested against its array before the access.  A bad one is
 // counted in a device-wide record of the kernel's translation unit (count,
 // first site, first index) and the access is skipped: no trap, no fault, the
@@ -55,32 +61,39 @@ struct LightFrame {
 #define VI_DEBUG_BOUNDS 0
 #endif
 enum DebugSite {
-    kSiteOctet = 1,       // volume octet load (sweep, march)
+    kSiteOctet = 1,       // volume footprint load (sweep, march)
     kSiteBrick = 2,       // brick flag load (sweep, march)
     kSiteTfAlpha = 3,     // TF alpha entry (sweep, march)
     kSiteTfColour = 4,    // TF RGBA entry (march)
     kSiteStackTex = 5,    // stack texture / slice of a lookup (march)
     kSiteStackStore = 6,  // stack element a sweep store writes
     kSitePixel = 7,       // output pixel (march)
-    kSiteRaw = 8,         // raw voxel read (octet and brick-range builds)
-    kSiteGrid = 9,        // octet, brick range or brick flag written by a grid build
-};
-
-struct VolumeView {
-    const void* data;  // octets
-    int nx, ny, nz;
-    float fnx, fny, fnz;  // (float)nx ...
+    kSiteRaw = 8,         // raw voxel read (pair-brick and brick-range builds)
+    kSiteGrid = 9,        // voxel pair, brick range or brick flag written by a grid build
 };
 
 // Bricks of 2^kBrickShift voxels per axis; flags[bz][by][bx] = 1 if a sample
 // whose trilinear footprint starts in the brick may have alpha > 0.  16^3
 // measured fastest: coarser bricks skip a little less, but each transparent
 // run is crossed in fewer steps (config-2 march 0.985 -> 0.908 ms against 8^3;
-// 4^3 and 32^3 were slower).
+// 4^3 and 32^3 were slower; 8^3 again 0.841 against 0.784 ms later on).
 #ifndef VI_BRICK_SHIFT
 #define VI_BRICK_SHIFT 4
 #endif
 constexpr int kBrickShift = VI_BRICK_SHIFT;
+constexpr int kBrick = 1 << kBrickShift;
+// Pair bricks: pairs per row, per plane and per brick, and the offsets of the
+// footprint's rows y + 1, z + 1 and y + 1, z + 1 from its first pair.
+constexpr int kPairRow = kBrick;
+constexpr int kPairPlane = kBrick * (kBrick + 1);
+constexpr int kPairsPerBrick = kBrick * (kBrick + 1) * (kBrick + 1);
+
+struct VolumeView {
+    const void* data;  // pair bricks
+    int nx, ny, nz;
+    int nbx, nby, nbz;    // bricks per axis
+    float fnx, fny, fnz;  // (float)nx ...
+};
 
 struct GridView {
     const uint8_t* flags;
@@ -180,10 +193,17 @@ cudaError_t launch_march(const MarchParams& p, int voxel_type, int format, int m
                          cudaStream_t s);
 cudaError_t launch_trace(const MarchParams& p, int voxel_type, int format, int mode, int x,
                          int y, int32_t* rec, int max_rec, int* n_rec, cudaStream_t s);
-// Footprint octets of every voxel and the value range of every brick (with its
+// The pair bricks of the volume and the value range of every brick (with its
 // one-voxel apron), in one pass over the raw voxels.
 cudaError_t launch_volume_grid(const void* raw, int nx, int ny, int nz, int voxel_type,
-                               void* octets, uint32_t* range, cudaStream_t s);
+                               void* pairs, uint32_t* range, cudaStream_t s);
+// Bytes of the pair bricks of an nx x ny x nz volume of voxel_bytes-byte voxels.
+inline size_t pair_brick_bytes(int nx, int ny, int nz, size_t voxel_bytes) {
+    const size_t bricks = (size_t)((nx + kBrick - 1) >> kBrickShift) *
+                          (size_t)((ny + kBrick - 1) >> kBrickShift) *
+                          (size_t)((nz + kBrick - 1) >> kBrickShift);
+    return bricks * (size_t)kPairsPerBrick * 2 * voxel_bytes;
+}
 // Device addresses of the fixed scratch behind vi_render_host_noalloc on the
 // current device (looked up once per device; no allocation).
 constexpr size_t kNoallocMaxPixels = 512 * 512;

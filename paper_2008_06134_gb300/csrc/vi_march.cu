@@ -286,8 +286,8 @@ __device__ __forceinline__ int march_sample(const MarchParams& p, const AlphaT& 
         const FootprintCell fc = footprint_cell(p.vol, __fmaf_rn(t, r.d[0], r.o[0]),
                                                 __fmaf_rn(t, r.d[1], r.o[1]),
                                                 __fmaf_rn(t, r.d[2], r.o[2]));
-        // The octet load is issued before the brick flag is known: the two loads
-        // overlap, and a sample in a transparent brick drops its octet unused.
+        // The footprint's loads are issued before the brick flag is known: they
+        // overlap, and a sample in a transparent brick drops its footprint unused.
         const size_t idx = footprint_index(p.vol, fc);
         const typename Octet<VoxT>::V q = octet_load<VoxT>(p.vol, idx);
         if (!footprint_may_be_lit(p.grid, fc)) {

@@ -5,7 +5,7 @@
 // and device memory free up.  Each slot is a context with its own CUDA stream:
 // the frames of different requests run their sweeps and marches concurrently
 // on the GPU, so small frames fill it together instead of one after another.
-// Volumes are registered once and kept resident (octets and brick ranges) up
+// Volumes are registered once and kept resident (pair bricks and brick ranges) up
 // to a count and a byte budget; the least recently used idle volume is
 // evicted when room is needed and reloaded from the caller's host copy on its
 // next request.  Each slot keeps its last attenuation stack for a later view of
@@ -454,7 +454,7 @@ void schedule(vi_server* s) {
             int rc = vi_detail::volume_load(&v->res, &v->used, 0, v->host, v->dtype, v->nx,
                                                   v->ny, v->nz, 0, sl->stream, nullptr);
             // Slots on other streams may read this volume next: they wait on
-            // this event (octets and brick ranges built) before they do.
+            // this event (pair bricks and brick ranges built) before they do.
             if (!rc && cudaEventRecord(v->ready, sl->stream) != cudaSuccess) rc = VI_ECUDA;
             if (rc) {
                 vi_detail::volume_release(&v->res, &v->used, sl->stream);  // a partial load

@@ -9,8 +9,8 @@
 // extinction form of Eq. 5-6 (DEPTH) the column carries the optical depth
 // D <- D + tau_k, tau_k = -ln(1 - alpha_k), capped at kDepthMax, and stores D.
 //
-// Memory: the volume is read through the read-only path (it fits in L2 for the
-// sizes this targets).  A warp covers a 16 x 2 tile of texels, so its 32
+// Memory: the volume's pair bricks are read through the read-only path (four
+// aligned loads per footprint; for the sizes this targets they fit in L2).  A warp covers a 16 x 2 tile of texels, so its 32
 // sample points form a compact patch of the slice plane and its trilinear
 // footprints share sectors; each store of slice k writes two 64-byte (FP32)
 // or 32-byte (16-bit) row segments.  Slices outside the cube only store (the inside slices of a
@@ -274,7 +274,7 @@ __device__ __forceinline__ void sweep_column(const SweepParams& p, const float* 
         if (dup) put(p, out, (size_t)k * slice + dup, one);
     }
     // Inside the cube, four slices at a time: their positions, brick flags and
-    // octets do not depend on T, so the loads of a batch are issued together
+    // footprints do not depend on T, so the loads of a batch are issued together
     // and their latencies overlap; T then runs through the batch in order.
     float T = DEPTH ? 0.0f : 1.0f;  // transmittance, or optical depth
     for (; k <= kout; k += kBatch) {
