@@ -318,6 +318,7 @@ vi::VolumeView volume_view(const vi_ctx* c) {
 vi::GridView grid_view(const vi_ctx* c) {
     vi::GridView g;
     g.flags = c->bflags;
+    g.skip = c->bflags ? c->bflags + nbricks(c) : nullptr;
     g.nbx = c->vr->nbx;
     g.nby = c->vr->nby;
 #if VI_DEBUG_BOUNDS
@@ -330,12 +331,15 @@ vi::GridView grid_view(const vi_ctx* c) {
 int refresh_flags(vi_ctx* c) {
     c->flags_ok = false;
     if (!c->vr->brange || !c->tfcnt || c->vr->vtype < 0 || !c->tf) return VI_OK;
-    int rc = ensure(c, reinterpret_cast<void**>(&c->bflags), &c->bflags_cap, (size_t)nbricks(c));
+    // Flags, skip distances and the passes' scratch: one byte per brick each.
+    const size_t nb = (size_t)nbricks(c);
+    int rc = ensure(c, reinterpret_cast<void**>(&c->bflags), &c->bflags_cap, 3 * nb);
     if (rc) return rc;
-    cudaError_t e = vi::launch_brick_flags(c->vr->brange, nbricks(c), c->tfcnt, c->M, c->vmin,
-                                           c->vmax, c->bflags, c->stream);
+    cudaError_t e = vi::launch_brick_flags(c->vr->brange, c->vr->nbx, c->vr->nby, c->vr->nbz,
+                                           c->tfcnt, c->M, c->vmin, c->vmax, c->bflags,
+                                           c->bflags + nb, c->bflags + 2 * nb, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e);
-    ++c->launches;
+    c->launches += 4;
     c->flags_ok = true;
     return VI_OK;
 }

@@ -47,7 +47,7 @@ struct vi_ctx {
     // alpha > 0 and per-brick flags (the value ranges belong to the volume).
     int* tfcnt = nullptr;
     size_t tfcnt_cap = 0;
-    uint8_t* bflags = nullptr;
+    uint8_t* bflags = nullptr;  // brick flags, skip distances, scratch (nbricks bytes each)
     size_t bflags_cap = 0;
     bool flags_ok = false;  // bflags match the current volume and TF
 

@@ -186,42 +186,66 @@ __device__ __forceinline__ VoxelCoord voxel_coord_inside(const VolumeView& v, fl
 }
 
 // Brick coordinates of the footprint's lower corner.  Each is monotone in the
-// position along a ray or a light column, so two samples in one brick have
-// every sample between them in that brick too.
+// position along a ray or a light column, so two samples whose bricks lie in
+// one box of bricks have every sample between them in that box too.
 __device__ __forceinline__ bool same_brick(const VoxelCoord& a, const VoxelCoord& b) {
     return ((a.x0 ^ b.x0) >> kBrickShift) == 0 && ((a.y0 ^ b.y0) >> kBrickShift) == 0 &&
            ((a.z0 ^ b.z0) >> kBrickShift) == 0;
 }
 
+// Whether b's brick lies within rad bricks of a's along every axis.
+__device__ __forceinline__ bool within_bricks(const VoxelCoord& a, const VoxelCoord& b, int rad) {
+    return abs((a.x0 >> kBrickShift) - (b.x0 >> kBrickShift)) <= rad &&
+           abs((a.y0 >> kBrickShift) - (b.y0 >> kBrickShift)) <= rad &&
+           abs((a.z0 >> kBrickShift) - (b.z0 >> kBrickShift)) <= rad;
+}
+
 // Parameter along P(s) = base + s dir at which the footprint's lower corner
-// leaves the brick of c (an estimate; callers verify with the exact path).
-__device__ __forceinline__ float brick_exit(const VolumeView& v, const VoxelCoord& c, float b0,
-                                            float b1, float b2, float d0, float d1, float d2) {
+// leaves the box of bricks within rad of c's brick along every axis (an
+// estimate; callers verify with the exact path).  rad = 0: c's brick.
+__device__ __forceinline__ float brick_exit(const VolumeView& v, const VoxelCoord& c, int rad,
+                                            float b0, float b1, float b2, float d0, float d1,
+                                            float d2) {
     const float base[3] = {b0, b1, b2}, dir[3] = {d0, d1, d2};
-    const int lo[3] = {c.x0 >> kBrickShift, c.y0 >> kBrickShift, c.z0 >> kBrickShift};
+    const int lo[3] = {(c.x0 >> kBrickShift) - rad, (c.y0 >> kBrickShift) - rad,
+                       (c.z0 >> kBrickShift) - rad};
     const float N[3] = {v.fnx, v.fny, v.fnz};
+    const int span = 2 * rad + 1;
     float s_exit = 3.0e38f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         // Cells [B b, B b + B - 1] <=> P in [(B b + 0.5) / N, (B b + B + 0.5) / N),
-        // B = 2^kBrickShift.
-        const float lo_p = __fdividef((float)(lo[a] << kBrickShift) + 0.5f, N[a]);
-        const float hi_p = __fdividef((float)((lo[a] + 1) << kBrickShift) + 0.5f, N[a]);
+        // B = 2^kBrickShift; the box spans bricks lo .. lo + span - 1.
+        const float lo_p = __fdividef((float)(lo[a] * (1 << kBrickShift)) + 0.5f, N[a]);
+        const float hi_p = __fdividef((float)((lo[a] + span) * (1 << kBrickShift)) + 0.5f, N[a]);
         if (dir[a] > 0.0f) s_exit = fminf(s_exit, __fdividef(hi_p - base[a], dir[a]));
         else if (dir[a] < 0.0f) s_exit = fminf(s_exit, __fdividef(lo_p - base[a], dir[a]));
     }
     return s_exit;
 }
 
+__device__ __forceinline__ int brick_index(const GridView& g, int x0, int y0, int z0) {
+    return ((z0 >> kBrickShift) * g.nby + (y0 >> kBrickShift)) * g.nbx + (x0 >> kBrickShift);
+}
+
+__device__ __forceinline__ bool brick_in_grid(const GridView& g, int x0, int y0, int z0) {
+    return VI_BOUNDS_OK(kSiteBrick, x0 >> kBrickShift, g.nbx) &&
+           VI_BOUNDS_OK(kSiteBrick, y0 >> kBrickShift, g.nby) &&
+           VI_BOUNDS_OK(kSiteBrick, z0 >> kBrickShift, g.nbz);
+}
+
 // Whether the brick holding the footprint's lower corner may yield alpha > 0.
 __device__ __forceinline__ bool brick_may_be_lit(const GridView& g, const VoxelCoord& c) {
-    if (!(VI_BOUNDS_OK(kSiteBrick, c.x0 >> kBrickShift, g.nbx) &&
-          VI_BOUNDS_OK(kSiteBrick, c.y0 >> kBrickShift, g.nby) &&
-          VI_BOUNDS_OK(kSiteBrick, c.z0 >> kBrickShift, g.nbz)))
-        return false;
-    const int b = ((c.z0 >> kBrickShift) * g.nby + (c.y0 >> kBrickShift)) * g.nbx +
-                  (c.x0 >> kBrickShift);
-    return __ldg(g.flags + b) != 0;
+    if (!brick_in_grid(g, c.x0, c.y0, c.z0)) return false;
+    return __ldg(g.flags + brick_index(g, c.x0, c.y0, c.z0)) != 0;
+}
+
+// Skip distance of the brick holding the footprint's lower corner: 0 if it
+// may yield alpha > 0, else 1 + the radius of the box of bricks around it
+// that cannot (see GridView).
+__device__ __forceinline__ int brick_skip(const GridView& g, const VoxelCoord& c) {
+    if (!brick_in_grid(g, c.x0, c.y0, c.z0)) return 1;
+    return __ldg(g.skip + brick_index(g, c.x0, c.y0, c.z0));
 }
 
 // Integer to float without the conversion pipe: v < 2^23 placed in the mantissa
@@ -352,14 +376,10 @@ __device__ __forceinline__ size_t footprint_index(const VolumeView& v, const Foo
     return pair_index(v, c.x0, c.y0, c.z0);
 }
 
+// The march's test (its skip distances: 0 exactly where the flag is set).
 __device__ __forceinline__ bool footprint_may_be_lit(const GridView& g, const FootprintCell& c) {
-    if (!(VI_BOUNDS_OK(kSiteBrick, c.x0 >> kBrickShift, g.nbx) &&
-          VI_BOUNDS_OK(kSiteBrick, c.y0 >> kBrickShift, g.nby) &&
-          VI_BOUNDS_OK(kSiteBrick, c.z0 >> kBrickShift, g.nbz)))
-        return false;
-    const int b = ((c.z0 >> kBrickShift) * g.nby + (c.y0 >> kBrickShift)) * g.nbx +
-                  (c.x0 >> kBrickShift);
-    return __ldg(g.flags + b) != 0;
+    if (!brick_in_grid(g, c.x0, c.y0, c.z0)) return false;
+    return __ldg(g.skip + brick_index(g, c.x0, c.y0, c.z0)) == 0;
 }
 
 // Trilinear value of a footprint's eight voxels (an octet) at its weights.  uint16 voxels are

@@ -10,6 +10,13 @@
 // starts in an unflagged brick has alpha exactly 0 -- a trilinear value lies
 // within its corners' range, and a lerp of two zero entries is zero -- so the
 // sweep and the march skip its gather without changing any result.
+//
+// For the march's runs through such bricks, each brick also gets its
+// L-infinity distance to the nearest brick that may be lit (the skip
+// distance): a ray in a brick at distance d can move through the box of
+// bricks within d - 1 of it in one step instead of brick by brick.  The
+// distance transform is separable under the maximum norm, so three passes,
+// one per axis, compute it exactly up to the cap.
 #include <cmath>
 #include <type_traits>
 
@@ -103,6 +110,32 @@ __global__ void brick_flag_kernel(const uint32_t* __restrict__ range, int nbrick
     flags[b] = (lit_prefix[e_hi + 1] - lit_prefix[e_lo]) > 0 ? 1 : 0;
 }
 
+// One pass of the skip distance along `axis` (0: x, 1: y, 2: z):
+// out(b) = min over |d| <= kSkipCap of max(|d|, in(b + d e_axis)), with
+// in = 0 for bricks that may be lit and kSkipCap + 1 for the others in the
+// first pass (src = the flags), the previous pass's output after it.  Bricks
+// beyond the grid hold no samples and count as unlit.  After the x, y and z
+// passes, out(b) = min(L-infinity distance to the nearest lit brick,
+// kSkipCap + 1).
+__global__ void skip_pass_kernel(const uint8_t* __restrict__ src, uint8_t* __restrict__ dst,
+                                 int nbx, int nby, int nbz, int axis, int from_flags) {
+    const int nb = nbx * nby * nbz;
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const int c[3] = {b % nbx, (b / nbx) % nby, b / (nbx * nby)};
+    const int n = axis == 0 ? nbx : (axis == 1 ? nby : nbz);
+    const int stride = axis == 0 ? 1 : (axis == 1 ? nbx : nbx * nby);
+    const int lo = max(-kSkipCap, -c[axis]), hi = min(kSkipCap, n - 1 - c[axis]);
+    int out = kSkipCap + 1;
+    for (int d = lo; d <= hi; ++d) {
+        const int at = b + d * stride;
+        if (!VI_BOUNDS_OK(kSiteGrid, at, nb)) continue;
+        const int v = from_flags ? (src[at] != 0 ? 0 : kSkipCap + 1) : (int)src[at];
+        out = min(out, max(abs(d), v));
+    }
+    dst[b] = (uint8_t)out;
+}
+
 }  // namespace
 
 cudaError_t launch_volume_grid(const void* raw, int nx, int ny, int nz, int voxel_type,
@@ -120,12 +153,17 @@ cudaError_t launch_volume_grid(const void* raw, int nx, int ny, int nz, int voxe
     return cudaGetLastError();
 }
 
-cudaError_t launch_brick_flags(const uint32_t* range, int nbricks, const int* lit_prefix, int M,
-                               float vmin, float vmax, uint8_t* flags, cudaStream_t s) {
+cudaError_t launch_brick_flags(const uint32_t* range, int nbx, int nby, int nbz,
+                               const int* lit_prefix, int M, float vmin, float vmax,
+                               uint8_t* flags, uint8_t* skip, uint8_t* tmp, cudaStream_t s) {
+    const int nbricks = nbx * nby * nbz;
     const double scale = (double)(M - 1) / ((double)vmax - (double)vmin);
     const int threads = 256, blocks = (nbricks + threads - 1) / threads;
     brick_flag_kernel<<<blocks, threads, 0, s>>>(range, nbricks, lit_prefix, M, (double)vmin,
                                                  scale, flags);
+    skip_pass_kernel<<<blocks, threads, 0, s>>>(flags, skip, nbx, nby, nbz, 0, 1);
+    skip_pass_kernel<<<blocks, threads, 0, s>>>(skip, tmp, nbx, nby, nbz, 1, 0);
+    skip_pass_kernel<<<blocks, threads, 0, s>>>(tmp, skip, nbx, nby, nbz, 2, 0);
     return cudaGetLastError();
 }
 

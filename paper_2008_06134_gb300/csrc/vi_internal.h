@@ -95,8 +95,17 @@ struct VolumeView {
     float fnx, fny, fnz;  // (float)nx ...
 };
 
+// Brick occupancy.  flags[b] != 0: brick b may yield alpha > 0 (the sweep's
+// test).  skip[b] (the march's): 0 for such a brick, else the L-infinity
+// distance, in bricks and capped at kSkipCap + 1, from b to the nearest brick
+// that may yield alpha > 0 -- so every brick within skip[b] - 1 of b along
+// each axis cannot.  Both arrays hold one byte per brick, index
+// (bz nby + by) nbx + bx.
+constexpr int kSkipCap = 31;
+
 struct GridView {
     const uint8_t* flags;
+    const uint8_t* skip;
     int nbx, nby;
 #if VI_DEBUG_BOUNDS
     int nbz;
@@ -230,8 +239,12 @@ cudaError_t enqueue_march_batch(const BatchFrame* frames, int count, unsigned lo
 // Writes `epoch` to *ready on stream s, ordered after the stream's earlier work
 // and released to the whole device.
 cudaError_t launch_post_ready(unsigned* ready, unsigned epoch, cudaStream_t s);
-cudaError_t launch_brick_flags(const uint32_t* range, int nbricks, const int* lit_prefix, int M,
-                               float vmin, float vmax, uint8_t* flags, cudaStream_t s);
+// Brick flags from the brick ranges and the TF's prefix count of entries with
+// alpha > 0, then the skip distances from the flags (three passes, one per
+// axis, through tmp: nbricks bytes of scratch).
+cudaError_t launch_brick_flags(const uint32_t* range, int nbx, int nby, int nbz,
+                               const int* lit_prefix, int M, float vmin, float vmax,
+                               uint8_t* flags, uint8_t* skip, uint8_t* tmp, cudaStream_t s);
 #if VI_DEBUG_BOUNDS
 // Copies the violation record of the sweep, march or grid kernels on the
 // current device to out[4] and clears it (waits for the device first).

@@ -204,14 +204,15 @@ __device__ __forceinline__ VoxelCoord sample_cell(const MarchParams& p, const Ra
 }
 
 // Last sample j >= i such that samples i..j all lie in bricks that cannot
-// yield alpha > 0 (sample i, at t with cell vc, is in one).  Walks up to
-// kWalk bricks along the ray: in each, the last sample is estimated from the
-// brick exit and confirmed with the exact index path (each brick coordinate
-// is monotone in the sample index, so samples between two confirmed ones
-// share their brick).  The walk stops at a brick that may be lit or at the
-// ray's exit.
-// Bricks a warp's transparent-run walk may cover per step (16 measured faster
-// than 4 or 8; 32 was no better).
+// yield alpha > 0 (sample i, at t with cell vc, is in one).  Each step takes
+// the box of bricks that the current brick's skip distance d clears (those
+// within d - 1 of it along every axis; d = 1: the brick alone), estimates the
+// last sample inside it from the box exit and confirms it with the exact
+// index path (each brick coordinate is monotone in the sample index, so the
+// samples between two confirmed ones lie in the box too).  The walk stops at
+// a brick that may be lit, at the ray's exit, or after kWalk steps.
+// Steps a warp's transparent-run walk may take (16 measured faster than 4 or
+// 8 with one brick per step; 32 was no better).
 #ifndef VI_MARCH_WALK
 #define VI_MARCH_WALK 16
 #endif
@@ -220,19 +221,24 @@ constexpr int kWalk = VI_MARCH_WALK;
 __device__ __forceinline__ int last_transparent(const MarchParams& p, const Ray& r, int i, float t,
                                                 VoxelCoord vc) {
     int s = i;
+    int d = brick_skip(p.grid, vc);
     for (int w = 0; w < kWalk; ++w) {
         int end = s;
-        const float t_exit = brick_exit(p.vol, vc, r.o[0], r.o[1], r.o[2], r.d[0], r.d[1], r.d[2]);
+        const int rad = d - 1;
+        const float t_exit =
+            brick_exit(p.vol, vc, rad, r.o[0], r.o[1], r.o[2], r.d[0], r.d[1], r.d[2]);
         const float steps = (fminf(t_exit, r.t1) - t) / p.cam.dt;
         if (steps >= 2.0f) {
             const int j = s + (int)fminf(steps, 1.0e7f) - 1;
             float tj;
             const VoxelCoord cj = sample_cell(p, r, j, &tj);
-            if (tj < r.t1 && same_brick(vc, cj)) end = j;
+            if (tj < r.t1 && within_bricks(vc, cj, rad)) end = j;
         }
         // The sample after the run: past the exit, or in a brick that may be lit.
         vc = sample_cell(p, r, end + 1, &t);
-        if (!(t < r.t1) || brick_may_be_lit(p.grid, vc)) return end;
+        if (!(t < r.t1)) return end;
+        d = brick_skip(p.grid, vc);
+        if (d == 0) return end;
         s = end + 1;  // transparent as well: the walk goes on from here
     }
     return s;
