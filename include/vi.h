@@ -157,7 +157,12 @@ int vi_set_point_light(vi_ctx* ctx, const float position[3], const float color[3
    B_k = prod_{j<k} (1 - alpha_j).  mode (VI_NONE, VI_SHADOW, VI_SHELL,
    VI_CONE) selects the coefficient vi_render reads; VI_NONE builds nothing.
    Needs a volume, a TF and a light (VI_ESTATE otherwise).  Asynchronous.
-   n_slices and slice_res must be >= 1 and n_slices * slice_res^2 <= 2^34. */
+   n_slices and slice_res must be >= 1 and n_slices * slice_res^2 <= 2^34, and
+   the stack must fit one 2D texture of the device: n_slices cells of
+   slice_res^2 texels, C = 2^c cells to a row (slice_res C within the texture
+   width, 131072 texels on sm_103a), ceil(n_slices / C) slice_res rows within
+   its height (65000); VI_EINVAL otherwise.  Every configuration up to 1024
+   slices of 2048^2 fits. */
 int vi_build_attenuation(vi_ctx* ctx, int n_slices, int slice_res, int mode,
                          const vi_build_opts* opts);
 

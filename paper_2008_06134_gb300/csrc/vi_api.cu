@@ -225,72 +225,56 @@ int enter(vi_ctx* c) {
 void mark_stale(vi_ctx* c) { c->stack_valid = false; }
 
 void destroy_stack_textures(vi_ctx* c) {
-    for (int g = 0; g < c->ntex; ++g) cudaDestroyTextureObject(c->sview.tex[g]);
+    if (c->ntex) cudaDestroyTextureObject(c->sview.tex);
     c->ntex = 0;
 }
 
-// Pitched stack for n slices of R x R texels of format fmt, and its texture
-// views (rebuilt only when the shape, format or buffer changes).
+// Pitched stack for n slices of R x R texels of format fmt in the cell layout
+// of vi::StackView, and its texture view (rebuilt, and the memory zeroed, only
+// when the shape, format or buffer changes).
 int setup_stack(vi_ctx* c, int n, int R, int fmt) {
-    const size_t esize = format_bytes(fmt);
-    const size_t pitch = (R * esize + 511) / 512 * 512;
-    int max_h = 0, max_w = 0;
-    cudaError_t e = cudaDeviceGetAttribute(&max_h, cudaDevAttrMaxTexture2DLinearHeight, c->device);
-    if (e == cudaSuccess)
-        e = cudaDeviceGetAttribute(&max_w, cudaDevAttrMaxTexture2DLinearWidth, c->device);
-    if (e != cudaSuccess) return cuda_fail(c, e);
-    if (R > max_w || R + 1 > max_h) return VI_EINVAL;
-    int spt_log2 = 0;
-    while (spt_log2 < 30 && ((size_t)2 << spt_log2) * (size_t)(R + 1) <= (size_t)max_h &&
-           (1 << (spt_log2 + 1)) <= n)
-        ++spt_log2;
-    const int spt = 1 << spt_log2;
-    const int ntex = (n + spt - 1) / spt;
-    if (ntex > vi::kMaxStackTextures) return VI_EINVAL;
-    const size_t bytes = (size_t)n * (size_t)(R + 1) * pitch + 512;
+    vi_detail::StackLayout L;
+    int rc = vi_detail::stack_layout(c->device, n, R, format_bytes(fmt), &L);
+    if (rc) return rc == VI_ECUDA ? cuda_fail(c, cudaGetLastError()) : rc;
     void* before = c->stack_mem;
-    int rc = ensure(c, &c->stack_mem, &c->stack_cap, bytes);
+    rc = ensure(c, &c->stack_mem, &c->stack_cap, L.bytes);
     if (rc) return rc;
     if (before != c->stack_mem) c->stack_valid = false;
     void* base = reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(c->stack_mem) + 511) &
                                          ~(uintptr_t)511);
-    const bool same = before == c->stack_mem && c->stack == base && c->row_pitch == pitch &&
-                      c->ntex == ntex && c->sview.spt_log2 == spt_log2 &&
+    const bool same = before == c->stack_mem && c->stack == base && c->row_pitch == L.pitch &&
+                      c->ntex == 1 && c->sview.cells_log2 == L.cells_log2 &&
                       c->stack_valid_shape_n == n && c->stack_valid_shape_R == R &&
                       c->stack_valid_shape_fmt == fmt;
     c->stack = base;
-    c->row_pitch = pitch;
+    c->row_pitch = L.pitch;
     if (same) return VI_OK;
     c->stack_valid = false;
     destroy_stack_textures(c);
-    cudaChannelFormatDesc ch = fmt == VI_F32 ? cudaCreateChannelDesc<float>()
-                                             : cudaCreateChannelDesc<unsigned short>();
-    for (int g = 0; g < ntex; ++g) {
-        const int slices = (g + 1) * spt <= n ? spt : n - g * spt;
-        cudaResourceDesc res;
-        std::memset(&res, 0, sizeof(res));
-        res.resType = cudaResourceTypePitch2D;
-        res.res.pitch2D.devPtr = static_cast<char*>(base) + (size_t)g * spt * (R + 1) * pitch;
-        res.res.pitch2D.desc = ch;
-        res.res.pitch2D.width = (size_t)R;
-        res.res.pitch2D.height = (size_t)slices * (R + 1);
-        res.res.pitch2D.pitchInBytes = pitch;
-        cudaTextureDesc td;
-        std::memset(&td, 0, sizeof(td));
-        td.addressMode[0] = cudaAddressModeClamp;
-        td.addressMode[1] = cudaAddressModeClamp;
-        td.filterMode = cudaFilterModePoint;
-        td.readMode = cudaReadModeElementType;
-        td.normalizedCoords = 0;
-        e = cudaCreateTextureObject(&c->sview.tex[g], &res, &td, nullptr);
-        if (e != cudaSuccess) {
-            c->ntex = g;
-            destroy_stack_textures(c);
-            return cuda_fail(c, e);
-        }
-        c->ntex = g + 1;
-    }
-    c->sview.spt_log2 = spt_log2;
+    // Lookups read outside a slice only with weight 0, but that must be a
+    // finite number: zero what no sweep writes (and everything, for brevity).
+    cudaError_t e = cudaMemsetAsync(base, 0, L.rows * L.pitch, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    cudaResourceDesc res;
+    std::memset(&res, 0, sizeof(res));
+    res.resType = cudaResourceTypePitch2D;
+    res.res.pitch2D.devPtr = base;
+    res.res.pitch2D.desc = fmt == VI_F32 ? cudaCreateChannelDesc<float>()
+                                         : cudaCreateChannelDesc<unsigned short>();
+    res.res.pitch2D.width = ((size_t)R) << L.cells_log2;
+    res.res.pitch2D.height = L.rows;
+    res.res.pitch2D.pitchInBytes = L.pitch;
+    cudaTextureDesc td;
+    std::memset(&td, 0, sizeof(td));
+    td.addressMode[0] = cudaAddressModeClamp;
+    td.addressMode[1] = cudaAddressModeClamp;
+    td.filterMode = cudaFilterModePoint;
+    td.readMode = cudaReadModeElementType;
+    td.normalizedCoords = 0;
+    e = cudaCreateTextureObject(&c->sview.tex, &res, &td, nullptr);
+    if (e != cudaSuccess) return cuda_fail(c, e);
+    c->ntex = 1;
+    c->sview.cells_log2 = L.cells_log2;
     c->stack_valid_shape_n = n;
     c->stack_valid_shape_R = R;
     c->stack_valid_shape_fmt = fmt;
@@ -422,6 +406,32 @@ int check_render_inputs(vi_ctx* c, const vi_camera* cam, int W, int H, float ste
 }  // namespace
 
 namespace vi_detail {
+
+int stack_layout(int device, int n, int R, size_t esize, StackLayout* out) {
+    int max_h = 0, max_w = 0, max_pitch = 0;
+    cudaError_t e = cudaDeviceGetAttribute(&max_h, cudaDevAttrMaxTexture2DLinearHeight, device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&max_w, cudaDevAttrMaxTexture2DLinearWidth, device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&max_pitch, cudaDevAttrMaxTexture2DLinearPitch, device);
+    if (e != cudaSuccess) return VI_ECUDA;
+    if (n < 1 || R < 1 || R > max_w || R > max_h) return VI_EINVAL;
+    // Cells a row of cells can hold: width and pitch limits.
+    auto fits_width = [&](int lg) {
+        return lg < 30 && ((size_t)R << lg) <= (size_t)max_w &&
+               ((((size_t)R * esize) << lg) + 511) / 512 * 512 <= (size_t)max_pitch;
+    };
+    auto rows_for = [&](int lg) { return (((size_t)n + ((size_t)1 << lg) - 1) >> lg) * (size_t)R; };
+    int lg = 0;
+    while ((((size_t)1 << lg) << lg) < (size_t)n && fits_width(lg + 1)) ++lg;
+    while (rows_for(lg) > (size_t)max_h && fits_width(lg + 1)) ++lg;
+    if (rows_for(lg) > (size_t)max_h) return VI_EINVAL;
+    out->cells_log2 = lg;
+    out->rows = rows_for(lg);
+    out->pitch = ((((size_t)R * esize) << lg) + 511) / 512 * 512;
+    out->bytes = out->rows * out->pitch + 512;
+    return VI_OK;
+}
 
 int ensure_mem(size_t* used, size_t budget, void** p, size_t* cap, size_t bytes, cudaStream_t s,
                cudaMemPool_t pool) {
@@ -845,6 +855,7 @@ int vi_build_attenuation(vi_ctx* c, int n, int R, int mode, const vi_build_opts*
     p.lt = lt;
     p.stack = c->stack;
     p.row_pitch = c->row_pitch;
+    p.cells_log2 = c->sview.cells_log2;
     p.opacity_correction = o.opacity_correction ? 1 : 0;
     p.spacing_vox = lt.dL * (float)nmax(c);
     p.comp_n = o.comp_n;
@@ -915,11 +926,14 @@ int vi_get_attenuation(vi_ctx* c, void* out, size_t out_bytes, int out_on_device
         return VI_EINVAL;
     out_on_device = out_on_device == VI_OUT_DEVICE;  // the copy is waited for either way
     const int n = c->lt.n, R = c->lt.R;
-    const size_t row = (size_t)R * format_bytes(c->bopts.format);
+    const size_t esize = format_bytes(c->bopts.format);
+    const size_t row = (size_t)R * esize;
     for (int k = 0; k < n; ++k) {
         cudaError_t e = cudaMemcpy2DAsync(
             static_cast<char*>(out) + (size_t)k * R * row, row,
-            static_cast<const char*>(c->stack) + (size_t)k * (R + 1) * c->row_pitch, c->row_pitch,
+            static_cast<const char*>(c->stack) +
+                vi::slice_origin(k, R, c->sview.cells_log2, c->row_pitch / esize) * esize,
+            c->row_pitch,
             row, (size_t)R, out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
             c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e);

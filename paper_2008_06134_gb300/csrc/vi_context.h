@@ -61,9 +61,9 @@ struct vi_ctx {
     size_t stack_cap = 0;
     void* stack = nullptr;
     size_t stack_bytes = 0;      // dense size n R^2 element bytes, as vi_get_attenuation returns
-    size_t row_pitch = 0;        // bytes per stack row (pitched layout, R + 1 rows per slice)
-    vi::StackView sview{};       // texture views of the stack
-    int ntex = 0;
+    size_t row_pitch = 0;        // bytes per stack row (the cell layout of vi::StackView)
+    vi::StackView sview{};       // texture view of the stack
+    int ntex = 0;                // 1 while sview.tex exists
     int stack_valid_shape_n = 0; // slice count, resolution and format the texture views
     int stack_valid_shape_R = 0; // were made for
     int stack_valid_shape_fmt = -1;
@@ -115,6 +115,18 @@ int volume_load(VolumeRes* v, size_t* used, size_t budget, const void* data, int
 // Frees the volume's buffers (ordered on `s` when they came from a pool).
 void volume_release(VolumeRes* v, size_t* used, cudaStream_t s);
 size_t volume_bytes(int dtype, int nx, int ny, int nz);
+
+// Layout of an n-slice R x R stack with esize-byte texels (vi::StackView):
+// 2^cells_log2 cells to a row of cells (the smallest power of two at least
+// sqrt(n), widened until the rows fit the texture height, within its width),
+// `rows` texel rows of `pitch` bytes, and the allocation (`bytes`, with room
+// to align the start to 512 bytes).  VI_EINVAL when the stack does not fit
+// one 2D texture of `device`; VI_ECUDA when its limits cannot be read.
+struct StackLayout {
+    int cells_log2;
+    size_t rows, pitch, bytes;
+};
+int stack_layout(int device, int n, int R, size_t esize, StackLayout* out);
 
 // Points the context at a volume it does not own and refreshes the brick
 // flags.  The stack goes stale unless keep_stack is set and the context was

@@ -433,18 +433,17 @@ __device__ __forceinline__ void tf_coord(float v, float vmin, float scale, int M
 // ---------------------------------------------------------------------------
 // Stack lookup (Eq. 9 slice, Eq. 10 UV): nearest slice k = clamp(floor(lambda
 // + 1/2), 0, n - 1), bilinear over texel centres at integer (tu, tv) with
-// clamp to edge.  floor-to-int is one cvt.rmi; offsets inside a slice are
-// 32-bit (R <= 65536, so R^2 - 1 fits an unsigned int).
+// clamp to edge.
 
 __device__ __forceinline__ int slice_index(float lam, int n) {
     return clampi(__float2int_rd(__fadd_rn(lam, 0.5f)), 0, n - 1);
 }
 
-// Bilinear lookup in slice k of the stack through its texture view.  Slice k
-// is rows [row0, row0 + R) of texture stack_tex[k >> spt_log2] with row0 =
-// (k & (2^spt_log2 - 1)) (R + 1); the extra row R repeats row R - 1, so the
-// footprint of the last row stays inside the slice, and the texture's clamp
-// addressing covers the last column.
+// Bilinear lookup in slice k of the stack through its texture view (the
+// cell layout of StackView).  Both coordinates are clamped to [0, R - 1]
+// first: past an edge the clamp-to-edge footprint holds copies of the edge
+// texel, and the clamped point reads the edge texel with weight 1 and its
+// neighbour (in the next cell, or zero) with weight 0 -- the same value.
 template <typename Fmt>
 __device__ __forceinline__ float bilinear(const StackView& sv, int k, int n, int R, float tu,
                                           float tv, int* rec = nullptr) {
@@ -452,22 +451,20 @@ __device__ __forceinline__ float bilinear(const StackView& sv, int k, int n, int
         rec[1] = clampi(__float2int_rd(tu), -1, R);
         rec[2] = clampi(__float2int_rd(tv), -1, R);
     }
-    // Columns: the texture's clamp addressing turns a footprint that reaches
-    // past either edge into two copies of the edge texel, which is exactly the
-    // clamp-to-edge result.  Rows: slices are stacked in one texture, so the
-    // row coordinate is clamped to the slice first (the guard row R covers the
-    // footprint of row R - 1).
-    const float fu = floorf(tu);
-    const float wu = tu - fu;
+    const float cu = fminf(fmaxf(tu, 0.0f), (float)(R - 1));
+    const float fu = floorf(cu);
+    const float wu = cu - fu;
     const float cv = fminf(fmaxf(tv, 0.0f), (float)(R - 1));
     const float fv = floorf(cv);
     const float wv = cv - fv;
     if (!(VI_BOUNDS_OK(kSiteStackTex, k, n) && VI_BOUNDS_OK(kSiteStackTex, (int)fv, R)))
         return 1.0f;
-    // Gather takes the footprint's lower-left texel plus one (exact integers).
-    const float row0 = (float)((k & ((1 << sv.spt_log2) - 1)) * (R + 1) + 1);
+    // Gather takes the footprint's lower-left texel plus one (exact integers):
+    // the cell's first column and row, plus one, are below 2^23.
+    const float x1 = u2f((unsigned)((k & ((1 << sv.cells_log2) - 1)) * R + 1));
+    const float y1 = u2f((unsigned)((k >> sv.cells_log2) * R + 1));
     float b00, b01, b10, b11;
-    Fmt::gather(sv.tex[k >> sv.spt_log2], fu + 1.0f, fv + row0, b00, b01, b10, b11);
+    Fmt::gather(sv.tex, fu + x1, fv + y1, b00, b01, b10, b11);
     const float top = fmaf(wu, b01 - b00, b00);
     const float bot = fmaf(wu, b11 - b10, b10);
     return fmaf(wv, bot - top, top);

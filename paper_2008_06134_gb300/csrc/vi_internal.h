@@ -112,17 +112,28 @@ struct GridView {
 #endif
 };
 
-// The attenuation stack in device memory.  Slice k, row j (0 <= j <= R) starts
-// at byte k (R + 1) row_pitch + j row_pitch; row R repeats row R - 1.  Texture g
-// views slices [g 2^spt_log2, (g + 1) 2^spt_log2) as one pitched 2D texture, R
-// texels wide and 2^spt_log2 (R + 1) rows high (2D linear textures are limited
-// in height, so a deep stack needs several).
-constexpr int kMaxStackTextures = 128;
-
+// The attenuation stack in device memory: one pitched 2D texture of R x R
+// cells, 2^cells_log2 cells to a row of cells.  Slice k is the cell in column
+// c = k & (2^cells_log2 - 1) and row r = k >> cells_log2: its texel (i, j) is
+// element (r R + j) pitch + c R + i.  One texture for every slice keeps the
+// lookup's texture handle the same for every lane (a per-lane handle costs a
+// loop over the handles a warp holds).  Lookups clamp their coordinates to the
+// slice, so a footprint never leaves its cell except with weight 0, and what
+// it reads there (the next cell, or a cell no slice uses) is finite: the
+// texture memory is zeroed whenever its layout changes.
 struct StackView {
-    int spt_log2;  // slices per texture = 2^spt_log2
-    cudaTextureObject_t tex[kMaxStackTextures];
+    cudaTextureObject_t tex;
+    int cells_log2;  // cells to a row of cells = 2^cells_log2
 };
+
+// Element offset of slice k's texel (0, 0), for a row pitch of `pitch`
+// elements.
+__host__ __device__ __forceinline__ size_t slice_origin(int k, int R, int cells_log2,
+                                                        size_t pitch) {
+    const size_t col = (size_t)(k & ((1 << cells_log2) - 1));
+    const size_t row = (size_t)(k >> cells_log2);
+    return row * (size_t)R * pitch + col * (size_t)R;
+}
 
 struct SweepParams {
     VolumeView vol;
@@ -133,6 +144,7 @@ struct SweepParams {
     LightFrame lt;
     void* stack;              // pitched: see StackView
     size_t row_pitch;         // bytes
+    int cells_log2;           // see StackView
     int opacity_correction;
     float spacing_vox;        // slice spacing in voxels (opacity correction exponent)
     float comp_n;             // darkening compensation exponent, 0 = off

@@ -147,9 +147,12 @@ size_t slot_growth(const Slot* sl, const Request* r, const ServerVolume* v) {
     const vi_request& q = r->req;
     const int fmt = q.mode == VI_NONE ? 0 : q.build.format;
     const size_t esize = fmt == VI_F32 ? 4 : 2;
-    const size_t pitch = ((size_t)q.slice_res * esize + 511) / 512 * 512;
-    const size_t stack = q.mode == VI_NONE ? 0
-                                           : (size_t)q.n_slices * (q.slice_res + 1) * pitch + 512;
+    vi_detail::StackLayout L;
+    const size_t stack =
+        q.mode == VI_NONE ||
+                vi_detail::stack_layout(sl->ctx->device, q.n_slices, q.slice_res, esize, &L) != VI_OK
+            ? 0
+            : L.bytes;
     constexpr int B = 1 << vi::kBrickShift;
     const size_t bricks =
         (size_t)((v->nx + B - 1) / B) * ((v->ny + B - 1) / B) * ((v->nz + B - 1) / B);

@@ -78,11 +78,28 @@ __device__ __forceinline__ bool texel_inside(const LightFrame& lt, int k, const 
     return P0 >= 0.0f && P0 <= 1.0f && P1 >= 0.0f && P1 <= 1.0f && P2 >= 0.0f && P2 <= 1.0f;
 }
 
-// One stack store; a checked build first tests the element against the stack.
+// Element offsets of the slices (the cell layout of StackView): slice k's
+// texels start slice_origin(k) elements past slice 0's.
+struct SliceAddr {
+    size_t cell_row;  // elements from a row of cells to the next: R pitch
+    int R, cells_log2;
+    __device__ __forceinline__ size_t at(int k) const {
+        return (size_t)(k >> cells_log2) * cell_row +
+               (size_t)((k & ((1 << cells_log2) - 1)) * R);
+    }
+};
+
+__device__ __forceinline__ SliceAddr slice_addr(const SweepParams& p, size_t esize) {
+    return SliceAddr{(size_t)p.lt.R * (p.row_pitch / esize), p.lt.R, p.cells_log2};
+}
+
+// One stack store; a checked build first tests the element against the stack
+// (its rows of cells).
 template <typename T>
 __device__ __forceinline__ void put(const SweepParams& p, T* out, size_t at, T v) {
     if (!VI_BOUNDS_OK(kSiteStackStore, (out + at) - static_cast<T*>(p.stack),
-                      (long long)p.lt.n * (p.lt.R + 1) * (long long)(p.row_pitch / sizeof(T))))
+                      (long long)(((p.lt.n - 1) >> p.cells_log2) + 1) * p.lt.R *
+                          (long long)(p.row_pitch / sizeof(T))))
         return;
     out[at] = v;
 }
@@ -96,7 +113,7 @@ template <typename VoxT, typename Fmt, bool DEPTH>
 __device__ __forceinline__ void sweep_lockstep(const SweepParams& p, const float* s_alpha,
                                                const float o[3], const float w[3], float spacing,
                                                int kin, int kout, bool valid,
-                                               typename Fmt::T* out, size_t slice, size_t dup) {
+                                               typename Fmt::T* out, SliceAddr slice) {
     const LightFrame& lt = p.lt;
     const bool has = kin <= kout;
     const int klo = __reduce_min_sync(0xffffffffu, has ? kin : lt.n);
@@ -106,8 +123,7 @@ __device__ __forceinline__ void sweep_lockstep(const SweepParams& p, const float
     int k = 0;
     for (; k < klo; ++k) {
         if (valid) {
-            put(p, out, (size_t)k * slice, one);
-            if (dup) put(p, out, (size_t)k * slice + dup, one);
+            put(p, out, slice.at(k), one);
         }
     }
     for (; k <= khi; k += kLockBatch) {
@@ -150,8 +166,7 @@ __device__ __forceinline__ void sweep_lockstep(const SweepParams& p, const float
                                : fminf(1.0f, T * powf(1.0f + alpha, p.comp_n));
             if (valid) {
                 const typename Fmt::T q = Fmt::pack(stored);
-                put(p, out, (size_t)(k + u) * slice, q);
-                if (dup) put(p, out, (size_t)(k + u) * slice + dup, q);
+                put(p, out, slice.at(k + u), q);
             }
             if (DEPTH)
                 T = fminf(T - log1pf(-alpha), kDepthMax);  // alpha = 1: tau = inf, capped
@@ -163,8 +178,7 @@ __device__ __forceinline__ void sweep_lockstep(const SweepParams& p, const float
     const typename Fmt::T last = Fmt::pack(T);
     for (; k < lt.n; ++k) {
         if (valid) {
-            put(p, out, (size_t)k * slice, last);
-            if (dup) put(p, out, (size_t)k * slice + dup, last);
+            put(p, out, slice.at(k), last);
         }
     }
 }
@@ -250,28 +264,24 @@ __device__ __forceinline__ void sweep_column(const SweepParams& p, const float* 
     int kin, kout;
     column_setup(p, i, j, o, w, spacing, kin, kout);
 
-    // Pitched stack: slice k, row j at byte (k (R + 1) + j) row_pitch.  The last
-    // row (j = R - 1) is written twice, its copy being row R.
-    const size_t slice = (size_t)(lt.R + 1) * p.row_pitch / sizeof(typename Fmt::T);
+    // Texel (i, j) of slice k: element slice.at(k) past texel (i, j) of slice 0.
+    const SliceAddr slice = slice_addr(p, sizeof(typename Fmt::T));
     typename Fmt::T* out = reinterpret_cast<typename Fmt::T*>(static_cast<char*>(p.stack) +
                                                               (size_t)j * p.row_pitch) + i;
-    const size_t dup = j == lt.R - 1 ? p.row_pitch / sizeof(typename Fmt::T) : 0;
 
     if (LOCKSTEP) {
         if (!valid) {
             kin = lt.n;
             kout = -1;
         }
-        sweep_lockstep<VoxT, Fmt, DEPTH>(p, s_alpha, o, w, spacing, kin, kout, valid, out, slice,
-                                         dup);
+        sweep_lockstep<VoxT, Fmt, DEPTH>(p, s_alpha, o, w, spacing, kin, kout, valid, out, slice);
         return;
     }
     // Before the cube: full light (transmittance 1, optical depth 0).
     const typename Fmt::T one = Fmt::pack(DEPTH ? 0.0f : 1.0f);
     int k = 0;
     for (; k < min(kin, lt.n); ++k) {
-        put(p, out, (size_t)k * slice, one);
-        if (dup) put(p, out, (size_t)k * slice + dup, one);
+        put(p, out, slice.at(k), one);
     }
     // Inside the cube, four slices at a time: their positions, brick flags and
     // footprints do not depend on T, so the loads of a batch are issued together
@@ -314,8 +324,7 @@ __device__ __forceinline__ void sweep_column(const SweepParams& p, const float* 
                 stored = DEPTH ? fmaxf(0.0f, T - p.comp_n * log1pf(alpha))
                                : fminf(1.0f, T * powf(1.0f + alpha, p.comp_n));
             const typename Fmt::T q = Fmt::pack(stored);
-            put(p, out, (size_t)(k + u) * slice, q);
-            if (dup) put(p, out, (size_t)(k + u) * slice + dup, q);
+            put(p, out, slice.at(k + u), q);
             if (DEPTH)
                 T = fminf(T - log1pf(-alpha), kDepthMax);  // alpha = 1: tau = inf, capped
             else
@@ -326,8 +335,7 @@ __device__ __forceinline__ void sweep_column(const SweepParams& p, const float* 
     // Past the cube: the light that left it.
     const typename Fmt::T last = Fmt::pack(T);
     for (; k < lt.n; ++k) {
-        put(p, out, (size_t)k * slice, last);
-        if (dup) put(p, out, (size_t)k * slice + dup, last);
+        put(p, out, slice.at(k), last);
     }
 }
 
@@ -442,7 +450,7 @@ __global__ void __launch_bounds__(kChunkThreads, VI_SWEEP_CHUNK_MIN_BLOCKS)
     const int R = lt.R, n = lt.n;
     const unsigned tiles_x = (unsigned)(R + TW - 1) / TW;
     const unsigned ntiles = tiles_x * ((unsigned)(R + TH - 1) / TH);
-    const size_t slice = (size_t)(R + 1) * p.row_pitch / sizeof(T_);
+    const SliceAddr slice = slice_addr(p, sizeof(T_));
     const T_ one = Fmt::pack(DEPTH ? 0.0f : 1.0f);
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(p.tile_counter, 1u);
@@ -484,13 +492,11 @@ __global__ void __launch_bounds__(kChunkThreads, VI_SWEEP_CHUNK_MIN_BLOCKS)
         const int klo = s_range[0], khi = s_range[1];  // klo > khi: the tile misses the cube
         T_* out = reinterpret_cast<T_*>(static_cast<char*>(p.stack) +
                                         (size_t)min(j, R - 1) * p.row_pitch) + min(i, R - 1);
-        const size_t dup = j == R - 1 ? p.row_pitch / sizeof(T_) : 0;
 
         // Before the tile's first slice in the cube: full light.
         for (int k = warp; k < min(klo, n); k += kChunkWarps)
             if (valid) {
-                put(p, out, (size_t)k * slice, one);
-                if (dup) put(p, out, (size_t)k * slice + dup, one);
+                put(p, out, slice.at(k), one);
             }
         // Rounds of kChunkWarps chunks over [klo, khi].
         for (int base = klo; base <= khi; base += kChunkWarps * kChunkLen) {
@@ -549,8 +555,7 @@ __global__ void __launch_bounds__(kChunkThreads, VI_SWEEP_CHUNK_MIN_BLOCKS)
                     if (COMP) v = fminf(1.0f, v * powf(1.0f + ex[u], p.comp_n));
                 }
                 const T_ q = Fmt::pack(v);
-                put(p, out, (size_t)k * slice, q);
-                if (dup) put(p, out, (size_t)k * slice + dup, q);
+                put(p, out, slice.at(k), q);
             }
             __syncthreads();  // every warp has read the carry and the totals
             if (warp == kChunkWarps - 1) s_carry[lane] = DEPTH ? pre + T : pre * T;
@@ -562,8 +567,7 @@ __global__ void __launch_bounds__(kChunkThreads, VI_SWEEP_CHUNK_MIN_BLOCKS)
         const T_ q = Fmt::pack(last);
         for (int k = max(khi + 1, 0) + warp; k < n; k += kChunkWarps)
             if (valid) {
-                put(p, out, (size_t)k * slice, q);
-                if (dup) put(p, out, (size_t)k * slice + dup, q);
+                put(p, out, slice.at(k), q);
             }
     }
 }
