@@ -963,10 +963,10 @@ def serving_setup(args):
                         q["slice_res"], q["mode"], q["camera"], q["width"], q["height"],
                         q["step_vox"], out, format=fmt, ert=q["ert"])
 
-    def run(slots, fmt, burst, reqs, graphs=False, batching=False):
+    def run(slots, fmt, burst, reqs, graphs=False, batching=False, eviction=vi.EVICT_COST):
         outs = [torch.empty((q["height"], q["width"], 4), device="cuda") for q in reqs]
         with vi.Server(0, slots=slots, memory_budget=budget, max_resident_volumes=6,
-                       graphs=graphs, batching=batching) as s:
+                       graphs=graphs, batching=batching, eviction=eviction) as s:
             vids = [s.add_volume(h, c) for h, c in zip(host, codes)]
             warm = torch.empty((64, 64, 4), device="cuda")
             for i in range(len(specs)):           # untimed: load every volume once
@@ -998,6 +998,8 @@ def serving_setup(args):
                               "p99": round(float(np.percentile(times[:, 2] - times[:, 1], 99)), 3)},
                "failed": failed,
                "volume_loads": st["volume_loads"] - base["volume_loads"],
+               "volume_load_mib": round((st["volume_load_bytes"] - base["volume_load_bytes"])
+                                        / float(1 << 20), 1),
                "volume_evictions": st["volume_evictions"] - base["volume_evictions"],
                "stack_reuses": st["stack_reuses"] - base["stack_reuses"],
                "peak_bytes": st["peak_bytes"]}
@@ -1014,31 +1016,36 @@ def serving_setup(args):
 
 def serving_summary(args):
     """The headline line's serving figures: 512 requests of the serving mix at
-    800/s, the plain path (one slot, one frame at a time, FP32 stacks) against
-    the served reduced-precision path (8 slots, FP16 stacks; per-slot marches
-    and batched marches), with the served frames' max error against the plain
-    FP32 frames."""
+    300/s and at 800/s, the plain path (one slot, one frame at a time, FP32
+    stacks) against the served reduced-precision path (8 slots, FP16 stacks;
+    at 800/s also with batched marches), with the served frames' max error
+    against the plain FP32 frames.  Volumes are evicted by reload cost
+    (GreedyDual, the server's default)."""
     import torch
     from paper_2008_06134_gb300 import vi
     a = argparse.Namespace(**vars(args))
-    a.rate, a.requests, a.slots = "800", 512, 8
+    a.rate, a.requests, a.slots = "300,800", 512, 8
     sv = serving_setup(a)
-    reqs = sv["mixes"][800.0]
-    out = {"requests": 512, "rate_per_s": 800, "slots": 8, "budget_gib": a.budget_gib,
-           "max_resident_volumes": 6}
-    plain, plain_outs = sv["run"](1, vi.F32, False, reqs)
-    out["plain-f32-1slot"] = {k: plain[k] for k in ("frames_per_s", "latency_ms", "failed")}
-    for name, batching in (("served-f16-8slots", False), ("served-f16-8slots-batched", True)):
-        row, outs = sv["run"](8, vi.F16, False, reqs, batching=batching)
-        err = max(float((x - y).abs().max()) for x, y in zip(outs, plain_outs))
-        out[name] = {k: row[k] for k in ("frames_per_s", "latency_ms", "failed")}
-        out[name]["max_abs_err_vs_plain_f32"] = float(f"{err:.3g}")
-        del outs
-    p99 = {k: out[k]["latency_ms"]["p99"] for k in out if isinstance(out[k], dict)}
-    out["served_f16_beats_plain_f32_p99"] = min(p99["served-f16-8slots"],
-                                                p99["served-f16-8slots-batched"]) \
-        <= p99["plain-f32-1slot"]
-    del plain_outs
+    out = {"requests": 512, "rates_per_s": [300, 800], "slots": 8, "budget_gib": a.budget_gib,
+           "max_resident_volumes": 6, "eviction": "reload cost (GreedyDual)"}
+    keys = ("frames_per_s", "latency_ms", "failed", "volume_loads", "volume_load_mib")
+    beats = {}
+    for rate in (300, 800):
+        reqs = sv["mixes"][float(rate)]
+        plain, plain_outs = sv["run"](1, vi.F32, False, reqs)
+        out[f"plain-f32-1slot-{rate}"] = {k: plain[k] for k in keys}
+        arms = [("served-f16-8slots", False)] + ([("served-f16-8slots-batched", True)]
+                                                  if rate == 800 else [])
+        for name, batching in arms:
+            row, outs = sv["run"](8, vi.F16, False, reqs, batching=batching)
+            err = max(float((x - y).abs().max()) for x, y in zip(outs, plain_outs))
+            out[f"{name}-{rate}"] = {k: row[k] for k in keys}
+            out[f"{name}-{rate}"]["max_abs_err_vs_plain_f32"] = float(f"{err:.3g}")
+            del outs
+        beats[rate] = (out[f"served-f16-8slots-{rate}"]["latency_ms"]["p99"]
+                       <= out[f"plain-f32-1slot-{rate}"]["latency_ms"]["p99"])
+        del plain_outs
+    out["served_f16_beats_plain_f32_p99"] = {f"{r}/s": b for r, b in beats.items()}
     torch.cuda.empty_cache()
     return out
 
@@ -1052,7 +1059,9 @@ def serving_workload(args):
     time: the plain path), and `--slots` concurrent slots with FP32 and with
     FP16 stacks, each under Poisson arrivals at `--rate` and as one burst; the
     FP32 served runs again with each request's device work launched as one
-    CUDA graph, and the served runs with batched marches.
+    CUDA graph, and the served runs with batched marches.  Every run evicts
+    volumes by their reload cost (GreedyDual); the plain run and the served
+    FP16 run are repeated with least-recently-used eviction.
     Reports per run frames/s and request latency (submission to completion)
     percentiles; the FP32 served frames are compared with the plain ones."""
     import torch
@@ -1077,6 +1086,12 @@ def serving_workload(args):
                 row["max_abs_err_vs_plain_f32"] = float(f"{err:.3g}")
             runs[f"served-{fname}-{args.slots}slots-poisson{rate:g}"] = row
             del outs
+        # Least-recently-used eviction in place of the reload-cost order.
+        row, _ = run(1, vi.F32, False, reqs, eviction=vi.EVICT_LRU)
+        runs[f"plain-f32-1slot-lru-poisson{rate:g}"] = row
+        row, outs = run(args.slots, vi.F16, False, reqs, eviction=vi.EVICT_LRU)
+        runs[f"served-f16-{args.slots}slots-lru-poisson{rate:g}"] = row
+        del outs
         # The same FP32 runs with each request's device work as one CUDA graph.
         row, outs = run(args.slots, vi.F32, False, reqs, graphs=True)
         row["frames_identical_to_plain"] = sum(bool(torch.equal(a, b))

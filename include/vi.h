@@ -332,9 +332,9 @@ int vi_debug_bounds(int device, uint64_t* violations, int* first_site, int64_t* 
    budget, so frames of different requests run on the GPU together.  Volumes
    are registered once and kept resident (pair bricks and brick ranges) up to
    max_resident_volumes (0 = no count limit) and memory_budget bytes in total
-   with the slots' buffers (0 = no byte limit); the least recently used idle
-   volume is evicted when room is needed and reloaded from the caller's host
-   copy when next requested.  A request that can never fit fails with
+   with the slots' buffers (0 = no byte limit); when room is needed an idle
+   volume is evicted (vi_server_set_eviction chooses which) and reloaded from
+   the caller's host copy when next requested.  A request that can never fit fails with
    VI_ENOMEM; others wait.  All host-side waits are bounded.
    Each slot keeps the attenuation stack of its last request.  A request with
    the same volume, TF (entries and range), light, stack shape, mode and build
@@ -378,6 +378,7 @@ typedef struct {
     uint64_t graph_instantiations;  /* executable graphs created (the rest were updated) */
     uint64_t batches;               /* batches of marches enqueued (vi_server_set_batching) */
     uint64_t batched_frames;        /* frames marched in those batches */
+    uint64_t volume_load_bytes;     /* raw voxel bytes copied in by volume_loads */
 } vi_server_stats;
 
 /* Create / destroy a server (destroy cancels queued requests, lets running
@@ -444,6 +445,24 @@ int vi_server_set_graphs(vi_server* server, int enabled);
    a null server or wait_ms outside [0, 1e7], VI_ECUDA if the batch stream
    or the status words cannot be made. */
 int vi_server_set_batching(vi_server* server, int enabled, double wait_ms);
+
+/* Which idle volume the server evicts when a request needs room (a volume
+   count or byte limit).  Serving is not in the paper; this is a residency
+   policy of the server.
+   VI_EVICT_COST (the default): GreedyDual with the reload cost as the cost.
+   The server keeps an aging clock; each use of a volume sets its credit to
+   the clock plus its reload cost (its raw voxel bytes in MiB: the
+   host-to-device copy and the pair-brick build grow with them); the idle
+   volume with the lowest credit is evicted (the least recently used among
+   equal credits) and the clock rises to its credit.  A volume that is costly
+   to reload therefore stays resident over cheap ones until it has gone
+   unused for about its reload cost's worth of the other volumes' evictions.
+   VI_EVICT_LRU: the least recently used idle volume.
+   Frames do not depend on the policy; only which requests pay a reload does.
+   Applies to evictions after the call.  Returns VI_EINVAL for a null server
+   or another policy. */
+enum { VI_EVICT_LRU = 0, VI_EVICT_COST = 1 };
+int vi_server_set_eviction(vi_server* server, int policy);
 
 #ifdef __cplusplus
 }

@@ -165,6 +165,7 @@ int camera_frame(const vi_camera* cam, int W, int H, float step_vox, int nmax, C
     c->W = W;
     c->H = H;
     c->dt = step_vox / (float)nmax;
+    c->inv_dt = 1.0f / c->dt;
     return VI_OK;
 }
 

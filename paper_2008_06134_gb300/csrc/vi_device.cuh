@@ -200,26 +200,38 @@ __device__ __forceinline__ bool within_bricks(const VoxelCoord& a, const VoxelCo
            abs((a.z0 >> kBrickShift) - (b.z0 >> kBrickShift)) <= rad;
 }
 
-// Parameter along P(s) = base + s dir at which the footprint's lower corner
-// leaves the box of bricks within rad of c's brick along every axis (an
-// estimate; callers verify with the exact path).  rad = 0: c's brick.
-__device__ __forceinline__ float brick_exit(const VolumeView& v, const VoxelCoord& c, int rad,
-                                            float b0, float b1, float b2, float d0, float d1,
-                                            float d2) {
-    const float base[3] = {b0, b1, b2}, dir[3] = {d0, d1, d2};
-    const int lo[3] = {(c.x0 >> kBrickShift) - rad, (c.y0 >> kBrickShift) - rad,
-                       (c.z0 >> kBrickShift) - rad};
+// A ray in voxel units for brick-box exits: X_a(t) = o_a N_a + t d_a N_a
+// (origin ox, reciprocal rate ix; ix is 0 on an axis the ray does not move
+// along).  The footprint's lower corner floor(X_a - 1/2) enters brick b at
+// X_a = B b + 1/2, B = 2^kBrickShift.
+struct VoxelRay {
+    float ox[3], ix[3];
+};
+
+__device__ __forceinline__ VoxelRay voxel_ray(const VolumeView& v, const float o[3],
+                                              const float d[3]) {
+    VoxelRay q;
     const float N[3] = {v.fnx, v.fny, v.fnz};
-    const int span = 2 * rad + 1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        q.ox[a] = o[a] * N[a];
+        q.ix[a] = d[a] != 0.0f ? __fdividef(1.0f, d[a] * N[a]) : 0.0f;
+    }
+    return q;
+}
+
+// Parameter t at which the footprint's lower corner leaves the box of bricks
+// within rad of c's brick along every axis (an estimate; callers verify with
+// the exact path).  rad = 0: c's brick.
+__device__ __forceinline__ float brick_exit(const VoxelRay& q, const VoxelCoord& c, int rad) {
+    const int b[3] = {c.x0 >> kBrickShift, c.y0 >> kBrickShift, c.z0 >> kBrickShift};
     float s_exit = 3.0e38f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        // Cells [B b, B b + B - 1] <=> P in [(B b + 0.5) / N, (B b + B + 0.5) / N),
-        // B = 2^kBrickShift; the box spans bricks lo .. lo + span - 1.
-        const float lo_p = __fdividef((float)(lo[a] * (1 << kBrickShift)) + 0.5f, N[a]);
-        const float hi_p = __fdividef((float)((lo[a] + span) * (1 << kBrickShift)) + 0.5f, N[a]);
-        if (dir[a] > 0.0f) s_exit = fminf(s_exit, __fdividef(hi_p - base[a], dir[a]));
-        else if (dir[a] < 0.0f) s_exit = fminf(s_exit, __fdividef(lo_p - base[a], dir[a]));
+        // Moving up, the box ends at brick b + rad + 1; moving down, at b - rad.
+        const int edge = q.ix[a] > 0.0f ? b[a] + rad + 1 : b[a] - rad;
+        const float plane = (float)(edge * (1 << kBrickShift)) + 0.5f;
+        if (q.ix[a] != 0.0f) s_exit = fminf(s_exit, (plane - q.ox[a]) * q.ix[a]);
     }
     return s_exit;
 }
@@ -238,6 +250,12 @@ __device__ __forceinline__ bool brick_in_grid(const GridView& g, int x0, int y0,
 __device__ __forceinline__ bool brick_may_be_lit(const GridView& g, const VoxelCoord& c) {
     if (!brick_in_grid(g, c.x0, c.y0, c.z0)) return false;
     return __ldg(g.flags + brick_index(g, c.x0, c.y0, c.z0)) != 0;
+}
+
+// The same test given the brick's index b (vol_brick of the lower corner).
+__device__ __forceinline__ bool brick_may_be_lit(const GridView& g, const VoxelCoord& c, int b) {
+    if (!brick_in_grid(g, c.x0, c.y0, c.z0)) return false;
+    return __ldg(g.flags + b) != 0;
 }
 
 // Skip distance of the brick holding the footprint's lower corner: 0 if it
@@ -277,13 +295,22 @@ struct Octet<uint8_t> {
     }
 };
 
+// Index of the brick holding voxel (x0, y0, z0): the same index in the pair
+// bricks and in the grid's flags and skip distances (one brick grid).
+__device__ __forceinline__ int vol_brick(const VolumeView& v, int x0, int y0, int z0) {
+    return ((z0 >> kBrickShift) * v.nby + (y0 >> kBrickShift)) * v.nbx + (x0 >> kBrickShift);
+}
+
 // The first pair of the footprint whose lower corner is voxel (x0, y0, z0),
-// in the pair bricks (see VolumeView).
-__device__ __forceinline__ size_t pair_index(const VolumeView& v, int x0, int y0, int z0) {
-    const int b = ((z0 >> kBrickShift) * v.nby + (y0 >> kBrickShift)) * v.nbx + (x0 >> kBrickShift);
+// in the pair bricks (see VolumeView), given that voxel's brick b.
+__device__ __forceinline__ size_t pair_index_in(int b, int x0, int y0, int z0) {
     constexpr int m = kBrick - 1;
     return (size_t)b * kPairsPerBrick +
            (size_t)(((z0 & m) * (kBrick + 1) + (y0 & m)) * kPairRow + (x0 & m));
+}
+
+__device__ __forceinline__ size_t pair_index(const VolumeView& v, int x0, int y0, int z0) {
+    return pair_index_in(vol_brick(v, x0, y0, z0), x0, y0, z0);
 }
 
 // What a trilinear fetch needs: the first pair of the footprint and the
@@ -292,12 +319,14 @@ __device__ __forceinline__ size_t pair_index(const VolumeView& v, int x0, int y0
 // onto voxel 0, so the upper corner's weight is 0 there.
 struct OctetRef {
     size_t idx;
+    int brick;  // the footprint's brick (vol_brick)
     float wx, wy, wz;
 };
 
 __device__ __forceinline__ OctetRef octet_ref(const VolumeView& v, const VoxelCoord& c) {
     OctetRef o;
-    o.idx = pair_index(v, c.x0, c.y0, c.z0);
+    o.brick = vol_brick(v, c.x0, c.y0, c.z0);
+    o.idx = pair_index_in(o.brick, c.x0, c.y0, c.z0);
     o.wx = c.cx < 0 ? 0.0f : c.wx;
     o.wy = c.cy < 0 ? 0.0f : c.wy;
     o.wz = c.cz < 0 ? 0.0f : c.wz;
@@ -376,10 +405,12 @@ __device__ __forceinline__ size_t footprint_index(const VolumeView& v, const Foo
     return pair_index(v, c.x0, c.y0, c.z0);
 }
 
-// The march's test (its skip distances: 0 exactly where the flag is set).
-__device__ __forceinline__ bool footprint_may_be_lit(const GridView& g, const FootprintCell& c) {
+// The march's test (its skip distances: 0 exactly where the flag is set),
+// given the brick's index b (vol_brick of the lower corner).
+__device__ __forceinline__ bool footprint_may_be_lit(const GridView& g, const FootprintCell& c,
+                                                     int b) {
     if (!brick_in_grid(g, c.x0, c.y0, c.z0)) return false;
-    return __ldg(g.skip + brick_index(g, c.x0, c.y0, c.z0)) == 0;
+    return __ldg(g.skip + b) == 0;
 }
 
 // Trilinear value of a footprint's eight voxels (an octet) at its weights.  uint16 voxels are

@@ -173,7 +173,8 @@ struct CameraFrame {
     float sx, sy;
     int perspective;
     int W, H;
-    float dt;  // step_vox / max(nx, ny, nz)
+    float dt;      // step_vox / max(nx, ny, nz)
+    float inv_dt;  // 1 / dt, for estimates only (the index path uses dt)
 };
 
 struct MarchParams {

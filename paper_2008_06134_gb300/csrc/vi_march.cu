@@ -222,12 +222,12 @@ __device__ __forceinline__ int last_transparent(const MarchParams& p, const Ray&
                                                 VoxelCoord vc) {
     int s = i;
     int d = brick_skip(p.grid, vc);
+    const VoxelRay q = voxel_ray(p.vol, r.o, r.d);
     for (int w = 0; w < kWalk; ++w) {
         int end = s;
         const int rad = d - 1;
-        const float t_exit =
-            brick_exit(p.vol, vc, rad, r.o[0], r.o[1], r.o[2], r.d[0], r.d[1], r.d[2]);
-        const float steps = (fminf(t_exit, r.t1) - t) / p.cam.dt;
+        const float t_exit = brick_exit(q, vc, rad);
+        const float steps = (fminf(t_exit, r.t1) - t) * p.cam.inv_dt;
         if (steps >= 2.0f) {
             const int j = s + (int)fminf(steps, 1.0e7f) - 1;
             float tj;
@@ -294,9 +294,10 @@ __device__ __forceinline__ int march_sample(const MarchParams& p, const AlphaT& 
                                                 __fmaf_rn(t, r.d[2], r.o[2]));
         // The footprint's loads are issued before the brick flag is known: they
         // overlap, and a sample in a transparent brick drops its footprint unused.
-        const size_t idx = footprint_index(p.vol, fc);
-        const typename Octet<VoxT>::V q = octet_load<VoxT>(p.vol, idx);
-        if (!footprint_may_be_lit(p.grid, fc)) {
+        const int b = vol_brick(p.vol, fc.x0, fc.y0, fc.z0);
+        const typename Octet<VoxT>::V q =
+            octet_load<VoxT>(p.vol, pair_index_in(b, fc.x0, fc.y0, fc.z0));
+        if (!footprint_may_be_lit(p.grid, fc, b)) {
             ++count;
             return A > p.ert ? kStopped : kEmpty;
         }

@@ -6,9 +6,10 @@
 // the frames of different requests run their sweeps and marches concurrently
 // on the GPU, so small frames fill it together instead of one after another.
 // Volumes are registered once and kept resident (pair bricks and brick ranges) up
-// to a count and a byte budget; the least recently used idle volume is
-// evicted when room is needed and reloaded from the caller's host copy on its
-// next request.  Each slot keeps its last attenuation stack for a later view of
+// to a count and a byte budget; when room is needed an idle volume is evicted
+// (by default the one whose GreedyDual credit -- reload cost plus an aging
+// clock -- is lowest, or the least recently used one) and reloaded from the
+// caller's host copy on its next request.  Each slot keeps its last attenuation stack for a later view of
 // the same scene.  Optionally a request's device work after its uploads is
 // captured and launched as one CUDA graph.  Completion is signalled by a stream
 // host callback; every wait on the host side is bounded (VI_ETIMEOUT).
@@ -36,6 +37,7 @@ struct ServerVolume {
     bool resident = false;
     int pins = 0;           // slots rendering from it
     uint64_t last_use = 0;  // admission counter at last use
+    double credit = 0;      // GreedyDual credit: the aging clock at last use + reload cost
     cudaEvent_t ready = nullptr;  // recorded after its last load; every reader's stream waits on it
 };
 
@@ -118,6 +120,8 @@ struct vi_server {
     cudaStream_t batch_stream = nullptr;
     std::vector<Slot*> pending;  // admitted this pass, march not yet enqueued
     double batch_wait_ms = 10000.0;
+    int eviction = VI_EVICT_COST;  // victim choice (vi_server_set_eviction)
+    double gd_clock = 0;           // GreedyDual aging clock: the credit of the last victim
 };
 
 namespace {
@@ -172,8 +176,42 @@ void evict(vi_server* s, ServerVolume* v, cudaStream_t stream) {
     ++s->stats.volume_evictions;
 }
 
+// Raw voxel bytes of a volume: what a reload copies from the host.
+size_t raw_bytes(const ServerVolume* v) {
+    return (size_t)v->nx * (size_t)v->ny * (size_t)v->nz * (v->dtype == VI_U16 ? 2 : 1);
+}
+
+// Reload cost of a volume, in MiB of raw voxels: its host-to-device copy and
+// its pair-brick build both grow with it.
+double reload_cost(const ServerVolume* v) { return (double)raw_bytes(v) / (1 << 20); }
+
+// The idle resident volume to evict next (never `keep`), or null.
+// VI_EVICT_LRU: the least recently used.  VI_EVICT_COST (GreedyDual, with the
+// reload cost as the cost): the lowest credit, where a volume's credit is set
+// at each use to the aging clock plus its reload cost and the clock rises to
+// each victim's credit -- so a volume that is costly to reload stays resident
+// over cheap ones until it has gone unused for long enough (ties: the least
+// recently used).
+ServerVolume* pick_victim(vi_server* s, int keep) {
+    ServerVolume* victim = nullptr;
+    for (int i = 0; i < (int)s->vols.size(); ++i) {
+        ServerVolume* v = s->vols[i];
+        if (i == keep || !v->resident || v->pins) continue;
+        if (!victim) {
+            victim = v;
+        } else if (s->eviction == VI_EVICT_COST && v->credit != victim->credit) {
+            if (v->credit < victim->credit) victim = v;
+        } else if (v->last_use < victim->last_use) {
+            victim = v;
+        }
+    }
+    if (victim && s->eviction == VI_EVICT_COST && victim->credit > s->gd_clock)
+        s->gd_clock = victim->credit;
+    return victim;
+}
+
 // Makes room for `extra` bytes: first frees the stacks of idle slots other
-// than `target`, then evicts idle volumes (least recently used first, never
+// than `target`, then evicts idle volumes (pick_victim's order, never
 // `keep`); true if the budget now allows it.
 bool make_room(vi_server* s, size_t extra, const Slot* target, int keep) {
     if (!s->budget) return true;
@@ -185,12 +223,7 @@ bool make_room(vi_server* s, size_t extra, const Slot* target, int keep) {
         }
     }
     while (bytes_in_use(s) + extra > s->budget) {
-        ServerVolume* victim = nullptr;
-        for (int i = 0; i < (int)s->vols.size(); ++i) {
-            ServerVolume* v = s->vols[i];
-            if (i == keep || !v->resident || v->pins) continue;
-            if (!victim || v->last_use < victim->last_use) victim = v;
-        }
+        ServerVolume* victim = pick_victim(s, keep);
         if (!victim) return false;
         evict(s, victim, target->stream);
     }
@@ -434,12 +467,7 @@ void schedule(vi_server* s) {
             int resident = 0;
             for (ServerVolume* o : s->vols) resident += o->resident;
             while (resident >= s->max_resident) {
-                ServerVolume* victim = nullptr;
-                for (int i = 0; i < (int)s->vols.size(); ++i) {
-                    ServerVolume* o = s->vols[i];
-                    if (i == vid || !o->resident || o->pins) continue;
-                    if (!victim || o->last_use < victim->last_use) victim = o;
-                }
+                ServerVolume* victim = pick_victim(s, vid);
                 if (!victim) break;
                 evict(s, victim, sl->stream);
                 --resident;
@@ -466,8 +494,10 @@ void schedule(vi_server* s) {
             }
             v->resident = true;
             ++s->stats.volume_loads;
+            s->stats.volume_load_bytes += raw_bytes(v);
         }
         v->last_use = ++s->admissions;
+        v->credit = s->gd_clock + reload_cost(v);
         sl->stack_use = s->admissions;
         ++v->pins;
         sl->req = r;
@@ -757,6 +787,13 @@ int vi_server_set_batching(vi_server* s, int enabled, double wait_ms) {
     }
     s->batching = enabled != 0;
     s->batch_wait_ms = wait_ms;
+    return VI_OK;
+}
+
+int vi_server_set_eviction(vi_server* s, int policy) {
+    if (!s || (policy != VI_EVICT_LRU && policy != VI_EVICT_COST)) return VI_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->eviction = policy;
     return VI_OK;
 }
 

@@ -138,7 +138,7 @@ __device__ __forceinline__ void sweep_lockstep(const SweepParams& p, const float
                                                          __fmaf_rn(sk, w[1], o[1]),
                                                          __fmaf_rn(sk, w[2], o[2]));
                 ref[u] = octet_ref(p.vol, vc);
-                lit[u] = brick_may_be_lit(p.grid, vc);
+                lit[u] = brick_may_be_lit(p.grid, vc, ref[u].brick);
             }
         }
         typename Octet<VoxT>::V oct[kLockBatch];
@@ -298,7 +298,7 @@ __device__ __forceinline__ void sweep_column(const SweepParams& p, const float* 
                                                      __fmaf_rn(sk, w[1], o[1]),
                                                      __fmaf_rn(sk, w[2], o[2]));
             ref[u] = octet_ref(p.vol, vc);
-            lit[u] = k + u <= kout && brick_may_be_lit(p.grid, vc);
+            lit[u] = k + u <= kout && brick_may_be_lit(p.grid, vc, ref[u].brick);
         }
         typename Octet<VoxT>::V oct[kBatch];
 #pragma unroll
@@ -518,7 +518,7 @@ __global__ void __launch_bounds__(kChunkThreads, VI_SWEEP_CHUNK_MIN_BLOCKS)
                             voxel_coord_inside(p.vol, __fmaf_rn(sk, w[0], o[0]),
                                                __fmaf_rn(sk, w[1], o[1]), __fmaf_rn(sk, w[2], o[2]));
                         ref[u] = octet_ref(p.vol, vc);
-                        lit[u] = brick_may_be_lit(p.grid, vc);
+                        lit[u] = brick_may_be_lit(p.grid, vc, ref[u].brick);
                     }
                 }
                 typename Octet<VoxT>::V oct[kChunkBatch];

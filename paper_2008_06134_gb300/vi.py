@@ -41,7 +41,8 @@ EXPORTS = ("vi_create", "vi_destroy", "vi_set_memory_budget", "vi_load_volume",
            "vi_measure_peaks", "vi_post_ready", "vi_render_batch", "vi_render_host_noalloc", "vi_debug_bounds", "vi_server_create", "vi_server_destroy",
            "vi_server_add_volume", "vi_server_submit", "vi_server_wait", "vi_server_cancel",
            "vi_server_timing", "vi_server_release", "vi_server_get_stats",
-           "vi_server_set_graphs", "vi_server_set_batching")
+           "vi_server_set_graphs", "vi_server_set_batching", "vi_server_set_eviction")
+EVICT_LRU, EVICT_COST = 0, 1
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = 0, 1, 2, 3, 4
 
 
@@ -90,7 +91,8 @@ class ServerStats(C.Structure):
                 ("resident_volumes", C.c_int), ("bytes_in_use", C.c_size_t),
                 ("peak_bytes", C.c_size_t), ("stack_reuses", C.c_uint64),
                 ("graph_launches", C.c_uint64), ("graph_instantiations", C.c_uint64),
-                ("batches", C.c_uint64), ("batched_frames", C.c_uint64)]
+                ("batches", C.c_uint64), ("batched_frames", C.c_uint64),
+                ("volume_load_bytes", C.c_uint64)]
 
 
 _libs = {}
@@ -140,6 +142,7 @@ def library(checked: bool = False) -> C.CDLL:
     L.vi_server_get_stats.argtypes = [vp, P(ServerStats)]
     L.vi_server_set_graphs.argtypes = [vp, i]
     L.vi_server_set_batching.argtypes = [vp, i, C.c_double]
+    L.vi_server_set_eviction.argtypes = [vp, i]
     L.vi_debug_bounds.argtypes = [i, P(C.c_uint64), P(i), P(C.c_int64)]
     _libs[path] = L
     return L
@@ -419,7 +422,8 @@ class Server:
 
     def __init__(self, device: int = 0, slots: int = 4, memory_budget: int = 0,
                  max_resident_volumes: int = 0, graphs: bool = False, checked: bool = False,
-                 batching: bool = False, batch_wait_ms: float = 10000.0):
+                 batching: bool = False, batch_wait_ms: float = 10000.0,
+                 eviction: int | None = None):
         L = library(checked)
         h = C.c_void_p()
         _check(L.vi_server_create(C.byref(h), int(device), int(slots), int(memory_budget),
@@ -430,6 +434,14 @@ class Server:
             self.set_graphs(True)
         if batching:
             self.set_batching(True, batch_wait_ms)
+        if eviction is not None:
+            self.set_eviction(eviction)
+
+    def set_eviction(self, policy: int) -> None:
+        """Choose which idle volume is evicted when room is needed:
+        EVICT_COST (GreedyDual on the reload cost, the default) or EVICT_LRU
+        (vi_server_set_eviction)."""
+        _check(self.L.vi_server_set_eviction(self.h, int(policy)), "vi_server_set_eviction")
 
     def set_batching(self, enabled: bool, wait_ms: float = 10000.0) -> None:
         """March the requests admitted in one scheduling pass as one batch of

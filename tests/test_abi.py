@@ -82,6 +82,7 @@ def test_server_calls_reject_bad_arguments_without_cuda(lib):
     assert lib.vi_server_cancel(null, 1) == vi.EINVAL
     assert lib.vi_server_get_stats(null, None) == vi.EINVAL
     assert lib.vi_server_set_graphs(null, 1) == vi.EINVAL
+    assert lib.vi_server_set_eviction(null, vi.EVICT_COST) == vi.EINVAL
     assert lib.vi_server_create(None, 0, 4, 0, 0) == vi.EINVAL
     h = C.c_void_p()
     assert lib.vi_server_create(C.byref(h), 0, 0, 0, 0) == vi.EINVAL      # no slots

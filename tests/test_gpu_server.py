@@ -398,3 +398,63 @@ def test_kept_stacks_are_evicted_least_recently_used(env):
             c.set_light(lights[scene])
             c.build_attenuation(24, 40, vi.SHELL)
             assert np.array_equal(frame, c.render(cam, 48, 40, 0.5).cpu().numpy())
+
+
+def residency_model(seq, costs, max_resident, policy):
+    """Loads and evictions of a server admitting the volumes of `seq` one at a
+    time with at most `max_resident` resident: LRU, or GreedyDual with the
+    reload cost as the cost (credit = clock + cost at each use; the lowest
+    credit is evicted, ties by least recent use; the clock rises to the
+    victim's credit)."""
+    resident, credit, last = set(), {}, {}
+    clock, loads, evictions = 0.0, 0, 0
+    for t, v in enumerate(seq, start=1):
+        if v not in resident:
+            while len(resident) >= max_resident:
+                if policy == "lru":
+                    victim = min(resident, key=lambda u: last[u])
+                else:
+                    victim = min(resident, key=lambda u: (credit[u], last[u]))
+                    clock = max(clock, credit[victim])
+                resident.remove(victim)
+                evictions += 1
+            resident.add(v)
+            loads += 1
+        last[v] = t
+        credit[v] = clock + costs[v]
+    return loads, evictions
+
+
+def test_eviction_policies_follow_their_definitions(env):
+    """One request at a time over three volumes with at most two resident: the
+    server's loads and evictions equal those of a plain model of each policy
+    (GreedyDual on the reload cost, and least recently used), the costly
+    volume is reloaded less often under GreedyDual, and the frames do not
+    depend on the policy."""
+    torch, ph, vi, vols, tfs = env
+    rng = np.random.default_rng(21)
+    seq = [1, 0, 2, 1] + [int(v) for v in rng.integers(3, size=36)]
+    costs = [v.nbytes / float(1 << 20) for v in vols]
+    assert max(costs) == costs[1]   # the 48^3 uint16 volume costs most to reload
+    cam = ph.orbit_camera(np.array([0.3, -0.5, 0.8]), True, 2.4)
+    frames, counts = {}, {}
+    for name, policy in (("cost", vi.EVICT_COST), ("lru", vi.EVICT_LRU)):
+        with vi.Server(0, slots=2, max_resident_volumes=2, eviction=policy) as s:
+            vids = [s.add_volume(v) for v in vols]
+            got = []
+            for v in seq:
+                tf, vmin, vmax = tfs[v]
+                out = torch.empty((24, 32, 4), device="cuda")
+                t = s.submit(vids[v], tf, vmin, vmax, (0.2, 0.4, -0.9), 8, 16, vi.SHADOW, cam,
+                             32, 24, 0.5, out)
+                assert s.wait(t) == (vi.REQ_DONE, vi.OK)
+                got.append(out.cpu().numpy())
+            st = s.stats()
+        frames[name] = got
+        counts[name] = (st["volume_loads"], st["volume_evictions"])
+        assert counts[name] == residency_model(seq, costs, 2, name), name
+    for a, b in zip(frames["cost"], frames["lru"]):
+        assert np.array_equal(a, b)
+    # The first four requests: LRU reloads the costly volume, GreedyDual keeps it.
+    assert residency_model(seq[:4], costs, 2, "cost")[0] == 3
+    assert residency_model(seq[:4], costs, 2, "lru")[0] == 4
