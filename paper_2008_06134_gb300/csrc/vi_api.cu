@@ -260,8 +260,11 @@ int setup_stack(vi_ctx* c, int n, int R, int fmt) {
     std::memset(&res, 0, sizeof(res));
     res.resType = cudaResourceTypePitch2D;
     res.res.pitch2D.devPtr = base;
-    res.res.pitch2D.desc = fmt == VI_F32 ? cudaCreateChannelDesc<float>()
-                                         : cudaCreateChannelDesc<unsigned short>();
+    // The texture unit widens binary16 texels exactly and reads UNORM16 texels
+    // as q / 65535 (normalised read mode); BF16 texels are read as raw bits.
+    res.res.pitch2D.desc = fmt == VI_F32   ? cudaCreateChannelDesc<float>()
+                           : fmt == VI_F16 ? cudaCreateChannelDescHalf()
+                                           : cudaCreateChannelDesc<unsigned short>();
     res.res.pitch2D.width = ((size_t)R) << L.cells_log2;
     res.res.pitch2D.height = L.rows;
     res.res.pitch2D.pitchInBytes = L.pitch;
@@ -270,7 +273,7 @@ int setup_stack(vi_ctx* c, int n, int R, int fmt) {
     td.addressMode[0] = cudaAddressModeClamp;
     td.addressMode[1] = cudaAddressModeClamp;
     td.filterMode = cudaFilterModePoint;
-    td.readMode = cudaReadModeElementType;
+    td.readMode = fmt == VI_UNORM16 ? cudaReadModeNormalizedFloat : cudaReadModeElementType;
     td.normalizedCoords = 0;
     e = cudaCreateTextureObject(&c->sview.tex, &res, &td, nullptr);
     if (e != cudaSuccess) return cuda_fail(c, e);

@@ -47,11 +47,14 @@ __device__ __forceinline__ bool bounds_ok(int site, long long i, long long n) {
 // a pitched 2D texture, given x = i0 + 1, y = j0 + 1 (exact integers, so the
 // footprint choice is exact); texture gather returns (i0, j0+1), (i0+1, j0+1),
 // (i0+1, j0), (i0, j0) in x, y, z, w.  Raw texels, no filtering: the weights
-// are applied in FP32 by the caller.
+// are applied in FP32 by the caller.  The texture unit converts each texel
+// to FP32 where it can do so exactly or to within an FP32 rounding: binary16
+// texels (a half-float texture; binary16 -> binary32 is exact) and UNORM16
+// texels (normalised read mode, q / 65535).  BF16 has no texture format: its
+// raw 16 bits are gathered and widened with a shift (also exact).
 struct F32 {
     using T = float;
     static __device__ __forceinline__ T pack(float x) { return x; }
-    static __device__ __forceinline__ float load(const T* p) { return __ldg(p); }
     static __device__ __forceinline__ void gather(cudaTextureObject_t t, float x, float y,
                                                   float& b00, float& b01, float& b10,
                                                   float& b11) {
@@ -62,23 +65,16 @@ struct F32 {
 struct F16 {
     using T = __half;
     static __device__ __forceinline__ T pack(float x) { return __float2half_rn(x); }
-    static __device__ __forceinline__ float load(const T* p) { return __half2float(__ldg(p)); }
     static __device__ __forceinline__ void gather(cudaTextureObject_t t, float x, float y,
                                                   float& b00, float& b01, float& b10,
                                                   float& b11) {
-        const uint4 g = tex2Dgather<uint4>(t, x, y, 0);  // raw binary16 bits
-        b00 = __half2float(__ushort_as_half((unsigned short)g.w));
-        b01 = __half2float(__ushort_as_half((unsigned short)g.z));
-        b10 = __half2float(__ushort_as_half((unsigned short)g.x));
-        b11 = __half2float(__ushort_as_half((unsigned short)g.y));
+        const float4 g = tex2Dgather<float4>(t, x, y, 0);  // binary16 texels, widened
+        b00 = g.w; b01 = g.z; b10 = g.x; b11 = g.y;
     }
 };
 struct BF16 {
     using T = __nv_bfloat16;
     static __device__ __forceinline__ T pack(float x) { return __float2bfloat16_rn(x); }
-    static __device__ __forceinline__ float load(const T* p) {
-        return __bfloat162float(__ldg(p));
-    }
     static __device__ __forceinline__ void gather(cudaTextureObject_t t, float x, float y,
                                                   float& b00, float& b01, float& b10,
                                                   float& b11) {
@@ -94,15 +90,11 @@ struct UNORM16 {
         x = fminf(fmaxf(x, 0.0f), 1.0f);
         return (T)__float2uint_rn(x * 65535.0f);
     }
-    static __device__ __forceinline__ float load(const T* p) {
-        return (float)__ldg(p) * (1.0f / 65535.0f);
-    }
     static __device__ __forceinline__ void gather(cudaTextureObject_t t, float x, float y,
                                                   float& b00, float& b01, float& b10,
                                                   float& b11) {
-        const uint4 g = tex2Dgather<uint4>(t, x, y, 0);
-        constexpr float s = 1.0f / 65535.0f;
-        b00 = (float)g.w * s; b01 = (float)g.z * s; b10 = (float)g.x * s; b11 = (float)g.y * s;
+        const float4 g = tex2Dgather<float4>(t, x, y, 0);  // normalised: q / 65535
+        b00 = g.w; b01 = g.z; b10 = g.x; b11 = g.y;
     }
 };
 
