@@ -45,16 +45,16 @@ FLOPS_LIT = {0: 0, 1: 6 + 2 + 12, 2: 6 + 2 + 6 * 12 + 7, 3: 6 + 2 + 8 * 12 + 9}
 # entry holds for the kernel sources it was taken from (hash of the files that
 # define the kernel); once they change the figure is stale and reported as null.
 NCU_TRAFFIC = {
-    "march_kernel": (("vi_march.cu", "vi_device.cuh", "vi_internal.h"), "2e3a160336cd5d92",
-                     34_468_352),
-    "sweep_kernel": (("vi_sweep.cu", "vi_device.cuh", "vi_internal.h"), "650103d3f4b5c509",
-                     240_914_944),
+    "march_kernel": (("vi_march.cu", "vi_device.cuh", "vi_internal.h"), "3f3c48e0526d1030",
+                     34_764_544),
+    "sweep_kernel": (("vi_sweep.cu", "vi_device.cuh", "vi_internal.h"), "1959ccd2f7c627ec",
+                     240_889_856),
 }
 
 
 # Other counters of the same march capture, for its candidate bounds: warp-level
 # instructions executed and L2 sectors (32 B) per launch.
-NCU_MARCH_COUNTERS = {"inst_executed": 522_300_222, "lts_sectors": 10_750_699}
+NCU_MARCH_COUNTERS = {"inst_executed": 473_672_572, "lts_sectors": 11_012_910}
 
 
 def march_bounds(march_s: float, sms: int, clock_mhz: float, peaks: dict, probe: dict):
@@ -99,6 +99,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-depth", type=int, default=3,
+                    help="contexts (streams) in the end-to-end pipeline")
     ap.add_argument("--cpu-baseline-only", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--no-summaries", action="store_true",
                     help="leave the serving and precision summaries out of the headline line")
@@ -440,21 +442,23 @@ def gb300_arm(args):
             secs += time.perf_counter() - t0
         serial = job_throughput(K, world, max_over_ranks(secs, dist, "cuda"))
 
-        # Pipelined: two contexts on two streams, so step s + 1's upload and
-        # sweep overlap step s's march and read-back.  Every step copies its
-        # volume and TF from pinned host memory and reads its frame back into
-        # pinned host memory, all through the C ABI (vi_render with
-        # VI_OUT_HOST_ASYNC; vi_sync completes the frame); the host waits for
-        # a frame before its buffers are reused.
-        streams = [torch.cuda.Stream(local), torch.cuda.Stream(local)]
+        # Pipelined: D contexts on D streams (--e2e-depth), so the uploads and
+        # sweeps of the next steps overlap step s's march and read-back.  Every
+        # step copies its volume and TF from pinned host memory and reads its
+        # frame back into pinned host memory, all through the C ABI (vi_render
+        # with VI_OUT_HOST_ASYNC; vi_sync completes the frame); the host waits
+        # for a frame before its buffers are reused.
+        depth = max(2, args.e2e_depth)
+        streams = [torch.cuda.Stream(local) for _ in range(depth)]
         ctxs = [vi.Context(local, stream=st) for st in streams]
         host_out = [torch.empty((H, W, 4), dtype=torch.float32, pin_memory=True)
-                    for _ in range(2)]
-        flushes = [torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda") for _ in range(2)]
+                    for _ in range(depth)]
+        flushes = [torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+                   for _ in range(depth)]
         checksum = 0.0
 
         def issue(s):
-            b = s & 1
+            b = s % depth
             c, st = ctxs[b], streams[b]
             with torch.cuda.stream(st):
                 flushes[b].fill_(s & 0xFF)
@@ -468,8 +472,8 @@ def gb300_arm(args):
 
         def collect(s):
             nonlocal checksum
-            ctxs[s & 1].sync()
-            checksum += float(host_out[s & 1][H // 2, W // 2, 3])   # the host reads the frame
+            ctxs[s % depth].sync()
+            checksum += float(host_out[s % depth][H // 2, W // 2, 3])  # the host reads the frame
 
         for s in range(args.warmup):
             issue(s)
@@ -479,10 +483,10 @@ def gb300_arm(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for s in range(K):
-            if s >= 2:
-                collect(s - 2)
+            if s >= depth:
+                collect(s - depth)
             issue(s)
-        for s in range(max(0, K - 2), K):
+        for s in range(max(0, K - depth), K):
             collect(s)
         secs = time.perf_counter() - t0
         for c in ctxs:
@@ -491,9 +495,10 @@ def gb300_arm(args):
                "unit": "frames/s",
                "h2d_bytes_per_step": int(sc.volume.nbytes + tf.nbytes),
                "d2h_bytes_per_step": int(H * W * 16),
-               "pipeline": "2 contexts on 2 streams; step s+1's upload and sweep overlap "
-                           "step s's march and read-back; the frame comes back through "
-                           "vi_render (VI_OUT_HOST_ASYNC) into pinned memory, vi_sync per frame",
+               "pipeline": f"{depth} contexts on {depth} streams; the next steps' uploads "
+                           "and sweeps overlap step s's march and read-back; the frame comes "
+                           "back through vi_render (VI_OUT_HOST_ASYNC) into pinned memory, "
+                           "vi_sync per frame; L2 flushed every step",
                "one_at_a_time_value": round(serial, 3)}
 
     if rank != 0:

@@ -347,6 +347,7 @@ int fill_march_params(vi_ctx* c, const vi_camera* cam, int W, int H, float step_
     p->stack = c->sview;
     const LightFrame& lt = p->lt;
     p->shells = c->bopts.shell_count > 1 ? c->bopts.shell_count : 1;
+    p->shell_reach = 0.0f;
     if (c->mode == VI_SHELL && c->lt_valid) {
         // Shell q holds the six points S +- q r e_a, as light-space offsets.
         for (int q = 1; q <= p->shells; ++q) {
@@ -360,6 +361,9 @@ int fill_march_params(vi_ctx* c, const vi_camera* cam, int W, int H, float step_
                     p->shell_off[q - 1][2 * a][k] = off[k];
                     p->shell_off[q - 1][2 * a + 1][k] = -off[k];
                 }
+                if (q == 1)
+                    p->shell_reach = std::max(p->shell_reach,
+                                              std::max(std::fabs(off[1]), std::fabs(off[2])));
             }
         }
     }

@@ -467,17 +467,19 @@ __device__ __forceinline__ int slice_index(float lam, int n) {
 // first: past an edge the clamp-to-edge footprint holds copies of the edge
 // texel, and the clamped point reads the edge texel with weight 1 and its
 // neighbour (in the next cell, or zero) with weight 0 -- the same value.
-template <typename Fmt>
+// CLAMP = false skips the clamp: only for a point whose coordinates are known
+// to lie in [0, R - 1] already (the clamp would change nothing).
+template <typename Fmt, bool CLAMP = true>
 __device__ __forceinline__ float bilinear(const StackView& sv, int k, int n, int R, float tu,
                                           float tv, int* rec = nullptr) {
     if (rec) {
         rec[1] = clampi(__float2int_rd(tu), -1, R);
         rec[2] = clampi(__float2int_rd(tv), -1, R);
     }
-    const float cu = fminf(fmaxf(tu, 0.0f), (float)(R - 1));
+    const float cu = CLAMP ? fminf(fmaxf(tu, 0.0f), (float)(R - 1)) : tu;
     const float fu = floorf(cu);
     const float wu = cu - fu;
-    const float cv = fminf(fmaxf(tv, 0.0f), (float)(R - 1));
+    const float cv = CLAMP ? fminf(fmaxf(tv, 0.0f), (float)(R - 1)) : tv;
     const float fv = floorf(cv);
     const float wv = cv - fv;
     if (!(VI_BOUNDS_OK(kSiteStackTex, k, n) && VI_BOUNDS_OK(kSiteStackTex, (int)fv, R)))
@@ -493,12 +495,23 @@ __device__ __forceinline__ float bilinear(const StackView& sv, int k, int n, int
     return fmaf(wv, bot - top, top);
 }
 
-template <typename Fmt>
+template <typename Fmt, bool CLAMP = true>
 __device__ __forceinline__ float stack_lookup(const StackView& sv, int n, int R, float lam, float tu,
                                               float tv, int* rec = nullptr) {
     const int k = slice_index(lam, n);
     if (rec) rec[0] = k;
-    return bilinear<Fmt>(sv, k, n, R, tu, tv, rec);
+    return bilinear<Fmt, CLAMP>(sv, k, n, R, tu, tv, rec);
+}
+
+// Whether every point (tu + du, tv + dv) with |du|, |dv| <= reach, each
+// coordinate added in binary32, lies in [0, R - 1]: then a lookup's clamp
+// changes nothing.  Rounding is monotone, so the rounded sums lie between
+// fl(t - reach) and fl(t + reach); t >= reach gives fl(t - reach) >= 0.  NaN
+// coordinates fail the test (every comparison with NaN is false).
+__device__ __forceinline__ bool lookups_inside(float tu, float tv, float reach, int R) {
+    const float hi = (float)(R - 1);
+    return tu >= reach && tv >= reach && __fadd_rn(tu, reach) <= hi &&
+           __fadd_rn(tv, reach) <= hi;
 }
 
 }  // namespace vi

@@ -188,6 +188,7 @@ struct MarchParams {
     CameraFrame cam;
     float shell_off[kMaxShells][6][3];  // light-space offsets of the shell points, per shell
     int shells;             // shells in use (1 .. kMaxShells)
+    float shell_reach;      // max |u|, |v| texel offset of the first shell's points
     float shell_r[kMaxShells];  // point light: world radius of shell q + 1
     float tanphi;           // point light: tan of the cone half angle
     int depth;              // 1: the stack holds optical depth; light factor exp(-value)

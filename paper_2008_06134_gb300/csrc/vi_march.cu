@@ -19,6 +19,7 @@
 #include <cuda.h>
 
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "vi.h"
@@ -26,13 +27,15 @@
 
 // Unrolling of the default kernels' lookup loops: the cone's two rings and the
 // shell's six points.  Fully unrolled, every gather of a sample is in flight at
-// once, which costs registers the 64-register budget does not have: the cone
-// kernel spilled 112 bytes a thread and reloaded them every sample (31 M local
-// loads per 1024^2 frame).  Ring by ring it spills 8 bytes and the config-2
-// march drops from 1.148 to 1.042 ms; the shell, three points at a time, from
-// 0.974 to 0.947 ms.
+// once, which costs registers the 64-register budget may not have.  The first
+// cone kernels spilled 112 bytes a thread that way and reloaded them every
+// sample (31 M local loads per 1024^2 frame), so they took the rings one after
+// the other (config-2 march 1.148 -> 1.042 ms).  The current cone kernel keeps
+// both rings in flight with 4 bytes of spills and is faster that way (0.595 ->
+// 0.585 ms, same box); the shell takes three points at a time (0.974 -> 0.947
+// ms against six when it was measured).
 #ifndef VI_CONE_RING_UNROLL
-#define VI_CONE_RING_UNROLL 1
+#define VI_CONE_RING_UNROLL 2
 #endif
 #ifndef VI_SHELL_UNROLL
 #define VI_SHELL_UNROLL 3
@@ -43,6 +46,12 @@ namespace vi {
 namespace {
 
 constexpr int kConeRingUnroll = VI_CONE_RING_UNROLL;
+
+// 1: the shell and cone lookups of a sample whose points all lie inside the
+// slice skip their coordinate clamps (lookups_inside); 0: always clamp.
+#ifndef VI_MARCH_UNCLAMPED
+#define VI_MARCH_UNCLAMPED 1
+#endif
 
 // A warp's pixel tile: kTileW x kTileH neighbouring rays marched in lockstep.
 // 4 x 8 measured fastest on the config-2 frame (march 0.987 ms, against 1.045 /
@@ -269,6 +278,45 @@ __device__ __forceinline__ float point_light_factor(const MarchParams& p, float 
     return light_factor<Fmt>(p, p.lt.n, p.lt.R, q0, q1, q2, rec);
 }
 
+// Sum of the first shell's six lookups (Section 3.2.3) around light-space
+// point (l0, l1, l2); CLAMP = false only where lookups_inside holds for the
+// shell's reach.
+template <typename Fmt, bool CLAMP>
+__device__ __forceinline__ float shell_sum(const MarchParams& p, int n, int R, float l0,
+                                           float l1, float l2) {
+    float sum = 0.0f;
+#pragma unroll kShellUnroll
+    for (int q = 0; q < 6; ++q)
+        sum += stack_lookup<Fmt, CLAMP>(p.stack, n, R, __fadd_rn(l0, p.shell_off[0][q][0]),
+                                        __fadd_rn(l1, p.shell_off[0][q][1]),
+                                        __fadd_rn(l2, p.shell_off[0][q][2]));
+    return sum;
+}
+
+// Sum of the cone's eight lookups (Section 3.2.3, Eq. 11) around light-space
+// point (l0, l1, l2): ring n = 1, 2 one slice spacing apart towards the
+// light, its four points B_proj turned by m pi/2 about L.  CLAMP = false only
+// where lookups_inside holds for the rings' reach.
+template <typename Fmt, bool CLAMP>
+__device__ __forceinline__ float cone_sum(const MarchParams& p, const Ray& r, int n, int R,
+                                          float l0, float l1, float l2) {
+    float sum = 0.0f;
+#pragma unroll kConeRingUnroll
+    for (int ring = 0; ring < 2; ++ring) {
+        // The ring's four points share lambda + offset, hence one slice.
+        const int k = slice_index(__fadd_rn(l0, -(float)(ring + 1)), n);
+        const float bu = ring ? r.nbu[1] : r.nbu[0], bv = ring ? r.nbv[1] : r.nbv[0];
+        // B_proj turned by m pi/2 about L: (bu, bv), (-bv, bu), (-bu, -bv), (bv, -bu).
+        const float du[4] = {bu, -bv, -bu, bv};
+        const float dv[4] = {bv, bu, -bv, -bu};
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+            sum += bilinear<Fmt, CLAMP>(p.stack, k, n, R, __fadd_rn(l1, du[m]),
+                                        __fadd_rn(l2, dv[m]));
+    }
+    return sum;
+}
+
 // One sample i of a ray.  Returns kEnded if t_i is past the exit (nothing
 // done), kStopped if early ray termination fired, kEmpty if the sample lies in
 // a brick that cannot yield alpha > 0 (counted, nothing composited), else
@@ -280,6 +328,10 @@ template <typename VoxT, typename Fmt, int MODE, bool TRACE, bool EXT, bool POIN
 __device__ __forceinline__ int march_sample(const MarchParams& p, const AlphaT& s_alpha,
                                             const Ray& r, int i, float& C0, float& C1, float& C2,
                                             float& A, int& count, int& lit, int32_t* rec) {
+    // Lookups without the clamp where every point is inside the slice: in the
+    // single-frame kernels (the batched kernel keeps one clamped path, which
+    // spills less at its register budget).
+    constexpr bool kUnclamped = VI_MARCH_UNCLAMPED && std::is_same<AlphaT, SharedAlpha>::value;
     float t, val;
     VoxelCoord vc;  // the trace's record of the cell
     if (TRACE) {
@@ -377,15 +429,17 @@ __device__ __forceinline__ int march_sample(const MarchParams& p, const AlphaT& 
                     int* rr = (TRACE && j < 8) ? rec + 11 + 3 * j : nullptr;
                     sum += light_factor<Fmt>(p, n, R, q0, q1, q2, rr);
                 }
-            } else {
-#pragma unroll kShellUnroll
+            } else if (TRACE) {
                 for (int q = 0; q < 6; ++q) {
                     float q0 = __fadd_rn(l0, p.shell_off[0][q][0]);
                     float q1 = __fadd_rn(l1, p.shell_off[0][q][1]);
                     float q2 = __fadd_rn(l2, p.shell_off[0][q][2]);
-                    sum += stack_lookup<Fmt>(p.stack, n, R, q0, q1, q2,
-                                             TRACE ? rec + 11 + 3 * q : nullptr);
+                    sum += stack_lookup<Fmt>(p.stack, n, R, q0, q1, q2, rec + 11 + 3 * q);
                 }
+            } else if (kUnclamped && lookups_inside(l1, l2, p.shell_reach, R)) {
+                sum = shell_sum<Fmt, false>(p, n, R, l0, l1, l2);
+            } else {
+                sum = shell_sum<Fmt, true>(p, n, R, l0, l1, l2);
             }
             coef = EXT ? sum * (1.0f / (float)(6 * shells)) : sum * (1.0f / 6.0f);
         } else if (MODE == 3) {
@@ -449,23 +503,27 @@ __device__ __forceinline__ int march_sample(const MarchParams& p, const AlphaT& 
                     int* rr = TRACE ? rec + 11 + 3 * j : nullptr;
                     sum += light_factor<Fmt>(p, n, R, lr, __fadd_rn(l1, cu), __fadd_rn(l2, cv), rr);
                 }
-            } else {
-#pragma unroll kConeRingUnroll
+            } else if (TRACE) {
                 for (int ring = 0; ring < 2; ++ring) {
-                    // The ring's four points share lambda + offset, hence one slice.
                     const int k = slice_index(__fadd_rn(l0, -(float)(ring + 1)), n);
                     const float bu = ring ? r.nbu[1] : r.nbu[0], bv = ring ? r.nbv[1] : r.nbv[0];
-                    // B_proj turned by m pi/2 about L: (bu, bv), (-bv, bu), (-bu, -bv), (bv, -bu).
                     const float du[4] = {bu, -bv, -bu, bv};
                     const float dv[4] = {bv, bu, -bv, -bu};
-#pragma unroll
                     for (int m = 0; m < 4; ++m) {
-                        int* rr = TRACE ? rec + 11 + 3 * (ring * 4 + m) : nullptr;
-                        if (TRACE) rr[0] = k;
+                        int* rr = rec + 11 + 3 * (ring * 4 + m);
+                        rr[0] = k;
                         sum += bilinear<Fmt>(p.stack, k, n, R, __fadd_rn(l1, du[m]),
                                              __fadd_rn(l2, dv[m]), rr);
                     }
                 }
+            } else {
+                // Every offset of both rings is within `reach` texels of (l1, l2).
+                const float reach = fmaxf(fmaxf(fabsf(r.nbu[0]), fabsf(r.nbv[0])),
+                                          fmaxf(fabsf(r.nbu[1]), fabsf(r.nbv[1])));
+                if (kUnclamped && lookups_inside(l1, l2, reach, R))
+                    sum = cone_sum<Fmt, false>(p, r, n, R, l0, l1, l2);
+                else
+                    sum = cone_sum<Fmt, true>(p, r, n, R, l0, l1, l2);
             }
             coef = sum * 0.125f;
         }
