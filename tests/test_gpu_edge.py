@@ -161,7 +161,7 @@ def test_host_and_device_buffers_agree(ctx, vi, orc):
 
 @pytest.mark.parametrize("case", ["one-slice", "one-texel", "one-voxel", "two-entry-tf",
                                   "axis-light", "view-parallel-light", "eye-inside",
-                                  "grazing-ortho", "wide-shell"])
+                                  "grazing-ortho", "wide-shell", "edge-shell", "edge-cone"])
 def test_degenerate_cases_match_oracle(ctx, orc, case):
     from paper_2008_06134_gb300 import phantoms as ph
     sc = small_scene(mode=3)
@@ -186,6 +186,18 @@ def test_degenerate_cases_match_oracle(ctx, orc, case):
     elif case == "wide-shell":
         sc.mode = 2
         sc.shell_radius_vox = 3.5
+    elif case in ("edge-shell", "edge-cone"):
+        # Lookup points that reach past the slice's texels for samples near the
+        # volume's silhouette (their coordinates must be clamped) and stay
+        # inside for samples near its centre (the clamps are skipped): both
+        # lookup paths of the shell and cone kernels in one frame.
+        if case == "edge-shell":
+            sc.mode = 2
+            sc.shell_radius_vox = 8.0
+        else:
+            sc.n_slices = 6
+            sc.cone_half_angle_deg = 30.0
+        sc.volume = np.full((24, 24, 24), 120, np.uint8)
     check_against_oracle(ctx, orc, sc)
 
 
