@@ -104,6 +104,29 @@ __device__ __forceinline__ void put(const SweepParams& p, T* out, size_t at, T v
     out[at] = v;
 }
 
+// Stores v into slices [k0, k1) of a column (out: the column's texel in slice
+// 0).  Slices run along a row of cells R elements apart, so each row of cells
+// takes one address computation and then one pointer step per store.
+// VI_SWEEP_FILL_ROWS 0: the address of every slice from its index instead.
+#ifndef VI_SWEEP_FILL_ROWS
+#define VI_SWEEP_FILL_ROWS 1
+#endif
+template <typename T>
+__device__ __forceinline__ void fill_slices(const SweepParams& p, T* out, const SliceAddr& slice,
+                                            int k0, int k1, T v) {
+    if (!VI_SWEEP_FILL_ROWS) {
+        for (int k = k0; k < k1; ++k) put(p, out, slice.at(k), v);
+        return;
+    }
+    const int per_row = 1 << slice.cells_log2;
+    for (int k = k0; k < k1;) {
+        const int row_end = min(k1, (k | (per_row - 1)) + 1);  // first slice of the next row
+        size_t at = slice.at(k);
+#pragma unroll 4
+        for (; k < row_end; ++k, at += (size_t)slice.R) put(p, out, at, v);
+    }
+}
+
 // The slices of a warp's 32 columns, in lockstep: every lane stores slice k at
 // the same step, so each slice's stores of the warp are coalesced.  A lane
 // applies alpha only inside its own interval [kin, kout]; elsewhere it stores
@@ -120,12 +143,8 @@ __device__ __forceinline__ void sweep_lockstep(const SweepParams& p, const float
     const int khi = __reduce_max_sync(0xffffffffu, has ? kout : -1);
     float T = DEPTH ? 0.0f : 1.0f;  // transmittance, or optical depth
     const typename Fmt::T one = Fmt::pack(T);
-    int k = 0;
-    for (; k < klo; ++k) {
-        if (valid) {
-            put(p, out, slice.at(k), one);
-        }
-    }
+    if (valid) fill_slices(p, out, slice, 0, klo, one);
+    int k = klo;
     for (; k <= khi; k += kLockBatch) {
         OctetRef ref[kLockBatch];
         bool lit[kLockBatch];
@@ -176,11 +195,7 @@ __device__ __forceinline__ void sweep_lockstep(const SweepParams& p, const float
     }
     if (klo <= khi) k = khi + 1;  // the last batch may have run past khi
     const typename Fmt::T last = Fmt::pack(T);
-    for (; k < lt.n; ++k) {
-        if (valid) {
-            put(p, out, slice.at(k), last);
-        }
-    }
+    if (valid) fill_slices(p, out, slice, k, lt.n, last);
 }
 
 // Column set-up of texel (i, j): the column's origin o and direction w, its
@@ -279,10 +294,8 @@ __device__ __forceinline__ void sweep_column(const SweepParams& p, const float* 
     }
     // Before the cube: full light (transmittance 1, optical depth 0).
     const typename Fmt::T one = Fmt::pack(DEPTH ? 0.0f : 1.0f);
-    int k = 0;
-    for (; k < min(kin, lt.n); ++k) {
-        put(p, out, slice.at(k), one);
-    }
+    int k = min(kin, lt.n);
+    fill_slices(p, out, slice, 0, k, one);
     // Inside the cube, four slices at a time: their positions, brick flags and
     // footprints do not depend on T, so the loads of a batch are issued together
     // and their latencies overlap; T then runs through the batch in order.
@@ -334,9 +347,7 @@ __device__ __forceinline__ void sweep_column(const SweepParams& p, const float* 
     if (kin <= kout) k = kout + 1;  // the last batch may have run past kout
     // Past the cube: the light that left it.
     const typename Fmt::T last = Fmt::pack(T);
-    for (; k < lt.n; ++k) {
-        put(p, out, slice.at(k), last);
-    }
+    fill_slices(p, out, slice, k, lt.n, last);
 }
 
 
