@@ -581,9 +581,15 @@ def gb300_arm(args):
     if world == 1 and not args.no_summaries:
         # The other configs' headline figures, so that every run records them:
         # the served reduced-precision path against the plain FP32 path
-        # (config 4), and the storage formats' error against the oracle (config 3).
+        # (config 4), the storage formats' error against the oracle (config 3)
+        # and the large-volume frame (config 5).
         line["serving"] = serving_summary(args)
         line["precision"] = precision_summary(args)
+        # The large-volume workload's figures (fewer steps than its own line).
+        large = large_result(args, 5, 2)
+        line["large"] = {k: large[k] for k in ("scene", "frames_per_s", "sweep_ms", "march_ms",
+                                               "gsamples_per_s", "sweep_gbs",
+                                               "sweep_frac_of_measured_hbm")}
     print(json.dumps(line), flush=True)
 
 
@@ -808,6 +814,11 @@ def variants_workload(args):
 
 
 def large_workload(args):
+    """The large-volume workload (see large_result), one JSON line."""
+    print(json.dumps(large_result(args, args.steps, args.warmup)), flush=True)
+
+
+def large_result(args, steps, warmup):
     """The large-volume workload: 1024^3 uint16 CT phantom (2 GiB, generated on
     the device), 1024 slices of 2048^2 stored FP16 (8 GiB), cone, 3840 x 2160
     perspective, step 0.5, ERT 0.99.  Frames/s, samples/s and the sweep's
@@ -844,27 +855,29 @@ def large_workload(args):
     torch.cuda.synchronize()
     samples = int(counts.sum().item())
     del counts
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         bld()
         rnd()
-    sweep_ms, march_ms = timed_frames(ctx, bld, rnd, flush, args.steps)
+    sweep_ms, march_ms = timed_frames(ctx, bld, rnd, flush, steps)
     sweep_bytes = vol.numel() * 2 + n * R * R * 2
     peaks, _ = measured_peaks()
     hbm = peaks.get("hbm_gbs") or 6800.0
-    print(json.dumps({"workload": "large", "metric": "frames/s", "unit": "frames/s",
-                      "scene": f"ct{args.large_n}-u16 (device-generated, seed 5), {n}x{R}^2 FP16, "
-                               f"cone 15, {W}x{H} perspective, step 0.5, ERT 0.99",
-                      "steps": args.steps, "warmup": args.warmup,
-                      "frames_per_s": round(1000.0 / (sweep_ms + march_ms), 2),
-                      "sweep_ms": round(sweep_ms, 4), "march_ms": round(march_ms, 4),
-                      "samples_per_frame": samples,
-                      "gsamples_per_s": round(samples / ((sweep_ms + march_ms) * 1e6), 2),
-                      "march_gsamples_per_s": round(samples / (march_ms * 1e6), 2),
-                      "sweep_algorithmic_bytes": sweep_bytes,
-                      "sweep_gbs": round(sweep_bytes / (sweep_ms * 1e6), 1),
-                      "sweep_frac_of_measured_hbm": round(sweep_bytes / (sweep_ms * 1e6) / hbm, 3),
-                      "volume_generation_s": round(gen_s, 2)}), flush=True)
     ctx.close()
+    del vol, out, flush
+    torch.cuda.empty_cache()
+    return {"workload": "large", "metric": "frames/s", "unit": "frames/s",
+            "scene": f"ct{args.large_n}-u16 (device-generated, seed 5), {n}x{R}^2 FP16, "
+                     f"cone 15, {W}x{H} perspective, step 0.5, ERT 0.99",
+            "steps": steps, "warmup": warmup,
+            "frames_per_s": round(1000.0 / (sweep_ms + march_ms), 2),
+            "sweep_ms": round(sweep_ms, 4), "march_ms": round(march_ms, 4),
+            "samples_per_frame": samples,
+            "gsamples_per_s": round(samples / ((sweep_ms + march_ms) * 1e6), 2),
+            "march_gsamples_per_s": round(samples / (march_ms * 1e6), 2),
+            "sweep_algorithmic_bytes": sweep_bytes,
+            "sweep_gbs": round(sweep_bytes / (sweep_ms * 1e6), 1),
+            "sweep_frac_of_measured_hbm": round(sweep_bytes / (sweep_ms * 1e6) / hbm, 3),
+            "volume_generation_s": round(gen_s, 2)}
 
 
 def oracle_workload(args):
