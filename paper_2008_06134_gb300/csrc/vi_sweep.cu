@@ -25,6 +25,14 @@ namespace {
 
 constexpr int kSweepThreads = 256;
 
+// 1: the per-lane sweep takes rows of tiles from the middle outwards (config
+// 2: 0.104 -> 0.097 ms); 0: raster order.  The lockstep sweep keeps raster
+// order (middle-out: 3.23 -> 3.38 ms on the 1024 x 2048^2 stack, whose many
+// tiles per warp leave little drain to fill and whose rows lose locality).
+#ifndef VI_SWEEP_TILE_ORDER
+#define VI_SWEEP_TILE_ORDER 1
+#endif
+
 // 1: persistent warps take tiles from a counter; 0: one tile per warp.
 #ifndef VI_SWEEP_PERSISTENT
 #define VI_SWEEP_PERSISTENT 1
@@ -438,8 +446,16 @@ __global__ void __launch_bounds__(kSweepThreads, LOCKSTEP ? VI_SWEEP_LOCKSTEP_MI
             tile = blockIdx.x * (kSweepThreads / 32) + (threadIdx.x >> 5);
         }
         if (tile >= ntiles) break;
+        int trow = (int)(tile / tiles_x);
+        if (VI_SWEEP_TILE_ORDER && !LOCKSTEP) {
+            // Rows of tiles from the middle outwards: 0, -1, +1, -2, ... from
+            // the middle row, so the long columns through the cube come first
+            // and the short ones fill the end.
+            const int ty = (int)(ntiles / tiles_x), r = trow;
+            trow = ty / 2 + ((r & 1) ? -((r + 1) >> 1) : (r >> 1));
+        }
         const int i = (int)(tile % tiles_x) * TW + (lane % TW);
-        const int j = (int)(tile / tiles_x) * TH + (lane / TW);
+        const int j = trow * TH + (lane / TW);
         sweep_column<VoxT, Fmt, DEPTH, LOCKSTEP>(p, s_alpha, i, j, i < R && j < R);
     }
 }
