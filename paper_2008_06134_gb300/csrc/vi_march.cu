@@ -569,12 +569,14 @@ __device__ __forceinline__ void load_alpha(const MarchParams& p, float* s_alpha)
 // there is little idle time to fill, and two bands of rows in flight (above
 // and below the middle) lose cache locality: 3840 x 2160 (53 per warp) 4.77 ->
 // 5.27 ms, so such frames keep raster order.  Centre-out columns as well gave
-// no more.
+// no more.  1920 x 1080 (13.4 per warp) is about 1 % faster middle-out
+// (config-3 cone march 1.201 -> 1.190 ms, shell 1.228 -> 1.215 ms), so the
+// bound is 16 tiles per warp.
 #ifndef VI_MARCH_TILE_ORDER
 #define VI_MARCH_TILE_ORDER 1
 #endif
 #ifndef VI_MARCH_CENTRE_OUT_TILES
-#define VI_MARCH_CENTRE_OUT_TILES 8
+#define VI_MARCH_CENTRE_OUT_TILES 16
 #endif
 constexpr bool kTileOrderAdaptive = VI_MARCH_TILE_ORDER == 1;
 constexpr unsigned kCentreOutTiles = VI_MARCH_CENTRE_OUT_TILES;
