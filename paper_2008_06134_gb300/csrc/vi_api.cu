@@ -6,6 +6,7 @@
 // host compiler so that no a*b+c is fused behind our back.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -167,6 +168,20 @@ int camera_frame(const vi_camera* cam, int W, int H, float step_vox, int nmax, C
     c->dt = step_vox / (float)nmax;
     c->inv_dt = 1.0f / c->dt;
     return VI_OK;
+}
+
+// Texel-slices from which the sweep runs in lockstep: VI_SWEEP_LOCKSTEP_MIN,
+// or the environment variable of that name when it holds a number (a test
+// sets it to run the lockstep kernel on stacks small enough to compare with
+// an FP64 stack element by element).
+double lockstep_threshold() {
+    const char* env = std::getenv("VI_SWEEP_LOCKSTEP_MIN");
+    if (env && *env) {
+        char* end = nullptr;
+        const double v = std::strtod(env, &end);
+        if (end != env && v >= 0.0) return v;
+    }
+    return (double)VI_SWEEP_LOCKSTEP_MIN;
 }
 
 size_t voxel_bytes(int t) { return t == VI_U8 ? 1 : 2; }
@@ -871,7 +886,7 @@ int vi_build_attenuation(vi_ctx* c, int n, int R, int mode, const vi_build_opts*
     rc = ensure(c, reinterpret_cast<void**>(&c->counter), &c->counter_cap, 256);
     if (rc) return rc;
     p.tile_counter = c->counter;
-    p.lockstep = (double)n * (double)R * (double)R >= (double)VI_SWEEP_LOCKSTEP_MIN ? 1 : 0;
+    p.lockstep = (double)n * (double)R * (double)R >= lockstep_threshold() ? 1 : 0;
     cudaError_t e = vi::launch_sweep(p, c->vr->vtype, o.format, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e);
     ++c->launches;
