@@ -162,7 +162,10 @@ int vi_set_point_light(vi_ctx* ctx, const float position[3], const float color[3
    slice_res^2 texels, C = 2^c cells to a row (slice_res C within the texture
    width, 131072 texels on sm_103a), ceil(n_slices / C) slice_res rows within
    its height (65000); VI_EINVAL otherwise.  Every configuration up to 1024
-   slices of 2048^2 fits. */
+   slices of 2048^2 fits.  Stacks of 2^29 texel-slices and more are swept with
+   a warp's columns in lockstep, smaller ones column by column; both give the
+   same values bit for bit.  The environment variable VI_SWEEP_LOCKSTEP_MIN, if
+   it holds a number, replaces that threshold (for tests). */
 int vi_build_attenuation(vi_ctx* ctx, int n_slices, int slice_res, int mode,
                          const vi_build_opts* opts);
 
