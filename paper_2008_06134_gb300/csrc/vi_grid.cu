@@ -40,6 +40,11 @@ namespace {
 #define VI_GRID_STAGE_UNROLL 8
 #endif
 constexpr int kStageUnroll = VI_GRID_STAGE_UNROLL;
+// 1: the staging loop walks rows with a fixed x per thread; 0: it derives x,
+// y and z of every staged voxel from a flat index.
+#ifndef VI_GRID_ROW_STAGING
+#define VI_GRID_ROW_STAGING 1
+#endif
 constexpr int kApron = kBrick + 1;
 constexpr int kGridThreads = kBrick * kBrick;
 static_assert(kApron * kApron * kApron * sizeof(uint16_t) <= 48 * 1024 && kGridThreads <= 1024,
@@ -59,15 +64,43 @@ __global__ void __launch_bounds__(kGridThreads)
     [[maybe_unused]] const size_t total = (size_t)nx * ny * nz;  // the checked build's bounds
     [[maybe_unused]] const long long npairs = (long long)nbx * nby * nbz * kPairsPerBrick;
     uint32_t lo = 0xffffu, hi = 0u;
+    if (VI_GRID_ROW_STAGING) {
+        // Threads as kApron columns x kRowLanes rows: a thread keeps its x and
+        // steps its row (y, z) by kRowLanes, so the voxel address takes no
+        // division per voxel.
+        constexpr int kRowLanes = kGridThreads / kApron;  // 15 for 16^3 bricks
+        constexpr int kRows = kApron * kApron;
+        const int t = threadIdx.x;
+        if (t < kRowLanes * kApron) {
+            const int x = t % kApron;
+            const int xc = min(x0 + x, nx - 1);
+            int r = t / kApron, y = r % kApron, z = r / kApron;
 #pragma unroll kStageUnroll
-    for (int t = threadIdx.x; t < kApron * kApron * kApron; t += kGridThreads) {
-        const int x = t % kApron, y = (t / kApron) % kApron, z = t / (kApron * kApron);
-        const size_t at = ((size_t)min(z0 + z, nz - 1) * ny + min(y0 + y, ny - 1)) * nx +
-                          min(x0 + x, nx - 1);
-        const VoxT val = VI_BOUNDS_OK(kSiteRaw, at, (long long)total) ? raw[at] : VoxT(0);
-        tile[z][y][x] = val;
-        lo = min(lo, (uint32_t)val);
-        hi = max(hi, (uint32_t)val);
+            for (; r < kRows; r += kRowLanes) {
+                const size_t at =
+                    ((size_t)min(z0 + z, nz - 1) * ny + min(y0 + y, ny - 1)) * nx + xc;
+                const VoxT val = VI_BOUNDS_OK(kSiteRaw, at, (long long)total) ? raw[at] : VoxT(0);
+                tile[z][y][x] = val;
+                lo = min(lo, (uint32_t)val);
+                hi = max(hi, (uint32_t)val);
+                y += kRowLanes;  // the next row: y + kRowLanes, carried into z
+                while (y >= kApron) {
+                    y -= kApron;
+                    ++z;
+                }
+            }
+        }
+    } else {
+#pragma unroll kStageUnroll
+        for (int t = threadIdx.x; t < kApron * kApron * kApron; t += kGridThreads) {
+            const int x = t % kApron, y = (t / kApron) % kApron, z = t / (kApron * kApron);
+            const size_t at = ((size_t)min(z0 + z, nz - 1) * ny + min(y0 + y, ny - 1)) * nx +
+                              min(x0 + x, nx - 1);
+            const VoxT val = VI_BOUNDS_OK(kSiteRaw, at, (long long)total) ? raw[at] : VoxT(0);
+            tile[z][y][x] = val;
+            lo = min(lo, (uint32_t)val);
+            hi = max(hi, (uint32_t)val);
+        }
     }
     __syncthreads();
     Pair* dst = static_cast<Pair*>(pairs) + (size_t)b * kPairsPerBrick;
