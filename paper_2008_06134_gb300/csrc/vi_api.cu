@@ -324,8 +324,11 @@ vi::GridView grid_view(const vi_ctx* c) {
     g.skip = c->bflags ? c->bflags + nbricks(c) : nullptr;
     g.nbx = c->vr->nbx;
     g.nby = c->vr->nby;
+    g.cnx = c->vr->nbx * vi::kCellsPerBrick;
+    g.cny = c->vr->nby * vi::kCellsPerBrick;
 #if VI_DEBUG_BOUNDS
     g.nbz = c->vr->nbz;
+    g.cnz = c->vr->nbz * vi::kCellsPerBrick;
 #endif
     return g;
 }
@@ -334,15 +337,17 @@ vi::GridView grid_view(const vi_ctx* c) {
 int refresh_flags(vi_ctx* c) {
     c->flags_ok = false;
     if (!c->vr->brange || !c->tfcnt || c->vr->vtype < 0 || !c->tf) return VI_OK;
-    // Flags, skip distances and the passes' scratch: one byte per brick each.
+    // Brick flags (a byte per brick), then the cells' skip distances and the
+    // passes' scratch (a byte per cell each).
     const size_t nb = (size_t)nbricks(c);
-    int rc = ensure(c, reinterpret_cast<void**>(&c->bflags), &c->bflags_cap, 3 * nb);
+    const size_t nc = nb * vi::kCellsPerBrick * vi::kCellsPerBrick * vi::kCellsPerBrick;
+    int rc = ensure(c, reinterpret_cast<void**>(&c->bflags), &c->bflags_cap, nb + 2 * nc);
     if (rc) return rc;
     cudaError_t e = vi::launch_brick_flags(c->vr->brange, c->vr->nbx, c->vr->nby, c->vr->nbz,
                                            c->tfcnt, c->M, c->vmin, c->vmax, c->bflags,
-                                           c->bflags + nb, c->bflags + 2 * nb, c->stream);
+                                           c->bflags + nb, c->bflags + nb + nc, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e);
-    c->launches += 4;
+    c->launches += 5;
     c->flags_ok = true;
     return VI_OK;
 }
@@ -492,10 +497,11 @@ void release_mem(size_t* used, void** p, size_t* cap, cudaStream_t s, cudaMemPoo
 }
 
 size_t volume_bytes(int dtype, int nx, int ny, int nz) {
-    constexpr int B = 1 << vi::kBrickShift;
     const size_t raw = (size_t)nx * (size_t)ny * (size_t)nz * voxel_bytes(dtype);
-    const size_t bricks = (size_t)((nx + B - 1) / B) * ((ny + B - 1) / B) * ((nz + B - 1) / B);
-    return raw + vi::pair_brick_bytes(nx, ny, nz, voxel_bytes(dtype)) + bricks * sizeof(uint32_t);
+    size_t bricks = 0, cells = 0;
+    vi::grid_counts(nx, ny, nz, &bricks, &cells);
+    return raw + vi::pair_brick_bytes(nx, ny, nz, voxel_bytes(dtype)) +
+           (bricks + cells) * sizeof(uint32_t);
 }
 
 int volume_load(VolumeRes* v, size_t* used, size_t budget, const void* data, int dtype, int nx,
@@ -505,17 +511,19 @@ int volume_load(VolumeRes* v, size_t* used, size_t budget, const void* data, int
     const int nbx = (nx + B - 1) / B, nby = (ny + B - 1) / B, nbz = (nz + B - 1) / B;
     // Check the whole footprint first, so a refusal leaves the old volume intact.
     const size_t pair_bytes = vi::pair_brick_bytes(nx, ny, nz, voxel_bytes(dtype));
+    size_t nbricks = 0, ncells = 0;
+    vi::grid_counts(nx, ny, nz, &nbricks, &ncells);
+    const size_t range_bytes = (nbricks + ncells) * sizeof(uint32_t);  // bricks, then cells
     const size_t have = std::max(v->raw_cap, bytes) - v->raw_cap +
                         std::max(v->pairs_cap, pair_bytes) - v->pairs_cap +
-                        std::max(v->brange_cap, (size_t)nbx * nby * nbz * sizeof(uint32_t)) -
-                        v->brange_cap;
+                        std::max(v->brange_cap, range_bytes) - v->brange_cap;
     if (budget && *used + have > budget) return VI_ENOMEM;
     int rc = ensure_mem(used, budget, &v->raw, &v->raw_cap, bytes, s, v->pool);
     if (rc) return rc;
     rc = ensure_mem(used, budget, &v->pairs, &v->pairs_cap, pair_bytes, s, v->pool);
     if (rc) return rc;
     rc = ensure_mem(used, budget, reinterpret_cast<void**>(&v->brange), &v->brange_cap,
-                    (size_t)nbx * nby * nbz * sizeof(uint32_t), s, v->pool);
+                    range_bytes, s, v->pool);
     if (rc) return rc;
     v->vtype = -1;
     cudaError_t e = cudaMemcpyAsync(v->raw, data, bytes,

@@ -177,25 +177,21 @@ __device__ __forceinline__ VoxelCoord voxel_coord_inside(const VolumeView& v, fl
     return c;
 }
 
-// Brick coordinates of the footprint's lower corner.  Each is monotone in the
-// position along a ray or a light column, so two samples whose bricks lie in
-// one box of bricks have every sample between them in that box too.
-__device__ __forceinline__ bool same_brick(const VoxelCoord& a, const VoxelCoord& b) {
-    return ((a.x0 ^ b.x0) >> kBrickShift) == 0 && ((a.y0 ^ b.y0) >> kBrickShift) == 0 &&
-           ((a.z0 ^ b.z0) >> kBrickShift) == 0;
+// Cell coordinates (the skip grid, 2^kCellShift voxels a side) of the
+// footprint's lower corner.  Each is monotone in the position along a ray or a
+// light column, so two samples whose cells lie in one box of cells have every
+// sample between them in that box too.
+// Whether b's cell lies within rad cells of a's along every axis.
+__device__ __forceinline__ bool within_cells(const VoxelCoord& a, const VoxelCoord& b, int rad) {
+    return abs((a.x0 >> kCellShift) - (b.x0 >> kCellShift)) <= rad &&
+           abs((a.y0 >> kCellShift) - (b.y0 >> kCellShift)) <= rad &&
+           abs((a.z0 >> kCellShift) - (b.z0 >> kCellShift)) <= rad;
 }
 
-// Whether b's brick lies within rad bricks of a's along every axis.
-__device__ __forceinline__ bool within_bricks(const VoxelCoord& a, const VoxelCoord& b, int rad) {
-    return abs((a.x0 >> kBrickShift) - (b.x0 >> kBrickShift)) <= rad &&
-           abs((a.y0 >> kBrickShift) - (b.y0 >> kBrickShift)) <= rad &&
-           abs((a.z0 >> kBrickShift) - (b.z0 >> kBrickShift)) <= rad;
-}
-
-// A ray in voxel units for brick-box exits: X_a(t) = o_a N_a + t d_a N_a
+// A ray in voxel units for cell-box exits: X_a(t) = o_a N_a + t d_a N_a
 // (origin ox, reciprocal rate ix; ix is 0 on an axis the ray does not move
-// along).  The footprint's lower corner floor(X_a - 1/2) enters brick b at
-// X_a = B b + 1/2, B = 2^kBrickShift.
+// along).  The footprint's lower corner floor(X_a - 1/2) enters cell b at
+// X_a = C b + 1/2, C = 2^kCellShift.
 struct VoxelRay {
     float ox[3], ix[3];
 };
@@ -212,17 +208,17 @@ __device__ __forceinline__ VoxelRay voxel_ray(const VolumeView& v, const float o
     return q;
 }
 
-// Parameter t at which the footprint's lower corner leaves the box of bricks
-// within rad of c's brick along every axis (an estimate; callers verify with
-// the exact path).  rad = 0: c's brick.
-__device__ __forceinline__ float brick_exit(const VoxelRay& q, const VoxelCoord& c, int rad) {
-    const int b[3] = {c.x0 >> kBrickShift, c.y0 >> kBrickShift, c.z0 >> kBrickShift};
+// Parameter t at which the footprint's lower corner leaves the box of cells
+// within rad of c's cell along every axis (an estimate; callers verify with
+// the exact path).  rad = 0: c's cell.
+__device__ __forceinline__ float cell_exit(const VoxelRay& q, const VoxelCoord& c, int rad) {
+    const int b[3] = {c.x0 >> kCellShift, c.y0 >> kCellShift, c.z0 >> kCellShift};
     float s_exit = 3.0e38f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        // Moving up, the box ends at brick b + rad + 1; moving down, at b - rad.
+        // Moving up, the box ends at cell b + rad + 1; moving down, at b - rad.
         const int edge = q.ix[a] > 0.0f ? b[a] + rad + 1 : b[a] - rad;
-        const float plane = (float)(edge * (1 << kBrickShift)) + 0.5f;
+        const float plane = (float)(edge * (1 << kCellShift)) + 0.5f;
         if (q.ix[a] != 0.0f) s_exit = fminf(s_exit, (plane - q.ox[a]) * q.ix[a]);
     }
     return s_exit;
@@ -250,12 +246,22 @@ __device__ __forceinline__ bool brick_may_be_lit(const GridView& g, const VoxelC
     return __ldg(g.flags + b) != 0;
 }
 
-// Skip distance of the brick holding the footprint's lower corner: 0 if it
-// may yield alpha > 0, else 1 + the radius of the box of bricks around it
-// that cannot (see GridView).
-__device__ __forceinline__ int brick_skip(const GridView& g, const VoxelCoord& c) {
-    if (!brick_in_grid(g, c.x0, c.y0, c.z0)) return 1;
-    return __ldg(g.skip + brick_index(g, c.x0, c.y0, c.z0));
+__device__ __forceinline__ int cell_index(const GridView& g, int x0, int y0, int z0) {
+    return ((z0 >> kCellShift) * g.cny + (y0 >> kCellShift)) * g.cnx + (x0 >> kCellShift);
+}
+
+__device__ __forceinline__ bool cell_in_grid(const GridView& g, int x0, int y0, int z0) {
+    return VI_BOUNDS_OK(kSiteBrick, x0 >> kCellShift, g.cnx) &&
+           VI_BOUNDS_OK(kSiteBrick, y0 >> kCellShift, g.cny) &&
+           VI_BOUNDS_OK(kSiteBrick, z0 >> kCellShift, g.cnz);
+}
+
+// Skip distance of the cell holding the footprint's lower corner: 0 if it may
+// yield alpha > 0, else 1 + the radius of the box of cells around it that
+// cannot (see GridView).
+__device__ __forceinline__ int cell_skip(const GridView& g, const VoxelCoord& c) {
+    if (!cell_in_grid(g, c.x0, c.y0, c.z0)) return 1;
+    return __ldg(g.skip + cell_index(g, c.x0, c.y0, c.z0));
 }
 
 // Integer to float without the conversion pipe: v < 2^23 placed in the mantissa
@@ -397,12 +403,11 @@ __device__ __forceinline__ size_t footprint_index(const VolumeView& v, const Foo
     return pair_index(v, c.x0, c.y0, c.z0);
 }
 
-// The march's test (its skip distances: 0 exactly where the flag is set),
-// given the brick's index b (vol_brick of the lower corner).
-__device__ __forceinline__ bool footprint_may_be_lit(const GridView& g, const FootprintCell& c,
-                                                     int b) {
-    if (!brick_in_grid(g, c.x0, c.y0, c.z0)) return false;
-    return __ldg(g.skip + b) == 0;
+// The march's test: whether the cell holding the footprint's lower corner may
+// yield alpha > 0 (its skip distance is 0 exactly then).
+__device__ __forceinline__ bool footprint_may_be_lit(const GridView& g, const FootprintCell& c) {
+    if (!cell_in_grid(g, c.x0, c.y0, c.z0)) return false;
+    return __ldg(g.skip + cell_index(g, c.x0, c.y0, c.z0)) == 0;
 }
 
 // Trilinear value of a footprint's eight voxels (an octet) at its weights.  uint16 voxels are

@@ -11,12 +11,16 @@
 // within its corners' range, and a lerp of two zero entries is zero -- so the
 // sweep and the march skip its gather without changing any result.
 //
-// For the march's runs through such bricks, each brick also gets its
-// L-infinity distance to the nearest brick that may be lit (the skip
-// distance): a ray in a brick at distance d can move through the box of
-// bricks within d - 1 of it in one step instead of brick by brick.  The
-// distance transform is separable under the maximum norm, so three passes,
-// one per axis, compute it exactly up to the cap.
+// The march tests its samples, and takes its runs, on a finer grid of cells
+// (2^kCellShift voxels a side, kCellsPerBrick^3 to a brick): each cell gets
+// the same kind of range and flag, and its L-infinity distance to the nearest
+// cell that may be lit (the skip distance): a ray in a cell at distance d can
+// move through the box of cells within d - 1 of it in one step instead of
+// cell by cell.  The distance transform is separable under the maximum norm,
+// so three passes, one per axis, compute it exactly up to the cap.  8^3 cells
+// inside the 16^3 pair bricks mark 25.8 % of config 2's volume as possibly
+// lit against 30.4 % for 16^3 (config-2 march 0.587 -> 0.565 ms; the sweep
+// keeps its test on the bricks, whose index it already has).
 #include <cmath>
 #include <type_traits>
 
@@ -54,7 +58,8 @@ static_assert(kApron * kApron * kApron * sizeof(uint16_t) <= 48 * 1024 && kGridT
 template <typename VoxT>
 __global__ void __launch_bounds__(kGridThreads)
     volume_grid_kernel(const VoxT* __restrict__ raw, int nx, int ny, int nz, int nbx, int nby,
-                       int nbz, void* __restrict__ pairs, uint32_t* __restrict__ range) {
+                       int nbz, void* __restrict__ pairs, uint32_t* __restrict__ range,
+                       uint32_t* __restrict__ cell_range) {
     using Pair = typename std::conditional<sizeof(VoxT) == 2, unsigned, unsigned short>::type;
     __shared__ VoxT tile[kApron][kApron][kApron];  // [z][y][x]
     __shared__ uint32_t part_lo[kGridThreads / 32], part_hi[kGridThreads / 32];
@@ -109,6 +114,31 @@ __global__ void __launch_bounds__(kGridThreads)
         const Pair v = (Pair)((unsigned)tile[z][y][x] |
                               ((unsigned)tile[z][y][x + 1] << (8 * sizeof(VoxT))));
         if (VI_BOUNDS_OK(kSiteGrid, (long long)b * kPairsPerBrick + t, npairs)) dst[t] = v;
+    }
+    // The brick's cells: a warp per cell takes the range over the cell's
+    // voxels and its one-voxel apron, (C + 1)^3 voxels of the staged tile.
+    {
+        constexpr int C = 1 << kCellShift, CA = C + 1;
+        constexpr int kCells = kCellsPerBrick * kCellsPerBrick * kCellsPerBrick;
+        const int cnx = nbx * kCellsPerBrick, cny = nby * kCellsPerBrick;
+        [[maybe_unused]] const long long ncells = (long long)cnx * cny * nbz * kCellsPerBrick;
+        const int lane = threadIdx.x & 31;
+        for (int cell = threadIdx.x >> 5; cell < kCells; cell += kGridThreads / 32) {
+            const int sx = cell % kCellsPerBrick, sy = (cell / kCellsPerBrick) % kCellsPerBrick,
+                      sz = cell / (kCellsPerBrick * kCellsPerBrick);
+            uint32_t clo = 0xffffu, chi = 0u;
+            for (int t = lane; t < CA * CA * CA; t += 32) {
+                const int x = sx * C + t % CA, y = sy * C + (t / CA) % CA, z = sz * C + t / (CA * CA);
+                const uint32_t val = (uint32_t)tile[z][y][x];
+                clo = min(clo, val);
+                chi = max(chi, val);
+            }
+            clo = __reduce_min_sync(0xffffffffu, clo);
+            chi = __reduce_max_sync(0xffffffffu, chi);
+            const long long at = ((long long)(bz * kCellsPerBrick + sz) * cny +
+                                  (by * kCellsPerBrick + sy)) * cnx + (bx * kCellsPerBrick + sx);
+            if (lane == 0 && VI_BOUNDS_OK(kSiteGrid, at, ncells)) cell_range[at] = (clo << 16) | chi;
+        }
     }
     lo = __reduce_min_sync(0xffffffffu, lo);
     hi = __reduce_max_sync(0xffffffffu, hi);
@@ -177,12 +207,15 @@ cudaError_t launch_volume_grid(const void* raw, int nx, int ny, int nz, int voxe
     const int nby = (ny + kBrick - 1) >> kBrickShift;
     const int nbz = (nz + kBrick - 1) >> kBrickShift;
     const unsigned blocks = (unsigned)nbx * nby * nbz;
+    uint32_t* cell_range = range + (size_t)blocks;  // after the brick ranges
     if (voxel_type == 0)
         volume_grid_kernel<uint8_t><<<blocks, kGridThreads, 0, s>>>(
-            static_cast<const uint8_t*>(raw), nx, ny, nz, nbx, nby, nbz, pairs, range);
+            static_cast<const uint8_t*>(raw), nx, ny, nz, nbx, nby, nbz, pairs, range,
+            cell_range);
     else
         volume_grid_kernel<uint16_t><<<blocks, kGridThreads, 0, s>>>(
-            static_cast<const uint16_t*>(raw), nx, ny, nz, nbx, nby, nbz, pairs, range);
+            static_cast<const uint16_t*>(raw), nx, ny, nz, nbx, nby, nbz, pairs, range,
+            cell_range);
     return cudaGetLastError();
 }
 
@@ -190,13 +223,18 @@ cudaError_t launch_brick_flags(const uint32_t* range, int nbx, int nby, int nbz,
                                const int* lit_prefix, int M, float vmin, float vmax,
                                uint8_t* flags, uint8_t* skip, uint8_t* tmp, cudaStream_t s) {
     const int nbricks = nbx * nby * nbz;
+    const int cnx = nbx * kCellsPerBrick, cny = nby * kCellsPerBrick, cnz = nbz * kCellsPerBrick;
+    const int ncells = cnx * cny * cnz;
     const double scale = (double)(M - 1) / ((double)vmax - (double)vmin);
     const int threads = 256, blocks = (nbricks + threads - 1) / threads;
+    const int cblocks = (ncells + threads - 1) / threads;
     brick_flag_kernel<<<blocks, threads, 0, s>>>(range, nbricks, lit_prefix, M, (double)vmin,
                                                  scale, flags);
-    skip_pass_kernel<<<blocks, threads, 0, s>>>(flags, skip, nbx, nby, nbz, 0, 1);
-    skip_pass_kernel<<<blocks, threads, 0, s>>>(skip, tmp, nbx, nby, nbz, 1, 0);
-    skip_pass_kernel<<<blocks, threads, 0, s>>>(tmp, skip, nbx, nby, nbz, 2, 0);
+    brick_flag_kernel<<<cblocks, threads, 0, s>>>(range + nbricks, ncells, lit_prefix, M,
+                                                  (double)vmin, scale, tmp);
+    skip_pass_kernel<<<cblocks, threads, 0, s>>>(tmp, skip, cnx, cny, cnz, 0, 1);
+    skip_pass_kernel<<<cblocks, threads, 0, s>>>(skip, tmp, cnx, cny, cnz, 1, 0);
+    skip_pass_kernel<<<cblocks, threads, 0, s>>>(tmp, skip, cnx, cny, cnz, 2, 0);
     return cudaGetLastError();
 }
 

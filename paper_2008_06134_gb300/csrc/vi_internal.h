@@ -95,20 +95,30 @@ struct VolumeView {
     float fnx, fny, fnz;  // (float)nx ...
 };
 
-// Brick occupancy.  flags[b] != 0: brick b may yield alpha > 0 (the sweep's
-// test).  skip[b] (the march's): 0 for such a brick, else the L-infinity
-// distance, in bricks and capped at kSkipCap + 1, from b to the nearest brick
-// that may yield alpha > 0 -- so every brick within skip[b] - 1 of b along
-// each axis cannot.  Both arrays hold one byte per brick, index
-// (bz nby + by) nbx + bx.
+// Occupancy.  flags[b] != 0: brick b may yield alpha > 0 (the sweep's test;
+// one byte per 16^3 brick, index (bz nby + by) nbx + bx).  The skip
+// distances live on a finer grid of cells, 2^kCellShift voxels a side (each
+// brick holds kCellsPerBrick^3 of them; index (cz cny + cy) cnx + cx):
+// skip[c] is 0 for a cell that may yield alpha > 0, else the L-infinity
+// distance, in cells and capped at kSkipCap + 1, from c to the nearest such
+// cell -- so every cell within skip[c] - 1 of c along each axis cannot.  The
+// march tests its samples and takes its transparent runs on the cells; the
+// lockstep sweep takes its runs on them.
+#ifndef VI_CELL_SHIFT
+#define VI_CELL_SHIFT 3
+#endif
+constexpr int kCellShift = VI_CELL_SHIFT;
+static_assert(kCellShift <= kBrickShift && kCellShift >= 1, "cells subdivide the bricks");
+constexpr int kCellsPerBrick = 1 << (kBrickShift - kCellShift);  // per axis
 constexpr int kSkipCap = 31;
 
 struct GridView {
     const uint8_t* flags;
     const uint8_t* skip;
-    int nbx, nby;
+    int nbx, nby;  // bricks per axis (flags)
+    int cnx, cny;  // cells per axis (skip)
 #if VI_DEBUG_BOUNDS
-    int nbz;
+    int nbz, cnz;
 #endif
 };
 
@@ -216,10 +226,19 @@ cudaError_t launch_march(const MarchParams& p, int voxel_type, int format, int m
                          cudaStream_t s);
 cudaError_t launch_trace(const MarchParams& p, int voxel_type, int format, int mode, int x,
                          int y, int32_t* rec, int max_rec, int* n_rec, cudaStream_t s);
-// The pair bricks of the volume and the value range of every brick (with its
-// one-voxel apron), in one pass over the raw voxels.
+// The pair bricks of the volume and the value range of every brick and of
+// every cell (each with its one-voxel apron), in one pass over the raw voxels.
+// range: nbricks brick ranges followed by ncells cell ranges (grid_counts).
 cudaError_t launch_volume_grid(const void* raw, int nx, int ny, int nz, int voxel_type,
                                void* pairs, uint32_t* range, cudaStream_t s);
+// Bricks and cells of an nx x ny x nz volume.
+inline void grid_counts(int nx, int ny, int nz, size_t* nbricks, size_t* ncells) {
+    const size_t nbx = (size_t)((nx + kBrick - 1) >> kBrickShift);
+    const size_t nby = (size_t)((ny + kBrick - 1) >> kBrickShift);
+    const size_t nbz = (size_t)((nz + kBrick - 1) >> kBrickShift);
+    *nbricks = nbx * nby * nbz;
+    *ncells = *nbricks * kCellsPerBrick * kCellsPerBrick * kCellsPerBrick;
+}
 // Bytes of the pair bricks of an nx x ny x nz volume of voxel_bytes-byte voxels.
 inline size_t pair_brick_bytes(int nx, int ny, int nz, size_t voxel_bytes) {
     const size_t bricks = (size_t)((nx + kBrick - 1) >> kBrickShift) *
@@ -254,8 +273,9 @@ cudaError_t enqueue_march_batch(const BatchFrame* frames, int count, unsigned lo
 // and released to the whole device.
 cudaError_t launch_post_ready(unsigned* ready, unsigned epoch, cudaStream_t s);
 // Brick flags from the brick ranges and the TF's prefix count of entries with
-// alpha > 0, then the skip distances from the flags (three passes, one per
-// axis, through tmp: nbricks bytes of scratch).
+// alpha > 0; cell flags from the cell ranges (into tmp), then the cells' skip
+// distances from them (three passes, one per axis, through tmp: ncells bytes).
+// range as launch_volume_grid writes it.
 cudaError_t launch_brick_flags(const uint32_t* range, int nbx, int nby, int nbz,
                                const int* lit_prefix, int M, float vmin, float vmax,
                                uint8_t* flags, uint8_t* skip, uint8_t* tmp, cudaStream_t s);

@@ -230,23 +230,23 @@ constexpr int kWalk = VI_MARCH_WALK;
 __device__ __forceinline__ int last_transparent(const MarchParams& p, const Ray& r, int i, float t,
                                                 VoxelCoord vc) {
     int s = i;
-    int d = brick_skip(p.grid, vc);
+    int d = cell_skip(p.grid, vc);
     const VoxelRay q = voxel_ray(p.vol, r.o, r.d);
     for (int w = 0; w < kWalk; ++w) {
         int end = s;
         const int rad = d - 1;
-        const float t_exit = brick_exit(q, vc, rad);
+        const float t_exit = cell_exit(q, vc, rad);
         const float steps = (fminf(t_exit, r.t1) - t) * p.cam.inv_dt;
         if (steps >= 2.0f) {
             const int j = s + (int)fminf(steps, 1.0e7f) - 1;
             float tj;
             const VoxelCoord cj = sample_cell(p, r, j, &tj);
-            if (tj < r.t1 && within_bricks(vc, cj, rad)) end = j;
+            if (tj < r.t1 && within_cells(vc, cj, rad)) end = j;
         }
         // The sample after the run: past the exit, or in a brick that may be lit.
         vc = sample_cell(p, r, end + 1, &t);
         if (!(t < r.t1)) return end;
-        d = brick_skip(p.grid, vc);
+        d = cell_skip(p.grid, vc);
         if (d == 0) return end;
         s = end + 1;  // transparent as well: the walk goes on from here
     }
@@ -349,7 +349,7 @@ __device__ __forceinline__ int march_sample(const MarchParams& p, const AlphaT& 
         const int b = vol_brick(p.vol, fc.x0, fc.y0, fc.z0);
         const typename Octet<VoxT>::V q =
             octet_load<VoxT>(p.vol, pair_index_in(b, fc.x0, fc.y0, fc.z0));
-        if (!footprint_may_be_lit(p.grid, fc, b)) {
+        if (!footprint_may_be_lit(p.grid, fc)) {
             ++count;
             return A > p.ert ? kStopped : kEmpty;
         }

@@ -164,7 +164,8 @@ size_t slot_growth(const Slot* sl, const Request* r, const ServerVolume* v) {
     const vi_ctx* c = sl->ctx;
     auto grow = [](size_t need, size_t cap) { return need > cap ? need - cap : 0; };
     return grow(stack, c->stack_cap) + grow(q.tf_entries * 16, c->tf_cap) +
-           grow((q.tf_entries + 1) * 4, c->tfcnt_cap) + grow(3 * bricks, c->bflags_cap) +
+           grow((q.tf_entries + 1) * 4, c->tfcnt_cap) + grow(bricks + 2 * bricks * vi::kCellsPerBrick * vi::kCellsPerBrick * vi::kCellsPerBrick,
+                c->bflags_cap) +
            grow(out, c->out_cap) + grow(256, c->counter_cap);
 }
 

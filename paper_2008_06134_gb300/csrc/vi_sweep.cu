@@ -160,19 +160,19 @@ __device__ __forceinline__ int transparent_run(const SweepParams& p, const float
                                                const float w[3], int k, int kout) {
     const LightFrame& lt = p.lt;
     const VoxelCoord c0 = slice_cell(lt, p.vol, k, o, w);
-    const int d = brick_skip(p.grid, c0);
+    const int d = cell_skip(p.grid, c0);
     if (d == 0) return k - 1;
     const int rad = d - 1;
     // Column parameter s where the footprint's lower corner leaves the box;
     // slice k' sits at s = min + k' dL - Lc.
     const VoxelRay q = voxel_ray(p.vol, o, w);
-    const float s_exit = brick_exit(q, c0, rad);
+    const float s_exit = cell_exit(q, c0, rad);
     const float kf = __fdividef(s_exit + lt.Lc - lt.min, lt.dL);
     if (!(kf < 2.0e9f)) return k;  // no exit estimate: the one slice
     const int j = min((int)kf - 1, kout);
     if (j <= k) return k;
     const VoxelCoord cj = slice_cell(lt, p.vol, j, o, w);
-    return within_bricks(c0, cj, rad) ? j : k;
+    return within_cells(c0, cj, rad) ? j : k;
 }
 
 // The slices of a warp's 32 columns, in lockstep: every lane stores slice k at
