@@ -45,16 +45,16 @@ FLOPS_LIT = {0: 0, 1: 6 + 2 + 12, 2: 6 + 2 + 6 * 12 + 7, 3: 6 + 2 + 8 * 12 + 9}
 # entry holds for the kernel sources it was taken from (hash of the files that
 # define the kernel); once they change the figure is stale and reported as null.
 NCU_TRAFFIC = {
-    "march_kernel": (("vi_march.cu", "vi_device.cuh", "vi_internal.h"), "8bc53dade405579c",
-                     34_112_512),
-    "sweep_kernel": (("vi_sweep.cu", "vi_device.cuh", "vi_internal.h"), "21d85310cfccaebf",
-                     240_620_544),
+    "march_kernel": (("vi_march.cu", "vi_device.cuh", "vi_internal.h"), "af44da2bee6d4b70",
+                     32_089_088),
+    "sweep_kernel": (("vi_sweep.cu", "vi_device.cuh", "vi_internal.h"), "8d8c05debacf7514",
+                     240_257_536),
 }
 
 
 # Other counters of the same march capture, for its candidate bounds: warp-level
 # instructions executed and L2 sectors (32 B) per launch.
-NCU_MARCH_COUNTERS = {"inst_executed": 473_672_572, "lts_sectors": 11_104_717}
+NCU_MARCH_COUNTERS = {"inst_executed": 453_145_357, "lts_sectors": 10_502_863}
 
 
 def march_bounds(march_s: float, sms: int, clock_mhz: float, peaks: dict, probe: dict):
@@ -581,8 +581,8 @@ def gb300_arm(args):
     if world == 1 and not args.no_summaries:
         # The other configs' headline figures, so that every run records them:
         # the served reduced-precision path against the plain FP32 path
-        # (config 4), the storage formats' error against the oracle (config 3)
-        # and the large-volume frame (config 5).
+        # (the serving mix), the storage formats' error against the oracle (the
+        # 512^3 blob frames) and the large-volume frame (1024^3).
         line["serving"] = serving_summary(args)
         line["precision"] = precision_summary(args)
         # The large-volume workload's figures (fewer steps than its own line).
@@ -612,8 +612,8 @@ def timed_frames(ctx, build, render, flush, steps):
 
 
 def precision_rows(steps: int, warmup: int, modes=("shell", "cone"), depth: bool = True):
-    """Storage formats FP32 / FP16 / BF16 / UNORM16 on the 512^3 blob scene
-    (config 3): frames/s of each and its per-channel error against the FP64
+    """Storage formats FP32 / FP16 / BF16 / UNORM16 on the 512^3 blob scene:
+    frames/s of each and its per-channel error against the FP64
     oracle on the centred 256x144 crop (the oracle builds its own FP64 stack).
     Returns (scene name, oracle seconds, rows)."""
     import numpy as np
@@ -695,7 +695,7 @@ def precision_rows(steps: int, warmup: int, modes=("shell", "cone"), depth: bool
 
 
 def precision_summary(args):
-    """The headline line's precision figures: config 3's cone frames in each
+    """The headline line's precision figures: the 512^3 blob cone frames in each
     storage format, their max error per RGBA channel against the FP64 oracle
     (256x144 crop) and their frame rate against FP32."""
     import oracle
@@ -970,7 +970,7 @@ def oracle_workload(args):
 
 
 def serving_setup(args):
-    """The serving mix (config 4): the registered volumes in pinned host memory,
+    """The serving mix: the registered volumes in pinned host memory,
     the request streams per Poisson rate, and run(slots, fmt, burst, reqs,
     graphs, batching), which serves one stream on a fresh server and returns
     (row of frames/s and latency percentiles, frames)."""

@@ -177,11 +177,11 @@ __device__ __forceinline__ VoxelCoord voxel_coord_inside(const VolumeView& v, fl
     return c;
 }
 
-// Cell coordinates (the skip grid, 2^kCellShift voxels a side) of the
-// footprint's lower corner.  Each is monotone in the position along a ray or a
-// light column, so two samples whose cells lie in one box of cells have every
-// sample between them in that box too.
-// Whether b's cell lies within rad cells of a's along every axis.
+// Whether b's cell lies within rad cells of a's along every axis.  A cell
+// here is the skip grid's cell (2^kCellShift voxels a side) of the
+// footprint's lower corner; each of its coordinates is monotone in the
+// position along a ray or a light column, so two samples whose cells lie in
+// one box of cells have every sample between them in that box too.
 __device__ __forceinline__ bool within_cells(const VoxelCoord& a, const VoxelCoord& b, int rad) {
     return abs((a.x0 >> kCellShift) - (b.x0 >> kCellShift)) <= rad &&
            abs((a.y0 >> kCellShift) - (b.y0 >> kCellShift)) <= rad &&

@@ -18,9 +18,11 @@
 // move through the box of cells within d - 1 of it in one step instead of
 // cell by cell.  The distance transform is separable under the maximum norm,
 // so three passes, one per axis, compute it exactly up to the cap.  8^3 cells
-// inside the 16^3 pair bricks mark 25.8 % of config 2's volume as possibly
-// lit against 30.4 % for 16^3 (config-2 march 0.587 -> 0.565 ms; the sweep
-// keeps its test on the bricks, whose index it already has).
+// inside the 16^3 pair bricks mark 25.8 % of a 256^3 CT phantom's volume as
+// possibly lit against 30.4 % for 16^3 (its cone march 0.587 -> 0.565 ms).
+// The lockstep sweep takes its transparent runs on the cells too; both
+// sweeps test their samples on the brick flags, whose index they already
+// have for the footprint (a per-sample cell test measured slower there).
 #include <cmath>
 #include <type_traits>
 

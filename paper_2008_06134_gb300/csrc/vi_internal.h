@@ -75,7 +75,8 @@ enum DebugSite {
 // Bricks of 2^kBrickShift voxels per axis; flags[bz][by][bx] = 1 if a sample
 // whose trilinear footprint starts in the brick may have alpha > 0.  16^3
 // measured fastest: coarser bricks skip a little less, but each transparent
-// run is crossed in fewer steps (config-2 march 0.985 -> 0.908 ms against 8^3;
+// run is crossed in fewer steps (256^3 CT cone march 0.985 -> 0.908 ms
+// against 8^3;
 // 4^3 and 32^3 were slower; 8^3 again 0.841 against 0.784 ms later on).
 #ifndef VI_BRICK_SHIFT
 #define VI_BRICK_SHIFT 4

@@ -30,10 +30,10 @@
 // once, which costs registers the 64-register budget may not have.  The first
 // cone kernels spilled 112 bytes a thread that way and reloaded them every
 // sample (31 M local loads per 1024^2 frame), so they took the rings one after
-// the other (config-2 march 1.148 -> 1.042 ms).  The current cone kernel keeps
-// both rings in flight with 4 bytes of spills and is faster that way (0.595 ->
-// 0.585 ms, same box); the shell takes three points at a time (0.974 -> 0.947
-// ms against six when it was measured).
+// the other (256^3 CT cone march at 1024^2: 1.148 -> 1.042 ms).  The current
+// cone kernel keeps both rings in flight with 4 bytes of spills and is faster
+// that way (0.595 -> 0.585 ms, measured side by side); the shell takes three
+// points at a time (0.974 -> 0.947 ms against six when it was measured).
 #ifndef VI_CONE_RING_UNROLL
 #define VI_CONE_RING_UNROLL 2
 #endif
@@ -54,8 +54,8 @@ constexpr int kConeRingUnroll = VI_CONE_RING_UNROLL;
 #endif
 
 // A warp's pixel tile: kTileW x kTileH neighbouring rays marched in lockstep.
-// 4 x 8 measured fastest on the config-2 frame (march 0.987 ms, against 1.045 /
-// 1.085 / 1.161 ms for 8 x 4, 2 x 16 and 16 x 2).
+// 4 x 8 measured fastest on the 256^3 CT cone frame at 1024^2 (march 0.987 ms,
+// against 1.045 / 1.085 / 1.161 ms for 8 x 4, 2 x 16 and 16 x 2).
 #ifndef VI_MARCH_TILE_W
 #define VI_MARCH_TILE_W 4
 #endif
@@ -66,7 +66,7 @@ constexpr int kShellUnroll = VI_SHELL_UNROLL;
 // One block of 1024 threads per SM (32 warps, 64 registers each): the same
 // occupancy as four blocks of 256, but one shared copy of the TF's alpha
 // column per SM instead of four, which leaves more of the unified L1 / shared
-// storage to L1 (config-2 march 0.870 ms, against 0.885 / 0.899 / 0.918 ms
+// storage to L1 (256^3 CT cone march 0.870 ms, against 0.885 / 0.899 / 0.918 ms
 // for blocks of 512 / 256 / 128).
 #ifndef VI_MARCH_THREADS
 #define VI_MARCH_THREADS 1024
@@ -212,16 +212,16 @@ __device__ __forceinline__ VoxelCoord sample_cell(const MarchParams& p, const Ra
                        __fmaf_rn(t, r.d[2], r.o[2]));
 }
 
-// Last sample j >= i such that samples i..j all lie in bricks that cannot
-// yield alpha > 0 (sample i, at t with cell vc, is in one).  Each step takes
-// the box of bricks that the current brick's skip distance d clears (those
-// within d - 1 of it along every axis; d = 1: the brick alone), estimates the
-// last sample inside it from the box exit and confirms it with the exact
-// index path (each brick coordinate is monotone in the sample index, so the
-// samples between two confirmed ones lie in the box too).  The walk stops at
-// a brick that may be lit, at the ray's exit, or after kWalk steps.
+// Last sample j >= i such that samples i..j all lie in skip-grid cells that
+// cannot yield alpha > 0 (sample i, at t with footprint cell vc, is in one).
+// Each step takes the box of cells that the current cell's skip distance d
+// clears (those within d - 1 of it along every axis; d = 1: the cell alone),
+// estimates the last sample inside it from the box exit and confirms it with
+// the exact index path (each cell coordinate is monotone in the sample index,
+// so the samples between two confirmed ones lie in the box too).  The walk
+// stops at a cell that may be lit, at the ray's exit, or after kWalk steps.
 // Steps a warp's transparent-run walk may take (16 measured faster than 4 or
-// 8 with one brick per step; 32 was no better).
+// 8 with one 16^3 brick per step; 32 was no better).
 #ifndef VI_MARCH_WALK
 #define VI_MARCH_WALK 16
 #endif
@@ -243,7 +243,7 @@ __device__ __forceinline__ int last_transparent(const MarchParams& p, const Ray&
             const VoxelCoord cj = sample_cell(p, r, j, &tj);
             if (tj < r.t1 && within_cells(vc, cj, rad)) end = j;
         }
-        // The sample after the run: past the exit, or in a brick that may be lit.
+        // The sample after the run: past the exit, or in a cell that may be lit.
         vc = sample_cell(p, r, end + 1, &t);
         if (!(t < r.t1)) return end;
         d = cell_skip(p.grid, vc);
@@ -564,13 +564,14 @@ __device__ __forceinline__ void load_alpha(const MarchParams& p, float* s_alpha)
 // default): there the rows are taken from the middle outwards (columns in
 // order), so the rows where rays cross the volume (costly) come first and the
 // cheap border rows last, where they fill the time the last costly tiles take
-// instead of leaving warps idle.  Config 2 (1024^2, 6.7 tiles per warp): march
+// instead of leaving warps idle.  The 256^3 CT cone frame (1024^2, 6.7 tiles
+// per warp): march
 // 0.870 -> 0.796 ms, every variant 3-10 % faster.  With many tiles per warp
 // there is little idle time to fill, and two bands of rows in flight (above
 // and below the middle) lose cache locality: 3840 x 2160 (53 per warp) 4.77 ->
 // 5.27 ms, so such frames keep raster order.  Centre-out columns as well gave
 // no more.  1920 x 1080 (13.4 per warp) is about 1 % faster middle-out
-// (config-3 cone march 1.201 -> 1.190 ms, shell 1.228 -> 1.215 ms), so the
+// (512^3 blob cone march 1.201 -> 1.190 ms, shell 1.228 -> 1.215 ms), so the
 // bound is 16 tiles per warp.
 #ifndef VI_MARCH_TILE_ORDER
 #define VI_MARCH_TILE_ORDER 1

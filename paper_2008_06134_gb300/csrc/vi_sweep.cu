@@ -47,7 +47,7 @@ constexpr int kSweepThreads = 256;
 
 // Resident blocks per SM the register allocation is fitted to.  Two (up to
 // 128 registers a thread) measured fastest: 0.119 ms on the 256 x 512^2
-// config-2 sweep, against 0.143 / 0.169 ms for three / four blocks; eight- or
+// sweep of a 256^3 CT phantom, against 0.143 / 0.169 ms for three / four blocks; eight- or
 // sixteen-slice batches were slower than four.
 #ifndef VI_SWEEP_MIN_BLOCKS
 #define VI_SWEEP_MIN_BLOCKS 2
@@ -62,7 +62,8 @@ constexpr int kBatch = VI_SWEEP_BATCH;
 // per SM (80 registers) measured 4.42 ms on the 1024 x 2048^2 FP16 sweep of the
 // 1024^3 workload, against 5.06 ms at four-slice batches and two blocks (4.60
 // and 4.68 ms at 2 x 4 and 3 x 3; 4.91 ms at 1 x 5).  The per-lane sweep is
-// fastest at 4 x 2 (0.111 ms on config 2; 0.121-0.179 ms for the others).
+// fastest at 4 x 2 (0.111 ms on the 256 x 512^2 sweep; 0.121-0.179 ms for
+// the others).
 #ifndef VI_SWEEP_LOCKSTEP_MIN_BLOCKS
 #define VI_SWEEP_LOCKSTEP_MIN_BLOCKS 3
 #endif
@@ -136,16 +137,17 @@ __device__ __forceinline__ void fill_slices(const SweepParams& p, T* out, const 
 }
 
 // Transparent runs of a column (the lockstep sweep, VI_SWEEP_SKIP 1): slice
-// k's footprint lies in a brick whose skip distance d says that every brick
-// within d - 1 of it (along each axis) cannot yield alpha > 0, so the slices
-// whose points stay in that box of bricks leave T unchanged and only store
-// it.  Returns the last slice of the run that starts at k (at most kout), or
-// k - 1 if slice k's brick may yield alpha > 0.  The run's end is estimated
-// from where the column leaves the box and confirmed on the index path: each
-// brick coordinate of P_k is monotone in k, so the slices between two
-// confirmed ones lie in the box too.  The per-lane sweep does not take runs:
+// k's footprint lies in a skip-grid cell whose skip distance d says that
+// every cell within d - 1 of it (along each axis) cannot yield alpha > 0, so
+// the slices whose points stay in that box of cells leave T unchanged and
+// only store it.  Returns the last slice of the run that starts at k (at most
+// kout), or k - 1 if slice k's cell may yield alpha > 0.  The run's end is
+// estimated from where the column leaves the box and confirmed on the index
+// path: each cell coordinate of P_k is monotone in k, so the slices between
+// two confirmed ones lie in the box too.  The per-lane sweep does not take runs:
 // its lanes sit at different slices, and one lane's run serialises against
-// its neighbours' batches (config-2 sweep 0.104 -> 0.118 ms with them).
+// its neighbours' batches (256 x 512^2 sweep of a 256^3 CT phantom 0.104 ->
+// 0.118 ms with them).
 #ifndef VI_SWEEP_SKIP
 #define VI_SWEEP_SKIP 1
 #endif
