@@ -203,6 +203,26 @@ int vi_attenuation_info(vi_ctx* ctx, int* n_slices, int* slice_res, int* format,
    the copy. */
 int vi_get_attenuation(vi_ctx* ctx, void* out, size_t out_bytes, int out_on_device);
 
+/* The empty-space skipping grid of the current volume and TF.  Skipping is
+   exact: a sample whose trilinear footprint (Section 3, the 3D texture
+   lookup) starts in a brick or cell whose voxels, with the one-voxel apron on
+   its high sides, cannot reach a TF entry with alpha > 0 (Section 3.1.1,
+   classification) has alpha 0 and contributes nothing to Eq. 3 or Eq. 4.
+   dims (may be NULL) receives { nbx, nby, nbz, cnx, cny, cnz }: bricks of
+   16^3 voxels and cells of 8^3 voxels per axis (bricks cover the volume,
+   rounded up; cells are 2 x 2 x 2 to a brick).  brick_flags (host, nbx nby
+   nbz bytes, x fastest) receives 1 for a brick that may yield alpha > 0, else
+   0.  cell_skip (host, cnx cny cnz bytes, x fastest) receives 0 for a cell
+   that may yield alpha > 0, else the L-infinity distance in cells to the
+   nearest such cell within the grid, capped at 32.  A flag is set whenever
+   the FP64 TF coordinates of the brick's or cell's value range reach an
+   entry with alpha > 0, and only when they come within one entry of one.
+   Either buffer may be NULL; a buffer shorter than its grid (brick_bytes,
+   cell_bytes) is VI_EINVAL.  VI_ESTATE without a volume and a TF.  Waits for
+   the copies. */
+int vi_get_skip_grid(vi_ctx* ctx, int* dims, uint8_t* brick_flags, size_t brick_bytes,
+                     uint8_t* cell_skip, size_t cell_bytes);
+
 /* Words per record written by vi_trace_pixel. */
 #define VI_TRACE_WORDS 40
 

@@ -1134,6 +1134,31 @@ int vi_debug_bounds(int device, uint64_t* violations, int* first_site, int64_t* 
 #endif
 }
 
+int vi_get_skip_grid(vi_ctx* c, int* dims, uint8_t* brick_flags, size_t brick_bytes,
+                     uint8_t* cell_skip, size_t cell_bytes) {
+    vi_detail::NvtxRange nvtx_range("vi_get_skip_grid");
+    int rc = enter(c);
+    if (rc) return rc;
+    if (!c->flags_ok || !c->bflags) return VI_ESTATE;
+    const vi::GridView g = grid_view(c);
+    const int nbz = c->vr->nbz, cnz = nbz * vi::kCellsPerBrick;
+    const size_t nb = (size_t)nbricks(c), nc = (size_t)g.cnx * g.cny * cnz;
+    if ((brick_flags && brick_bytes < nb) || (cell_skip && cell_bytes < nc)) return VI_EINVAL;
+    if (dims) {
+        const int d[6] = {g.nbx, g.nby, nbz, g.cnx, g.cny, cnz};
+        std::memcpy(dims, d, sizeof(d));
+    }
+    if (brick_flags) {
+        cudaError_t e = cudaMemcpyAsync(brick_flags, g.flags, nb, cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+    }
+    if (cell_skip) {
+        cudaError_t e = cudaMemcpyAsync(cell_skip, g.skip, nc, cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e);
+    }
+    return cuda_fail(c, cudaStreamSynchronize(c->stream));
+}
+
 int vi_launch_count(vi_ctx* c, uint64_t* count) {
     if (!c || !count) return VI_EINVAL;
     *count = c->launches;

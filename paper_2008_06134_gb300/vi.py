@@ -41,7 +41,8 @@ EXPORTS = ("vi_create", "vi_destroy", "vi_set_memory_budget", "vi_load_volume",
            "vi_measure_peaks", "vi_post_ready", "vi_render_batch", "vi_render_host_noalloc", "vi_debug_bounds", "vi_server_create", "vi_server_destroy",
            "vi_server_add_volume", "vi_server_submit", "vi_server_wait", "vi_server_cancel",
            "vi_server_timing", "vi_server_release", "vi_server_get_stats",
-           "vi_server_set_graphs", "vi_server_set_batching", "vi_server_set_eviction")
+           "vi_server_set_graphs", "vi_server_set_batching", "vi_server_set_eviction",
+           "vi_get_skip_grid")
 EVICT_LRU, EVICT_COST = 0, 1
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = 0, 1, 2, 3, 4
 
@@ -126,6 +127,7 @@ def library(checked: bool = False) -> C.CDLL:
     L.vi_get_attenuation.argtypes = [vp, vp, sz, i]
     L.vi_trace_pixel.argtypes = [vp, P(Camera), i, i, f, P(RenderOpts), i, i, vp, i, P(i)]
     L.vi_launch_count.argtypes = [vp, P(C.c_uint64)]
+    L.vi_get_skip_grid.argtypes = [vp, P(i), vp, sz, vp, sz]
     L.vi_render_host_noalloc.argtypes = [vp, P(Camera), i, i, f, vp, P(RenderOpts)]
     L.vi_post_ready.argtypes = [vp]
     L.vi_measure_peaks.argtypes = [i, P(C.c_double), P(C.c_double)]
@@ -328,6 +330,19 @@ class Context:
         _check(self.L.vi_get_attenuation(self.h, C.c_void_p(out.ctypes.data), out.nbytes, 0),
                "vi_get_attenuation")
         return out
+
+    def get_skip_grid(self):
+        """vi_get_skip_grid: (brick_flags, cell_skip) as uint8 arrays
+        (nbz, nby, nbx) and (cnz, cny, cnx)."""
+        dims = (C.c_int * 6)()
+        _check(self.L.vi_get_skip_grid(self.h, dims, None, 0, None, 0), "vi_get_skip_grid")
+        nbx, nby, nbz, cnx, cny, cnz = list(dims)
+        flags = np.empty((nbz, nby, nbx), dtype=np.uint8)
+        skip = np.empty((cnz, cny, cnx), dtype=np.uint8)
+        _check(self.L.vi_get_skip_grid(self.h, dims, C.c_void_p(flags.ctypes.data), flags.nbytes,
+                                       C.c_void_p(skip.ctypes.data), skip.nbytes),
+               "vi_get_skip_grid")
+        return flags, skip
 
     def trace_pixel(self, cam, W, H, step_vox, x, y, ert=2.0, bg=(0, 0, 0, 0), ambient=0.0,
                     opacity_correction=0, max_rec=8192, slice_filter=SLICE_NEAREST) -> np.ndarray:

@@ -62,6 +62,7 @@ def test_null_context_is_rejected_without_cuda(lib):
     assert lib.vi_attenuation_info(null, None, None, None, None) == vi.EINVAL
     assert lib.vi_get_attenuation(null, null, 0, 0) == vi.EINVAL
     assert lib.vi_launch_count(null, None) == vi.EINVAL
+    assert lib.vi_get_skip_grid(null, None, None, 0, None, 0) == vi.EINVAL
     assert lib.vi_create(None, 0, null) == vi.EINVAL
 
 
