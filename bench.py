@@ -47,7 +47,7 @@ FLOPS_LIT = {0: 0, 1: 6 + 2 + 12, 2: 6 + 2 + 6 * 12 + 7, 3: 6 + 2 + 8 * 12 + 9}
 NCU_TRAFFIC = {
     "march_kernel": (("vi_march.cu", "vi_device.cuh", "vi_internal.h"), "af44da2bee6d4b70",
                      32_089_088),
-    "sweep_kernel": (("vi_sweep.cu", "vi_device.cuh", "vi_internal.h"), "8d8c05debacf7514",
+    "sweep_kernel": (("vi_sweep.cu", "vi_device.cuh", "vi_internal.h"), "e6828894ef5d6882",
                      240_257_536),
 }
 

@@ -57,6 +57,18 @@ constexpr int kSweepThreads = 256;
 #define VI_SWEEP_BATCH 4
 #endif
 constexpr int kBatch = VI_SWEEP_BATCH;
+// 1: a batch's footprint loads are issued for every slice inside the column's
+// interval, beside its brick-flag loads, instead of after them for the
+// flagged slices only (the loads then overlap the flags' latency; a slice in
+// an unflagged brick drops its footprint unused).  Slower: the 256 x 512^2
+// sweep of a 256^3 CT phantom 0.096 -> 0.141 ms, the 1024 x 2048^2 sweep of
+// the 1024^3 volume 3.19 -> 3.22 ms.  The flags are a few KB and hit in L1,
+// so the wait they cost is short, while the footprints of the empty space
+// inside the cube come through L2 and DRAM.
+#ifndef VI_SWEEP_SPECULATE
+#define VI_SWEEP_SPECULATE 0
+#endif
+constexpr bool kSpeculate = VI_SWEEP_SPECULATE;
 // The lockstep sweep (stacks of 2^29 texel-slices and more) keeps fewer loads
 // per lane in flight and more warps per SM: two-slice batches at three blocks
 // per SM (80 registers) measured 4.42 ms on the 1024 x 2048^2 FP16 sweep of the
@@ -228,7 +240,8 @@ __device__ __forceinline__ void sweep_lockstep(const SweepParams& p, const float
         typename Octet<VoxT>::V oct[kLockBatch];
 #pragma unroll
         for (int u = 0; u < kLockBatch; ++u)
-            if (lit[u]) oct[u] = octet_load<VoxT>(p.vol, ref[u].idx);
+            if (kSpeculate ? k + u >= kin && k + u <= kout : lit[u])
+                oct[u] = octet_load<VoxT>(p.vol, ref[u].idx);
 #pragma unroll
         for (int u = 0; u < kLockBatch; ++u) {
             if (k + u > khi) break;
@@ -384,7 +397,7 @@ __device__ __forceinline__ void sweep_column(const SweepParams& p, const float* 
         typename Octet<VoxT>::V oct[kBatch];
 #pragma unroll
         for (int u = 0; u < kBatch; ++u)
-            if (lit[u]) oct[u] = octet_load<VoxT>(p.vol, ref[u].idx);
+            if (kSpeculate ? k + u <= kout : lit[u]) oct[u] = octet_load<VoxT>(p.vol, ref[u].idx);
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
             if (k + u > kout) break;
