@@ -41,7 +41,7 @@ FLOPS_BASE = 8 + 6 + 21 + 14 + 15
 FLOPS_LIT = {0: 0, 1: 6 + 2 + 12, 2: 6 + 2 + 6 * 12 + 7, 3: 6 + 2 + 8 * 12 + 9}
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
-# ncu capture of this workload, summarised in profiles/<kernel>_ct256*.md.  Each
+# ncu capture of this workload (its summary is kept under profiles/).  Each
 # entry holds for the kernel sources it was taken from (hash of the files that
 # define the kernel); once they change the figure is stale and reported as null.
 NCU_TRAFFIC = {
